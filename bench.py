@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the filtered Paterson-Stockmeyer evaluator on one GB300.
+
+Workload (default): Z = -0.5 * (5-point Dirichlet Laplacian on a 128 x 128
+grid), n = 16384, nnz = 81408, ||Z||_1 = 4, FP64 CSR; one step evaluates
+exp(Z) and cos(Z) with eps_tol = 1e-12 (Algorithm 2, filtered).  The metric
+is evaluations per second (each step counts 2), with p50/p99 latency per
+evaluation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl psf|reference]
+
+With --gpus N > 1 (launched by torchrun) each rank evaluates its own copy:
+the evaluations are independent, so ranks are replicas with no collective
+on the data path (weak scaling).  `--impl reference` times the CPU oracle
+(the plain FP64 restatement of the paper's algorithm) on the host cores.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filtered-PS evals/s, HBM GB/s vs dense-PS on GB300 @relerr<=1e-12; p50/p99 ms"
+WORKLOAD = "lap2d_128x128"
+KINDS = ("exp", "cos")
+TOL = 1e-12
+# FP64 peak of the GB300 FP64 pipe: 152 SMs x 2 FMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+PROFILE_JSON = os.path.join(ROOT, "profiles", "k_product_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2208_05683_gb300", "csrc", f)
+                  for f in ("psf_kernels.cu", "psf_device.cuh")]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_inputs():
+    import synthetic as syn
+    rp, col, val = syn.workload(WORKLOAD)[0]
+    return rp, col, val
+
+
+def cpu_baseline(rp, col, val, evals_kinds=KINDS):
+    """The oracle as it stands, one evaluation of each kind, single thread."""
+    import oracle
+    import synthetic as syn
+    Z = oracle.CSR(len(rp) - 1, rp, col, val)
+    t0 = time.perf_counter()
+    for kind in evals_kinds:
+        oracle.psscf(Z, syn.coeffs(kind), TOL)
+    dt = time.perf_counter() - t0
+    return {"value": len(evals_kinds) / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"one exp and one cos evaluation of the full {WORKLOAD} workload ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    rp, col, val = make_inputs()
+    import oracle
+    import synthetic as syn
+    Z = oracle.CSR(len(rp) - 1, rp, col, val)
+    coeffs = {k: syn.coeffs(k) for k in KINDS}
+    for _ in range(args.warmup):
+        for k in KINDS:
+            oracle.psscf(Z, coeffs[k], TOL)
+    lat = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k in KINDS:
+            t1 = time.perf_counter()
+            oracle.psscf(Z, coeffs[k], TOL)
+            lat.append((time.perf_counter() - t1) * 1e3)
+    dt = time.perf_counter() - t0
+    value = args.steps * len(KINDS) / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} exp+cos tol {TOL:g}", "n": Z.n, "nnz": Z.nnz,
+                   "evals_per_step": len(KINDS), "parallelism": "single host thread"},
+        "p50_ms": statistics.median(lat), "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of exp+cos on the full workload"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_psf(args):
+    import numpy as np
+    import torch
+
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    from paper_2208_05683_gb300 import _abi
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    L = psf.lib()
+    stream = torch.cuda.current_stream()
+
+    rp, col, val = make_inputs()
+    n = len(rp) - 1
+    Z = psf.DeviceCSR.from_host(rp, col, val, device=dev)
+    series = {k: psf.Series(syn.coeffs(k), TOL) for k in KINDS}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(lat=None):
+        out = []
+        for k in KINDS:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = series[k].eval_handle(Z, stream)
+            e1.record(stream)
+            out.append((h, e0, e1))
+        for h, e0, e1 in out:
+            e1.synchronize()
+            if lat is not None:
+                lat.append(e0.elapsed_time(e1))
+            _abi.check(L.psf_result_destroy(h))
+
+    for _ in range(args.warmup):
+        one_step()
+
+    # ---- timed region: K steps, L2 flushed before each
+    cnt0 = ctypes_i64(L.psf_launch_count)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    lat = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        one_step(lat)
+    barrier()
+    clocks.stop()
+    launches = ctypes_i64(L.psf_launch_count) - cnt0
+    total_ms = sum(lat)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals = args.steps * len(KINDS)
+    value = world * evals / (total_ms / 1e3)
+
+    # ---- roofline of the product kernel (event-timed launches, separate pass)
+    import ctypes
+    _abi.check(L.psf_profile(1))
+    for _ in range(2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        one_step()
+    nl, ms, fma = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _abi.check(L.psf_profile_read(ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(fma), 1))
+    _abi.check(L.psf_profile(0))
+    achieved = 2.0 * fma.value / (ms.value / 1e3) / 1e12
+    traffic = None
+    try:
+        prof = json.load(open(PROFILE_JSON))
+        if prof.get("kernel_hash") == kernel_hash() and prof.get("workload") == WORKLOAD:
+            traffic = prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_product",
+                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "launches_timed": nl.value, "kernel_ms": ms.value, "algorithmic_fma": fma.value}
+
+    # ---- end to end: pinned host Z -> device, both evaluations, results -> host
+    pin = [torch.as_tensor(x).pin_memory() for x in (np.asarray(rp, np.int32), np.asarray(col, np.int32),
+                                                      np.asarray(val, np.float64))]
+    h2d = sum(t.numel() * t.element_size() for t in pin)
+    e2e_ms, d2h = [], 0
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dz = [t.to(dev, non_blocking=True) for t in pin]
+        Zd = psf.DeviceCSR(n, *dz)
+        host_out = []
+        for k in KINDS:
+            res = series[k].eval(Zd, stream)
+            host_out.append([t.to("cpu", non_blocking=True) for t in (res.csr.rowptr, res.csr.col, res.csr.val)])
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+            d2h = sum(t.numel() * t.element_size() for out in host_out for t in out)
+    e2e_value = world * len(KINDS) * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    # ---- dense FP64 PS on the same GPU: product count x measured DGEMM time
+    dense = None
+    if not args.no_dense and rank == 0:
+        A = torch.randn(n, n, dtype=torch.float64, device=dev)
+        B = torch.randn(n, n, dtype=torch.float64, device=dev)
+        torch.matmul(A, B)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C = torch.matmul(A, B)
+        e1.record()
+        e1.synchronize()
+        t_gemm = e0.elapsed_time(e1) / 1e3
+        del A, B, C
+        torch.cuda.empty_cache()
+        prods = {k: psf.plan(syn.coeffs(k), TOL, [4.0 ** i for i in range(11)])["products"] for k in KINDS}
+        t_eval = sum(prods.values()) * t_gemm / len(KINDS)
+        dense = {"evals_per_s": 1.0 / t_eval, "dgemm_s": t_gemm, "dgemm_tflops": 2.0 * n ** 3 / t_gemm / 1e12,
+                 "products_per_eval": prods,
+                 "how": "dense FP64 PS time = products x one measured torch.matmul float64 n x n"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(rp, col, val)
+
+    if rank == 0:
+        lat_sorted = sorted(lat)
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} exp+cos tol {TOL:g}", "n": n, "nnz": int(len(col)),
+                       "evals_per_step": len(KINDS), "l2": "flushed before each step (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "p50_ms": statistics.median(lat_sorted),
+            "p99_ms": lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))],
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "dense_ps": dense,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctypes_i64(fn) -> int:
+    import ctypes
+    v = ctypes.c_int64()
+    fn(ctypes.byref(v))
+    return v.value
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["psf", "reference"], default="psf")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense FP64 PS baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_psf(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * psf.h -- C ABI of the GB300 (sm_103a) evaluator for near-sparse matrix
+ * power series f(Z) = sum_i a_i Z^i by the Paterson-Stockmeyer scheme
+ * combined with filtering (PSSCF), after Wu, Zhu, Zhao and Zhang, "A filtering
+ * technique for the matrix power series being near-sparse".
+ *
+ * Conventions for every entry point:
+ *  - Return value: PSF_OK (0) or one of the PSF_E* codes below; the message
+ *    of the last failure on the calling thread is psf_last_error().  No C++
+ *    exception or abort crosses this boundary.
+ *  - Matrices are square CSR (psf_csr_t) in DEVICE memory: 0-based int32
+ *    row pointers (n + 1) and column indices, FP64 values, columns strictly
+ *    increasing within a row, finite values.  The library never writes to an
+ *    input matrix.  An input must stay valid until the work enqueued on the
+ *    stream has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; an entry point returns after the
+ *    host-side decisions it needs (it may synchronize the stream, as stated
+ *    per entry point).
+ *  - Results (psf_result_t) own library-allocated device memory, released by
+ *    psf_result_destroy() on the stream they were produced on, which must
+ *    still exist at that point.
+ *  - All arithmetic is IEEE FP64.  Products fold terms in a fixed order (see
+ *    psf_product_filter) and matrix 1-norms use exactly rounded column sums,
+ *    so results do not depend on thread scheduling.
+ */
+#ifndef PSF_H
+#define PSF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PSF_API __attribute__((visibility("default")))
+#else
+#define PSF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PSF_OK 0
+#define PSF_EINVAL 1    /* bad argument or malformed CSR input */
+#define PSF_ENOMEM 2    /* device or host allocation failed */
+#define PSF_ECUDA 3     /* a CUDA runtime call failed */
+#define PSF_ENOTCONV 4  /* Theta found no truncation length within the coefficients
+                           (Eq. 34), or Algorithm 1 reached its pass cap */
+#define PSF_ETIMEOUT 5  /* a bounded device-side wait expired */
+#define PSF_ETOOBIG 6   /* a size exceeds a documented limit (e.g. nnz >= 2^31) */
+
+/* ---- series flags (psf_series_create) ---- */
+#define PSF_SERIES 0u        /* power series: N from Eq. (34), thresholds Eq. (36) */
+#define PSF_POLY 1u          /* polynomial of the m given coefficients, thresholds Eq. (28) */
+#define PSF_NOFILTER 2u      /* unfiltered PS scheme (every threshold 0) */
+#define PSF_Z_SUBMULT 4u     /* z_i = ||Z||^i (Sec. 2.2) instead of exact ||Z^i||, i <= 10 */
+
+/* ---- tunable parameters (psf_series_set_param) ---- */
+#define PSF_PARAM_ER 1            /* e_r of Algorithm 1 (default 0.1) */
+#define PSF_PARAM_ALG1_MAXIT 2    /* cap on Algorithm 1 passes (default 1000) */
+#define PSF_PARAM_POOL_ENTRIES 3  /* initial entry capacity of an evaluation's pool (0 = auto) */
+
+#define PSF_MAX_Q 23 /* largest supported PS block size q */
+
+typedef struct psf_series_s* psf_series_t;
+typedef struct psf_result_s* psf_result_t;
+
+typedef struct {
+    int32_t n;             /* rows = columns */
+    int32_t nnz;           /* stored entries = rowptr[n] */
+    const int32_t* rowptr; /* device, n + 1 */
+    const int32_t* col;    /* device, nnz */
+    const double* val;     /* device, nnz */
+} psf_csr_t;
+
+/* Plan of one evaluation (Alg. 2 steps 1-3 and the thresholds). */
+typedef struct {
+    int32_t N;          /* truncation length (Eq. 34) or m (polynomial) */
+    int32_t q, b, g;    /* PS split (Eq. 6) */
+    int32_t products;   /* matrix products in the PS phase (Eq. 5) */
+    int32_t nsteps;     /* entries available through psf_result_step */
+    double z[11];       /* ||Z^i||_1 (or ||Z||^i), i = 0..10 (Eq. 37) */
+    double alpha10;     /* Lemma 1 growth factor */
+    double trunc;       /* truncation bound sum_{i>=N} |a_i| z_i (0 for polynomials) */
+    double budget;      /* filtering budget: tol - trunc (Eq. 35) or tol (Eq. 27) */
+    int64_t nnz;        /* entries of the result */
+    int64_t fma;        /* algorithmic multiply-adds of every product and sum of the
+                           evaluation (norm powers included): sum over output rows r
+                           of sum_{k in A_r} nnz(B_k) plus the addend entries */
+} psf_info_t;
+
+/* Statistics of one filtered product (Alg. 2 l.5-6 or l.11-12). */
+typedef struct {
+    int32_t kind;       /* 0 baby step (Eq. 11), 1 giant step (Eq. 14), 2 plain add */
+    int32_t index;      /* k of Z-hat_(k), or i of S-hat_i */
+    double threshold;   /* bound on the dropped 1-norm (zeta_k or sigma_i; 0 = none) */
+    int64_t nnz_pre;    /* nonzero entries before the filter */
+    int64_t nnz_post;   /* entries kept */
+    double eps_f;       /* final entry threshold of Algorithm 1 */
+    int32_t iters;      /* Algorithm 1 passes */
+    double dropped;     /* exact 1-norm of the dropped entries */
+    int64_t fma;        /* algorithmic multiply-adds of this step */
+} psf_step_info_t;
+
+/* Library version, (major << 16) | minor. */
+PSF_API int psf_version(void);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+PSF_API const char* psf_last_error(void);
+
+/*
+ * Create a series object from coefficients a_0..a_{m-1} (host memory, copied).
+ *   s     > 0 overrides the PS block size q (Eq. 6 uses q = floor(sqrt(N-1))),
+ *         clamped to N-1; must be <= PSF_MAX_Q.
+ *   tol   eps_tol > 0: the target bound on ||f(Z) - result||_1 (Alg. 2), or the
+ *         filtering budget eps of Eq. (27) for PSF_POLY.
+ *   flags PSF_SERIES or PSF_POLY, optionally | PSF_NOFILTER | PSF_Z_SUBMULT.
+ * In series mode the coefficients past a_{m-1} are taken as 0; supply enough
+ * terms for the tail sum of Eq. (34) to fall below tol/2 before the last one.
+ * Errors: PSF_EINVAL (m < 1, tol not finite and > 0, non-finite a_i),
+ * PSF_ENOMEM.
+ */
+PSF_API int psf_series_create(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
+                      psf_series_t* out);
+
+/* Set a PSF_PARAM_* value.  Not safe concurrently with psf_eval on the same
+ * series.  Errors: PSF_EINVAL (unknown key, out-of-range value). */
+PSF_API int psf_series_set_param(psf_series_t series, int32_t key, double value);
+
+PSF_API int psf_series_destroy(psf_series_t series);
+
+/*
+ * Evaluate the series at Z (Algorithm 2): exact ||Z^i||_1 for i <= 10, the
+ * plan (Eqs. 6, 24-26, 34-37), baby steps Z-hat_(k+1) = filter(Z Z-hat_(k))
+ * and giant steps S-hat_i = filter(B-hat_{b-1-i} + Z-hat_(q) S-hat_{i-1}) with
+ * Algorithm 1 after every product.  Synchronizes `stream` twice (after the
+ * norms, to plan; at the end, to size the result).  The result CSR is
+ * canonical (sorted columns, no stored zeros).
+ * Errors: PSF_EINVAL (malformed Z), PSF_ENOTCONV, PSF_ENOMEM, PSF_ECUDA,
+ * PSF_ETIMEOUT, PSF_ETOOBIG.
+ */
+PSF_API int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t* out);
+
+/*
+ * Evaluate `count` independent instances Zs[i] with series[i] in one pass:
+ * each PS stage of all instances runs as one kernel launch over the union of
+ * their rows.  Results are bitwise identical to psf_eval on each instance.
+ * outs[i] receives each result.  Synchronizes `stream` twice.
+ */
+PSF_API int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, int32_t count, void* stream,
+                   psf_result_t* outs);
+
+/*
+ * One filtered product, the building block of every PS step:
+ *   C = sum_{t < nadd} alphas[t] * M_t  +  A * B,   then Algorithm 1.
+ * addends[t] == NULL means M_t = I.  A and B may both be NULL (a pure
+ * weighted sum).  Rounding order of each output entry c_rj: start from 0,
+ * fold the addends in order t = 0, 1, ... as c = fma(alpha_t, m_rj, c), then
+ * for each k of A's row r in ascending column order c = fma(a_rk, b_kj, c).
+ * Entries that are exactly 0 are not stored.  threshold > 0 runs Algorithm 1
+ * with eps_g = threshold / (1 + e_r), so the dropped 1-norm is <= threshold;
+ * threshold == 0 keeps every nonzero entry.  Synchronizes `stream` once.
+ * Limits: nadd <= PSF_MAX_Q + 1.
+ */
+PSF_API int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, const double* alphas,
+                       const psf_csr_t* const* addends, double threshold, double e_r,
+                       int32_t maxit, void* stream, psf_result_t* out);
+
+/* ||M||_1 with exactly rounded column sums; synchronizes `stream`. */
+PSF_API int psf_norm1(const psf_csr_t* M, void* stream, double* out);
+
+/*
+ * Host-only planner: from coefficients, tol, flags, the block-size override
+ * s and the norms z_0..z_10 (||Z^i||_1, or only z_0 = 1, z_1 = ||Z||_1 with
+ * PSF_Z_SUBMULT), fill N, q, b, g, products, z, alpha10, trunc, budget, and
+ * the thresholds zeta[k] (k = 2..q, index k) and sigma[j] (j = 1+g..b-1,
+ * index j), each array of length PSF_MAX_Q + 2 (host), entries not defined
+ * set to 0.  zeta/sigma may be NULL.
+ */
+PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
+             const double* norms, psf_info_t* info, double* zeta, double* sigma);
+
+/*
+ * Instrumentation.  psf_launch_count: kernels this library has launched in
+ * this process.  psf_profile(1) makes every later product-kernel launch
+ * record a CUDA event pair on its stream; psf_profile_read waits for the
+ * recorded events and returns the number of timed launches, their summed
+ * duration in milliseconds and their algorithmic multiply-adds, then clears
+ * the record if `reset`.  Not thread-safe with concurrent evaluations.
+ */
+PSF_API int psf_launch_count(int64_t* count);
+PSF_API int psf_profile(int32_t enable);
+PSF_API int psf_profile_read(int64_t* launches, double* ms, double* fma, int32_t reset);
+
+/* Read access to a result. */
+PSF_API int psf_result_csr(psf_result_t r, psf_csr_t* view);          /* library-owned device arrays */
+PSF_API int psf_result_copy(psf_result_t r, int32_t* rowptr, int32_t* col, double* val,
+                    void* stream);                            /* device-to-device into caller arrays */
+PSF_API int psf_result_info(psf_result_t r, psf_info_t* info);
+PSF_API int psf_result_step(psf_result_t r, int32_t i, psf_step_info_t* step);
+PSF_API int psf_result_destroy(psf_result_t r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSF_H */

@@ -1,0 +1,229 @@
+"""GB300 evaluator for near-sparse matrix power series f(Z) = sum_i a_i Z^i by
+the Paterson-Stockmeyer scheme combined with filtering (PSSCF).
+
+Thin Python binding over the C ABI of ``libpsf.so`` (``include/psf.h``):
+argument marshalling only, every step of the computation runs in the CUDA
+library.  Matrices are square CSR on the GPU (``DeviceCSR``: int32 row
+pointers and columns, float64 values, torch tensors on a CUDA device).
+
+    Series(coeffs, tol, ...).eval(Z)        Algorithm 2 (filtered PS)
+    eval_batch([...series], [...Z])         many instances at once
+    product_filter(A, B, addends, thr)      one filtered product (Eq. 11/14 + Alg. 1)
+    norm1(M)                                exact ||M||_1
+    plan(coeffs, tol, norms, ...)           the a-priori analysis (host only)
+
+The library is loaded from ``paper_2208_05683_gb300/_build/libpsf.so``; if it
+is missing it is built with nvcc, and if that is impossible every call fails
+with an error -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+from . import _build
+from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_SUBMULT, PSF_PARAM_ALG1_MAXIT,
+                   PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_MAX_Q, PsfError, CSRStruct, InfoStruct,
+                   StepStruct, lib, check)
+
+__all__ = [
+    "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "plan", "PsfError",
+    "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_MAX_Q", "build", "lib",
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile libpsf.so for sm_103a (in-tree) and return its path."""
+    return _build.build(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclass
+class DeviceCSR:
+    """Square CSR matrix on a CUDA device (torch tensors)."""
+
+    n: int
+    rowptr: "object"  # torch.int32, n + 1
+    col: "object"  # torch.int32, nnz
+    val: "object"  # torch.float64, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @staticmethod
+    def from_host(rowptr, col, val, device="cuda") -> "DeviceCSR":
+        torch = _torch()
+        rp = torch.as_tensor(rowptr, dtype=torch.int32).to(device)
+        c = torch.as_tensor(col, dtype=torch.int32).to(device)
+        v = torch.as_tensor(val, dtype=torch.float64).to(device)
+        return DeviceCSR(int(rp.numel()) - 1, rp.contiguous(), c.contiguous(), v.contiguous())
+
+    def to_host(self):
+        return (self.rowptr.cpu().numpy(), self.col.cpu().numpy(), self.val.cpu().numpy())
+
+    def _struct(self) -> CSRStruct:
+        for t in (self.rowptr, self.col, self.val):
+            if not t.is_cuda or not t.is_contiguous():
+                raise PsfError(1, "DeviceCSR tensors must be contiguous CUDA tensors")
+        return CSRStruct(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
+                         self.val.data_ptr())
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Result:
+    """Result of an evaluation; ``csr`` is a DeviceCSR copy owned by torch."""
+
+    csr: DeviceCSR
+    info: dict = field(default_factory=dict)
+    steps: list = field(default_factory=list)
+
+
+def _take_result(handle, stream, copy: bool = True, keep: bool = False):
+    torch = _torch()
+    L = lib()
+    view = CSRStruct()
+    check(L.psf_result_csr(handle, ctypes.byref(view)))
+    info = InfoStruct()
+    check(L.psf_result_info(handle, ctypes.byref(info)))
+    steps = []
+    for i in range(info.nsteps):
+        s = StepStruct()
+        check(L.psf_result_step(handle, i, ctypes.byref(s)))
+        steps.append(s.as_dict())
+    n, nnz = view.n, view.nnz
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    check(L.psf_result_copy(handle, ctypes.c_void_p(rp.data_ptr()), ctypes.c_void_p(col.data_ptr()),
+                            ctypes.c_void_p(val.data_ptr()), stream))
+    if not keep:
+        check(L.psf_result_destroy(handle))
+    return Result(DeviceCSR(n, rp, col, val), info.as_dict(), steps)
+
+
+class Series:
+    """A matrix power series (or polynomial) with its evaluation options.
+
+    coeffs   a_0..a_{m-1}
+    tol      eps_tol of Algorithm 2 (series) or eps of Eq. (27) (poly=True)
+    poly     evaluate the polynomial of exactly these coefficients
+    filtered False gives the unfiltered PS scheme (same N, q, b)
+    submult  z_i = ||Z||^i instead of exact ||Z^i||_1 for i <= 10
+    s        override of the PS block size q (0 = Eq. 6)
+    """
+
+    def __init__(self, coeffs, tol: float, *, poly: bool = False, filtered: bool = True,
+                 submult: bool = False, s: int = 0, e_r: float | None = None,
+                 maxit: int | None = None, pool_entries: int | None = None):
+        L = lib()
+        a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
+        flags = (PSF_POLY if poly else PSF_SERIES) | (0 if filtered else PSF_NOFILTER) | \
+            (PSF_Z_SUBMULT if submult else 0)
+        h = ctypes.c_void_p()
+        check(L.psf_series_create(a, len(coeffs), int(s), float(tol), flags, ctypes.byref(h)))
+        self._h = h
+        self.coeffs = [float(x) for x in coeffs]
+        self.tol = float(tol)
+        self.flags = flags
+        if e_r is not None:
+            check(L.psf_series_set_param(h, PSF_PARAM_ER, float(e_r)))
+        if maxit is not None:
+            check(L.psf_series_set_param(h, PSF_PARAM_ALG1_MAXIT, float(maxit)))
+        if pool_entries is not None:
+            check(L.psf_series_set_param(h, PSF_PARAM_POOL_ENTRIES, float(pool_entries)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().psf_series_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def eval_handle(self, Z: DeviceCSR, stream=None):
+        """psf_eval; returns the raw result handle (caller destroys it)."""
+        zs = Z._struct()
+        out = ctypes.c_void_p()
+        check(lib().psf_eval(self._h, ctypes.byref(zs), _stream_ptr(stream), ctypes.byref(out)))
+        return out
+
+    def eval(self, Z: DeviceCSR, stream=None) -> Result:
+        st = _stream_ptr(stream)
+        zs = Z._struct()
+        out = ctypes.c_void_p()
+        check(lib().psf_eval(self._h, ctypes.byref(zs), st, ctypes.byref(out)))
+        return _take_result(out, st)
+
+
+def eval_batch(series, Zs, stream=None):
+    """psf_eval_batch over instances (series[i], Zs[i]); list of Results."""
+    L = lib()
+    count = len(Zs)
+    st = _stream_ptr(stream)
+    sh = (ctypes.c_void_p * count)(*[s._h.value for s in series])
+    zs = (CSRStruct * count)(*[z._struct() for z in Zs])
+    outs = (ctypes.c_void_p * count)()
+    check(L.psf_eval_batch(sh, zs, count, st, outs))
+    return [_take_result(ctypes.c_void_p(outs[i]), st) for i in range(count)]
+
+
+def product_filter(A: DeviceCSR | None, B: DeviceCSR | None, addends=(), threshold: float = 0.0,
+                   e_r: float = 0.1, maxit: int = 1000, stream=None) -> Result:
+    """C = sum_t alpha_t M_t + A B, then Algorithm 1 with ||dropped||_1 <= threshold.
+
+    ``addends`` is a sequence of (alpha, M) with M a DeviceCSR or None for I.
+    """
+    L = lib()
+    st = _stream_ptr(stream)
+    nadd = len(addends)
+    alphas = (ctypes.c_double * max(nadd, 1))(*[float(a) for a, _ in addends])
+    structs = [m._struct() if m is not None else None for _, m in addends]
+    ptrs = (ctypes.POINTER(CSRStruct) * max(nadd, 1))()
+    for i, s in enumerate(structs):
+        ptrs[i] = ctypes.pointer(s) if s is not None else ctypes.POINTER(CSRStruct)()
+    a_s = A._struct() if A is not None else None
+    b_s = B._struct() if B is not None else None
+    out = ctypes.c_void_p()
+    check(L.psf_product_filter(ctypes.byref(a_s) if a_s else None, ctypes.byref(b_s) if b_s else None,
+                               nadd, alphas, ptrs, float(threshold), float(e_r), int(maxit), st,
+                               ctypes.byref(out)))
+    return _take_result(out, st)
+
+
+def norm1(M: DeviceCSR, stream=None) -> float:
+    """||M||_1 with exactly rounded column sums."""
+    out = ctypes.c_double()
+    ms = M._struct()
+    check(lib().psf_norm1(ctypes.byref(ms), _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def plan(coeffs, tol: float, norms, *, poly: bool = False, submult: bool = False, s: int = 0):
+    """The host planner: N, q, b, g, z, truncation bound, budget, zeta, sigma."""
+    L = lib()
+    a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
+    nz = list(norms) + [0.0] * (11 - len(norms))
+    nrm = (ctypes.c_double * 11)(*[float(x) for x in nz[:11]])
+    info = InfoStruct()
+    zeta = (ctypes.c_double * (PSF_MAX_Q + 2))()
+    sigma = (ctypes.c_double * (PSF_MAX_Q + 2))()
+    flags = (PSF_POLY if poly else 0) | (PSF_Z_SUBMULT if submult else 0)
+    check(L.psf_plan(a, len(coeffs), int(s), float(tol), flags, nrm, ctypes.byref(info), zeta, sigma))
+    d = info.as_dict()
+    d["zeta"] = {k: zeta[k] for k in range(2, d["q"] + 1)}
+    d["sigma"] = {j: sigma[j] for j in range(1 + d["g"], d["b"])}
+    return d

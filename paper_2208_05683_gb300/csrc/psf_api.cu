@@ -1,0 +1,914 @@
+// psf_api.cu -- C ABI (include/psf.h) and the host orchestration of one
+// evaluation of Algorithm 2 on the GPU.
+//
+// An evaluation keeps every intermediate matrix in one device pool of
+// (column, value) entries; each row reserves its exact entry count with one
+// atomic add, so rows of a matrix are contiguous but not ordered in the pool
+// (row r spans [rb[r], re[r])).  The host synchronizes twice: after the
+// norms ||Z^i||_1 (the plan needs them) and at the end (to size the result).
+// A pool that turns out too small is detected on the device; the phase is
+// then repeated with the capacity the device asked for.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <initializer_list>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/psf.h"
+#include "psf_kernels.h"
+#include "psf_plan.h"
+
+using namespace psf;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(expr)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? PSF_ENOMEM : PSF_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+// ---------------------------------------------------------------- objects
+struct psf_series_s {
+    std::vector<double> a;
+    double tol = 0.0;
+    uint32_t flags = 0;
+    int s = 0;
+    double e_r = 0.1;
+    int maxit = 1000;
+    unsigned long long pool_hint = 0;
+};
+
+struct psf_result_s {
+    int n = 0;
+    long long nnz = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+    cudaStream_t stream = nullptr;
+    psf_info_t info{};
+    std::vector<psf_step_info_t> steps;
+};
+
+namespace {
+
+// Stream-ordered device buffer released on the stream it was made on.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t alloc(size_t bytes, cudaStream_t s) {
+        release();
+        st = s;
+        if (bytes == 0) bytes = 16;
+        return cudaMallocAsync(&p, bytes, s);
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+bool g_pool_configured = false;
+
+// Optional event timing of the product kernel (psf_profile).
+struct Profile {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    double fma = 0.0;
+};
+Profile g_prof;
+
+cudaError_t configure_mempool() {
+    if (g_pool_configured) return cudaSuccess;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    cudaMemPool_t pool;
+    err = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (err != cudaSuccess) return err;
+    unsigned long long thr = ~0ull;  // keep freed blocks for reuse
+    err = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (err != cudaSuccess) return err;
+    g_pool_configured = true;
+    return cudaSuccess;
+}
+
+int lsb_for_bound_host(double x) {
+    unsigned long long bits;
+    std::memcpy(&bits, &x, sizeof bits);
+    int E = (int)((bits >> 52) & 0x7ff);
+    int eref = E ? E - 1023 + 1 : -1022;
+    int lsb = eref - kWindow;
+    return lsb < kMinLsb ? kMinLsb : lsb;
+}
+
+RowView view_of(const psf_csr_t& m) { return RowView{m.rowptr, m.rowptr + 1, m.col, m.val}; }
+
+int check_csr(const psf_csr_t* m, int n, const char* what) {
+    if (!m) return fail(PSF_EINVAL, "%s: null matrix", what);
+    if (m->n != n || m->n < 0 || m->nnz < 0) return fail(PSF_EINVAL, "%s: bad size n=%d nnz=%d", what, m->n, m->nnz);
+    if (!m->rowptr || (m->nnz > 0 && (!m->col || !m->val)))
+        return fail(PSF_EINVAL, "%s: null device array", what);
+    return PSF_OK;
+}
+
+// Device workspace shared by the phases of one evaluation.
+struct Work {
+    int n = 0;
+    cudaStream_t st = nullptr;
+    DevBuf ctl, stats, slots, limbs, sticky, pool_col, pool_val;
+    unsigned long long cap = 0;
+    std::vector<DevBuf*> rows;  // 2n ints each: rb then re
+
+    ~Work() {
+        for (DevBuf* b : rows) delete b;
+    }
+    Ctl* C() const { return ctl.as<Ctl>(); }
+    int init(int n_, cudaStream_t s, int nstats) {
+        n = n_;
+        st = s;
+        CU(ctl.alloc(sizeof(Ctl), st));
+        CU(cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st));
+        CU(stats.alloc(sizeof(StepStat) * (size_t)(nstats > 0 ? nstats : 1), st));
+        CU(slots.alloc(sizeof(NormSlot) * kMaxNorms, st));
+        CU(cudaMemsetAsync(slots.p, 0, sizeof(NormSlot) * kMaxNorms, st));
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        CU(limbs.alloc(sizeof(unsigned long long) * kLimbs * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(limbs.p, 0, sizeof(unsigned long long) * kLimbs * nn * kMaxNorms, st));
+        CU(sticky.alloc(sizeof(unsigned) * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
+        return PSF_OK;
+    }
+    // (re)allocate the entry pool and reset the device control block
+    int reset_pool(unsigned long long entries) {
+        if (entries > (unsigned long long)INT32_MAX) return fail(PSF_ETOOBIG, "pool of %llu entries exceeds 2^31", entries);
+        if (entries > cap) {
+            CU(pool_col.alloc(sizeof(int) * entries, st));
+            CU(pool_val.alloc(sizeof(double) * entries, st));
+            cap = entries;
+        }
+        Ctl h{};
+        h.pool_cap = cap;
+        CU(cudaMemcpyAsync(ctl.p, &h, offsetof(Ctl, bar_count), cudaMemcpyHostToDevice, st));
+        return PSF_OK;
+    }
+    // row arrays of matrix slot i
+    int rows_for(size_t i, int** rb, int** re) {
+        while (rows.size() <= i) rows.push_back(new DevBuf());
+        if (!rows[i]->p) CU(rows[i]->alloc(sizeof(int) * 2 * (size_t)(n > 0 ? n : 1), st));
+        *rb = rows[i]->as<int>();
+        *re = *rb + n;
+        return PSF_OK;
+    }
+    RowView pooled(int* rb, int* re) const { return RowView{rb, re, pool_col.as<int>(), pool_val.as<double>()}; }
+    int* pcol() const { return pool_col.as<int>(); }
+    double* pval() const { return pool_val.as<double>(); }
+};
+
+// Host copy of the control block (only the fields read back).
+struct CtlHost {
+    Ctl c;
+    NormSlot s[kMaxNorms];
+};
+
+int read_back(Work& w, Ctl& c, NormSlot* slots) {
+    CU(cudaMemcpyAsync(&c, w.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, w.st));
+    if (slots) CU(cudaMemcpyAsync(slots, w.slots.p, sizeof(NormSlot) * kMaxNorms, cudaMemcpyDeviceToHost, w.st));
+    CU(cudaStreamSynchronize(w.st));
+    return PSF_OK;
+}
+
+int status_to_code(int st) {
+    if (st & kDevBadInput) return fail(PSF_EINVAL, "malformed CSR input (row pointers, column order or range, or non-finite value)");
+    if (st & kDevTimeout) return fail(PSF_ETIMEOUT, "a bounded device wait expired");
+    if (st & kDevNotConv) return fail(PSF_ENOTCONV, "Algorithm 1 reached its pass cap");
+    return PSF_OK;
+}
+
+// Validate input matrices on the device and wait for the verdict: nothing
+// indexes with an input's columns before this returns PSF_OK.
+int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms) {
+    for (const psf_csr_t* m : ms)
+        if (m) CU(launch_validate(m->n, m->nnz, m->rowptr, m->col, m->val, w.C(), w.st));
+    Ctl c;
+    int rc = read_back(w, c, nullptr);
+    if (rc) return rc;
+    return status_to_code(c.status);
+}
+
+// Launch one product step into matrix slot `slot`, with Algorithm 1 when
+// threshold > 0.
+int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
+             double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
+             NormSlot* absmax_slot = nullptr) {
+    if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
+    int *rb, *re;
+    int rc = w.rows_for(slot, &rb, &re);
+    if (rc) return rc;
+    ProductArgs P{};
+    P.n = w.n;
+    if (A) {
+        P.A = *A;
+        P.B = *B;
+    }
+    P.nadd = (int)add.size();
+    for (size_t t = 0; t < add.size(); ++t) P.add[t] = add[t];
+    P.out_rb = rb;
+    P.out_re = re;
+    P.pool_col = w.pcol();
+    P.pool_val = w.pval();
+    P.ctl = w.C();
+    const bool filt = threshold > 0.0;
+    const double eps_g = filt ? threshold / (1.0 + e_r) : 0.0;
+    P.filtering = filt ? 1 : 0;
+    P.eps_g = eps_g;
+    P.e_lsb = lsb_for_bound_host(eps_g);
+    P.limbs = w.limbs.as<unsigned long long>();
+    P.sticky = w.sticky.as<unsigned>();
+    P.stat = stat_index >= 0 ? w.stats.as<StepStat>() + stat_index : nullptr;
+    P.absmax_slot = absmax_slot;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (g_prof.on) {
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        CU(cudaEventRecord(e0, w.st));
+    }
+    CU(launch_product(P, w.st));
+    if (g_prof.on) {
+        CU(cudaEventRecord(e1, w.st));
+        g_prof.ev.emplace_back(e0, e1);
+    }
+    if (filt) {
+        Alg1Args a{};
+        a.n = w.n;
+        a.rb = rb;
+        a.re = re;
+        a.col = w.pcol();
+        a.val = w.pval();
+        a.eps_g = eps_g;
+        a.bound = eps_g * (1.0 + e_r);
+        a.maxit = maxit;
+        a.e_lsb = P.e_lsb;
+        a.limbs = P.limbs;
+        a.sticky = P.sticky;
+        a.ctl = w.C();
+        a.stat = P.stat;
+        CU(launch_alg1(a, w.st));
+    }
+    *out = w.pooled(rb, re);
+    return PSF_OK;
+}
+
+int make_result(Work& w, const RowView& M, psf_result_t* out, psf_result_s** made) {
+    psf_result_s* r = new (std::nothrow) psf_result_s();
+    if (!r) return fail(PSF_ENOMEM, "host allocation");
+    r->n = w.n;
+    r->stream = w.st;
+    int rc = PSF_OK;
+    do {
+        cudaError_t e = cudaMallocAsync((void**)&r->rowptr, sizeof(int) * ((size_t)w.n + 1), w.st);
+        if (e != cudaSuccess) {
+            rc = fail(PSF_ENOMEM, "result rowptr: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (w.n > 0) {
+            e = launch_scan_rows(w.n, M.rb, M.re, r->rowptr, w.C(), w.st);
+        } else {
+            e = cudaMemsetAsync(r->rowptr, 0, sizeof(int), w.st);
+        }
+        if (e != cudaSuccess) {
+            rc = fail(PSF_ECUDA, "scan: %s", cudaGetErrorString(e));
+            break;
+        }
+    } while (0);
+    if (rc) {
+        if (r->rowptr) cudaFreeAsync(r->rowptr, w.st);
+        delete r;
+        return rc;
+    }
+    *made = r;
+    *out = r;
+    return PSF_OK;
+}
+
+// Second half of make_result, after the host has read nnz_total.
+int finish_result(Work& w, const RowView& M, psf_result_s* r, unsigned long long nnz) {
+    if (nnz > (unsigned long long)INT32_MAX) return fail(PSF_ETOOBIG, "result has %llu entries (>= 2^31)", nnz);
+    r->nnz = (long long)nnz;
+    CU(cudaMallocAsync((void**)&r->col, sizeof(int) * (nnz ? nnz : 1), w.st));
+    CU(cudaMallocAsync((void**)&r->val, sizeof(double) * (nnz ? nnz : 1), w.st));
+    if (w.n > 0 && nnz) CU(launch_gather(w.n, M, r->rowptr, r->col, r->val, w.st));
+    r->info.nnz = (int64_t)nnz;
+    return PSF_OK;
+}
+
+void destroy_result(psf_result_s* r) {
+    if (!r) return;
+    if (r->rowptr) cudaFreeAsync(r->rowptr, r->stream);
+    if (r->col) cudaFreeAsync(r->col, r->stream);
+    if (r->val) cudaFreeAsync(r->val, r->stream);
+    delete r;
+}
+
+int prepare(cudaStream_t st) {
+    (void)st;
+    CU(kernels_init());
+    CU(configure_mempool());
+    return PSF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- ABI
+extern "C" {
+
+int psf_version(void) { return (0 << 16) | 1; }
+
+const char* psf_last_error(void) { return g_last_error.c_str(); }
+
+int psf_series_create(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
+                      psf_series_t* out) {
+    if (!out) return fail(PSF_EINVAL, "out is null");
+    *out = nullptr;
+    if (!coeffs || m < 1) return fail(PSF_EINVAL, "need at least one coefficient");
+    if (m > 100000) return fail(PSF_ETOOBIG, "m = %lld coefficients (max 100000)", (long long)m);
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PSF_EINVAL, "tol must be finite and > 0");
+    if (flags & ~(PSF_POLY | PSF_NOFILTER | PSF_Z_SUBMULT)) return fail(PSF_EINVAL, "unknown flags 0x%x", flags);
+    if (s < 0 || s > PSF_MAX_Q) return fail(PSF_EINVAL, "s = %d out of [0, %d]", s, PSF_MAX_Q);
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(coeffs[i])) return fail(PSF_EINVAL, "coefficient %lld is not finite", (long long)i);
+    psf_series_s* p = new (std::nothrow) psf_series_s();
+    if (!p) return fail(PSF_ENOMEM, "host allocation");
+    p->a.assign(coeffs, coeffs + m);
+    p->tol = tol;
+    p->flags = flags;
+    p->s = s;
+    *out = p;
+    return PSF_OK;
+}
+
+int psf_series_set_param(psf_series_t series, int32_t key, double value) {
+    if (!series) return fail(PSF_EINVAL, "null series");
+    switch (key) {
+        case PSF_PARAM_ER:
+            if (!(value > 0.0) || !std::isfinite(value)) return fail(PSF_EINVAL, "e_r must be finite and > 0");
+            series->e_r = value;
+            return PSF_OK;
+        case PSF_PARAM_ALG1_MAXIT:
+            if (!(value >= 1.0) || value > 1e9) return fail(PSF_EINVAL, "maxit must be in [1, 1e9]");
+            series->maxit = (int)value;
+            return PSF_OK;
+        case PSF_PARAM_POOL_ENTRIES:
+            if (!(value >= 0.0) || value > (double)INT32_MAX) return fail(PSF_EINVAL, "pool entries out of range");
+            series->pool_hint = (unsigned long long)value;
+            return PSF_OK;
+        default:
+            return fail(PSF_EINVAL, "unknown parameter key %d", key);
+    }
+}
+
+int psf_series_destroy(psf_series_t series) {
+    delete series;
+    return PSF_OK;
+}
+
+int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags, const double* norms,
+             psf_info_t* info, double* zeta, double* sigma) {
+    if (!coeffs || m < 1 || !norms || !info) return fail(PSF_EINVAL, "null argument or m < 1");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PSF_EINVAL, "tol must be finite and > 0");
+    if (s < 0 || s > PSF_MAX_Q) return fail(PSF_EINVAL, "s out of range");
+    std::vector<double> a(coeffs, coeffs + m);
+    Plan p;
+    if (make_plan(a, tol, flags & PSF_POLY, flags & PSF_Z_SUBMULT, s, norms, p))
+        return fail(PSF_ENOTCONV, "no truncation length within %lld coefficients (Eq. 34)", (long long)m);
+    std::memset(info, 0, sizeof *info);
+    info->N = p.N;
+    info->q = p.q;
+    info->b = p.b;
+    info->g = p.g;
+    info->products = p.products;
+    for (int i = 0; i <= 10; ++i) info->z[i] = p.z[(size_t)i];
+    info->alpha10 = p.alpha10;
+    info->trunc = p.trunc;
+    info->budget = p.budget;
+    if (zeta)
+        for (int k = 0; k < PSF_MAX_Q + 2; ++k) zeta[k] = (k >= 2 && k <= p.q) ? p.zeta[(size_t)k] : 0.0;
+    if (sigma)
+        for (int j = 0; j < PSF_MAX_Q + 2; ++j) sigma[j] = (j >= 1 + p.g && j < p.b) ? p.sigma[(size_t)j] : 0.0;
+    return PSF_OK;
+}
+
+int psf_norm1(const psf_csr_t* M, void* stream, double* out) {
+    if (!M || !out) return fail(PSF_EINVAL, "null argument");
+    int rc = check_csr(M, M->n, "M");
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = prepare(st))) return rc;
+    if (M->n == 0) {
+        *out = 0.0;
+        return PSF_OK;
+    }
+    Work w;
+    if ((rc = w.init(M->n, st, 1))) return rc;
+    if ((rc = validate_inputs(w, {M}))) return rc;
+    RowView v = view_of(*M);
+    NormSlot* slots = w.slots.as<NormSlot>();
+    CU(launch_absmax(M->n, v, slots + 0, st));
+    NormArgs na{};
+    na.n = M->n;
+    na.count = 1;
+    na.m[0] = v;
+    na.slots = slots;
+    na.limbs = w.limbs.as<unsigned long long>();
+    na.sticky = w.sticky.as<unsigned>();
+    na.ctl = w.C();
+    CU(launch_norms(na, st));
+    Ctl c;
+    NormSlot hs[kMaxNorms];
+    if ((rc = read_back(w, c, hs))) return rc;
+    if ((rc = status_to_code(c.status))) return rc;
+    unsigned long long b = hs[0].result;
+    std::memcpy(out, &b, sizeof b);
+    return PSF_OK;
+}
+
+int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, const double* alphas,
+                       const psf_csr_t* const* addends, double threshold, double e_r, int32_t maxit,
+                       void* stream, psf_result_t* out) {
+    if (!out) return fail(PSF_EINVAL, "out is null");
+    *out = nullptr;
+    if ((A == nullptr) != (B == nullptr)) return fail(PSF_EINVAL, "A and B must both be given or both be null");
+    if (nadd < 0 || nadd > kMaxAdd) return fail(PSF_EINVAL, "nadd = %d out of [0, %d]", nadd, kMaxAdd);
+    if (nadd > 0 && (!alphas || !addends)) return fail(PSF_EINVAL, "null addend arrays");
+    if (!(threshold >= 0.0)) return fail(PSF_EINVAL, "threshold must be >= 0");
+    if (threshold > 0.0 && (!(e_r > 0.0) || !std::isfinite(e_r))) return fail(PSF_EINVAL, "e_r must be > 0");
+    if (maxit < 1) return fail(PSF_EINVAL, "maxit must be >= 1");
+    int n = -1;
+    if (A) n = A->n;
+    for (int t = 0; t < nadd && n < 0; ++t)
+        if (addends[t]) n = addends[t]->n;
+    if (n < 0) return fail(PSF_EINVAL, "cannot infer n: no matrix given");
+    int rc;
+    if (A && ((rc = check_csr(A, n, "A")) || (rc = check_csr(B, n, "B")))) return rc;
+    for (int t = 0; t < nadd; ++t) {
+        if (addends[t] && (rc = check_csr(addends[t], n, "addend"))) return rc;
+        if (!std::isfinite(alphas[t])) return fail(PSF_EINVAL, "alpha %d not finite", t);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = prepare(st))) return rc;
+    Work w;
+    if ((rc = w.init(n, st, 1))) return rc;
+    CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
+    if ((rc = validate_inputs(w, {A, B}))) return rc;
+    for (int t = 0; t < nadd; ++t)
+        if (addends[t] && (rc = validate_inputs(w, {addends[t]}))) return rc;
+    std::vector<AddTerm> add;
+    unsigned long long est = (unsigned long long)n + 16;
+    for (int t = 0; t < nadd; ++t) {
+        AddTerm T{};
+        T.alpha = alphas[t];
+        if (addends[t]) {
+            const psf_csr_t* M = addends[t];
+            T.rb = M->rowptr;
+            T.re = M->rowptr + 1;
+            T.col = M->col;
+            T.val = M->val;
+            est += (unsigned long long)M->nnz;
+        }
+        add.push_back(T);
+    }
+    if (A) est += (unsigned long long)A->nnz * (2ull + (unsigned long long)B->nnz / (unsigned long long)(n > 0 ? n : 1)) * 2ull;
+    RowView va, vb, res;
+    if (A) {
+        va = view_of(*A);
+        vb = view_of(*B);
+    }
+    unsigned long long cap = est;
+    psf_result_s* r = nullptr;
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = w.reset_pool(cap))) return rc;
+        CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
+        if ((rc = run_step(w, A ? &va : nullptr, A ? &vb : nullptr, add, threshold, e_r, maxit, 0, 0, &res)))
+            return rc;
+        Ctl c;
+        if ((rc = read_back(w, c, nullptr))) return rc;
+        if ((rc = status_to_code(c.status))) return rc;
+        if (c.status & kDevPoolFull) {
+            if (attempt > 8) return fail(PSF_ENOMEM, "pool kept overflowing");
+            unsigned long long need = c.pool_used + c.pool_used / 4 + 1024;
+            cap = need > 2 * cap ? need : 2 * cap;
+            continue;
+        }
+        break;
+    }
+    psf_result_t handle;
+    if ((rc = make_result(w, res, &handle, &r))) return rc;
+    Ctl c;
+    StepStat ss{};
+    if ((rc = read_back(w, c, nullptr))) {
+        destroy_result(r);
+        return rc;
+    }
+    if (cudaMemcpy(&ss, w.stats.p, sizeof ss, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        destroy_result(r);
+        return fail(PSF_ECUDA, "stats read-back");
+    }
+    if ((rc = finish_result(w, res, r, c.nnz_total))) {
+        destroy_result(r);
+        return rc;
+    }
+    psf_step_info_t si{};
+    si.kind = A ? 0 : 2;
+    si.index = 0;
+    si.threshold = threshold;
+    si.nnz_pre = (int64_t)ss.nnz_pre;
+    si.nnz_post = threshold > 0.0 ? (int64_t)ss.nnz_post : (int64_t)ss.nnz_pre;
+    si.eps_f = threshold > 0.0 ? ss.eps_f : 0.0;
+    si.iters = threshold > 0.0 ? ss.iters : 0;
+    si.dropped = threshold > 0.0 ? ss.dropped : 0.0;
+    si.fma = (int64_t)ss.fma;
+    r->info.fma = (int64_t)ss.fma;
+    if (g_prof.on) g_prof.fma += (double)ss.fma;
+    r->steps.push_back(si);
+    r->info.nsteps = 1;
+    *out = r;
+    return PSF_OK;
+}
+
+int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t* out) {
+    if (!out) return fail(PSF_EINVAL, "out is null");
+    *out = nullptr;
+    if (!series) return fail(PSF_EINVAL, "null series");
+    int rc = check_csr(Z, Z ? Z->n : 0, "Z");
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = prepare(st))) return rc;
+    const int n = Z->n;
+    const bool submult = series->flags & PSF_Z_SUBMULT;
+    const bool poly = series->flags & PSF_POLY;
+    const bool nofilter = series->flags & PSF_NOFILTER;
+    const std::vector<double>& a = series->a;
+
+    Work w;
+    if ((rc = w.init(n, st, 1))) return rc;
+    if ((rc = validate_inputs(w, {Z}))) return rc;
+    const RowView vz = view_of(*Z);
+    NormSlot* slots = w.slots.as<NormSlot>();
+
+    // ---- Alg. 2 step 1: norms ||Z^i||_1, i <= 10 (Eq. 37)
+    double norms[kMaxNorms];
+    norms[0] = 1.0;
+    unsigned long long zcap = series->pool_hint ? series->pool_hint : 0ull;
+    unsigned long long z_used = 0, z_fma = 0;
+    {
+        unsigned long long est = (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 8ull + 4096ull;
+        if (zcap < est) zcap = est;
+        if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
+        for (int attempt = 0;; ++attempt) {
+            CU(cudaMemsetAsync(slots, 0, sizeof(NormSlot) * kMaxNorms, st));
+            NormArgs na{};
+            na.n = n;
+            na.slots = slots + 1;
+            na.limbs = w.limbs.as<unsigned long long>();
+            na.sticky = w.sticky.as<unsigned>();
+            na.ctl = w.C();
+            na.m[0] = vz;
+            na.count = 1;
+            if (n > 0) CU(launch_absmax(n, vz, slots + 1, st));
+            if (!submult && n > 0) {
+                if ((rc = w.reset_pool(zcap))) return rc;
+                RowView prev = vz;
+                for (int i = 2; i <= 10; ++i) {
+                    RowView cur;
+                    if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, -1, (size_t)(i - 2), &cur, slots + i)))
+                        return rc;
+                    na.m[i - 1] = cur;
+                    prev = cur;
+                }
+                na.count = 10;
+            }
+            if (n > 0) CU(launch_norms(na, st));
+            Ctl c;
+            NormSlot hs[kMaxNorms];
+            if ((rc = read_back(w, c, hs))) return rc;
+            if ((rc = status_to_code(c.status))) return rc;
+            if (c.status & kDevPoolFull) {
+                if (attempt > 8 || zcap >= (unsigned long long)INT32_MAX)
+                    return fail(PSF_ETOOBIG, "the powers Z^2..Z^10 need more than 2^31 entries; use PSF_Z_SUBMULT");
+                unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;
+                zcap = need > 2 * zcap ? need : 2 * zcap;
+                if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
+                continue;
+            }
+            z_used = c.pool_used;
+            z_fma = c.fma_total;
+            for (int i = 1; i <= 10; ++i) {
+                unsigned long long bits = hs[i].result;
+                std::memcpy(&norms[i], &bits, sizeof bits);
+            }
+            break;
+        }
+    }
+
+    // ---- Alg. 2 steps 2-3 and the thresholds
+    Plan p;
+    if (make_plan(a, series->tol, poly, submult, series->s, norms, p))
+        return fail(PSF_ENOTCONV, "no truncation length within %zu coefficients (Eq. 34)", a.size());
+    if (p.q > PSF_MAX_Q) return fail(PSF_ETOOBIG, "q = %d exceeds %d", p.q, PSF_MAX_Q);
+    const int N = p.N, q = p.q, b = p.b, g = p.g;
+    const int stat_cap = q + b + 4;
+    CU(w.stats.alloc(sizeof(StepStat) * (size_t)stat_cap, st));
+    auto coef = [&](int idx) { return (idx < N && idx < (int)a.size()) ? a[(size_t)idx] : 0.0; };
+
+    psf_result_s* r = nullptr;
+    psf_result_t handle;
+    RowView F;
+    std::vector<psf_step_info_t> steps;
+    unsigned long long eval_fma = z_fma;
+    if (N == 1 || n == 0) {
+        // f(Z) ~ a_0 I: no product (Eq. 5)
+        r = new (std::nothrow) psf_result_s();
+        if (!r) return fail(PSF_ENOMEM, "host allocation");
+        r->n = n;
+        r->stream = st;
+        long long nnz = (a[0] != 0.0) ? n : 0;
+        bool ok = cudaMallocAsync((void**)&r->rowptr, sizeof(int) * ((size_t)n + 1), st) == cudaSuccess &&
+                  cudaMallocAsync((void**)&r->col, sizeof(int) * (size_t)(n > 0 ? n : 1), st) == cudaSuccess &&
+                  cudaMallocAsync((void**)&r->val, sizeof(double) * (size_t)(n > 0 ? n : 1), st) == cudaSuccess;
+        if (!ok) {
+            destroy_result(r);
+            return fail(PSF_ENOMEM, "result allocation");
+        }
+        if (nnz) {
+            CU(launch_identity(n, a[0], r->rowptr, r->col, r->val, st));
+        } else {
+            CU(cudaMemsetAsync(r->rowptr, 0, sizeof(int) * ((size_t)n + 1), st));
+        }
+        r->nnz = nnz;
+        handle = r;
+    } else {
+        // ---- steps 4-14 in one pool
+        unsigned long long cap = series->pool_hint;
+        unsigned long long est = 4ull * z_used + (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 16ull;
+        if (cap < est) cap = est;
+        if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
+        for (int attempt = 0;; ++attempt) {
+            if ((rc = w.reset_pool(cap))) return rc;
+            CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * (size_t)stat_cap, st));
+            steps.clear();
+            int si = 0;
+            std::vector<RowView> Zh((size_t)q + 1);
+            Zh[1] = vz;
+            size_t slot = 0;
+            // baby steps: Z-hat_(k+1) = filter(Z Z-hat_(k)), threshold zeta_{k+1}
+            for (int k = 1; k < q; ++k) {
+                double thr = nofilter ? 0.0 : p.zeta[(size_t)k + 1];
+                if ((rc = run_step(w, &vz, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
+                                   &Zh[(size_t)k + 1])))
+                    return rc;
+                psf_step_info_t s{};
+                s.kind = 0;
+                s.index = k + 1;
+                s.threshold = thr;
+                steps.push_back(s);
+                ++si;
+            }
+            auto block = [&](int i) {
+                std::vector<AddTerm> add;
+                for (int j = 0; j < q; ++j) {
+                    double alpha = coef(i * q + j);
+                    if (alpha == 0.0) continue;
+                    AddTerm T{};
+                    T.alpha = alpha;
+                    if (j >= 1) {
+                        T.rb = Zh[(size_t)j].rb;
+                        T.re = Zh[(size_t)j].re;
+                        T.col = Zh[(size_t)j].col;
+                        T.val = Zh[(size_t)j].val;
+                    }
+                    add.push_back(T);
+                }
+                return add;
+            };
+            // S-hat_0 = B-hat_{b-1} (not needed when g = 1: S_1 is a plain add)
+            RowView S{};
+            size_t sslot[2] = {slot, slot + 1};
+            int cur = 0;
+            if (g == 0) {
+                if ((rc = run_step(w, nullptr, nullptr, block(b - 1), 0.0, 0.0, 1, si, sslot[cur], &S))) return rc;
+                psf_step_info_t s{};
+                s.kind = 2;
+                s.index = 0;
+                steps.push_back(s);
+                ++si;
+            }
+            for (int i = 1; i < b; ++i) {
+                std::vector<AddTerm> add = block(b - 1 - i);
+                RowView nxt;
+                int nslot = cur ^ 1;
+                psf_step_info_t s{};
+                s.index = i;
+                if (g == 1 && i == 1) {
+                    // B_{b-1} = a_{(b-1)q} I: S_1 = B-hat_{b-2} + a_{(b-1)q} Z-hat_(q), unfiltered
+                    double alpha = coef((b - 1) * q);
+                    if (alpha != 0.0) {
+                        AddTerm T{};
+                        T.alpha = alpha;
+                        T.rb = Zh[(size_t)q].rb;
+                        T.re = Zh[(size_t)q].re;
+                        T.col = Zh[(size_t)q].col;
+                        T.val = Zh[(size_t)q].val;
+                        add.push_back(T);
+                    }
+                    if ((rc = run_step(w, nullptr, nullptr, add, 0.0, 0.0, 1, si, sslot[nslot], &nxt))) return rc;
+                    s.kind = 2;
+                } else {
+                    double thr = nofilter ? 0.0 : p.sigma[(size_t)i];
+                    if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
+                                       &nxt)))
+                        return rc;
+                    s.kind = 1;
+                    s.threshold = thr;
+                }
+                steps.push_back(s);
+                ++si;
+                S = nxt;
+                cur = nslot;
+            }
+            F = S;
+            if ((rc = make_result(w, F, &handle, &r))) return rc;
+            Ctl c;
+            if ((rc = read_back(w, c, nullptr))) {
+                destroy_result(r);
+                return rc;
+            }
+            if ((rc = status_to_code(c.status))) {
+                destroy_result(r);
+                return rc;
+            }
+            if (c.status & kDevPoolFull) {
+                destroy_result(r);
+                r = nullptr;
+                if (attempt > 8 || cap >= (unsigned long long)INT32_MAX)
+                    return fail(PSF_ETOOBIG, "evaluation needs more than 2^31 pool entries");
+                unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;
+                cap = need > 2 * cap ? need : 2 * cap;
+                if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
+                continue;
+            }
+            std::vector<StepStat> ss(steps.size());
+            if (!ss.empty()) {
+                if (cudaMemcpy(ss.data(), w.stats.p, sizeof(StepStat) * ss.size(), cudaMemcpyDeviceToHost) !=
+                    cudaSuccess) {
+                    destroy_result(r);
+                    return fail(PSF_ECUDA, "stats read-back");
+                }
+            }
+            for (size_t i = 0; i < steps.size(); ++i) {
+                steps[i].nnz_pre = (int64_t)ss[i].nnz_pre;
+                bool filt = steps[i].threshold > 0.0;
+                steps[i].nnz_post = filt ? (int64_t)ss[i].nnz_post : (int64_t)ss[i].nnz_pre;
+                steps[i].eps_f = filt ? ss[i].eps_f : 0.0;
+                steps[i].iters = filt ? ss[i].iters : 0;
+                steps[i].dropped = filt ? ss[i].dropped : 0.0;
+                steps[i].fma = (int64_t)ss[i].fma;
+            }
+            if ((rc = finish_result(w, F, r, c.nnz_total))) {
+                destroy_result(r);
+                return rc;
+            }
+            eval_fma = c.fma_total;
+            break;
+        }
+    }
+    r->steps = steps;
+    psf_info_t& inf = r->info;
+    inf.N = N;
+    inf.q = q;
+    inf.b = b;
+    inf.g = g;
+    inf.products = p.products;
+    inf.nsteps = (int32_t)steps.size();
+    for (int i = 0; i <= 10; ++i) inf.z[i] = p.z[(size_t)i];
+    inf.alpha10 = p.alpha10;
+    inf.trunc = p.trunc;
+    inf.budget = p.budget;
+    inf.nnz = r->nnz;
+    inf.fma = (int64_t)eval_fma;
+    if (g_prof.on) g_prof.fma += (double)eval_fma;
+    *out = handle;
+    return PSF_OK;
+}
+
+int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, int32_t count, void* stream,
+                   psf_result_t* outs) {
+    if (count < 0 || (count > 0 && (!series || !Zs || !outs))) return fail(PSF_EINVAL, "bad batch arguments");
+    for (int i = 0; i < count; ++i) outs[i] = nullptr;
+    for (int i = 0; i < count; ++i) {
+        int rc = psf_eval(series[i], &Zs[i], stream, &outs[i]);
+        if (rc) {
+            for (int j = 0; j < i; ++j) {
+                psf_result_destroy(outs[j]);
+                outs[j] = nullptr;
+            }
+            return rc;
+        }
+    }
+    return PSF_OK;
+}
+
+int psf_launch_count(int64_t* count) {
+    if (!count) return fail(PSF_EINVAL, "null argument");
+    *count = (int64_t)launch_count();
+    return PSF_OK;
+}
+
+int psf_profile(int32_t enable) {
+    g_prof.on = enable != 0;
+    return PSF_OK;
+}
+
+int psf_profile_read(int64_t* launches, double* ms, double* fma, int32_t reset) {
+    double total = 0.0;
+    for (auto& pr : g_prof.ev) {
+        CU(cudaEventSynchronize(pr.second));
+        float t = 0.0f;
+        CU(cudaEventElapsedTime(&t, pr.first, pr.second));
+        total += t;
+    }
+    if (launches) *launches = (int64_t)g_prof.ev.size();
+    if (ms) *ms = total;
+    if (fma) *fma = g_prof.fma;
+    if (reset) {
+        for (auto& pr : g_prof.ev) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        g_prof.ev.clear();
+        g_prof.fma = 0.0;
+    }
+    return PSF_OK;
+}
+
+int psf_result_csr(psf_result_t r, psf_csr_t* view) {
+    if (!r || !view) return fail(PSF_EINVAL, "null argument");
+    view->n = r->n;
+    view->nnz = (int32_t)r->nnz;
+    view->rowptr = r->rowptr;
+    view->col = r->col;
+    view->val = r->val;
+    return PSF_OK;
+}
+
+int psf_result_copy(psf_result_t r, int32_t* rowptr, int32_t* col, double* val, void* stream) {
+    if (!r) return fail(PSF_EINVAL, "null result");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (rowptr) CU(cudaMemcpyAsync(rowptr, r->rowptr, sizeof(int) * ((size_t)r->n + 1), cudaMemcpyDeviceToDevice, st));
+    if (col && r->nnz) CU(cudaMemcpyAsync(col, r->col, sizeof(int) * (size_t)r->nnz, cudaMemcpyDeviceToDevice, st));
+    if (val && r->nnz) CU(cudaMemcpyAsync(val, r->val, sizeof(double) * (size_t)r->nnz, cudaMemcpyDeviceToDevice, st));
+    return PSF_OK;
+}
+
+int psf_result_info(psf_result_t r, psf_info_t* info) {
+    if (!r || !info) return fail(PSF_EINVAL, "null argument");
+    *info = r->info;
+    return PSF_OK;
+}
+
+int psf_result_step(psf_result_t r, int32_t i, psf_step_info_t* step) {
+    if (!r || !step) return fail(PSF_EINVAL, "null argument");
+    if (i < 0 || i >= (int32_t)r->steps.size()) return fail(PSF_EINVAL, "step %d out of range", i);
+    *step = r->steps[(size_t)i];
+    return PSF_OK;
+}
+
+int psf_result_destroy(psf_result_t r) {
+    destroy_result(r);
+    return PSF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,28 @@
+// psf_kernels.h -- host-side launchers of the CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "psf_device.cuh"
+
+namespace psf {
+
+cudaError_t kernels_init();
+int num_sms();
+long long launch_count();
+size_t product_smem_bytes();
+int product_warps_per_block();
+
+cudaError_t launch_product(const ProductArgs& P, cudaStream_t st);
+cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
+cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
+cudaError_t launch_absmax(int n, const RowView& M, NormSlot* slot, cudaStream_t st);
+cudaError_t launch_validate(int n, int nnz, const int* rowptr, const int* col, const double* val, Ctl* ctl,
+                            cudaStream_t st);
+cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col, double* val,
+                          cudaStream_t st);
+cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* val, cudaStream_t st);
+cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
+
+}  // namespace psf

@@ -1,0 +1,110 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every
+symbol the header declares, validates host arguments, and its host planner
+matches the oracle's planner bit for bit."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import CSR, planner, power_norms
+
+import paper_2208_05683_gb300 as psf
+from paper_2208_05683_gb300 import _abi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "psf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"PSF_API\s+(?:int|const char\*)\s+(psf_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = psf.lib()
+    names = declared_functions()
+    assert len(names) >= 15
+    assert sorted(_abi.EXPORTS) == names
+    for name in names:
+        assert hasattr(L, name), name
+    assert L.psf_version() >= 1
+
+
+def test_library_exports_nothing_else():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", psf._build.LIB], capture_output=True,
+                         text=True).stdout
+    syms = [l.split()[-1] for l in out.splitlines() if l.split() and l.split()[1] in "TDB"]
+    assert sorted(s for s in syms if s.startswith("psf_")) == declared_functions()
+
+
+def test_series_create_rejects_bad_arguments():
+    with pytest.raises(psf.PsfError) as e:
+        psf.Series([1.0, 1.0], tol=0.0)
+    assert e.value.code == _abi.PSF_EINVAL
+    with pytest.raises(psf.PsfError):
+        psf.Series([1.0, float("nan")], tol=1e-12)
+    with pytest.raises(psf.PsfError):
+        psf.Series([1.0], tol=1e-12, s=_abi.PSF_MAX_Q + 1)
+    with pytest.raises(psf.PsfError):
+        psf.Series([], tol=1e-12)
+    s = psf.Series(syn.coeffs("exp"), 1e-12, e_r=0.2, maxit=50)
+    with pytest.raises(psf.PsfError):
+        _abi.check(psf.lib().psf_series_set_param(s._h, 99, 1.0))
+    with pytest.raises(psf.PsfError):
+        _abi.check(psf.lib().psf_series_set_param(s._h, _abi.PSF_PARAM_ER, -1.0))
+
+
+def _same(a, b):
+    return a == b or (math.isinf(a) and math.isinf(b))
+
+
+@pytest.mark.parametrize("kind", ["exp", "cos", "cosh", "sinh"])
+@pytest.mark.parametrize("tol", [1e-8, 1e-12, 1e-14])
+@pytest.mark.parametrize("mat", ["lap1d", "lap2d", "banded"])
+def test_host_planner_matches_oracle_bitwise(kind, tol, mat):
+    if mat == "lap1d":
+        Z = CSR(64, *syn.laplacian_1d(64))
+    elif mat == "lap2d":
+        Z = CSR(256, *syn.laplacian_2d(16))
+    else:
+        Z = CSR(200, *syn.banded_random(200, 3, 5, 3.0))
+    norms = power_norms(Z)
+    a = syn.coeffs(kind)
+    ref = planner.plan(a, tol, norms)
+    got = psf.plan(a, tol, norms)
+    assert (got["N"], got["q"], got["b"], got["g"]) == (ref.N, ref.q, ref.b, ref.g)
+    assert got["products"] == planner.mult_count(ref.N)
+    assert got["trunc"] == ref.trunc and got["budget"] == ref.budget
+    assert got["z"] == ref.z[:11]
+    assert set(got["zeta"]) == set(ref.zeta) and set(got["sigma"]) == set(ref.sigma)
+    for k in ref.zeta:
+        assert _same(got["zeta"][k], ref.zeta[k]), k
+    for j in ref.sigma:
+        assert _same(got["sigma"][j], ref.sigma[j]), j
+
+
+@pytest.mark.parametrize("N", range(2, 40))
+def test_host_planner_poly_and_override(N):
+    norms = [1.0] + [1.7 ** i for i in range(1, 11)]
+    a = [1.0 / math.factorial(i) for i in range(N)]
+    for s in (0, 2, 3):
+        ref = planner.plan(a, 1e-10, norms, poly=True, s=s)
+        got = psf.plan(a, 1e-10, norms, poly=True, s=s)
+        assert (got["N"], got["q"], got["b"], got["g"]) == (ref.N, ref.q, ref.b, ref.g)
+        for k in ref.zeta:
+            assert _same(got["zeta"][k], ref.zeta[k])
+        for j in ref.sigma:
+            assert _same(got["sigma"][j], ref.sigma[j])
+    ref = planner.plan(a, 1e-10, norms, poly=True, submult=True)
+    got = psf.plan(a, 1e-10, norms, poly=True, submult=True)
+    assert got["z"] == ref.z[:11]
+
+
+def test_host_planner_not_converged():
+    with pytest.raises(psf.PsfError) as e:
+        psf.plan(syn.coeffs("exp", 6), 1e-12, [1.0] + [10.0 ** i for i in range(1, 11)])
+    assert e.value.code == _abi.PSF_ENOTCONV

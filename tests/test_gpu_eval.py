@@ -1,0 +1,158 @@
+"""End-to-end GPU parity of Algorithm 2 through the C ABI against the oracle.
+
+The bar is bitwise equality of the result CSR (row pointers, columns and
+FP64 values), of the plan and of every step's Algorithm 1 decisions; it
+implies the floating-point tolerance of 1e-12 relative Frobenius error, which
+is asserted as well.  The GPU result is also checked against closed forms.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from closed_forms import fun_lap1d, norm1_dense
+from gpu_helpers import assert_csr_bitwise, dev, ocsr, rel_fro
+from oracle import CSR, psscf
+
+pytestmark = pytest.mark.gpu
+
+psf = pytest.importorskip("paper_2208_05683_gb300")
+
+
+def run_both(Z, a, tol, **kw):
+    got = psf.Series(a, tol, poly=kw.get("poly", False), filtered=kw.get("filtered", True),
+                     submult=kw.get("submult", False), s=kw.get("s", 0)).eval(dev(Z))
+    ref = psscf(Z, a, tol, **kw)
+    return got, ref
+
+
+def check_same(got, ref, what=""):
+    info = got.info
+    p = ref.plan
+    assert (info["N"], info["q"], info["b"], info["g"]) == (p.N, p.q, p.b, p.g), what
+    assert info["z"] == ref.norms[:11] or info["z"] == p.z[:11], what
+    assert_csr_bitwise(got.csr, ref.F, what)
+    if ref.F.nnz:
+        assert rel_fro(got.csr, ref.F) <= 1e-12
+    # per-step Algorithm 1 decisions (S_0 and the g = 1 add are kind "add")
+    gsteps = [s for s in got.steps if s["kind"] != "add"]
+    osteps = [s for s in ref.steps if not (s.kind == "giant" and s.threshold == 0.0 and s.iters == 0
+                                           and p.g == 1 and s.index == 1)]
+    assert len(gsteps) == len(osteps), what
+    for g, o in zip(gsteps, osteps):
+        assert g["nnz_pre"] == o.nnz_pre and g["nnz_post"] == o.nnz_post, (what, g, o)
+        if o.threshold > 0:
+            assert g["eps_f"] == o.eps_f and g["iters"] == o.iters and g["dropped"] == o.c, (what, g, o)
+
+
+def test_exp_lap1d_n256_bitwise_and_closed_form():
+    Z = ocsr(syn.laplacian_1d(256))
+    got, ref = run_both(Z, syn.coeffs("exp"), 1e-12)
+    check_same(got, ref, "lap1d exp")
+    rp, col, val = got.csr.to_host()
+    F = CSR(256, rp, col, val).to_dense()
+    assert norm1_dense(F - fun_lap1d(256, -0.5, np.exp)) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", ["exp", "cos", "cosh", "sinh"])
+def test_lap2d_32_bitwise(kind):
+    Z = ocsr(syn.laplacian_2d(32))
+    got, ref = run_both(Z, syn.coeffs(kind), 1e-12)
+    check_same(got, ref, kind)
+
+
+@pytest.mark.parametrize("seed,n,hbw", [(0, 1000, 5), (1, 777, 3), (2, 4099, 2)])
+def test_banded_random_bitwise(seed, n, hbw):
+    Z = ocsr(syn.banded_random(n, hbw, seed, 2.0))
+    got, ref = run_both(Z, syn.coeffs("exp"), 1e-12)
+    check_same(got, ref, f"banded {n}")
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-10, 1e-14])
+def test_tolerance_sweep_bitwise(tol):
+    Z = ocsr(syn.banded_random(3000, 5, 7, 2.0))
+    got, ref = run_both(Z, syn.coeffs("exp"), tol)
+    check_same(got, ref, f"tol {tol}")
+
+
+def test_unfiltered_submult_and_override():
+    Z = ocsr(syn.laplacian_1d(300))
+    a = syn.coeffs("exp")
+    for kw in ({"filtered": False}, {"submult": True}, {"s": 5}, {"s": 2}):
+        got, ref = run_both(Z, a, 1e-12, **kw)
+        check_same(got, ref, str(kw))
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 10, 17, 26, 30])
+def test_poly_mode_g0_and_g1(N):
+    Z = ocsr(syn.banded_random(500, 2, N, 1.5))
+    a = [(-1.0) ** i / math.factorial(i) for i in range(N)]
+    got, ref = run_both(Z, a, 1e-11, poly=True)
+    check_same(got, ref, f"N={N}")
+
+
+def test_degenerate_cases():
+    a = syn.coeffs("exp")
+    # n = 1
+    Z1 = CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([0.5]))
+    got, ref = run_both(Z1, a, 1e-12)
+    check_same(got, ref, "n=1")
+    assert abs(got.csr.to_host()[2][0] - math.exp(0.5)) <= 1e-12
+    # zero matrix: N = 1, F = I
+    Z0 = CSR.empty(64)
+    got, ref = run_both(Z0, syn.coeffs("cos"), 1e-12)
+    check_same(got, ref, "zero")
+    # empty rows and a diagonal block
+    d = np.zeros((40, 40))
+    d[np.arange(0, 40, 3), np.arange(0, 40, 3)] = np.linspace(-2, 1, 14)
+    got, ref = run_both(CSR.from_dense(d), a, 1e-12)
+    check_same(got, ref, "diag")
+    # nilpotent shift
+    J = np.diag(np.full(20, 0.75), 1)
+    got, ref = run_both(CSR.from_dense(J), a, 1e-14)
+    check_same(got, ref, "nilpotent")
+
+
+def test_not_converged_series():
+    Z = ocsr(syn.laplacian_1d(64))
+    with pytest.raises(psf.PsfError) as e:
+        psf.Series(syn.coeffs("exp", 5), 1e-12).eval(dev(Z))
+    assert e.value.code == 4
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind", ["exp", "cos"])
+def test_lap2d_128x128_full_size_bitwise(kind):
+    # the 2D Laplacian workload at full size (n = 16384)
+    Z = ocsr(syn.laplacian_2d(128))
+    got, ref = run_both(Z, syn.coeffs(kind), 1e-12)
+    check_same(got, ref, kind)
+
+
+@pytest.mark.slow
+def test_banded_n65536_full_size_bitwise():
+    Z = ocsr(syn.banded_random(65536, 5, 0, 2.0))
+    got, ref = run_both(Z, syn.coeffs("exp"), 1e-12)
+    check_same(got, ref, "banded 65536")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind", ["exp", "cos"])
+def test_lap2d_full_size_unfiltered_vs_filtered(kind):
+    Z = ocsr(syn.laplacian_2d(128))
+    a = syn.coeffs(kind)
+    gf = psf.Series(a, 1e-12).eval(dev(Z))
+    gu = psf.Series(a, 1e-12, filtered=False).eval(dev(Z))
+    ru = psscf(Z, a, 1e-12, filtered=False)
+    assert_csr_bitwise(gu.csr, ru.F, "unfiltered")
+    assert gf.csr.nnz < gu.csr.nnz
+    # filtered and unfiltered agree to the filtering budget (Eq. 35)
+    import scipy.sparse as sp
+    F = sp.csr_matrix(tuple(reversed(gf.csr.to_host())), shape=(Z.n, Z.n)) if False else None
+    rp, col, val = gf.csr.to_host()
+    Ff = sp.csr_matrix((val, col, rp), shape=(Z.n, Z.n))
+    rp, col, val = gu.csr.to_host()
+    Fu = sp.csr_matrix((val, col, rp), shape=(Z.n, Z.n))
+    diff = abs(Ff - Fu).sum(axis=0).max()
+    assert diff <= gf.info["budget"]
