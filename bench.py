@@ -340,8 +340,26 @@ def ctypes_i64(fn) -> int:
     return v.value
 
 
+def run_case(args):
+    """One evaluation of one series on the workload, nothing else: the
+    command the ncu captures under profiles/ run."""
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    torch.cuda.set_device(0)
+    rp, col, val = syn.workload(args.case)[0]
+    Z = psf.DeviceCSR.from_host(rp, col, val, device="cuda:0")
+    # a pool large enough that no phase is repeated: kernel launch order is fixed
+    res = psf.Series(syn.coeffs(args.kind), TOL, pool_entries=200_000_000).eval(Z)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "kind": args.kind, "nnz": res.csr.nnz, "N": res.info["N"],
+                      "fma": res.info["fma"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default=None, help="run one evaluation of this workload and exit")
+    ap.add_argument("--kind", default="exp")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -349,7 +367,9 @@ def main():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense FP64 PS baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_psf(args)

@@ -23,8 +23,8 @@ from dataclasses import dataclass, field
 
 from . import _build
 from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_SUBMULT, PSF_PARAM_ALG1_MAXIT,
-                   PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_MAX_Q, PsfError, CSRStruct, InfoStruct,
-                   StepStruct, lib, check)
+                   PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_WINDOW_CAP, PSF_MAX_Q,
+                   PsfError, CSRStruct, InfoStruct, StepStruct, lib, check)
 
 __all__ = [
     "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "plan", "PsfError",
@@ -123,11 +123,14 @@ class Series:
     filtered False gives the unfiltered PS scheme (same N, q, b)
     submult  z_i = ||Z||^i instead of exact ||Z^i||_1 for i <= 10
     s        override of the PS block size q (0 = Eq. 6)
+    kernel   product kernel: "auto", "window" (dense column window) or "bitmap"
+    window_cap  column-window limit of the window kernel (0 = largest that fits)
     """
 
     def __init__(self, coeffs, tol: float, *, poly: bool = False, filtered: bool = True,
                  submult: bool = False, s: int = 0, e_r: float | None = None,
-                 maxit: int | None = None, pool_entries: int | None = None):
+                 maxit: int | None = None, pool_entries: int | None = None,
+                 kernel: str = "auto", window_cap: int = 0):
         L = lib()
         a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
         flags = (PSF_POLY if poly else PSF_SERIES) | (0 if filtered else PSF_NOFILTER) | \
@@ -144,6 +147,11 @@ class Series:
             check(L.psf_series_set_param(h, PSF_PARAM_ALG1_MAXIT, float(maxit)))
         if pool_entries is not None:
             check(L.psf_series_set_param(h, PSF_PARAM_POOL_ENTRIES, float(pool_entries)))
+        kid = {"auto": 0, "window": 1, "bitmap": 2}[kernel]
+        if kid:
+            check(L.psf_series_set_param(h, PSF_PARAM_KERNEL, float(kid)))
+        if window_cap:
+            check(L.psf_series_set_param(h, PSF_PARAM_WINDOW_CAP, float(window_cap)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -52,7 +52,14 @@ struct psf_series_s {
     int s = 0;
     double e_r = 0.1;
     int maxit = 1000;
-    unsigned long long pool_hint = 0;
+    unsigned long long pool_hint = 0;  // user-set initial capacity (entries)
+    unsigned long long z_need = 0;     // largest pool the norm phase has needed
+    unsigned long long ps_need = 0;    // largest pool the PS phase has needed
+    // B-operand mean row lengths seen by the previous evaluation, per step:
+    // they pick the thread-group size of the product kernel (tuning only)
+    std::vector<double> len_z, len_baby, len_giant;
+    int kernel = 0;      // PSF_PARAM_KERNEL
+    int window_cap = 0;  // PSF_PARAM_WINDOW_CAP
 };
 
 struct psf_result_s {
@@ -140,9 +147,11 @@ int check_csr(const psf_csr_t* m, int n, const char* what) {
 struct Work {
     int n = 0;
     cudaStream_t st = nullptr;
-    DevBuf ctl, stats, slots, limbs, sticky, pool_col, pool_val;
+    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val;
     unsigned long long cap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
+    bool bitmap_kernel = false;  // rows too wide for the window kernel: use the bitmap kernel
+    int window_cap = 0;          // > 0: limit of the window kernel's column window
 
     ~Work() {
         for (DevBuf* b : rows) delete b;
@@ -157,8 +166,8 @@ struct Work {
         CU(slots.alloc(sizeof(NormSlot) * kMaxNorms, st));
         CU(cudaMemsetAsync(slots.p, 0, sizeof(NormSlot) * kMaxNorms, st));
         size_t nn = (size_t)(n > 0 ? n : 1);
-        CU(limbs.alloc(sizeof(unsigned long long) * kLimbs * nn * kMaxNorms, st));
-        CU(cudaMemsetAsync(limbs.p, 0, sizeof(unsigned long long) * kLimbs * nn * kMaxNorms, st));
+        CU(words.alloc(sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
         CU(sticky.alloc(sizeof(unsigned) * nn * kMaxNorms, st));
         CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
         return PSF_OK;
@@ -211,20 +220,29 @@ int status_to_code(int st) {
 
 // Validate input matrices on the device and wait for the verdict: nothing
 // indexes with an input's columns before this returns PSF_OK.
-int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms) {
+int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms, int* maxwin = nullptr) {
     for (const psf_csr_t* m : ms)
         if (m) CU(launch_validate(m->n, m->nnz, m->rowptr, m->col, m->val, w.C(), w.st));
     Ctl c;
     int rc = read_back(w, c, nullptr);
     if (rc) return rc;
+    if (maxwin) *maxwin = c.maxwin;
     return status_to_code(c.status);
+}
+
+// Thread-group size of the window product kernel for a mean B-row length.
+int group_for(double blen) {
+    if (blen >= 192.0) return 256;
+    if (blen >= 96.0) return 128;
+    if (blen >= 48.0) return 64;
+    return 32;
 }
 
 // Launch one product step into matrix slot `slot`, with Algorithm 1 when
 // threshold > 0.
 int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
              double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
-             NormSlot* absmax_slot = nullptr) {
+             NormSlot* absmax_slot = nullptr, double blen = 0.0) {
     if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
@@ -247,7 +265,7 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     P.filtering = filt ? 1 : 0;
     P.eps_g = eps_g;
     P.e_lsb = lsb_for_bound_host(eps_g);
-    P.limbs = w.limbs.as<unsigned long long>();
+    P.words = w.words.as<unsigned long long>();
     P.sticky = w.sticky.as<unsigned>();
     P.stat = stat_index >= 0 ? w.stats.as<StepStat>() + stat_index : nullptr;
     P.absmax_slot = absmax_slot;
@@ -257,7 +275,11 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
         CU(cudaEventCreate(&e1));
         CU(cudaEventRecord(e0, w.st));
     }
-    CU(launch_product(P, w.st));
+    if (w.bitmap_kernel) {
+        CU(launch_product(P, w.st));
+    } else {
+        CU(launch_product_win(P, group_for(blen), w.window_cap, w.st));
+    }
     if (g_prof.on) {
         CU(cudaEventRecord(e1, w.st));
         g_prof.ev.emplace_back(e0, e1);
@@ -273,7 +295,7 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
         a.bound = eps_g * (1.0 + e_r);
         a.maxit = maxit;
         a.e_lsb = P.e_lsb;
-        a.limbs = P.limbs;
+        a.words = P.words;
         a.sticky = P.sticky;
         a.ctl = w.C();
         a.stat = P.stat;
@@ -382,6 +404,14 @@ int psf_series_set_param(psf_series_t series, int32_t key, double value) {
             if (!(value >= 1.0) || value > 1e9) return fail(PSF_EINVAL, "maxit must be in [1, 1e9]");
             series->maxit = (int)value;
             return PSF_OK;
+        case PSF_PARAM_KERNEL:
+            if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(PSF_EINVAL, "kernel must be 0, 1 or 2");
+            series->kernel = (int)value;
+            return PSF_OK;
+        case PSF_PARAM_WINDOW_CAP:
+            if (!(value >= 0.0) || value > 1e9) return fail(PSF_EINVAL, "window cap out of range");
+            series->window_cap = (int)value;
+            return PSF_OK;
         case PSF_PARAM_POOL_ENTRIES:
             if (!(value >= 0.0) || value > (double)INT32_MAX) return fail(PSF_EINVAL, "pool entries out of range");
             series->pool_hint = (unsigned long long)value;
@@ -443,7 +473,7 @@ int psf_norm1(const psf_csr_t* M, void* stream, double* out) {
     na.count = 1;
     na.m[0] = v;
     na.slots = slots;
-    na.limbs = w.limbs.as<unsigned long long>();
+    na.words = w.words.as<unsigned long long>();
     na.sticky = w.sticky.as<unsigned>();
     na.ctl = w.C();
     CU(launch_norms(na, st));
@@ -483,9 +513,12 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     Work w;
     if ((rc = w.init(n, st, 1))) return rc;
     CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
-    if ((rc = validate_inputs(w, {A, B}))) return rc;
+    int maxwin = 0;
+    if ((rc = validate_inputs(w, {A, B}, &maxwin))) return rc;
     for (int t = 0; t < nadd; ++t)
-        if (addends[t] && (rc = validate_inputs(w, {addends[t]}))) return rc;
+        if (addends[t] && (rc = validate_inputs(w, {addends[t]}, &maxwin))) return rc;
+    w.bitmap_kernel = (long long)maxwin * 4 > (long long)product_win_cap(256);
+    const double blen = B && n > 0 ? (double)B->nnz / n : 0.0;
     std::vector<AddTerm> add;
     unsigned long long est = (unsigned long long)n + 16;
     for (int t = 0; t < nadd; ++t) {
@@ -512,7 +545,8 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     for (int attempt = 0;; ++attempt) {
         if ((rc = w.reset_pool(cap))) return rc;
         CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
-        if ((rc = run_step(w, A ? &va : nullptr, A ? &vb : nullptr, add, threshold, e_r, maxit, 0, 0, &res)))
+        if ((rc = run_step(w, A ? &va : nullptr, A ? &vb : nullptr, add, threshold, e_r, maxit, 0, 0, &res,
+                           nullptr, blen)))
             return rc;
         Ctl c;
         if ((rc = read_back(w, c, nullptr))) return rc;
@@ -574,26 +608,34 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     const std::vector<double>& a = series->a;
 
     Work w;
-    if ((rc = w.init(n, st, 1))) return rc;
-    if ((rc = validate_inputs(w, {Z}))) return rc;
+    if ((rc = w.init(n, st, 16))) return rc;
+    int zwin = 0;
+    if ((rc = validate_inputs(w, {Z}, &zwin))) return rc;
+    w.bitmap_kernel = series->kernel == 2 ||
+                      (series->kernel == 0 && (long long)zwin * 4 > (long long)product_win_cap(256));
+    w.window_cap = series->window_cap;
     const RowView vz = view_of(*Z);
+    const double zlen = n > 0 ? (double)Z->nnz / n : 0.0;
+    double znnz[kMaxNorms] = {0.0};  // nnz(Z^i) of this evaluation
+    znnz[1] = (double)Z->nnz;
     NormSlot* slots = w.slots.as<NormSlot>();
 
     // ---- Alg. 2 step 1: norms ||Z^i||_1, i <= 10 (Eq. 37)
     double norms[kMaxNorms];
     norms[0] = 1.0;
-    unsigned long long zcap = series->pool_hint ? series->pool_hint : 0ull;
+    unsigned long long zcap = series->pool_hint;
+    if (zcap < series->z_need + series->z_need / 8) zcap = series->z_need + series->z_need / 8;
     unsigned long long z_used = 0, z_fma = 0;
     {
-        unsigned long long est = (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 8ull + 4096ull;
-        if (zcap < est) zcap = est;
+        unsigned long long est = (unsigned long long)Z->nnz * 256ull + (unsigned long long)n * 8ull + 4096ull;
+        if (series->z_need == 0 && zcap < est) zcap = est;
         if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
             CU(cudaMemsetAsync(slots, 0, sizeof(NormSlot) * kMaxNorms, st));
             NormArgs na{};
             na.n = n;
             na.slots = slots + 1;
-            na.limbs = w.limbs.as<unsigned long long>();
+            na.words = w.words.as<unsigned long long>();
             na.sticky = w.sticky.as<unsigned>();
             na.ctl = w.C();
             na.m[0] = vz;
@@ -601,10 +643,14 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             if (n > 0) CU(launch_absmax(n, vz, slots + 1, st));
             if (!submult && n > 0) {
                 if ((rc = w.reset_pool(zcap))) return rc;
+                CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * 16, st));
                 RowView prev = vz;
                 for (int i = 2; i <= 10; ++i) {
                     RowView cur;
-                    if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, -1, (size_t)(i - 2), &cur, slots + i)))
+                    double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
+                                                                          : zlen * (i - 1) * (i - 1);
+                    if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, i - 2, (size_t)(i - 2), &cur, slots + i,
+                                       blen)))
                         return rc;
                     na.m[i - 1] = cur;
                     prev = cur;
@@ -626,6 +672,17 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             }
             z_used = c.pool_used;
             z_fma = c.fma_total;
+            if (z_used > series->z_need) series->z_need = z_used;
+            if (!submult && n > 0) {
+                StepStat zs[9];
+                if (cudaMemcpy(zs, w.stats.p, sizeof zs, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return fail(PSF_ECUDA, "stats read-back");
+                series->len_z.assign(9, 0.0);
+                for (int i = 2; i <= 10; ++i) {
+                    znnz[i] = (double)zs[i - 2].nnz_pre;
+                    series->len_z[(size_t)(i - 2)] = znnz[i - 1] / n;
+                }
+            }
             for (int i = 1; i <= 10; ++i) {
                 unsigned long long bits = hs[i].result;
                 std::memcpy(&norms[i], &bits, sizeof bits);
@@ -673,8 +730,9 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     } else {
         // ---- steps 4-14 in one pool
         unsigned long long cap = series->pool_hint;
+        if (cap < series->ps_need + series->ps_need / 8) cap = series->ps_need + series->ps_need / 8;
         unsigned long long est = 4ull * z_used + (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 16ull;
-        if (cap < est) cap = est;
+        if (series->ps_need == 0 && cap < est) cap = est;
         if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
             if ((rc = w.reset_pool(cap))) return rc;
@@ -687,8 +745,11 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             // baby steps: Z-hat_(k+1) = filter(Z Z-hat_(k)), threshold zeta_{k+1}
             for (int k = 1; k < q; ++k) {
                 double thr = nofilter ? 0.0 : p.zeta[(size_t)k + 1];
+                double blen = (size_t)(k - 1) < series->len_baby.size()
+                                  ? series->len_baby[(size_t)(k - 1)]
+                                  : (k <= 10 && znnz[k] > 0.0 ? znnz[k] / n : zlen * k * k);
                 if ((rc = run_step(w, &vz, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
-                                   &Zh[(size_t)k + 1])))
+                                   &Zh[(size_t)k + 1], nullptr, blen)))
                     return rc;
                 psf_step_info_t s{};
                 s.kind = 0;
@@ -748,8 +809,11 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     s.kind = 2;
                 } else {
                     double thr = nofilter ? 0.0 : p.sigma[(size_t)i];
+                    double blen = (size_t)(i - 1) < series->len_giant.size()
+                                      ? series->len_giant[(size_t)(i - 1)]
+                                      : (znnz[10] > 0.0 ? znnz[10] / n : zlen * 100.0);
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
-                                       &nxt)))
+                                       &nxt, nullptr, blen)))
                         return rc;
                     s.kind = 1;
                     s.threshold = thr;
@@ -797,11 +861,29 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 steps[i].dropped = filt ? ss[i].dropped : 0.0;
                 steps[i].fma = (int64_t)ss[i].fma;
             }
+            // B-operand row lengths of this evaluation, for the next one
+            series->len_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0.0);
+            series->len_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
+            {
+                double prev_len = zlen;  // Z-hat_(1) = Z
+                size_t idx = 0;
+                for (int k = 1; k < q; ++k, ++idx) {
+                    series->len_baby[(size_t)(k - 1)] = prev_len;
+                    prev_len = (double)steps[idx].nnz_post / n;
+                }
+                double s_len = 0.0;
+                if (g == 0) s_len = (double)steps[idx++].nnz_post / n;  // S-hat_0
+                for (int i = 1; i < b; ++i, ++idx) {
+                    series->len_giant[(size_t)(i - 1)] = s_len;
+                    s_len = (double)steps[idx].nnz_post / n;
+                }
+            }
             if ((rc = finish_result(w, F, r, c.nnz_total))) {
                 destroy_result(r);
                 return rc;
             }
             eval_fma = c.fma_total;
+            if (c.pool_used > series->ps_need) series->ps_need = c.pool_used;
             break;
         }
     }

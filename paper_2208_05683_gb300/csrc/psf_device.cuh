@@ -8,7 +8,7 @@
 namespace psf {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kLimbs = 4;     // exact column sums: 256-bit fixed point per column
+constexpr int kChunks = 8;    // exact column sums: 8 x 32-bit chunks = 256-bit fixed point
 constexpr int kWindow = 190;  // bits between the fixed point's LSB and 2^E_ref
 constexpr int kMinLsb = -1000;
 constexpr int kMaxAdd = 24;   // addend terms of one product (PSF_MAX_Q + 1)
@@ -29,6 +29,7 @@ struct Ctl {
     unsigned long long pool_cap;
     unsigned long long cslot[2];   // Algorithm 1 column-sum maxima (bits of doubles >= 0)
     unsigned long long nnz_total;  // row-length scan result
+    int maxwin;                    // widest row (last - first column + 1) of validated inputs
     int status;
     unsigned bar_count;  // fields from here on survive a pool reset
     unsigned bar_gen;
@@ -81,7 +82,7 @@ struct ProductArgs {
     int filtering;  // 1: first pass of Algorithm 1 on |x| <= eps_g
     double eps_g;
     int e_lsb;
-    unsigned long long* limbs;  // kLimbs * n
+    unsigned long long* words;  // kChunks * n, column-sum chunks
     unsigned* sticky;           // n
     StepStat* stat;
     NormSlot* absmax_slot;      // optional: record max |x|
@@ -95,7 +96,7 @@ struct Alg1Args {
     double* val;
     double eps_g, bound;
     int maxit, e_lsb;
-    unsigned long long* limbs;
+    unsigned long long* words;
     unsigned* sticky;
     Ctl* ctl;
     StepStat* stat;
@@ -106,7 +107,7 @@ struct NormArgs {
     int count;  // matrices
     RowView m[kMaxNorms];
     NormSlot* slots;            // count
-    unsigned long long* limbs;  // count * kLimbs * n
+    unsigned long long* words;  // count * kChunks * n
     unsigned* sticky;           // count * n
     Ctl* ctl;
 };
@@ -161,26 +162,27 @@ __device__ __forceinline__ int lsb_for_bound(unsigned long long xbits) {
     return lsb < kMinLsb ? kMinLsb : lsb;
 }
 
-// Add x at 64-bit limb L of a column whose limbs are `stride` apart, with
-// carry propagation.  Concurrent callers may interleave: every carry out of a
-// limb is added to the next one exactly once.
-__device__ __forceinline__ void limb_add(unsigned long long* limbs, size_t stride, int L,
-                                         unsigned long long x) {
-    while (x != 0ull && L < kLimbs) {
-        unsigned long long old = atomicAdd(limbs + (size_t)L * stride, x);
-        x = (old + x < old) ? 1ull : 0ull;
-        ++L;
-    }
+// |x| as the bit pattern of a non-negative double: for such patterns the
+// unsigned integer order is the order of the values, so magnitude tests need
+// no floating-point instruction.
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// Exact accumulation of v >= 0 (v < 2^(e_lsb + kWindow)) into the column
-// whose first limb is at `limbs` (limb stride `stride`).  Bits below 2^e_lsb
-// are truncated and noted in `sticky`.
-__device__ __forceinline__ void exact_add(unsigned long long* limbs, size_t stride, unsigned* sticky,
-                                          double v, int e_lsb) {
-    unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-    int E = (int)(bits >> 52);
-    unsigned long long M = bits & ((1ull << 52) - 1);
+// Exact column sums with deferred carries.  A column's fixed-point value is
+//   sum_c  w[c] * 2^(32 c + e_lsb),  c = 0 .. kChunks-1,
+// where every 64-bit word w[c] only ever receives addends below 2^32.  A
+// word therefore absorbs 2^31 additions without overflow, additions need no
+// carry handling and are fire-and-forget reductions; carries are propagated
+// once, when the column is read (chunk_round).
+
+// Add v (0 <= v < 2^(e_lsb + kWindow)) to the column whose chunk 0 is at w
+// (chunk stride `stride`).  Bits below 2^e_lsb are truncated and recorded in
+// *sticky.
+__device__ __forceinline__ void exact_add(unsigned long long* w, size_t stride, unsigned* sticky,
+                                          unsigned long long vbits, int e_lsb) {
+    int E = (int)(vbits >> 52);
+    unsigned long long M = vbits & ((1ull << 52) - 1);
     int e;
     if (E) {
         M |= (1ull << 52);
@@ -198,37 +200,51 @@ __device__ __forceinline__ void exact_add(unsigned long long* limbs, size_t stri
         if (M == 0ull) return;
         o = 0;
     }
-    int L = o >> 6, s = o & 63;
-    unsigned long long lo = M << s;
-    unsigned long long hi = s ? (M >> (64 - s)) : 0ull;
-    limb_add(limbs, stride, L, lo);
-    if (hi) limb_add(limbs, stride, L + 1, hi);
+    int L = o >> 5, s = o & 31;
+    unsigned long long lo = M << s;                      // bits [0, 64) of M * 2^s
+    unsigned long long hi = s ? (M >> (64 - s)) : 0ull;  // bits [64, 85)
+    unsigned long long c0 = lo & 0xffffffffull, c1 = lo >> 32;
+    if (c0) atomicAdd(w + (size_t)L * stride, c0);
+    if (c1) atomicAdd(w + (size_t)(L + 1) * stride, c1);
+    if (hi) atomicAdd(w + (size_t)(L + 2) * stride, hi);
 }
 
-// Round the fixed-point value sum_l w[l] 2^(64 l + e_lsb) (plus a truncated
-// positive remainder when `sticky`) to the nearest double, ties to even.
-__device__ __forceinline__ double exact_round(const unsigned long long w[kLimbs], bool sticky,
+// Read a column's chunks (L2 reads: they were written by other SMs'
+// reductions), clear them, propagate the carries and round the value to the
+// nearest double, ties to even (a truncated positive remainder, flagged by
+// `sticky`, breaks ties upward).
+__device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stride, unsigned* sticky,
                                               int e_lsb) {
+    unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
+    unsigned long long carry = 0ull;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        unsigned long long t = __ldcg(w + (size_t)c * stride) + carry;
+        w[(size_t)c * stride] = 0ull;
+        limb[c >> 1] |= (t & 0xffffffffull) << (32 * (c & 1));
+        carry = t >> 32;
+    }
+    bool st = __ldcg(sticky) != 0u;
+    *sticky = 0u;
     int top = -1;
-    for (int i = kLimbs - 1; i >= 0; --i)
-        if (w[i]) {
-            top = i * 64 + 63 - __clzll((long long)w[i]);
+    for (int i = 3; i >= 0; --i)
+        if (limb[i]) {
+            top = i * 64 + 63 - __clzll((long long)limb[i]);
             break;
         }
     if (top < 0) return 0.0;
-    if (top <= 52) return ldexp((double)w[0], e_lsb);  // < 2^53: exact
+    if (top <= 52) return ldexp((double)limb[0], e_lsb);  // < 2^53: exact
     int shift = top - 52;
     int wi = shift >> 6, ws = shift & 63;
-    unsigned long long M = w[wi] >> ws;
-    if (ws && wi + 1 < kLimbs) M |= w[wi + 1] << (64 - ws);
+    unsigned long long M = limb[wi] >> ws;
+    if (ws && wi + 1 < 4) M |= limb[wi + 1] << (64 - ws);
     M &= (1ull << 53) - 1;
     int rpos = shift - 1;
-    int rbit = (int)((w[rpos >> 6] >> (rpos & 63)) & 1ull);
-    bool st = sticky;
+    int rbit = (int)((limb[rpos >> 6] >> (rpos & 63)) & 1ull);
     if (!st) {
         int sw = rpos >> 6, sb = rpos & 63;
-        if (sb && (w[sw] & ((1ull << sb) - 1))) st = true;
-        for (int i = 0; i < sw && !st; ++i) st = w[i] != 0ull;
+        if (sb && (limb[sw] & ((1ull << sb) - 1))) st = true;
+        for (int i = 0; i < sw && !st; ++i) st = limb[i] != 0ull;
     }
     if (rbit && (st || (M & 1ull))) {
         ++M;

@@ -20,9 +20,10 @@ pytestmark = pytest.mark.gpu
 psf = pytest.importorskip("paper_2208_05683_gb300")
 
 
-def run_both(Z, a, tol, **kw):
+def run_both(Z, a, tol, kernel="auto", window_cap=0, **kw):
     got = psf.Series(a, tol, poly=kw.get("poly", False), filtered=kw.get("filtered", True),
-                     submult=kw.get("submult", False), s=kw.get("s", 0)).eval(dev(Z))
+                     submult=kw.get("submult", False), s=kw.get("s", 0), kernel=kernel,
+                     window_cap=window_cap).eval(dev(Z))
     ref = psscf(Z, a, tol, **kw)
     return got, ref
 
@@ -60,6 +61,31 @@ def test_lap2d_32_bitwise(kind):
     Z = ocsr(syn.laplacian_2d(32))
     got, ref = run_both(Z, syn.coeffs(kind), 1e-12)
     check_same(got, ref, kind)
+
+
+@pytest.mark.parametrize("kernel,window_cap", [("window", 0), ("bitmap", 0), ("window", 256), ("window", 64)])
+def test_product_kernels_agree_bitwise(kernel, window_cap):
+    # both product kernels, and the window kernel with rows split into
+    # several column chunks, give the oracle's result bit for bit
+    Z = ocsr(syn.laplacian_2d(24))
+    for kind in ("exp", "cos"):
+        got, ref = run_both(Z, syn.coeffs(kind), 1e-12, kernel=kernel, window_cap=window_cap)
+        check_same(got, ref, f"{kernel} cap {window_cap} {kind}")
+    Zb = ocsr(syn.banded_random(700, 6, 3, 2.0))
+    got, ref = run_both(Zb, syn.coeffs("exp"), 1e-12, kernel=kernel, window_cap=window_cap)
+    check_same(got, ref, f"{kernel} cap {window_cap} banded")
+
+
+def test_group_sizes_follow_previous_evaluation():
+    # the second evaluation of a series uses the row lengths of the first to
+    # pick its thread-group sizes; the result must not change
+    Z = ocsr(syn.laplacian_2d(40))
+    s = psf.Series(syn.coeffs("exp"), 1e-12)
+    r1 = s.eval(dev(Z))
+    r2 = s.eval(dev(Z))
+    ref = psscf(Z, syn.coeffs("exp"), 1e-12)
+    assert_csr_bitwise(r1.csr, ref.F, "first")
+    assert_csr_bitwise(r2.csr, ref.F, "second")
 
 
 @pytest.mark.parametrize("seed,n,hbw", [(0, 1000, 5), (1, 777, 3), (2, 4099, 2)])
@@ -149,7 +175,6 @@ def test_lap2d_full_size_unfiltered_vs_filtered(kind):
     assert gf.csr.nnz < gu.csr.nnz
     # filtered and unfiltered agree to the filtering budget (Eq. 35)
     import scipy.sparse as sp
-    F = sp.csr_matrix(tuple(reversed(gf.csr.to_host())), shape=(Z.n, Z.n)) if False else None
     rp, col, val = gf.csr.to_host()
     Ff = sp.csr_matrix((val, col, rp), shape=(Z.n, Z.n))
     rp, col, val = gu.csr.to_host()
