@@ -190,7 +190,7 @@ def run_psf(args):
     rp, col, val = make_inputs()
     n = len(rp) - 1
     Z = psf.DeviceCSR.from_host(rp, col, val, device=dev)
-    series = {k: psf.Series(syn.coeffs(k), TOL) for k in KINDS}
+    series = {k: psf.Series(syn.coeffs(k), TOL, kernel=args.kernel) for k in KINDS}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def barrier():
@@ -318,6 +318,7 @@ def run_psf(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{WORKLOAD} exp+cos tol {TOL:g}", "n": n, "nnz": int(len(col)),
                        "evals_per_step": len(KINDS), "l2": "flushed before each step (256 MB write)",
+                       "kernel": args.kernel,
                        "parallelism": f"replicas x{world}"},
             "p50_ms": statistics.median(lat_sorted),
             "p99_ms": lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))],
@@ -350,7 +351,7 @@ def run_case(args):
     rp, col, val = syn.workload(args.case)[0]
     Z = psf.DeviceCSR.from_host(rp, col, val, device="cuda:0")
     # a pool large enough that no phase is repeated: kernel launch order is fixed
-    res = psf.Series(syn.coeffs(args.kind), TOL, pool_entries=200_000_000).eval(Z)
+    res = psf.Series(syn.coeffs(args.kind), TOL, pool_entries=200_000_000, kernel=args.kernel).eval(Z)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "kind": args.kind, "nnz": res.csr.nnz, "N": res.info["N"],
                       "fma": res.info["fma"]}))
@@ -360,6 +361,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None, help="run one evaluation of this workload and exit")
     ap.add_argument("--kind", default="exp")
+    ap.add_argument("--kernel", choices=["auto", "window", "bitmap"], default="auto",
+                    help="product kernel (auto = compact bitmap kernel)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

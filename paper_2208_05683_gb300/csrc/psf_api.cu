@@ -305,6 +305,19 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     return PSF_OK;
 }
 
+// Copy a canonical CSR input into the pool (4-entry aligned rows), as row
+// slot `slot`; the product kernels read every B row and addend row there.
+int pool_copy(Work& w, const psf_csr_t& m, size_t slot, RowView* out) {
+    int *rb, *re;
+    int rc = w.rows_for(slot, &rb, &re);
+    if (rc) return rc;
+    CU(launch_copy_rows(m.n, m.rowptr, m.col, m.val, rb, re, w.pcol(), w.pval(), w.C(), w.st));
+    *out = w.pooled(rb, re);
+    return PSF_OK;
+}
+
+constexpr size_t kSlotZp = 60;  // row slot of the pooled copy of Z
+
 int make_result(Work& w, const RowView& M, psf_result_t* out, psf_result_s** made) {
     psf_result_s* r = new (std::nothrow) psf_result_s();
     if (!r) return fail(PSF_ENOMEM, "host allocation");
@@ -517,34 +530,39 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     if ((rc = validate_inputs(w, {A, B}, &maxwin))) return rc;
     for (int t = 0; t < nadd; ++t)
         if (addends[t] && (rc = validate_inputs(w, {addends[t]}, &maxwin))) return rc;
-    w.bitmap_kernel = (long long)maxwin * 4 > (long long)product_win_cap(256);
+    w.bitmap_kernel = true;
+    (void)maxwin;
     const double blen = B && n > 0 ? (double)B->nnz / n : 0.0;
-    std::vector<AddTerm> add;
-    unsigned long long est = (unsigned long long)n + 16;
-    for (int t = 0; t < nadd; ++t) {
-        AddTerm T{};
-        T.alpha = alphas[t];
-        if (addends[t]) {
-            const psf_csr_t* M = addends[t];
-            T.rb = M->rowptr;
-            T.re = M->rowptr + 1;
-            T.col = M->col;
-            T.val = M->val;
-            est += (unsigned long long)M->nnz;
-        }
-        add.push_back(T);
-    }
-    if (A) est += (unsigned long long)A->nnz * (2ull + (unsigned long long)B->nnz / (unsigned long long)(n > 0 ? n : 1)) * 2ull;
-    RowView va, vb, res;
+    unsigned long long est = (unsigned long long)n * 8ull + 16;
+    for (int t = 0; t < nadd; ++t)
+        if (addends[t]) est += (unsigned long long)addends[t]->nnz * 2ull + 4ull * n;
     if (A) {
-        va = view_of(*A);
-        vb = view_of(*B);
+        est += (unsigned long long)B->nnz + 4ull * n;
+        est += (unsigned long long)A->nnz * (2ull + (unsigned long long)B->nnz / (unsigned long long)(n > 0 ? n : 1)) * 2ull;
     }
+    RowView va, vb, res;
+    if (A) va = view_of(*A);
     unsigned long long cap = est;
     psf_result_s* r = nullptr;
     for (int attempt = 0;; ++attempt) {
         if ((rc = w.reset_pool(cap))) return rc;
         CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
+        // B and the addend matrices are read from pooled copies
+        std::vector<AddTerm> add;
+        for (int t = 0; t < nadd; ++t) {
+            AddTerm T{};
+            T.alpha = alphas[t];
+            if (addends[t]) {
+                RowView mv;
+                if ((rc = pool_copy(w, *addends[t], 2 + (size_t)t, &mv))) return rc;
+                T.rb = mv.rb;
+                T.re = mv.re;
+                T.col = mv.col;
+                T.val = mv.val;
+            }
+            add.push_back(T);
+        }
+        if (A && (rc = pool_copy(w, *B, 1, &vb))) return rc;
         if ((rc = run_step(w, A ? &va : nullptr, A ? &vb : nullptr, add, threshold, e_r, maxit, 0, 0, &res,
                            nullptr, blen)))
             return rc;
@@ -611,8 +629,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     if ((rc = w.init(n, st, 16))) return rc;
     int zwin = 0;
     if ((rc = validate_inputs(w, {Z}, &zwin))) return rc;
-    w.bitmap_kernel = series->kernel == 2 ||
-                      (series->kernel == 0 && (long long)zwin * 4 > (long long)product_win_cap(256));
+    w.bitmap_kernel = series->kernel != 1;  // compact kernel unless the window kernel is asked for
     w.window_cap = series->window_cap;
     const RowView vz = view_of(*Z);
     const double zlen = n > 0 ? (double)Z->nnz / n : 0.0;
@@ -627,7 +644,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     if (zcap < series->z_need + series->z_need / 8) zcap = series->z_need + series->z_need / 8;
     unsigned long long z_used = 0, z_fma = 0;
     {
-        unsigned long long est = (unsigned long long)Z->nnz * 256ull + (unsigned long long)n * 8ull + 4096ull;
+        unsigned long long est = (unsigned long long)Z->nnz * 256ull + (unsigned long long)n * 64ull + 4096ull;
         if (series->z_need == 0 && zcap < est) zcap = est;
         if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
@@ -644,7 +661,9 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             if (!submult && n > 0) {
                 if ((rc = w.reset_pool(zcap))) return rc;
                 CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * 16, st));
-                RowView prev = vz;
+                RowView zp;
+                if ((rc = pool_copy(w, *Z, kSlotZp, &zp))) return rc;
+                RowView prev = zp;
                 for (int i = 2; i <= 10; ++i) {
                     RowView cur;
                     double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
@@ -731,7 +750,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
         // ---- steps 4-14 in one pool
         unsigned long long cap = series->pool_hint;
         if (cap < series->ps_need + series->ps_need / 8) cap = series->ps_need + series->ps_need / 8;
-        unsigned long long est = 4ull * z_used + (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 16ull;
+        unsigned long long est = 4ull * z_used + (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 64ull;
         if (series->ps_need == 0 && cap < est) cap = est;
         if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
@@ -740,7 +759,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             steps.clear();
             int si = 0;
             std::vector<RowView> Zh((size_t)q + 1);
-            Zh[1] = vz;
+            if ((rc = pool_copy(w, *Z, kSlotZp, &Zh[1]))) return rc;  // Z-hat_(1) = Z, pooled
             size_t slot = 0;
             // baby steps: Z-hat_(k+1) = filter(Z Z-hat_(k)), threshold zeta_{k+1}
             for (int k = 1; k < q; ++k) {

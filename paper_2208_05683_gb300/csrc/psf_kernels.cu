@@ -19,46 +19,42 @@
 namespace psf {
 
 // ---------------------------------------------------------------- k_product
-// One warp computes one output row.  Shared memory per warp:
-//   bm[kBmWords]      bitmap of output columns in the chunk [c0, c0 + 32 kBmWords)
-//   prefix[kBmWords]  number of set bits before each bitmap word
-//   colbuf[kAccCap]   column of each accumulator slot (ascending)
-//   acc[kAccCap]      FP64 accumulators, slot = rank of the column in the chunk
-//   kb/kl/ka/ke       B-row begin, length, a_rk and element prefix of up to 32
-//                     entries k of A's row (one segment)
-//   sc/sv             kStages staged 32-entry pieces of B rows (cp.async ring)
-// A row whose pattern exceeds a chunk (wider than the bitmap or with more
-// than kAccCap entries) is processed in several column chunks.
-constexpr int kBmWords = 256;
+// Compact-accumulator kernel: one warp computes one output row, with no
+// block-level synchronisation.  Shared memory per warp:
+//   pm[kBmWords]       bitmap of the row's output columns in the chunk
+//                      [c0, c0 + 32 kBmWords) (.y) with the number of set
+//                      bits before each word (.x)
+//   colbuf[kAccCap]    column - c0 of each accumulator slot (ascending)
+//   acc[kAccCap]       FP64 accumulators, slot = rank of the column in the chunk
+//   ka/kb/kl           coefficient and B-row range of up to 32 entries of A's row
+// Symbolic pass: for each B row, lane l covers a contiguous slice of the row
+// and ORs whole runs of columns into a bitmap word at a time.  Numeric pass:
+// the addends in order, then the B rows in ascending k, each entry folded
+// as acc[slot] = fma(a, b, acc[slot]) with a warp barrier between rows (the
+// fixed rounding order of the product); B is read in 32-entry pieces, two
+// pieces ahead in registers.  A row whose pattern exceeds the
+// chunk (wider than the bitmap or with more than kAccCap entries) is
+// processed in several column chunks.
+constexpr int kBmWords = 160;
 constexpr int kBmBits = kBmWords * 32;
-constexpr int kAccCap = 1024;
+constexpr int kAccCap = 672;
 constexpr int kProdWarps = 4;
-constexpr int kStages = 8;
 
 struct WarpSmem {
-    unsigned bm[kBmWords];
-    int prefix[kBmWords];
-    int colbuf[kAccCap];
+    uint2 pm[kBmWords];  // .x = set bits before the word (prefix), .y = bitmap word
     double acc[kAccCap];
     double ka[32];
     int kb[32];
     int kl[32];
-    int ke[33];
-    int sc[kStages][32];
-    double sv[kStages][32];
+    unsigned short colbuf[kAccCap];
 };
 
 size_t product_smem_bytes() { return sizeof(WarpSmem) * kProdWarps + sizeof(AddTerm) * kMaxAdd; }
 int product_warps_per_block() { return kProdWarps; }
 
-__device__ __forceinline__ void bm_set(WarpSmem& S, int off) {
-    atomicOr(&S.bm[off >> 5], 1u << (off & 31));
-}
-
-
 __device__ __forceinline__ int slot_of(const WarpSmem& S, int off) {
-    int w = off >> 5, b = off & 31;
-    return S.prefix[w] + __popc(S.bm[w] & ((1u << b) - 1u));
+    const uint2 e = S.pm[off >> 5];
+    return (int)e.x + __popc(e.y & ((1u << (off & 31)) - 1u));
 }
 
 // first position in [s, e) with col >= c (col ascending)
@@ -85,11 +81,38 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Load the segment [seg, seg + cnt) of A's row: k, a_rk and the range of B's
-// row k restricted to columns [c0, c1) (the whole row when `whole`).
-__device__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1, int lane,
-                             WarpSmem& S) {
-    int len = 0;
+// Set the bitmap bits of the columns in [c0, cend) of col[s .. e).  Lane l
+// walks the contiguous slice [s + l m, s + (l + 1) m) and issues one atomic OR
+// per bitmap word it meets (a run of columns costs one atomic).
+__device__ __forceinline__ void slice_bits(const int* col, int s, int e, int c0, int cend, int lane,
+                                           WarpSmem& S) {
+    const int m = (e - s + 31) >> 5;
+    const int q0 = s + lane * m, q1 = min(e, q0 + m);
+    unsigned curw = 0xffffffffu, mask = 0u;
+    for (int q = q0; q < q1; q += 4) {
+        int cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cs[u] = q + u < q1 ? col[q + u] : INT_MIN;  // independent loads
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int c = cs[u];
+            if (c < c0 || c >= cend) continue;
+            unsigned off = (unsigned)(c - c0), w = off >> 5;
+            if (w != curw) {
+                if (mask) atomicOr(&S.pm[curw].y, mask);
+                curw = w;
+                mask = 0u;
+            }
+            mask |= 1u << (off & 31);
+        }
+    }
+    if (mask) atomicOr(&S.pm[curw].y, mask);
+}
+
+// Load the segment [seg, seg + cnt) of A's row: a_rk and the range of B's row
+// k restricted to columns [c0, c1) (the whole row when `whole`).
+__device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1,
+                                             int lane, WarpSmem& S) {
     if (lane < cnt) {
         int k = P.A.col[seg + lane];
         int b = P.B.rb[k], e = P.B.re[k];
@@ -101,58 +124,27 @@ __device__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole,
         S.ka[lane] = P.A.val[seg + lane];
         S.kb[lane] = b;
         S.kl[lane] = e - b;
-        len = e - b;
     }
-    int ex = warp_excl_scan(len, lane);
-    S.ke[lane] = ex;
-    if (lane == 31) S.ke[32] = ex + len;
     __syncwarp();
 }
 
-// Set the bitmap bits of every output column in [c0, cend) of row r.  The
-// B rows of a segment are walked as one flattened sequence of entries, so
-// every lane has an independent load in each step.
-__device__ void build_bitmap(const ProductArgs& P, const AddTerm* add, int nadd, int r, int c0, int cend,
+// Bitmap of every output column of row r in [c0, cend).
+__device__ __forceinline__ void build_bitmap(const ProductArgs& P, const AddTerm* add, int nadd, int r, int c0, int cend,
                              int pa0, int pa1, bool whole, int lane, WarpSmem& S) {
-    for (int w = lane; w < kBmWords; w += 32) S.bm[w] = 0u;
+    for (int w = lane; w < kBmWords; w += 32) S.pm[w].y = 0u;
     __syncwarp();
     for (int t = 0; t < nadd; ++t) {
         const AddTerm& T = add[t];
         if (!T.rb) {
-            if (lane == 0 && r >= c0 && r < cend) bm_set(S, r - c0);
+            if (lane == 0 && r >= c0 && r < cend) atomicOr(&S.pm[(r - c0) >> 5].y, 1u << ((r - c0) & 31));
         } else {
-            int s = T.rb[r], e = T.re[r];
-            for (int q = s + lane; q < e; q += 32) {
-                int c = T.col[q];
-                if (c >= c0 && c < cend) bm_set(S, c - c0);
-            }
+            slice_bits(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
         }
     }
     for (int seg = pa0; seg < pa1; seg += 32) {
         const int cnt = min(32, pa1 - seg);
         load_segment(P, seg, cnt, whole, c0, cend, lane, S);
-        const int F = S.ke[cnt];
-        constexpr int U = 4;
-        for (int f0 = 0; f0 < F; f0 += 32 * U) {
-            int cols[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int f = f0 + u * 32 + lane;
-                cols[u] = -1;
-                if (f < F) {
-                    int lo = 0, hi = cnt - 1;  // last i with ke[i] <= f
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (S.ke[mid] <= f) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    cols[u] = P.B.col[S.kb[lo] + (f - S.ke[lo])];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (cols[u] >= c0 && cols[u] < cend) bm_set(S, cols[u] - c0);
-        }
+        for (int i = 0; i < cnt; ++i) slice_bits(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
         __syncwarp();
     }
     __syncwarp();
@@ -163,13 +155,13 @@ __device__ int scan_bitmap(int lane, WarpSmem& S) {
     constexpr int per = kBmWords / 32;
     int base = lane * per, s = 0;
 #pragma unroll
-    for (int i = 0; i < per; ++i) s += __popc(S.bm[base + i]);
+    for (int i = 0; i < per; ++i) s += __popc(S.pm[base + i].y);
     int run = warp_excl_scan(s, lane);
     int total = __shfl_sync(kFull, run + s, 31);
 #pragma unroll
     for (int i = 0; i < per; ++i) {
-        S.prefix[base + i] = run;
-        run += __popc(S.bm[base + i]);
+        S.pm[base + i].x = (unsigned)run;
+        run += __popc(S.pm[base + i].y);
     }
     __syncwarp();
     return total;
@@ -177,7 +169,7 @@ __device__ int scan_bitmap(int lane, WarpSmem& S) {
 
 __device__ int count_bitmap(int lane, const WarpSmem& S) {
     int s = 0;
-    for (int w = lane; w < kBmWords; w += 32) s += __popc(S.bm[w]);
+    for (int w = lane; w < kBmWords; w += 32) s += __popc(S.pm[w].y);
     return warp_sum(s);
 }
 
@@ -186,10 +178,10 @@ __device__ int count_bitmap(int lane, const WarpSmem& S) {
 __device__ int cut_column(int lane, const WarpSmem& S, int c0) {
     int found = INT_MAX;
     for (int w = lane; w < kBmWords; w += 32) {
-        int pc = __popc(S.bm[w]);
-        if (S.prefix[w] <= kAccCap && kAccCap < S.prefix[w] + pc) {
-            int need = kAccCap - S.prefix[w];  // set bits of this word inside the chunk
-            unsigned bits = S.bm[w];
+        const int pc = __popc(S.pm[w].y), pre = (int)S.pm[w].x;
+        if (pre <= kAccCap && kAccCap < pre + pc) {
+            int need = kAccCap - pre;  // set bits of this word inside the chunk
+            unsigned bits = S.pm[w].y;
             for (int i = 0; i < need; ++i) bits &= bits - 1u;  // drop the lowest `need`
             found = c0 + w * 32 + (__ffs(bits) - 1);
         }
@@ -197,61 +189,41 @@ __device__ int cut_column(int lane, const WarpSmem& S, int c0) {
     return warp_min(found);
 }
 
-// Next (segment entry, 32-entry piece) of the flattened B-row sequence.
-__device__ __forceinline__ void next_piece(const WarpSmem& S, int cnt, int& i, int& ch) {
-    ++ch;
-    if (ch * 32 >= S.kl[i]) {
-        ch = 0;
-        do {
-            ++i;
-        } while (i < cnt && S.kl[i] == 0);
-    }
-}
-
-__device__ __forceinline__ void issue_piece(const ProductArgs& P, WarpSmem& S, int cnt, int i, int ch, int slot,
-                                            int lane) {
-    if (i < cnt) {
-        int off = ch * 32 + lane;
-        if (off < S.kl[i]) {
-            int q = S.kb[i] + off;
-            cp_async4(&S.sc[slot][lane], P.B.col + q);
-            cp_async8(&S.sv[slot][lane], P.B.val + q);
+// acc[slot(j)] = fma(a_rk, b_kj, acc[slot(j)]) for the segment's k in
+// order.  A B row is read in groups of four 32-entry pieces whose loads are
+// all issued before any of them is folded in; the pieces of one row hold
+// distinct columns, so only consecutive rows need a warp barrier.
+__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane, WarpSmem& S) {
+    const int* __restrict__ bcol = P.B.col;
+    const double* __restrict__ bval = P.B.val;
+    for (int kk = 0; kk < cnt; ++kk) {
+        const int len = S.kl[kk];
+        if (len == 0) continue;
+        const int* rc = bcol + S.kb[kk] + lane;
+        const double* rv = bval + S.kb[kk] + lane;
+        const double a = S.ka[kk];
+        for (int off = 0; off < len; off += 128) {
+            int cs[4];
+            double vs[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = off + u * 32;
+                cs[u] = -1;
+                if (q + lane < len) {
+                    cs[u] = rc[q];
+                    vs[u] = rv[q];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (cs[u] >= 0) {
+                    const int i = slot_of(S, cs[u] - c0);
+                    S.acc[i] = __fma_rn(a, vs[u], S.acc[i]);
+                }
+            }
         }
+        __syncwarp();  // next B row: order of the fma chain
     }
-    cp_async_commit();
-}
-
-// acc[slot(j)] = fma(a_rk, b_kj, acc[slot(j)]) for k of the segment in
-// order; B pieces arrive through a kStages-deep cp.async ring.
-__device__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane, WarpSmem& S) {
-    int ci = 0, cch = 0;
-    while (ci < cnt && S.kl[ci] == 0) ++ci;
-    int ii = ci, ich = 0;
-#pragma unroll 1
-    for (int s = 0; s < kStages - 1; ++s) {
-        issue_piece(P, S, cnt, ii, ich, s, lane);
-        if (ii < cnt) next_piece(S, cnt, ii, ich);
-    }
-    int slot = 0;
-    while (ci < cnt) {
-        cp_async_wait<kStages - 2>();
-        int off = cch * 32 + lane;
-        if (off < S.kl[ci]) {
-            int c = S.sc[slot][lane];
-            double v = S.sv[slot][lane];
-            int i = slot_of(S, c - c0);
-            S.acc[i] = __fma_rn(S.ka[ci], v, S.acc[i]);
-        }
-        int pi = ci;
-        next_piece(S, cnt, ci, cch);
-        if (ci != pi) __syncwarp();
-        // refill the slot consumed one piece ago
-        issue_piece(P, S, cnt, ii, ich, (slot + kStages - 1) % kStages, lane);
-        if (ii < cnt) next_piece(S, cnt, ii, ich);
-        slot = (slot + 1) % kStages;
-    }
-    cp_async_wait<0>();
-    __syncwarp();
 }
 
 __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
@@ -270,11 +242,10 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
     }
     __syncthreads();
     WarpSmem& S = warps[wib];
-    const int r = blockIdx.x * kProdWarps + wib;
     const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
     unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
 
-    if (r < P.n) {
+    for (int r = blockIdx.x * kProdWarps + wib; r < P.n; r += gridDim.x * kProdWarps) {
         // ---- column window of row r and the row's multiply-add count
         int lo = INT_MAX, hi = -1;
         for (int t = 0; t < nadd; ++t) {
@@ -309,129 +280,129 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
                 my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
         lo = warp_min(lo);
         hi = warp_max(hi);
-
         if (hi < lo) {
             if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
+            continue;
+        }
+
+        // ---- exact entry count of the row, reserve it in the pool
+        long long total = 0;
+        bool reuse = false;
+        int chunk_total = 0;
+        if (hi - lo + 1 <= kBmBits) {
+            build_bitmap(P, add, nadd, r, lo, hi + 1, pa0, pa1, true, lane, S);
+            chunk_total = scan_bitmap(lane, S);
+            total = chunk_total;
+            reuse = true;
         } else {
-            // ---- exact entry count of the row, reserve it in the pool
-            long long total = 0;
-            bool reuse = false;
-            int chunk_total = 0;
-            if (hi - lo + 1 <= kBmBits) {
-                build_bitmap(P, add, nadd, r, lo, hi + 1, pa0, pa1, true, lane, S);
+            for (long long c0 = lo; c0 <= hi; c0 += kBmBits) {
+                int cend = (int)min((long long)hi + 1, c0 + kBmBits);
+                build_bitmap(P, add, nadd, r, (int)c0, cend, pa0, pa1, false, lane, S);
+                total += count_bitmap(lane, S);
+            }
+        }
+        unsigned long long base = 0ull;
+        const unsigned long long need = (unsigned long long)((total + 3) & ~3LL);  // 4-entry aligned rows
+        if (lane == 0) base = atomicAdd(&P.ctl->pool_used, need);
+        base = __shfl_sync(kFull, base, 0);
+        if (base + need > P.ctl->pool_cap) {
+            if (lane == 0) {
+                atomicOr(&P.ctl->status, kDevPoolFull);
+                P.out_rb[r] = P.out_re[r] = 0;
+            }
+            continue;
+        }
+        const bool single = reuse && chunk_total <= kAccCap;
+        int written = 0;
+        int c0 = lo;
+        while (c0 <= hi) {
+            int cend = (int)min((long long)hi + 1, (long long)c0 + kBmBits);
+            if (!reuse) {
+                build_bitmap(P, add, nadd, r, c0, cend, pa0, pa1, false, lane, S);
                 chunk_total = scan_bitmap(lane, S);
-                total = chunk_total;
-                reuse = true;
-            } else {
-                for (long long c0 = lo; c0 <= hi; c0 += kBmBits) {
-                    int cend = (int)min((long long)hi + 1, c0 + kBmBits);
-                    build_bitmap(P, add, nadd, r, (int)c0, cend, pa0, pa1, false, lane, S);
-                    total += count_bitmap(lane, S);
+            }
+            reuse = false;
+            int c1 = cend, cnt = chunk_total;
+            if (chunk_total > kAccCap) {
+                c1 = cut_column(lane, S, c0);
+                cnt = kAccCap;
+            }
+            // slot -> column offset, zero the accumulators
+            for (int w = lane; w < kBmWords; w += 32) {
+                unsigned bits = S.pm[w].y;
+                int idx = (int)S.pm[w].x;
+                while (bits) {
+                    int b = __ffs(bits) - 1;
+                    int off = w * 32 + b;
+                    if (c0 + off < c1) S.colbuf[idx] = (unsigned short)off;
+                    ++idx;
+                    bits &= bits - 1u;
                 }
             }
-            unsigned long long base = 0ull;
-            if (lane == 0) base = atomicAdd(&P.ctl->pool_used, (unsigned long long)total);
-            base = __shfl_sync(kFull, base, 0);
-            if (base + (unsigned long long)total > P.ctl->pool_cap) {
-                if (lane == 0) {
-                    atomicOr(&P.ctl->status, kDevPoolFull);
-                    P.out_rb[r] = P.out_re[r] = 0;
-                }
-            } else {
-                const bool single = reuse && chunk_total <= kAccCap;
-                int written = 0;
-                int c0 = lo;
-                while (c0 <= hi) {
-                    int cend = (int)min((long long)hi + 1, (long long)c0 + kBmBits);
-                    if (!reuse) {
-                        build_bitmap(P, add, nadd, r, c0, cend, pa0, pa1, false, lane, S);
-                        chunk_total = scan_bitmap(lane, S);
-                    }
-                    reuse = false;
-                    int c1 = cend, cnt = chunk_total;
-                    if (chunk_total > kAccCap) {
-                        c1 = cut_column(lane, S, c0);
-                        cnt = kAccCap;
-                    }
-                    // slot -> column, zero the accumulators
-                    for (int w = lane; w < kBmWords; w += 32) {
-                        unsigned bits = S.bm[w];
-                        int idx = S.prefix[w];
-                        while (bits) {
-                            int b = __ffs(bits) - 1;
-                            int c = c0 + w * 32 + b;
-                            if (c < c1) S.colbuf[idx] = c;
-                            ++idx;
-                            bits &= bits - 1u;
-                        }
-                    }
-                    for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
-                    __syncwarp();
+            for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
+            __syncwarp();
 
-                    // ---- weighted sum of the addends, t ascending
-                    for (int t = 0; t < nadd; ++t) {
-                        const AddTerm& T = add[t];
-                        const double alpha = T.alpha;
-                        if (!T.rb) {
-                            if (lane == 0 && r >= c0 && r < c1) {
-                                int i = slot_of(S, r - c0);
-                                S.acc[i] = __fma_rn(alpha, 1.0, S.acc[i]);
-                            }
-                        } else {
-                            int s = T.rb[r], e = T.re[r];
-                            for (int q = s + lane; q < e; q += 32) {
-                                int c = T.col[q];
-                                if (c >= c0 && c < c1) {
-                                    int i = slot_of(S, c - c0);
-                                    S.acc[i] = __fma_rn(alpha, T.val[q], S.acc[i]);
-                                }
-                            }
-                        }
-                        __syncwarp();
+            // ---- weighted sum of the addends, t ascending
+            for (int t = 0; t < nadd; ++t) {
+                const AddTerm& T = add[t];
+                const double alpha = T.alpha;
+                if (!T.rb) {
+                    if (lane == 0 && r >= c0 && r < c1) {
+                        int i = slot_of(S, r - c0);
+                        S.acc[i] = __fma_rn(alpha, 1.0, S.acc[i]);
                     }
-
-                    // ---- product A B: k of row r ascending
-                    for (int seg = pa0; seg < pa1; seg += 32) {
-                        const int cnt_seg = min(32, pa1 - seg);
-                        load_segment(P, seg, cnt_seg, single, c0, c1, lane, S);
-                        accumulate_segment(P, cnt_seg, c0, lane, S);
-                    }
-
-                    // ---- write back the nonzero entries in column order; the
-                    // entries with |x| <= eps_g enter the column sums of the
-                    // first pass of Algorithm 1
-                    for (int i0 = 0; i0 < cnt; i0 += 32) {
-                        int i = i0 + lane;
-                        double x = 0.0;
-                        int c = 0;
-                        if (i < cnt) {
-                            x = S.acc[i];
-                            c = S.colbuf[i];
+                } else {
+                    int s = T.rb[r], e = T.re[r];
+                    for (int q = s + lane; q < e; q += 32) {
+                        int c = T.col[q];
+                        if (c >= c0 && c < c1) {
+                            int i = slot_of(S, c - c0);
+                            S.acc[i] = __fma_rn(alpha, T.val[q], S.acc[i]);
                         }
-                        unsigned long long xb = mag_bits(x);
-                        bool nz = i < cnt && xb != 0ull;
-                        unsigned m = __ballot_sync(kFull, nz);
-                        if (nz) {
-                            long long pos = (long long)base + written + __popc(m & lanemask_lt());
-                            P.pool_col[pos] = c;
-                            P.pool_val[pos] = x;
-                            my_absmax = xb > my_absmax ? xb : my_absmax;
-                            if (P.filtering && xb <= eps_bits) {
-                                exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, P.e_lsb);
-                                ++my_cand;
-                            }
-                        }
-                        written += __popc(m);
                     }
-                    __syncwarp();
-                    c0 = c1;
                 }
-                if (lane == 0) {
-                    P.out_rb[r] = (int)base;
-                    P.out_re[r] = (int)(base + written);
-                    my_written = (unsigned long long)written;
-                }
+                __syncwarp();
             }
+
+            // ---- product A B: k of row r ascending
+            for (int seg = pa0; seg < pa1; seg += 32) {
+                const int cnt_seg = min(32, pa1 - seg);
+                load_segment(P, seg, cnt_seg, single, c0, c1, lane, S);
+                accumulate_segment(P, cnt_seg, c0, lane, S);
+            }
+
+            // ---- write back the nonzero entries in column order; the entries
+            // with |x| <= eps_g enter the column sums of Algorithm 1's first pass
+            for (int i0 = 0; i0 < cnt; i0 += 32) {
+                int i = i0 + lane;
+                double x = 0.0;
+                int c = 0;
+                if (i < cnt) {
+                    x = S.acc[i];
+                    c = c0 + (int)S.colbuf[i];
+                }
+                unsigned long long xb = mag_bits(x);
+                bool nz = i < cnt && xb != 0ull;
+                unsigned m = __ballot_sync(kFull, nz);
+                if (nz) {
+                    long long pos = (long long)base + written + __popc(m & lanemask_lt());
+                    P.pool_col[pos] = c;
+                    P.pool_val[pos] = x;
+                    my_absmax = xb > my_absmax ? xb : my_absmax;
+                    if (P.filtering && xb <= eps_bits) {
+                        exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, P.e_lsb);
+                        ++my_cand;
+                    }
+                }
+                written += __popc(m);
+            }
+            __syncwarp();
+            c0 = c1;
+        }
+        if (lane == 0) {
+            P.out_rb[r] = (int)base;
+            P.out_re[r] = (int)(base + written);
+            my_written += (unsigned long long)written;
         }
     }
     // ---- block totals for the step statistics
@@ -458,44 +429,94 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
 
 // ---------------------------------------------------------------- k_product_win
 // Row-group kernel with a dense column-window accumulator.  A group of G
-// threads (G = 32..256, several groups per block) computes one output row at
+// threads (G = 32..256, 256 / G groups per block) computes one output row at
 // a time: acc[c - c0] holds column c of the chunk [c0, c0 + cap) of the row's
-// window, so no symbolic pass and no slot lookup is needed.  The addend
-// terms are folded in order t = 0, 1, ... and the B rows in ascending k, with
-// a group barrier between consecutive k: every output entry sees exactly the
-// fixed fma order of the product definition.  B rows reach shared memory in
-// pieces of G * kWinE entries through a kWinStages-deep cp.async ring; each
-// thread copies and later reads only its own elements.  Rows whose window
-// exceeds `cap` are processed in several column chunks (their pool space is
-// reserved up front from an upper bound); other rows reserve their exact
-// entry count after accumulation.
+// column window, so no symbolic pass and no slot lookup is needed.
+//
+// The row is a sequence of items, each a coefficient and a row of a pooled
+// matrix: first the addends alpha_t M_t (t ascending; the identity is an item
+// without a row), then a_rk B_k for k of A's row ascending.  Every output
+// entry is folded as acc = fma(coef, m, acc) item after item, with a group
+// barrier between items: exactly the fixed rounding order of the product.
+//
+// Item rows reach shared memory by TMA bulk copies (cp.async.bulk) into a
+// kTmaStages-deep ring of stages; one thread of the group issues the copies
+// kTmaStages pieces ahead, completion is tracked by one mbarrier per stage,
+// and the group barrier after each piece releases its stage.  Pool rows start
+// at multiples of 4 entries and own a multiple of 4 slots, so every copy is
+// 16-byte aligned and sized.  A row whose window exceeds `cap` is processed in
+// several column chunks (its pool space is reserved up front from an upper
+// bound); other rows reserve their exact entry count after accumulation.
 constexpr int kWinThreads = 256;
-constexpr int kWinStages = 4;
-constexpr int kWinE = 2;
+constexpr int kTmaStages = 4;
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;  // 2 s
+
+struct Item {
+    double a;  // coefficient
+    int b, e;  // row range [b, e) in the pool; b < 0 marks the identity
+};
 
 template <int G>
-struct WinGroup {
+struct WinCfg {
     static constexpr int NG = kWinThreads / G;
     static constexpr int NW = G / 32;
-    static constexpr int PIECE = G * kWinE;
-    // per-group layout after acc[cap]
-    int sc[kWinStages][PIECE];
-    double sv[kWinStages][PIECE];
-    double ka[G];
-    int kb[G];
-    int kl[G];
-    long long red[NW];
+    static constexpr int SENT = 4 * G;  // entries per stage
+};
+
+// per-group shared memory after acc[cap]
+template <int G>
+struct WinGroup {
+    int sc[kTmaStages][WinCfg<G>::SENT];
+    double sv[kTmaStages][WinCfg<G>::SENT];
+    unsigned long long bar[kTmaStages];
+    Item items[G];
+    long long red[WinCfg<G>::NW];
     int misc[4];
 };
 
 template <int G>
 __host__ __device__ size_t win_group_bytes(int cap) {
-    return ((size_t)cap * sizeof(double) + sizeof(WinGroup<G>) + 15) & ~(size_t)15;
+    return ((size_t)cap * sizeof(double) + sizeof(WinGroup<G>) + 127) & ~(size_t)127;
 }
 
+constexpr size_t kWinHeader = (sizeof(AddTerm) * kMaxAdd + 127) & ~(size_t)127;
+
 template <int G>
-size_t win_smem_bytes(int cap) {
-    return sizeof(AddTerm) * kMaxAdd + win_group_bytes<G>(cap) * WinGroup<G>::NG;
+__host__ __device__ size_t win_smem_bytes(int cap) {
+    return kWinHeader + win_group_bytes<G>(cap) * WinCfg<G>::NG;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase of `bar` with the given parity; false after kWaitBudgetNs
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitBudgetNs) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 template <int G>
@@ -508,116 +529,105 @@ __device__ __forceinline__ void group_sync(int g) {
 }
 
 // group-wide reductions through the per-group scratch (all G threads call)
-template <int G>
-__device__ __forceinline__ long long group_sum(long long v, WinGroup<G>& S, int g, int gt) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+template <int G, class T, class Op>
+__device__ __forceinline__ T group_reduce(T v, Op op, WinGroup<G>& S, int g, int gt) {
+    for (int o = 16; o; o >>= 1) v = op(v, (T)__shfl_xor_sync(kFull, v, o));
     if constexpr (G == 32) {
         return v;
     } else {
         group_sync<G>(g);
-        if ((gt & 31) == 0) S.red[gt >> 5] = v;
+        if ((gt & 31) == 0) S.red[gt >> 5] = (long long)v;
         group_sync<G>(g);
-        long long t = 0;
+        T t = (T)S.red[0];
 #pragma unroll
-        for (int w = 0; w < WinGroup<G>::NW; ++w) t += S.red[w];
+        for (int w = 1; w < WinCfg<G>::NW; ++w) t = op(t, (T)S.red[w]);
         return t;
     }
 }
+
+// Piece cursor over the items [0, cnt) of a segment: item i, offset `off`
+// (entries from the 4-aligned start of its range).  Identity items are one
+// piece without data.
 template <int G>
-__device__ __forceinline__ int group_min(int v, WinGroup<G>& S, int g, int gt) {
-    v = warp_min(v);
-    if constexpr (G == 32) {
-        return v;
-    } else {
-        group_sync<G>(g);
-        if ((gt & 31) == 0) S.red[gt >> 5] = v;
-        group_sync<G>(g);
-        long long t = S.red[0];
-#pragma unroll
-        for (int w = 1; w < WinGroup<G>::NW; ++w) t = min(t, S.red[w]);
-        return (int)t;
-    }
+__device__ __forceinline__ void piece_first(const WinGroup<G>& S, int cnt, int& i, int& off) {
+    i = 0;
+    off = 0;
+    while (i < cnt && S.items[i].b >= 0 && S.items[i].e <= S.items[i].b) ++i;
 }
 template <int G>
-__device__ __forceinline__ int group_max(int v, WinGroup<G>& S, int g, int gt) {
-    v = warp_max(v);
-    if constexpr (G == 32) {
-        return v;
-    } else {
-        group_sync<G>(g);
-        if ((gt & 31) == 0) S.red[gt >> 5] = v;
-        group_sync<G>(g);
-        long long t = S.red[0];
-#pragma unroll
-        for (int w = 1; w < WinGroup<G>::NW; ++w) t = max(t, S.red[w]);
-        return (int)t;
+__device__ __forceinline__ void piece_next(const WinGroup<G>& S, int cnt, int& i, int& off) {
+    const Item& it = S.items[i];
+    if (it.b >= 0) {
+        off += WinCfg<G>::SENT;
+        if ((it.b & ~3) + off < it.e) return;
     }
+    off = 0;
+    do {
+        ++i;
+    } while (i < cnt && S.items[i].b >= 0 && S.items[i].e <= S.items[i].b);
 }
 
+// Issue the TMA copies of piece (i, off) into ring slot `slot` (one thread).
 template <int G>
-__device__ __forceinline__ void win_next(const WinGroup<G>& S, int cnt, int& i, int& off) {
-    off += WinGroup<G>::PIECE;
-    if (off >= S.kl[i]) {
-        off = 0;
-        do {
-            ++i;
-        } while (i < cnt && S.kl[i] == 0);
-    }
-}
-
-template <int G>
-__device__ __forceinline__ void win_issue(const ProductArgs& P, WinGroup<G>& S, int cnt, int i, int off, int stage,
-                                          int gt) {
-    if (i < cnt) {
-#pragma unroll
-        for (int e = 0; e < kWinE; ++e) {
-            int o = off + gt + e * G;
-            if (o < S.kl[i]) {
-                int q = S.kb[i] + o;
-                cp_async4(&S.sc[stage][gt + e * G], P.B.col + q);
-                cp_async8(&S.sv[stage][gt + e * G], P.B.val + q);
-            }
-        }
-    }
-    cp_async_commit();
+__device__ __forceinline__ void piece_issue(const int* col, const double* val, WinGroup<G>& S, int i, int off,
+                                            int slot) {
+    const Item& it = S.items[i];
+    const int ab = it.b & ~3;
+    const int p0 = ab + off;
+    const int p1 = min(it.e, p0 + WinCfg<G>::SENT);
+    const unsigned cnt4 = (unsigned)((p1 - p0 + 3) & ~3);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&S.bar[slot], cnt4 * (unsigned)(sizeof(int) + sizeof(double)));
+    tma_load(&S.sc[slot][0], col + p0, cnt4 * (unsigned)sizeof(int), &S.bar[slot]);
+    tma_load(&S.sv[slot][0], val + p0, cnt4 * (unsigned)sizeof(double), &S.bar[slot]);
 }
 
 template <int G>
 __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int cap) {
-    constexpr int NG = WinGroup<G>::NG;
-    constexpr int NW = WinGroup<G>::NW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
+    constexpr int NG = WinCfg<G>::NG;
+    constexpr int NW = WinCfg<G>::NW;
+    constexpr int SENT = WinCfg<G>::SENT;
+    extern __shared__ __align__(16) unsigned char smem_win[];
     const int g = threadIdx.x / G, gt = threadIdx.x % G, lane = threadIdx.x & 31, gw = gt >> 5;
-    unsigned char* gbase = smem_raw + sizeof(AddTerm) * kMaxAdd + win_group_bytes<G>(cap) * g;
+    AddTerm* add = reinterpret_cast<AddTerm*>(smem_win);
+    unsigned char* gbase = smem_win + kWinHeader + win_group_bytes<G>(cap) * g;
     double* acc = reinterpret_cast<double*>(gbase);
     WinGroup<G>& S = *reinterpret_cast<WinGroup<G>*>(gbase + (size_t)cap * sizeof(double));
     const int nadd = P.nadd;
     for (int t = threadIdx.x; t < nadd; t += blockDim.x) add[t] = P.add[t];
+    if (gt == 0) {
+        for (int s = 0; s < kTmaStages; ++s) mbar_init(&S.bar[s], 1);
+        S.misc[2] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
     unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
+    unsigned consumed = 0, issued = 0;  // pieces through the ring (group-uniform)
+    bool alive = true;
+    // every item row (B rows and addend rows) is a row of the pool
+    const int* pcol = P.pool_col;
+    const double* pval = P.pool_val;
 
-    for (int r = blockIdx.x * NG + g; r < P.n; r += gridDim.x * NG) {
+    for (int r = blockIdx.x * NG + g; r < P.n && alive; r += gridDim.x * NG) {
         // ---- window [lo, hi] of row r and its multiply-add count
         int lo = INT_MAX, hi = -1;
         long long ub = 0;  // entry upper bound: products plus addend entries
-        if (gt == 0)
-            for (int t = 0; t < nadd; ++t) {
-                const AddTerm& T = add[t];
-                if (!T.rb) {
-                    lo = min(lo, r);
-                    hi = max(hi, r);
-                    ub += 1;
-                } else {
-                    int s = T.rb[r], e = T.re[r];
-                    ub += e - s;
-                    if (s < e) {
-                        lo = min(lo, T.col[s]);
-                        hi = max(hi, T.col[e - 1]);
-                    }
+        for (int t = gt; t < nadd; t += G) {
+            const AddTerm& T = add[t];
+            if (!T.rb) {
+                lo = min(lo, r);
+                hi = max(hi, r);
+                ub += 1;
+            } else {
+                int s = T.rb[r], e = T.re[r];
+                ub += e - s;
+                if (s < e) {
+                    lo = min(lo, T.col[s]);
+                    hi = max(hi, T.col[e - 1]);
                 }
             }
+        }
         int pa0 = 0, pa1 = 0;
         if (P.A.rb) {
             pa0 = P.A.rb[r];
@@ -632,9 +642,9 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
                 hi = max(hi, P.B.col[e - 1]);
             }
         }
-        lo = group_min<G>(lo, S, g, gt);
-        hi = group_max<G>(hi, S, g, gt);
-        ub = group_sum<G>(ub, S, g, gt);
+        lo = group_reduce<G, int>(lo, [](int x, int y) { return min(x, y); }, S, g, gt);
+        hi = group_reduce<G, int>(hi, [](int x, int y) { return max(x, y); }, S, g, gt);
+        ub = group_reduce<G, long long>(ub, [](long long x, long long y) { return x + y; }, S, g, gt);
         if (gt == 0) my_fma += (unsigned long long)ub;
         if (hi < lo) {
             if (gt == 0) P.out_rb[r] = P.out_re[r] = 0;
@@ -647,15 +657,12 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
         bool ok = true;
         if (!single) {
             // reserve the upper bound min(W, products + addend entries) now
-            long long need = min(W, ub);
+            long long need = (min(W, ub) + 3) & ~3LL;
             if (gt == 0) {
                 unsigned long long b = atomicAdd(&P.ctl->pool_used, (unsigned long long)need);
-                if (b + (unsigned long long)need > P.ctl->pool_cap) {
-                    atomicOr(&P.ctl->status, kDevPoolFull);
-                    S.misc[0] = 0;
-                } else {
-                    S.misc[0] = 1;
-                }
+                bool fits = b + (unsigned long long)need <= P.ctl->pool_cap;
+                if (!fits) atomicOr(&P.ctl->status, kDevPoolFull);
+                S.misc[0] = fits ? 1 : 0;
                 S.misc[1] = (int)(b & 0x7fffffff);
             }
             group_sync<G>(g);
@@ -664,85 +671,108 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
             group_sync<G>(g);
         }
         long long written = 0;
-        for (long long c0l = lo; c0l <= hi && ok; c0l += cap) {
+        const int ntot = nadd + (pa1 - pa0);
+        for (long long c0l = lo; c0l <= hi && ok && alive; c0l += cap) {
             const int c0 = (int)c0l;
             const int wlen = (int)min((long long)cap, (long long)hi - c0 + 1);
             const int c1 = c0 + wlen;
             for (int i = gt; i < wlen; i += G) acc[i] = 0.0;
-            group_sync<G>(g);
-            // ---- weighted sum of the addends, t ascending
-            for (int t = 0; t < nadd; ++t) {
-                const AddTerm& T = add[t];
-                const double alpha = T.alpha;
-                if (!T.rb) {
-                    if (gt == 0 && r >= c0 && r < c1) acc[r - c0] = __fma_rn(alpha, 1.0, acc[r - c0]);
-                } else {
-                    int s = T.rb[r], e = T.re[r];
-                    for (int q = s + gt; q < e; q += G) {
-                        int c = T.col[q];
-                        if (c >= c0 && c < c1) acc[c - c0] = __fma_rn(alpha, T.val[q], acc[c - c0]);
-                    }
-                }
-                group_sync<G>(g);
-            }
-            // ---- product: k of row r ascending
-            for (int seg = pa0; seg < pa1; seg += G) {
-                const int cnt = min(G, pa1 - seg);
+            for (int seg = 0; seg < ntot && alive; seg += G) {
+                // ---- items of this segment: addends first, then A's row
+                const int cnt = min(G, ntot - seg);
+                group_sync<G>(g);  // previous segment's items fully consumed
                 if (gt < cnt) {
-                    int k = P.A.col[seg + gt];
-                    int b = P.B.rb[k], e = P.B.re[k];
-                    if (!single) {
-                        int b2 = lower_bound_col(P.B.col, b, e, c0);
-                        e = lower_bound_col(P.B.col, b2, e, c1);
+                    int idx = seg + gt;
+                    Item it;
+                    int b, e;
+                    if (idx < nadd) {
+                        const AddTerm& T = add[idx];
+                        it.a = T.alpha;
+                        if (!T.rb) {
+                            b = -1;
+                            e = 0;
+                        } else {
+                            b = T.rb[r];
+                            e = T.re[r];
+                        }
+                    } else {
+                        int p = pa0 + idx - nadd;
+                        int k = P.A.col[p];
+                        it.a = P.A.val[p];
+                        b = P.B.rb[k];
+                        e = P.B.re[k];
+                    }
+                    if (b >= 0 && !single) {
+                        int b2 = lower_bound_col(pcol, b, e, c0);
+                        e = lower_bound_col(pcol, b2, e, c1);
                         b = b2;
                     }
-                    S.ka[gt] = P.A.val[seg + gt];
-                    S.kb[gt] = b;
-                    S.kl[gt] = e - b;
+                    it.b = b;
+                    it.e = e;
+                    S.items[gt] = it;
                 }
                 group_sync<G>(g);
-                int ci = 0, coff = 0;
-                while (ci < cnt && S.kl[ci] == 0) ++ci;
-                int ii = ci, ioff = 0;
-#pragma unroll 1
-                for (int st = 0; st < kWinStages - 1; ++st) {
-                    win_issue<G>(P, S, cnt, ii, ioff, st, gt);
-                    if (ii < cnt) win_next<G>(S, cnt, ii, ioff);
-                }
-                int stage = 0;
-                while (ci < cnt) {
-                    cp_async_wait<kWinStages - 2>();
-                    const double a = S.ka[ci];
-                    const int len = S.kl[ci];
-#pragma unroll
-                    for (int e = 0; e < kWinE; ++e) {
-                        int o = coff + gt + e * G;
-                        if (o < len) {
-                            int c = S.sc[stage][gt + e * G];
-                            double v = S.sv[stage][gt + e * G];
-                            acc[c - c0] = __fma_rn(a, v, acc[c - c0]);
-                        }
+                // ---- pieces through the TMA ring
+                int ci, coff, ii, ioff;
+                piece_first<G>(S, cnt, ci, coff);
+                ii = ci;
+                ioff = coff;
+                // prologue: fill the ring up to kTmaStages pieces ahead
+                while (ii < cnt && issued - consumed < (unsigned)kTmaStages) {
+                    if (S.items[ii].b >= 0) {
+                        if (gt == 0) piece_issue<G>(pcol, pval, S, ii, ioff, (int)(issued % kTmaStages));
+                        ++issued;
                     }
-                    int pi = ci;
-                    win_next<G>(S, cnt, ci, coff);
-                    if (ci != pi) group_sync<G>(g);
-                    win_issue<G>(P, S, cnt, ii, ioff, (stage + kWinStages - 1) % kWinStages, gt);
-                    if (ii < cnt) win_next<G>(S, cnt, ii, ioff);
-                    stage = (stage + 1) % kWinStages;
+                    piece_next<G>(S, cnt, ii, ioff);
                 }
-                cp_async_wait<0>();
-                group_sync<G>(g);
+                while (ci < cnt) {
+                    const Item it = S.items[ci];
+                    if (it.b < 0) {
+                        // identity item: acc[r] = fma(alpha, 1, acc[r])
+                        if (gt == 0 && r >= c0 && r < c1) acc[r - c0] = __fma_rn(it.a, 1.0, acc[r - c0]);
+                    } else {
+                        const int slot = (int)(consumed % kTmaStages);
+                        const bool got = mbar_wait(&S.bar[slot], (consumed / kTmaStages) & 1u);
+                        if (!got) {
+                            atomicOr(&P.ctl->status, kDevTimeout);
+                            S.misc[2] = 1;
+                        }
+                        const int ab = it.b & ~3;
+                        const int p0 = ab + coff;
+                        const int lo_i = max(it.b, p0) - p0, hi_i = min(it.e, p0 + SENT) - p0;
+                        for (int i = lo_i + gt; i < hi_i; i += G) {
+                            int c = S.sc[slot][i];
+                            double v = S.sv[slot][i];
+                            acc[c - c0] = __fma_rn(it.a, v, acc[c - c0]);
+                        }
+                        ++consumed;
+                    }
+                    piece_next<G>(S, cnt, ci, coff);
+                    group_sync<G>(g);  // item done: order of the fma chain, stage released
+                    if (S.misc[2]) {
+                        alive = false;
+                        break;
+                    }
+                    while (ii < cnt && issued - consumed < (unsigned)kTmaStages) {
+                        if (S.items[ii].b >= 0) {
+                            if (gt == 0) piece_issue<G>(pcol, pval, S, ii, ioff, (int)(issued % kTmaStages));
+                            ++issued;
+                        }
+                        piece_next<G>(S, cnt, ii, ioff);
+                    }
+                }
             }
+            if (!alive) break;
+            group_sync<G>(g);
             // ---- write-back: each warp sweeps a contiguous part of the window
             const int part = ((wlen + NW * 32 - 1) / (NW * 32)) * 32;
-            const int p0 = gw * part, p1 = min(wlen, p0 + part);
+            const int q0 = gw * part, q1 = min(wlen, q0 + part);
             int mycount = 0;
-            for (int i0 = p0; i0 < p1; i0 += 32) {
+            for (int i0 = q0; i0 < q1; i0 += 32) {
                 int i = i0 + lane;
-                bool nz = i < p1 && mag_bits(acc[i]) != 0ull;
+                bool nz = i < q1 && mag_bits(acc[i]) != 0ull;
                 mycount += __popc(__ballot_sync(kFull, nz));
             }
-            // exclusive prefix of the warp counts within the group
             int before = 0, total = mycount;
             if constexpr (G > 32) {
                 if (lane == 0) S.red[gw] = mycount;
@@ -757,13 +787,11 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
             }
             if (single) {
                 if (gt == 0) {
-                    unsigned long long b = atomicAdd(&P.ctl->pool_used, (unsigned long long)total);
-                    if (b + (unsigned long long)total > P.ctl->pool_cap) {
-                        atomicOr(&P.ctl->status, kDevPoolFull);
-                        S.misc[0] = 0;
-                    } else {
-                        S.misc[0] = 1;
-                    }
+                    unsigned long long need = (unsigned long long)((total + 3) & ~3);
+                    unsigned long long b = atomicAdd(&P.ctl->pool_used, need);
+                    bool fits = b + need <= P.ctl->pool_cap;
+                    if (!fits) atomicOr(&P.ctl->status, kDevPoolFull);
+                    S.misc[0] = fits ? 1 : 0;
                     S.misc[1] = (int)(b & 0x7fffffff);
                 }
                 group_sync<G>(g);
@@ -773,11 +801,11 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
                 if (!ok) break;
             }
             long long pos0 = base + written + before;
-            for (int i0 = p0; i0 < p1; i0 += 32) {
+            for (int i0 = q0; i0 < q1; i0 += 32) {
                 int i = i0 + lane;
-                double x = i < p1 ? acc[i] : 0.0;
+                double x = i < q1 ? acc[i] : 0.0;
                 unsigned long long xb = mag_bits(x);
-                bool nz = i < p1 && xb != 0ull;
+                bool nz = i < q1 && xb != 0ull;
                 unsigned m = __ballot_sync(kFull, nz);
                 if (nz) {
                     long long pos = pos0 + __popc(m & lanemask_lt());
@@ -793,10 +821,9 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
                 pos0 += __popc(m);
             }
             written += total;
-            group_sync<G>(g);
         }
         if (gt == 0) {
-            if (ok) {
+            if (ok && alive) {
                 P.out_rb[r] = (int)base;
                 P.out_re[r] = (int)(base + written);
                 my_written += (unsigned long long)written;
@@ -805,6 +832,13 @@ __global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int 
             }
         }
         group_sync<G>(g);
+    }
+    if (!alive && gt == 0) {
+        // bounded drain of the copies still in flight before the block exits
+        while (consumed < issued) {
+            mbar_wait(&S.bar[consumed % kTmaStages], (consumed / kTmaStages) & 1u);
+            ++consumed;
+        }
     }
     // ---- block totals for the step statistics
     __shared__ unsigned long long blk[4];
@@ -1072,6 +1106,37 @@ __global__ void k_gather(int n, RowView src, const int* rowptr, int* col, double
     }
 }
 
+// Copy a canonical CSR matrix into the pool: each row gets a 4-entry aligned
+// slot of round-up(len, 4) entries (the layout the TMA copies rely on).
+__global__ void k_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
+                            int* pool_col, double* pool_val, Ctl* ctl) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = gw; r < n; r += nwarps) {
+        int s = rowptr[r], e = rowptr[r + 1];
+        unsigned long long need = (unsigned long long)((e - s + 3) & ~3);
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(&ctl->pool_used, need);
+        base = __shfl_sync(kFull, base, 0);
+        if (base + need > ctl->pool_cap) {
+            if (lane == 0) {
+                atomicOr(&ctl->status, kDevPoolFull);
+                rb[r] = re[r] = 0;
+            }
+            continue;
+        }
+        for (int q = lane; q < e - s; q += 32) {
+            pool_col[base + q] = col[s + q];
+            pool_val[base + q] = val[s + q];
+        }
+        if (lane == 0) {
+            rb[r] = (int)base;
+            re[r] = (int)base + (e - s);
+        }
+    }
+}
+
 __global__ void k_identity(int n, double alpha, int* rowptr, int* col, double* val) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) {
@@ -1096,14 +1161,14 @@ static std::atomic<long long> g_launches{0};
 
 long long launch_count() { return g_launches.load(); }
 
-// smem budget of one k_product_win block: three blocks fit on one SM
-constexpr size_t kWinBlockBudget = 74 * 1024;
+// smem budget of one k_product_win block: two blocks fit on one SM
+constexpr size_t kWinBlockBudget = 112 * 1024;
 
 template <int G>
 static int win_cap() {
-    size_t fixed = sizeof(AddTerm) * kMaxAdd + sizeof(WinGroup<G>) * WinGroup<G>::NG + 16 * WinGroup<G>::NG;
-    size_t per = (kWinBlockBudget - fixed) / WinGroup<G>::NG / sizeof(double);
-    return (int)(per & ~(size_t)31);
+    int cap = 32 * G;
+    while (cap > 64 && win_smem_bytes<G>(cap) > kWinBlockBudget) cap -= 32;
+    return cap;
 }
 
 template <int G>
@@ -1116,8 +1181,9 @@ template <int G>
 static cudaError_t win_launch(const ProductArgs& P, int cap_limit, cudaStream_t st) {
     const int full = win_cap<G>();
     const int cap = (cap_limit > 0 && cap_limit < full) ? cap_limit : full;
-    long long blocks = ((long long)P.n + WinGroup<G>::NG - 1) / WinGroup<G>::NG;
-    if (blocks > 65535LL * 64) blocks = 65535LL * 64;
+    long long blocks = ((long long)P.n + WinCfg<G>::NG - 1) / WinCfg<G>::NG;
+    const long long maxb = (long long)g_sms * 2 * 8;
+    if (blocks > maxb) blocks = maxb;
     k_product_win<G><<<(unsigned)blocks, kWinThreads, win_smem_bytes<G>(full), st>>>(P, cap);
     ++g_launches;
     return cudaGetLastError();
@@ -1172,6 +1238,7 @@ int num_sms() { return g_sms; }
 cudaError_t launch_product(const ProductArgs& P, cudaStream_t st) {
     if (P.n <= 0) return cudaSuccess;
     int blocks = (P.n + kProdWarps - 1) / kProdWarps;
+    if (blocks > g_sms * 6 * 4) blocks = g_sms * 6 * 4;
     k_product<<<blocks, kProdWarps * 32, product_smem_bytes(), st>>>(P);
     ++g_launches;
     return cudaGetLastError();
@@ -1230,6 +1297,16 @@ cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col
 
 cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* val, cudaStream_t st) {
     k_identity<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, alpha, rowptr, col, val);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
+                             int* pool_col, double* pool_val, Ctl* ctl, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int blocks = (n + 7) / 8;
+    if (blocks > g_sms * 16) blocks = g_sms * 16;
+    k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -25,6 +25,8 @@ cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, C
 cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col, double* val,
                           cudaStream_t st);
 cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* val, cudaStream_t st);
+cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
+                             int* pool_col, double* pool_val, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
 
 }  // namespace psf
