@@ -242,7 +242,7 @@ int group_for(double blen) {
 // threshold > 0.
 int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
              double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
-             NormSlot* absmax_slot = nullptr, double blen = 0.0) {
+             NormSlot* absmax_slot = nullptr, double blen = 0.0, double alen = 0.0) {
     if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
@@ -276,7 +276,8 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
         CU(cudaEventRecord(e0, w.st));
     }
     if (w.bitmap_kernel) {
-        CU(launch_product(P, w.st));
+        // table map when a row folds many products per window column
+        CU(launch_product(P, alen * blen >= 2048.0, w.st));
     } else {
         CU(launch_product_win(P, group_for(blen), w.window_cap, w.st));
     }
@@ -564,7 +565,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
         }
         if (A && (rc = pool_copy(w, *B, 1, &vb))) return rc;
         if ((rc = run_step(w, A ? &va : nullptr, A ? &vb : nullptr, add, threshold, e_r, maxit, 0, 0, &res,
-                           nullptr, blen)))
+                           nullptr, blen, A && n > 0 ? (double)A->nnz / n : 0.0)))
             return rc;
         Ctl c;
         if ((rc = read_back(w, c, nullptr))) return rc;
@@ -669,7 +670,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
                                                                           : zlen * (i - 1) * (i - 1);
                     if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, i - 2, (size_t)(i - 2), &cur, slots + i,
-                                       blen)))
+                                       blen, zlen)))
                         return rc;
                     na.m[i - 1] = cur;
                     prev = cur;
@@ -768,7 +769,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                                   ? series->len_baby[(size_t)(k - 1)]
                                   : (k <= 10 && znnz[k] > 0.0 ? znnz[k] / n : zlen * k * k);
                 if ((rc = run_step(w, &vz, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
-                                   &Zh[(size_t)k + 1], nullptr, blen)))
+                                   &Zh[(size_t)k + 1], nullptr, blen, zlen)))
                     return rc;
                 psf_step_info_t s{};
                 s.kind = 0;
@@ -831,8 +832,9 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     double blen = (size_t)(i - 1) < series->len_giant.size()
                                       ? series->len_giant[(size_t)(i - 1)]
                                       : (znnz[10] > 0.0 ? znnz[10] / n : zlen * 100.0);
+                    const double alen = (q <= 10 && znnz[q] > 0.0) ? znnz[q] / n : zlen * q * q;
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
-                                       &nxt, nullptr, blen)))
+                                       &nxt, nullptr, blen, alen)))
                         return rc;
                     s.kind = 1;
                     s.threshold = thr;

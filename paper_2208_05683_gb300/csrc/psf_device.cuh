@@ -256,6 +256,36 @@ __device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stri
     return ldexp((double)M, shift + e_lsb);
 }
 
+// Per-warp sub-allocator of the entry pool: a warp takes kArena entries (or
+// the request, if larger) from the shared counter with one atomic and carves
+// its rows out of them, so rows cost no contended atomic.  Every request and
+// arena is a multiple of 4 entries (rows start 16-byte aligned).  Returns
+// the row's first entry, or -1 when the pool is full (recorded in status).
+constexpr unsigned long long kArena = 512;
+
+struct Arena {
+    unsigned long long next = 0, end = 0;
+};
+
+__device__ __forceinline__ long long arena_take(Arena& a, unsigned long long need, Ctl* ctl, int lane) {
+    if (a.next + need > a.end) {
+        const unsigned long long chunk = need > kArena ? need : kArena;
+        unsigned long long b = 0ull;
+        if (lane == 0) b = atomicAdd(&ctl->pool_used, chunk);
+        b = __shfl_sync(kFull, b, 0);
+        if (b + chunk > ctl->pool_cap) {
+            if (lane == 0) atomicOr(&ctl->status, kDevPoolFull);
+            a.next = a.end = 0;
+            return -1;
+        }
+        a.next = b;
+        a.end = b + chunk;
+    }
+    const unsigned long long r = a.next;
+    a.next += need;
+    return (long long)r;
+}
+
 // Grid-wide barrier for cooperative launches, with a bounded wait: after
 // `budget_ns` it records kDevTimeout and returns false.
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned long long budget_ns) {

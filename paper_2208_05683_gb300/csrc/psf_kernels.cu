@@ -20,28 +20,40 @@ namespace psf {
 
 // ---------------------------------------------------------------- k_product
 // Compact-accumulator kernel: one warp computes one output row, with no
-// block-level synchronisation.  Shared memory per warp:
-//   pm[kBmWords]       bitmap of the row's output columns in the chunk
-//                      [c0, c0 + 32 kBmWords) (.y) with the number of set
-//                      bits before each word (.x)
-//   colbuf[kAccCap]    column - c0 of each accumulator slot (ascending)
-//   acc[kAccCap]       FP64 accumulators, slot = rank of the column in the chunk
-//   ka/kb/kl           coefficient and B-row range of up to 32 entries of A's row
-// Symbolic pass: for each B row, lane l covers a contiguous slice of the row
-// and ORs whole runs of columns into a bitmap word at a time.  Numeric pass:
-// the addends in order, then the B rows in ascending k, each entry folded
-// as acc[slot] = fma(a, b, acc[slot]) with a warp barrier between rows (the
-// fixed rounding order of the product); B is read in 32-entry pieces, two
-// pieces ahead in registers.  A row whose pattern exceeds the
-// chunk (wider than the bitmap or with more than kAccCap entries) is
-// processed in several column chunks.
-constexpr int kBmWords = 160;
+// block-level synchronisation.  The row's output pattern is found first (the
+// symbolic pass), each output column gets an accumulator slot (its rank in
+// the pattern), then the products are folded in (the numeric pass).  Two
+// ways to map a column offset o = c - c0 to its slot, a template parameter:
+//
+//  table  (TAB = true)   tab[o] (16 bit) holds first a flag, set by plain
+//         stores of every contributing entry, then the slot, after a ballot
+//         scan.  O(window) set-up per row, one load per lookup: for rows with
+//         many products per column of the window.
+//  bitmap (TAB = false)  pm[o / 32] holds a 32-column bitmap word, set by
+//         atomic ORs (one per run of columns a lane meets), and the number of
+//         set bits before it; slot = prefix + popcount of the lower bits.
+//         O(window / 32) set-up per row: for thin rows.
+//
+// Numeric pass: the addends in order, then the B rows in ascending k, each
+// entry folded as acc[slot] = fma(a, b, acc[slot]); a warp barrier separates
+// consecutive rows (the fixed rounding order of the product).  B rows are
+// read in 128-entry chunks (four 32-entry pieces; the entries of a chunk
+// have distinct columns, so its four read-modify-writes are independent).
+// A row whose pattern exceeds the chunk (wider than the map or with more
+// than kAccCap entries) is processed in several column chunks.
+constexpr int kTabCap = 4160;  // columns of the table map
+constexpr int kBmWords = 160;  // bitmap words of the bitmap map
 constexpr int kBmBits = kBmWords * 32;
 constexpr int kAccCap = 672;
-constexpr int kProdWarps = 4;
 
-struct WarpSmem {
-    uint2 pm[kBmWords];  // .x = set bits before the word (prefix), .y = bitmap word
+template <bool TAB>
+struct ProdSmem;
+
+template <>
+struct ProdSmem<true> {
+    static constexpr int kCols = kTabCap;
+    static constexpr int kWarps = 2;
+    unsigned short tab[kTabCap];
     double acc[kAccCap];
     double ka[32];
     int kb[32];
@@ -49,13 +61,24 @@ struct WarpSmem {
     unsigned short colbuf[kAccCap];
 };
 
-size_t product_smem_bytes() { return sizeof(WarpSmem) * kProdWarps + sizeof(AddTerm) * kMaxAdd; }
-int product_warps_per_block() { return kProdWarps; }
+template <>
+struct ProdSmem<false> {
+    static constexpr int kCols = kBmBits;
+    static constexpr int kWarps = 4;
+    uint2 pm[kBmWords];  // .x = set bits before the word, .y = bitmap word
+    double acc[kAccCap];
+    double ka[32];
+    int kb[32];
+    int kl[32];
+    unsigned short colbuf[kAccCap];
+};
 
-__device__ __forceinline__ int slot_of(const WarpSmem& S, int off) {
-    const uint2 e = S.pm[off >> 5];
-    return (int)e.x + __popc(e.y & ((1u << (off & 31)) - 1u));
+template <bool TAB>
+size_t prod_smem_bytes() {
+    return sizeof(ProdSmem<TAB>) * ProdSmem<TAB>::kWarps + sizeof(AddTerm) * kMaxAdd;
 }
+size_t product_smem_bytes() { return prod_smem_bytes<true>(); }
+int product_warps_per_block() { return ProdSmem<true>::kWarps; }
 
 // first position in [s, e) with col >= c (col ascending)
 __device__ __forceinline__ int lower_bound_col(const int* col, int s, int e, int c) {
@@ -67,52 +90,18 @@ __device__ __forceinline__ int lower_bound_col(const int* col, int s, int e, int
     return s;
 }
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Set the bitmap bits of the columns in [c0, cend) of col[s .. e).  Lane l
-// walks the contiguous slice [s + l m, s + (l + 1) m) and issues one atomic OR
-// per bitmap word it meets (a run of columns costs one atomic).
-__device__ __forceinline__ void slice_bits(const int* col, int s, int e, int c0, int cend, int lane,
-                                           WarpSmem& S) {
-    const int m = (e - s + 31) >> 5;
-    const int q0 = s + lane * m, q1 = min(e, q0 + m);
-    unsigned curw = 0xffffffffu, mask = 0u;
-    for (int q = q0; q < q1; q += 4) {
-        int cs[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) cs[u] = q + u < q1 ? col[q + u] : INT_MIN;  // independent loads
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int c = cs[u];
-            if (c < c0 || c >= cend) continue;
-            unsigned off = (unsigned)(c - c0), w = off >> 5;
-            if (w != curw) {
-                if (mask) atomicOr(&S.pm[curw].y, mask);
-                curw = w;
-                mask = 0u;
-            }
-            mask |= 1u << (off & 31);
-        }
-    }
-    if (mask) atomicOr(&S.pm[curw].y, mask);
+// slot of column offset o (o inside the current chunk's pattern)
+__device__ __forceinline__ int slot_lookup(const ProdSmem<true>& S, int o) { return S.tab[o]; }
+__device__ __forceinline__ int slot_lookup(const ProdSmem<false>& S, int o) {
+    const uint2 e = S.pm[o >> 5];
+    return (int)e.x + __popc(e.y & ((1u << (o & 31)) - 1u));
 }
 
 // Load the segment [seg, seg + cnt) of A's row: a_rk and the range of B's row
 // k restricted to columns [c0, c1) (the whole row when `whole`).
+template <bool TAB>
 __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1,
-                                             int lane, WarpSmem& S) {
+                                             int lane, ProdSmem<TAB>& S) {
     if (lane < cnt) {
         int k = P.A.col[seg + lane];
         int b = P.B.rb[k], e = P.B.re[k];
@@ -128,108 +117,282 @@ __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int 
     __syncwarp();
 }
 
-// Bitmap of every output column of row r in [c0, cend).
-__device__ __forceinline__ void build_bitmap(const ProductArgs& P, const AddTerm* add, int nadd, int r, int c0, int cend,
-                             int pa0, int pa1, bool whole, int lane, WarpSmem& S) {
-    for (int w = lane; w < kBmWords; w += 32) S.pm[w].y = 0u;
+// ---- symbolic pass, table map: plain flag stores, four pieces per step
+__device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int e, int c0, int cend, int lane,
+                                         ProdSmem<true>& S) {
+    for (int q0 = s; q0 < e; q0 += 128) {
+        int cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * 32 + lane;
+            cs[u] = q < e ? col[q] : INT_MIN;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (cs[u] >= c0 && cs[u] < cend) S.tab[cs[u] - c0] = 1;
+    }
+}
+__device__ __forceinline__ void mark_one(int o, ProdSmem<true>& S) { S.tab[o] = 1; }
+__device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<true>& S) {
+    uint4* t4 = reinterpret_cast<uint4*>(S.tab);
+    const int n16 = (wlen + 7) >> 3;
+    for (int i = lane; i < n16; i += 32) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ---- symbolic pass, bitmap map: lane l walks a contiguous slice of the row
+// and ORs whole runs of columns into a bitmap word at a time
+__device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int e, int c0, int cend, int lane,
+                                         ProdSmem<false>& S) {
+    const int m = (e - s + 31) >> 5;
+    const int q0 = s + lane * m, q1 = min(e, q0 + m);
+    unsigned curw = 0xffffffffu, mask = 0u;
+    for (int q = q0; q < q1; q += 4) {
+        int cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cs[u] = q + u < q1 ? col[q + u] : INT_MIN;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int c = cs[u];
+            if (c < c0 || c >= cend) continue;
+            unsigned off = (unsigned)(c - c0), w = off >> 5;
+            if (w != curw) {
+                if (mask) atomicOr(&S.pm[curw].y, mask);
+                curw = w;
+                mask = 0u;
+            }
+            mask |= 1u << (off & 31);
+        }
+    }
+    if (mask) atomicOr(&S.pm[curw].y, mask);
+}
+__device__ __forceinline__ void mark_one(int o, ProdSmem<false>& S) { atomicOr(&S.pm[o >> 5].y, 1u << (o & 31)); }
+__device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false>& S) {
+    const int nw = (wlen + 31) >> 5;
+    for (int w = lane; w < nw; w += 32) S.pm[w].y = 0u;
+}
+
+// Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
+template <bool TAB>
+__device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, int r, int c0, int cend,
+                                          int pa0, int pa1, bool whole, int lane, ProdSmem<TAB>& S) {
+    clear_map(cend - c0, lane, S);
     __syncwarp();
     for (int t = 0; t < nadd; ++t) {
         const AddTerm& T = add[t];
         if (!T.rb) {
-            if (lane == 0 && r >= c0 && r < cend) atomicOr(&S.pm[(r - c0) >> 5].y, 1u << ((r - c0) & 31));
+            if (lane == 0 && r >= c0 && r < cend) mark_one(r - c0, S);
         } else {
-            slice_bits(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
+            mark_row(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
         }
     }
     for (int seg = pa0; seg < pa1; seg += 32) {
         const int cnt = min(32, pa1 - seg);
-        load_segment(P, seg, cnt, whole, c0, cend, lane, S);
-        for (int i = 0; i < cnt; ++i) slice_bits(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+        load_segment<TAB>(P, seg, cnt, whole, c0, cend, lane, S);
+        for (int i = 0; i < cnt; ++i) mark_row(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
         __syncwarp();
     }
     __syncwarp();
 }
 
-// prefix[] from bm[]; returns the number of set bits.
-__device__ int scan_bitmap(int lane, WarpSmem& S) {
-    constexpr int per = kBmWords / 32;
-    int base = lane * per, s = 0;
-#pragma unroll
-    for (int i = 0; i < per; ++i) s += __popc(S.pm[base + i].y);
-    int run = warp_excl_scan(s, lane);
-    int total = __shfl_sync(kFull, run + s, 31);
-#pragma unroll
-    for (int i = 0; i < per; ++i) {
-        S.pm[base + i].x = (unsigned)run;
-        run += __popc(S.pm[base + i].y);
+// number of marked columns in [0, wlen)
+__device__ __forceinline__ int count_marks(int wlen, int lane, const ProdSmem<true>& S) {
+    int total = 0;
+    for (int i0 = 0; i0 < wlen; i0 += 32) {
+        int i = i0 + lane;
+        total += __popc(__ballot_sync(kFull, i < wlen && S.tab[i] != 0));
     }
-    __syncwarp();
     return total;
 }
-
-__device__ int count_bitmap(int lane, const WarpSmem& S) {
+__device__ __forceinline__ int count_marks(int wlen, int lane, const ProdSmem<false>& S) {
     int s = 0;
-    for (int w = lane; w < kBmWords; w += 32) s += __popc(S.pm[w].y);
+    for (int w = lane; w < ((wlen + 31) >> 5); w += 32) s += __popc(S.pm[w].y);
     return warp_sum(s);
 }
 
-// Column at which the chunk must stop so that it holds exactly kAccCap
-// entries (called when the chunk holds more).
-__device__ int cut_column(int lane, const WarpSmem& S, int c0) {
-    int found = INT_MAX;
-    for (int w = lane; w < kBmWords; w += 32) {
-        const int pc = __popc(S.pm[w].y), pre = (int)S.pm[w].x;
-        if (pre <= kAccCap && kAccCap < pre + pc) {
-            int need = kAccCap - pre;  // set bits of this word inside the chunk
-            unsigned bits = S.pm[w].y;
-            for (int i = 0; i < need; ++i) bits &= bits - 1u;  // drop the lowest `need`
-            found = c0 + w * 32 + (__ffs(bits) - 1);
+// Number the marked columns of [0, wlen) in ascending order and fill
+// colbuf.  Only the first kAccCap get a slot; returns their count and sets
+// *cut to the offset of the first column without one (wlen if all fit).
+__device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<true>& S, int* cut) {
+    int run = 0, cutoff = wlen;
+    for (int i0 = 0; i0 < wlen; i0 += 32) {
+        const int i = i0 + lane;
+        const bool f = i < wlen && S.tab[i] != 0;
+        const unsigned m = __ballot_sync(kFull, f);
+        const int slot = run + __popc(m & lanemask_lt());
+        if (f && slot < kAccCap) {
+            S.tab[i] = (unsigned short)slot;
+            S.colbuf[slot] = (unsigned short)i;
+        }
+        if (run <= kAccCap && run + __popc(m) > kAccCap) {
+            const unsigned fo = __ballot_sync(kFull, f && slot == kAccCap);
+            cutoff = i0 + __ffs(fo) - 1;
+        }
+        run += __popc(m);
+        if (cutoff < wlen) break;
+    }
+    __syncwarp();
+    *cut = cutoff;
+    return min(run, kAccCap);
+}
+__device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<false>& S, int* cut) {
+    constexpr int per = kBmWords / 32;
+    const int nw = (wlen + 31) >> 5;
+    const int base = lane * per;
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) s += base + i < nw ? __popc(S.pm[base + i].y) : 0;
+    int run = warp_excl_scan(s, lane);
+    const int total = __shfl_sync(kFull, run + s, 31);
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+        if (base + i < nw) {
+            S.pm[base + i].x = (unsigned)run;
+            run += __popc(S.pm[base + i].y);
         }
     }
-    return warp_min(found);
+    __syncwarp();
+    int cutoff = wlen;
+    if (total > kAccCap) {
+        int found = INT_MAX;
+        for (int w = lane; w < nw; w += 32) {
+            const int pc = __popc(S.pm[w].y), pre = (int)S.pm[w].x;
+            if (pre <= kAccCap && kAccCap < pre + pc) {
+                unsigned bits = S.pm[w].y;
+                for (int i = 0; i < kAccCap - pre; ++i) bits &= bits - 1u;  // drop the lowest ones
+                found = w * 32 + (__ffs(bits) - 1);
+            }
+        }
+        cutoff = warp_min(found);
+    }
+    for (int w = lane; w < nw; w += 32) {
+        unsigned bits = S.pm[w].y;
+        int idx = (int)S.pm[w].x;
+        while (bits) {
+            const int o = w * 32 + __ffs(bits) - 1;
+            if (o < cutoff) S.colbuf[idx] = (unsigned short)o;
+            ++idx;
+            bits &= bits - 1u;
+        }
+    }
+    __syncwarp();
+    *cut = cutoff;
+    return min(total, kAccCap);
 }
 
-// acc[slot(j)] = fma(a_rk, b_kj, acc[slot(j)]) for the segment's k in
-// order.  A B row is read in groups of four 32-entry pieces whose loads are
-// all issued before any of them is folded in; the pieces of one row hold
-// distinct columns, so only consecutive rows need a warp barrier.
-__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane, WarpSmem& S) {
+// The 128 entries [off, off + 128) of B row kk of the segment, four 32-entry
+// pieces, one element of each per lane (column -1: no element).
+struct Chunk {
+    int c[4];
+    double v[4];
+};
+
+template <bool TAB>
+__device__ __forceinline__ void chunk_load(const int* __restrict__ bcol, const double* __restrict__ bval,
+                                           const ProdSmem<TAB>& S, int kk, int off, int lane, Chunk& ch) {
+    const int len = S.kl[kk];
+    const int* rc = bcol + S.kb[kk] + lane;
+    const double* rv = bval + S.kb[kk] + lane;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int q = off + u * 32;
+        ch.c[u] = -1;
+        if (q + lane < len) {
+            ch.c[u] = rc[q];
+            ch.v[u] = rv[q];
+        }
+    }
+}
+
+template <bool TAB>
+__device__ __forceinline__ void chunk_next(const ProdSmem<TAB>& S, int cnt, int& kk, int& off) {
+    off += 128;
+    if (off >= S.kl[kk]) {
+        off = 0;
+        do {
+            ++kk;
+        } while (kk < cnt && S.kl[kk] == 0);
+    }
+}
+
+// Fold a chunk in: its columns are distinct, so the four read-modify-writes
+// are independent and are interleaved.
+template <bool TAB>
+__device__ __forceinline__ void chunk_fold(ProdSmem<TAB>& S, const Chunk& ch, double a, int c0) {
+    int i[4];
+    double x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) i[u] = ch.c[u] >= 0 ? slot_lookup(S, ch.c[u] - c0) : -1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (i[u] >= 0) x[u] = S.acc[i[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (i[u] >= 0) S.acc[i[u]] = __fma_rn(a, ch.v[u], x[u]);
+}
+
+// acc[slot(j)] = fma(a_rk, b_kj, acc[slot(j)]) for the segment's k in order.
+// Table map: chunks stream through three register sets (the loads of the
+// next two are in flight while one is folded in).  Bitmap map (more warps,
+// fewer registers): one chunk at a time.  A warp barrier separates
+// consecutive B rows (the order of the fma chain).
+__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane,
+                                                   ProdSmem<true>& S) {
+    const int* __restrict__ bcol = P.B.col;
+    const double* __restrict__ bval = P.B.val;
+    int k0 = 0, o0 = 0;
+    while (k0 < cnt && S.kl[k0] == 0) ++k0;
+    if (k0 >= cnt) return;
+    Chunk A, B, C;
+    chunk_load<true>(bcol, bval, S, k0, o0, lane, A);
+    int k1 = k0, o1 = o0;
+    chunk_next<true>(S, cnt, k1, o1);
+    int k2 = k1, o2 = o1;
+    if (k1 < cnt) {
+        chunk_load<true>(bcol, bval, S, k1, o1, lane, B);
+        chunk_next<true>(S, cnt, k2, o2);
+    }
+    auto step = [&](Chunk& X, Chunk& Z) -> bool {
+        if (k2 < cnt) chunk_load<true>(bcol, bval, S, k2, o2, lane, Z);
+        chunk_fold<true>(S, X, S.ka[k0], c0);
+        if (k1 >= cnt) return false;
+        if (k1 != k0) __syncwarp();
+        k0 = k1;
+        o0 = o1;
+        k1 = k2;
+        o1 = o2;
+        if (k2 < cnt) chunk_next<true>(S, cnt, k2, o2);
+        return true;
+    };
+    for (;;) {
+        if (!step(A, C)) break;
+        if (!step(B, A)) break;
+        if (!step(C, B)) break;
+    }
+    __syncwarp();
+}
+__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane,
+                                                   ProdSmem<false>& S) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
     for (int kk = 0; kk < cnt; ++kk) {
-        const int len = S.kl[kk];
-        if (len == 0) continue;
-        const int* rc = bcol + S.kb[kk] + lane;
-        const double* rv = bval + S.kb[kk] + lane;
+        if (S.kl[kk] == 0) continue;
         const double a = S.ka[kk];
-        for (int off = 0; off < len; off += 128) {
-            int cs[4];
-            double vs[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = off + u * 32;
-                cs[u] = -1;
-                if (q + lane < len) {
-                    cs[u] = rc[q];
-                    vs[u] = rv[q];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (cs[u] >= 0) {
-                    const int i = slot_of(S, cs[u] - c0);
-                    S.acc[i] = __fma_rn(a, vs[u], S.acc[i]);
-                }
-            }
+        for (int off = 0; off < S.kl[kk]; off += 128) {
+            Chunk ch;
+            chunk_load<false>(bcol, bval, S, kk, off, lane, ch);
+            chunk_fold<false>(S, ch, a, c0);
         }
-        __syncwarp();  // next B row: order of the fma chain
+        __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
+template <bool TAB>
+__global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_product(ProductArgs P) {
+    constexpr int kWarps = ProdSmem<TAB>::kWarps;
+    constexpr int kCols = ProdSmem<TAB>::kCols;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
-    WarpSmem* warps = reinterpret_cast<WarpSmem*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
+    ProdSmem<TAB>* warps = reinterpret_cast<ProdSmem<TAB>*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nadd = P.nadd;
     for (int t = threadIdx.x; t < nadd; t += blockDim.x) add[t] = P.add[t];
@@ -241,11 +404,12 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
         blk_absmax = 0ull;
     }
     __syncthreads();
-    WarpSmem& S = warps[wib];
+    ProdSmem<TAB>& S = warps[wib];
     const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
     unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
+    Arena arena;
 
-    for (int r = blockIdx.x * kProdWarps + wib; r < P.n; r += gridDim.x * kProdWarps) {
+    for (int r = blockIdx.x * kWarps + wib; r < P.n; r += gridDim.x * kWarps) {
         // ---- column window of row r and the row's multiply-add count
         int lo = INT_MAX, hi = -1;
         for (int t = 0; t < nadd; ++t) {
@@ -288,57 +452,32 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
         // ---- exact entry count of the row, reserve it in the pool
         long long total = 0;
         bool reuse = false;
-        int chunk_total = 0;
-        if (hi - lo + 1 <= kBmBits) {
-            build_bitmap(P, add, nadd, r, lo, hi + 1, pa0, pa1, true, lane, S);
-            chunk_total = scan_bitmap(lane, S);
-            total = chunk_total;
+        if (hi - lo + 1 <= kCols) {
+            build_map<TAB>(P, add, nadd, r, lo, hi + 1, pa0, pa1, true, lane, S);
+            total = count_marks(hi - lo + 1, lane, S);
             reuse = true;
         } else {
-            for (long long c0 = lo; c0 <= hi; c0 += kBmBits) {
-                int cend = (int)min((long long)hi + 1, c0 + kBmBits);
-                build_bitmap(P, add, nadd, r, (int)c0, cend, pa0, pa1, false, lane, S);
-                total += count_bitmap(lane, S);
+            for (long long c0 = lo; c0 <= hi; c0 += kCols) {
+                int cend = (int)min((long long)hi + 1, c0 + kCols);
+                build_map<TAB>(P, add, nadd, r, (int)c0, cend, pa0, pa1, false, lane, S);
+                total += count_marks(cend - (int)c0, lane, S);
             }
         }
-        unsigned long long base = 0ull;
-        const unsigned long long need = (unsigned long long)((total + 3) & ~3LL);  // 4-entry aligned rows
-        if (lane == 0) base = atomicAdd(&P.ctl->pool_used, need);
-        base = __shfl_sync(kFull, base, 0);
-        if (base + need > P.ctl->pool_cap) {
-            if (lane == 0) {
-                atomicOr(&P.ctl->status, kDevPoolFull);
-                P.out_rb[r] = P.out_re[r] = 0;
-            }
+        const long long base = arena_take(arena, (unsigned long long)((total + 3) & ~3LL), P.ctl, lane);
+        if (base < 0) {
+            if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
             continue;
         }
-        const bool single = reuse && chunk_total <= kAccCap;
+        const bool single = reuse && total <= kAccCap;
         int written = 0;
         int c0 = lo;
         while (c0 <= hi) {
-            int cend = (int)min((long long)hi + 1, (long long)c0 + kBmBits);
-            if (!reuse) {
-                build_bitmap(P, add, nadd, r, c0, cend, pa0, pa1, false, lane, S);
-                chunk_total = scan_bitmap(lane, S);
-            }
+            int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
+            if (!reuse) build_map<TAB>(P, add, nadd, r, c0, cend, pa0, pa1, false, lane, S);
             reuse = false;
-            int c1 = cend, cnt = chunk_total;
-            if (chunk_total > kAccCap) {
-                c1 = cut_column(lane, S, c0);
-                cnt = kAccCap;
-            }
-            // slot -> column offset, zero the accumulators
-            for (int w = lane; w < kBmWords; w += 32) {
-                unsigned bits = S.pm[w].y;
-                int idx = (int)S.pm[w].x;
-                while (bits) {
-                    int b = __ffs(bits) - 1;
-                    int off = w * 32 + b;
-                    if (c0 + off < c1) S.colbuf[idx] = (unsigned short)off;
-                    ++idx;
-                    bits &= bits - 1u;
-                }
-            }
+            int cut;
+            const int cnt = assign_slots(cend - c0, lane, S, &cut);
+            const int c1 = c0 + cut;
             for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
             __syncwarp();
 
@@ -348,7 +487,7 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
                 const double alpha = T.alpha;
                 if (!T.rb) {
                     if (lane == 0 && r >= c0 && r < c1) {
-                        int i = slot_of(S, r - c0);
+                        int i = slot_lookup(S, r - c0);
                         S.acc[i] = __fma_rn(alpha, 1.0, S.acc[i]);
                     }
                 } else {
@@ -356,7 +495,7 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
                     for (int q = s + lane; q < e; q += 32) {
                         int c = T.col[q];
                         if (c >= c0 && c < c1) {
-                            int i = slot_of(S, c - c0);
+                            int i = slot_lookup(S, c - c0);
                             S.acc[i] = __fma_rn(alpha, T.val[q], S.acc[i]);
                         }
                     }
@@ -367,7 +506,7 @@ __global__ void __launch_bounds__(kProdWarps * 32) k_product(ProductArgs P) {
             // ---- product A B: k of row r ascending
             for (int seg = pa0; seg < pa1; seg += 32) {
                 const int cnt_seg = min(32, pa1 - seg);
-                load_segment(P, seg, cnt_seg, single, c0, c1, lane, S);
+                load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S);
                 accumulate_segment(P, cnt_seg, c0, lane, S);
             }
 
@@ -889,6 +1028,17 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     double eps_f = A.eps_g, c = 0.0;
     int it = 0;
     bool alive = true;
+    if (__ldcg(&A.stat->ncand) == 0ull) {
+        // the product left no entry with |x| <= eps_g: the first pass finds an
+        // empty candidate matrix (c = 0), nothing is dropped
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            A.stat->eps_f = eps_f;
+            A.stat->iters = 1;
+            A.stat->dropped = 0.0;
+            A.stat->nnz_post = A.stat->nnz_pre;
+        }
+        return;
+    }
     for (;;) {
         // finalize: round each column sum, clear the accumulator, max
         unsigned long long local = 0ull;
@@ -1113,17 +1263,12 @@ __global__ void k_copy_rows(int n, const int* rowptr, const int* col, const doub
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    Arena arena;
     for (int r = gw; r < n; r += nwarps) {
         int s = rowptr[r], e = rowptr[r + 1];
-        unsigned long long need = (unsigned long long)((e - s + 3) & ~3);
-        unsigned long long base = 0ull;
-        if (lane == 0) base = atomicAdd(&ctl->pool_used, need);
-        base = __shfl_sync(kFull, base, 0);
-        if (base + need > ctl->pool_cap) {
-            if (lane == 0) {
-                atomicOr(&ctl->status, kDevPoolFull);
-                rb[r] = re[r] = 0;
-            }
+        const long long base = arena_take(arena, (unsigned long long)((e - s + 3) & ~3), ctl, lane);
+        if (base < 0) {
+            if (lane == 0) rb[r] = re[r] = 0;
             continue;
         }
         for (int q = lane; q < e - s; q += 32) {
@@ -1215,8 +1360,11 @@ cudaError_t kernels_init() {
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_product, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)product_smem_bytes());
+    err = cudaFuncSetAttribute(k_product<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)prod_smem_bytes<true>());
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_product<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)prod_smem_bytes<false>());
     if (err != cudaSuccess) return err;
     if ((err = win_init<32>()) != cudaSuccess) return err;
     if ((err = win_init<64>()) != cudaSuccess) return err;
@@ -1235,13 +1383,22 @@ cudaError_t kernels_init() {
 
 int num_sms() { return g_sms; }
 
-cudaError_t launch_product(const ProductArgs& P, cudaStream_t st) {
-    if (P.n <= 0) return cudaSuccess;
-    int blocks = (P.n + kProdWarps - 1) / kProdWarps;
-    if (blocks > g_sms * 6 * 4) blocks = g_sms * 6 * 4;
-    k_product<<<blocks, kProdWarps * 32, product_smem_bytes(), st>>>(P);
+template <bool TAB>
+static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
+    constexpr int kWarps = ProdSmem<TAB>::kWarps;
+    // one wave of resident blocks, rows strided over the warps (each warp
+    // keeps one pool arena)
+    long long blocks = ((long long)P.n + kWarps - 1) / kWarps;
+    const long long cap = (long long)g_sms * (TAB ? 7 : 6);
+    if (blocks > cap) blocks = cap;
+    k_product<TAB><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
     ++g_launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st) {
+    if (P.n <= 0) return cudaSuccess;
+    return table ? prod_launch<true>(P, st) : prod_launch<false>(P, st);
 }
 
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {
@@ -1305,7 +1462,7 @@ cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const dou
                              int* pool_col, double* pool_val, Ctl* ctl, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int blocks = (n + 7) / 8;
-    if (blocks > g_sms * 16) blocks = g_sms * 16;
+    if (blocks > g_sms * 4) blocks = g_sms * 4;
     k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl);
     ++g_launches;
     return cudaGetLastError();

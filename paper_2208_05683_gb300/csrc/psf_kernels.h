@@ -13,7 +13,7 @@ long long launch_count();
 size_t product_smem_bytes();
 int product_warps_per_block();
 
-cudaError_t launch_product(const ProductArgs& P, cudaStream_t st);
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st);
 cudaError_t launch_product_win(const ProductArgs& P, int group, int cap_limit, cudaStream_t st);
 int product_win_cap(int group);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
