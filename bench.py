@@ -361,8 +361,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None, help="run one evaluation of this workload and exit")
     ap.add_argument("--kind", default="exp")
-    ap.add_argument("--kernel", choices=["auto", "window", "bitmap"], default="auto",
-                    help="product kernel (auto = compact bitmap kernel)")
+    ap.add_argument("--kernel", choices=["auto", "table", "bitmap"], default="auto",
+                    help="slot map of the product kernel (auto: by products per row)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

@@ -23,7 +23,8 @@ from dataclasses import dataclass, field
 
 from . import _build
 from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_SUBMULT, PSF_PARAM_ALG1_MAXIT,
-                   PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_WINDOW_CAP, PSF_MAX_Q,
+                   PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS,
+                   PSF_PARAM_CHUNK_SLOTS, PSF_MAX_Q,
                    PsfError, CSRStruct, InfoStruct, StepStruct, lib, check)
 
 __all__ = [
@@ -123,14 +124,14 @@ class Series:
     filtered False gives the unfiltered PS scheme (same N, q, b)
     submult  z_i = ||Z||^i instead of exact ||Z^i||_1 for i <= 10
     s        override of the PS block size q (0 = Eq. 6)
-    kernel   product kernel: "auto", "window" (dense column window) or "bitmap"
-    window_cap  column-window limit of the window kernel (0 = largest that fits)
+    kernel   slot map of the product kernel: "auto", "table" or "bitmap"
+    chunk_cols, chunk_slots  > 0: smaller row chunks (to exercise row chunking)
     """
 
     def __init__(self, coeffs, tol: float, *, poly: bool = False, filtered: bool = True,
                  submult: bool = False, s: int = 0, e_r: float | None = None,
                  maxit: int | None = None, pool_entries: int | None = None,
-                 kernel: str = "auto", window_cap: int = 0):
+                 kernel: str = "auto", chunk_cols: int = 0, chunk_slots: int = 0):
         L = lib()
         a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
         flags = (PSF_POLY if poly else PSF_SERIES) | (0 if filtered else PSF_NOFILTER) | \
@@ -147,11 +148,13 @@ class Series:
             check(L.psf_series_set_param(h, PSF_PARAM_ALG1_MAXIT, float(maxit)))
         if pool_entries is not None:
             check(L.psf_series_set_param(h, PSF_PARAM_POOL_ENTRIES, float(pool_entries)))
-        kid = {"auto": 0, "window": 1, "bitmap": 2}[kernel]
+        kid = {"auto": 0, "table": 1, "bitmap": 2}[kernel]
         if kid:
             check(L.psf_series_set_param(h, PSF_PARAM_KERNEL, float(kid)))
-        if window_cap:
-            check(L.psf_series_set_param(h, PSF_PARAM_WINDOW_CAP, float(window_cap)))
+        if chunk_cols:
+            check(L.psf_series_set_param(h, PSF_PARAM_CHUNK_COLS, float(chunk_cols)))
+        if chunk_slots:
+            check(L.psf_series_set_param(h, PSF_PARAM_CHUNK_SLOTS, float(chunk_slots)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

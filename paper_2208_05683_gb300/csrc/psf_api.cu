@@ -58,8 +58,9 @@ struct psf_series_s {
     // B-operand mean row lengths seen by the previous evaluation, per step:
     // they pick the thread-group size of the product kernel (tuning only)
     std::vector<double> len_z, len_baby, len_giant;
-    int kernel = 0;      // PSF_PARAM_KERNEL
-    int window_cap = 0;  // PSF_PARAM_WINDOW_CAP
+    int kernel = 0;       // PSF_PARAM_KERNEL
+    int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
+    int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS
 };
 
 struct psf_result_s {
@@ -150,8 +151,8 @@ struct Work {
     DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val;
     unsigned long long cap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
-    bool bitmap_kernel = false;  // rows too wide for the window kernel: use the bitmap kernel
-    int window_cap = 0;          // > 0: limit of the window kernel's column window
+    int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
+    int chunk_cols = 0, chunk_slots = 0;
 
     ~Work() {
         for (DevBuf* b : rows) delete b;
@@ -185,6 +186,14 @@ struct Work {
         CU(cudaMemcpyAsync(ctl.p, &h, offsetof(Ctl, bar_count), cudaMemcpyHostToDevice, st));
         return PSF_OK;
     }
+    // Column-sum accumulators are zero between steps; a phase cut short by a
+    // pool overflow can leave some set, so they are cleared before its retry.
+    int clear_sums() {
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
+        return PSF_OK;
+    }
     // row arrays of matrix slot i
     int rows_for(size_t i, int** rb, int** re) {
         while (rows.size() <= i) rows.push_back(new DevBuf());
@@ -211,9 +220,13 @@ int read_back(Work& w, Ctl& c, NormSlot* slots) {
     return PSF_OK;
 }
 
+// A phase whose pool overflowed is discarded and run again with a larger
+// pool, so only the bits that hold whatever the pool size are reported then.
 int status_to_code(int st) {
     if (st & kDevBadInput) return fail(PSF_EINVAL, "malformed CSR input (row pointers, column order or range, or non-finite value)");
     if (st & kDevTimeout) return fail(PSF_ETIMEOUT, "a bounded device wait expired");
+    if (st & kDevPoolFull) return PSF_OK;
+    if (st & kDevInternal) return fail(PSF_ECUDA, "internal error: a pool entry held a column outside the matrix");
     if (st & kDevNotConv) return fail(PSF_ENOTCONV, "Algorithm 1 reached its pass cap");
     return PSF_OK;
 }
@@ -230,12 +243,13 @@ int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms, int* ma
     return status_to_code(c.status);
 }
 
-// Thread-group size of the window product kernel for a mean B-row length.
-int group_for(double blen) {
-    if (blen >= 192.0) return 256;
-    if (blen >= 96.0) return 128;
-    if (blen >= 48.0) return 64;
-    return 32;
+
+// Pool entries a warp takes at a time: about eight rows of the expected size.
+unsigned long long arena_for(double row_len) {
+    double a = 8.0 * row_len;
+    if (a < 32.0) a = 32.0;
+    if (a > 512.0) a = 512.0;
+    return ((unsigned long long)a + 3ull) & ~3ull;
 }
 
 // Launch one product step into matrix slot `slot`, with Algorithm 1 when
@@ -269,18 +283,20 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     P.sticky = w.sticky.as<unsigned>();
     P.stat = stat_index >= 0 ? w.stats.as<StepStat>() + stat_index : nullptr;
     P.absmax_slot = absmax_slot;
+    P.chunk_cols = w.chunk_cols;
+    P.chunk_slots = w.chunk_slots;
+    P.arena = arena_for(alen > 0.0 ? alen * (blen > 1.0 ? blen : 1.0) : 8.0 * (add.size() + 1));
+    if (P.stat) CU(cudaMemcpyAsync(&P.stat->pool_start, &w.C()->pool_used, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToDevice, w.st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (g_prof.on) {
         CU(cudaEventCreate(&e0));
         CU(cudaEventCreate(&e1));
         CU(cudaEventRecord(e0, w.st));
     }
-    if (w.bitmap_kernel) {
-        // table map when a row folds many products per window column
-        CU(launch_product(P, alen * blen >= 2048.0, w.st));
-    } else {
-        CU(launch_product_win(P, group_for(blen), w.window_cap, w.st));
-    }
+    // table map when a row folds many products per window column
+    const bool table = w.slot_map == 1 || (w.slot_map == 0 && alen * blen >= 2048.0);
+    CU(launch_product(P, table, w.st));
     if (g_prof.on) {
         CU(cudaEventRecord(e1, w.st));
         g_prof.ev.emplace_back(e0, e1);
@@ -312,12 +328,20 @@ int pool_copy(Work& w, const psf_csr_t& m, size_t slot, RowView* out) {
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
     if (rc) return rc;
-    CU(launch_copy_rows(m.n, m.rowptr, m.col, m.val, rb, re, w.pcol(), w.pval(), w.C(), w.st));
+    CU(launch_copy_rows(m.n, m.rowptr, m.col, m.val, rb, re, w.pcol(), w.pval(), w.C(),
+                        arena_for(m.n > 0 ? (double)m.nnz / m.n : 1.0), w.st));
     *out = w.pooled(rb, re);
     return PSF_OK;
 }
 
 constexpr size_t kSlotZp = 60;  // row slot of the pooled copy of Z
+
+// ctl->mark[i] <- the pool counter, in stream order
+int mark_pool(Work& w, int i) {
+    CU(cudaMemcpyAsync(&w.C()->mark[i], &w.C()->pool_used, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                       w.st));
+    return PSF_OK;
+}
 
 int make_result(Work& w, const RowView& M, psf_result_t* out, psf_result_s** made) {
     psf_result_s* r = new (std::nothrow) psf_result_s();
@@ -422,9 +446,13 @@ int psf_series_set_param(psf_series_t series, int32_t key, double value) {
             if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(PSF_EINVAL, "kernel must be 0, 1 or 2");
             series->kernel = (int)value;
             return PSF_OK;
-        case PSF_PARAM_WINDOW_CAP:
-            if (!(value >= 0.0) || value > 1e9) return fail(PSF_EINVAL, "window cap out of range");
-            series->window_cap = (int)value;
+        case PSF_PARAM_CHUNK_COLS:
+            if (!(value >= 0.0) || value > 1e9) return fail(PSF_EINVAL, "chunk columns out of range");
+            series->chunk_cols = value > 0.0 && value < 32.0 ? 32 : (int)value;
+            return PSF_OK;
+        case PSF_PARAM_CHUNK_SLOTS:
+            if (!(value >= 0.0) || value > 1e9) return fail(PSF_EINVAL, "chunk slots out of range");
+            series->chunk_slots = (int)value;
             return PSF_OK;
         case PSF_PARAM_POOL_ENTRIES:
             if (!(value >= 0.0) || value > (double)INT32_MAX) return fail(PSF_EINVAL, "pool entries out of range");
@@ -479,13 +507,16 @@ int psf_norm1(const psf_csr_t* M, void* stream, double* out) {
     Work w;
     if ((rc = w.init(M->n, st, 1))) return rc;
     if ((rc = validate_inputs(w, {M}))) return rc;
-    RowView v = view_of(*M);
+    if ((rc = w.reset_pool((unsigned long long)M->nnz + 4ull * M->n + 2048ull * num_sms() * 8))) return rc;
+    RowView v;
+    if ((rc = mark_pool(w, 0)) || (rc = pool_copy(w, *M, 0, &v)) || (rc = mark_pool(w, 1))) return rc;
     NormSlot* slots = w.slots.as<NormSlot>();
-    CU(launch_absmax(M->n, v, slots + 0, st));
+    CU(launch_absmax(w.pval(), w.C(), 0, slots + 0, st));
     NormArgs na{};
     na.n = M->n;
     na.count = 1;
-    na.m[0] = v;
+    na.pool_col = w.pcol();
+    na.pool_val = w.pval();
     na.slots = slots;
     na.words = w.words.as<unsigned long long>();
     na.sticky = w.sticky.as<unsigned>();
@@ -531,7 +562,6 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     if ((rc = validate_inputs(w, {A, B}, &maxwin))) return rc;
     for (int t = 0; t < nadd; ++t)
         if (addends[t] && (rc = validate_inputs(w, {addends[t]}, &maxwin))) return rc;
-    w.bitmap_kernel = true;
     (void)maxwin;
     const double blen = B && n > 0 ? (double)B->nnz / n : 0.0;
     unsigned long long est = (unsigned long long)n * 8ull + 16;
@@ -571,6 +601,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
         if ((rc = read_back(w, c, nullptr))) return rc;
         if ((rc = status_to_code(c.status))) return rc;
         if (c.status & kDevPoolFull) {
+            if ((rc = w.clear_sums())) return rc;
             if (attempt > 8) return fail(PSF_ENOMEM, "pool kept overflowing");
             unsigned long long need = c.pool_used + c.pool_used / 4 + 1024;
             cap = need > 2 * cap ? need : 2 * cap;
@@ -630,8 +661,9 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     if ((rc = w.init(n, st, 16))) return rc;
     int zwin = 0;
     if ((rc = validate_inputs(w, {Z}, &zwin))) return rc;
-    w.bitmap_kernel = series->kernel != 1;  // compact kernel unless the window kernel is asked for
-    w.window_cap = series->window_cap;
+    w.slot_map = series->kernel;
+    w.chunk_cols = series->chunk_cols;
+    w.chunk_slots = series->chunk_slots;
     const RowView vz = view_of(*Z);
     const double zlen = n > 0 ? (double)Z->nnz / n : 0.0;
     double znnz[kMaxNorms] = {0.0};  // nnz(Z^i) of this evaluation
@@ -650,39 +682,46 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
         if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
             CU(cudaMemsetAsync(slots, 0, sizeof(NormSlot) * kMaxNorms, st));
+            // matrices of the norm kernel: the pooled Z, then Z^2 .. Z^10, each
+            // delimited in the pool by counter snapshots
             NormArgs na{};
             na.n = n;
             na.slots = slots + 1;
             na.words = w.words.as<unsigned long long>();
             na.sticky = w.sticky.as<unsigned>();
             na.ctl = w.C();
-            na.m[0] = vz;
             na.count = 1;
-            if (n > 0) CU(launch_absmax(n, vz, slots + 1, st));
-            if (!submult && n > 0) {
+            if (n > 0) {
                 if ((rc = w.reset_pool(zcap))) return rc;
+                na.pool_col = w.pcol();
+                na.pool_val = w.pval();
                 CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * 16, st));
                 RowView zp;
-                if ((rc = pool_copy(w, *Z, kSlotZp, &zp))) return rc;
-                RowView prev = zp;
-                for (int i = 2; i <= 10; ++i) {
-                    RowView cur;
-                    double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
-                                                                          : zlen * (i - 1) * (i - 1);
-                    if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, i - 2, (size_t)(i - 2), &cur, slots + i,
-                                       blen, zlen)))
-                        return rc;
-                    na.m[i - 1] = cur;
-                    prev = cur;
+                if ((rc = mark_pool(w, 0)) || (rc = pool_copy(w, *Z, kSlotZp, &zp)) || (rc = mark_pool(w, 1)))
+                    return rc;
+                CU(launch_absmax(w.pval(), w.C(), 0, slots + 1, st));
+                if (!submult) {
+                    RowView prev = zp;
+                    for (int i = 2; i <= 10; ++i) {
+                        RowView cur;
+                        double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
+                                                                              : zlen * (i - 1) * (i - 1);
+                        if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, i - 2, (size_t)(i - 2), &cur,
+                                           slots + i, blen, zlen)))
+                            return rc;
+                        if ((rc = mark_pool(w, i))) return rc;
+                        prev = cur;
+                    }
+                    na.count = 10;
                 }
-                na.count = 10;
+                CU(launch_norms(na, st));
             }
-            if (n > 0) CU(launch_norms(na, st));
             Ctl c;
             NormSlot hs[kMaxNorms];
             if ((rc = read_back(w, c, hs))) return rc;
             if ((rc = status_to_code(c.status))) return rc;
             if (c.status & kDevPoolFull) {
+                if ((rc = w.clear_sums())) return rc;
                 if (attempt > 8 || zcap >= (unsigned long long)INT32_MAX)
                     return fail(PSF_ETOOBIG, "the powers Z^2..Z^10 need more than 2^31 entries; use PSF_Z_SUBMULT");
                 unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;
@@ -858,6 +897,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             if (c.status & kDevPoolFull) {
                 destroy_result(r);
                 r = nullptr;
+                if ((rc = w.clear_sums())) return rc;
                 if (attempt > 8 || cap >= (unsigned long long)INT32_MAX)
                     return fail(PSF_ETOOBIG, "evaluation needs more than 2^31 pool entries");
                 unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;

@@ -21,6 +21,7 @@ enum : int {
     kDevPoolFull = 2,
     kDevNotConv = 4,
     kDevTimeout = 8,
+    kDevInternal = 16,  // a pool entry held a column outside [0, n) (skipped)
 };
 
 // Control block of one evaluation, in device memory.
@@ -35,10 +36,12 @@ struct Ctl {
     unsigned bar_gen;
     int pad;
     unsigned long long fma_total;  // algorithmic multiply-adds of all products
+    unsigned long long mark[kMaxNorms + 1];  // pool counter snapshots delimiting the norm matrices
 };
 
 // Device half of psf_step_info_t.
 struct StepStat {
+    unsigned long long pool_start;  // pool counter before the step's product
     unsigned long long nnz_pre, nnz_post, ncand, fma;
     double eps_f, dropped;
     int iters, pad;
@@ -86,6 +89,9 @@ struct ProductArgs {
     unsigned* sticky;           // n
     StepStat* stat;
     NormSlot* absmax_slot;      // optional: record max |x|
+    int chunk_cols;             // > 0: fewer columns per chunk (exercises chunking)
+    int chunk_slots;            // > 0: fewer accumulator slots per chunk
+    unsigned long long arena;   // pool entries a warp takes at a time (multiple of 4)
 };
 
 struct Alg1Args {
@@ -102,10 +108,13 @@ struct Alg1Args {
     StepStat* stat;
 };
 
+// Matrix i of the norm kernel occupies the pool entries [mark[i], mark[i+1])
+// (gaps read as exact zeros).
 struct NormArgs {
     int n;
     int count;  // matrices
-    RowView m[kMaxNorms];
+    const int* pool_col;
+    const double* pool_val;
     NormSlot* slots;            // count
     unsigned long long* words;  // count * kChunks * n
     unsigned* sticky;           // count * n
@@ -256,26 +265,33 @@ __device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stri
     return ldexp((double)M, shift + e_lsb);
 }
 
-// Per-warp sub-allocator of the entry pool: a warp takes kArena entries (or
+// Per-warp sub-allocator of the entry pool: a warp takes `size` entries (or
 // the request, if larger) from the shared counter with one atomic and carves
 // its rows out of them, so rows cost no contended atomic.  Every request and
 // arena is a multiple of 4 entries (rows start 16-byte aligned).  Returns
-// the row's first entry, or -1 when the pool is full (recorded in status).
-constexpr unsigned long long kArena = 512;
-
+// the row's first entry, or -1 when the pool is full (recorded in status);
+// the counter then keeps counting past the capacity.  The flat scans over a
+// step's pool range read every entry of it, so the unused tail of an arena
+// is cleared to exact zeros when the warp moves on (arena_close at the end).
 struct Arena {
     unsigned long long next = 0, end = 0;
 };
 
-__device__ __forceinline__ long long arena_take(Arena& a, unsigned long long need, Ctl* ctl, int lane) {
+__device__ __forceinline__ void arena_close(Arena& a, double* pool_val, int lane) {
+    for (unsigned long long q = a.next + lane; q < a.end; q += 32) pool_val[q] = 0.0;
+    a.next = a.end = 0;
+}
+
+__device__ __forceinline__ long long arena_take(Arena& a, unsigned long long need, unsigned long long size, Ctl* ctl,
+                                                double* pool_val, int lane) {
     if (a.next + need > a.end) {
-        const unsigned long long chunk = need > kArena ? need : kArena;
+        arena_close(a, pool_val, lane);
+        const unsigned long long chunk = need > size ? need : size;
         unsigned long long b = 0ull;
         if (lane == 0) b = atomicAdd(&ctl->pool_used, chunk);
         b = __shfl_sync(kFull, b, 0);
         if (b + chunk > ctl->pool_cap) {
             if (lane == 0) atomicOr(&ctl->status, kDevPoolFull);
-            a.next = a.end = 0;
             return -1;
         }
         a.next = b;
@@ -284,6 +300,18 @@ __device__ __forceinline__ long long arena_take(Arena& a, unsigned long long nee
     const unsigned long long r = a.next;
     a.next += need;
     return (long long)r;
+}
+
+// Column sums of a flat scan: an entry whose column lies outside [0, n)
+// cannot come from a correct pool; it is skipped and flagged, never used as
+// an index.
+__device__ __forceinline__ void exact_add_checked(unsigned long long* words, unsigned* sticky, int col, int n,
+                                                  unsigned long long vbits, int e_lsb, Ctl* ctl) {
+    if ((unsigned)col < (unsigned)n) {
+        exact_add(words + col, (size_t)n, sticky + col, vbits, e_lsb);
+    } else {
+        atomicOr(&ctl->status, kDevInternal);
+    }
 }
 
 // Grid-wide barrier for cooperative launches, with a bounded wait: after

@@ -1,15 +1,16 @@
 // psf_kernels.cu -- CUDA kernels of the filtered Paterson-Stockmeyer
 // evaluator (sm_103a, FP64 throughout).
 //
-//  k_product      one fused step C = sum_t alpha_t M_t + A B: column window,
-//                 bitmap of the output pattern, exact per-row reservation in
-//                 the pool, FP64 accumulation in shared memory, write-back of
-//                 the nonzero entries, and the first pass of Algorithm 1
-//                 (exact column sums of the entries |x| <= eps_g).
+//  k_product      one fused step C = sum_t alpha_t M_t + A B: output pattern
+//                 and slot map of each row, exact row reservation in the
+//                 pool, FP64 accumulation in shared memory, write-back of the
+//                 nonzero entries, and the first pass of Algorithm 1 (exact
+//                 column sums of the entries |x| <= eps_g).
 //  k_alg1         the remaining passes of Algorithm 1 (Sec. 3.1.1) and the
 //                 final in-place compaction, one cooperative launch.
 //  k_norms        exact 1-norms of up to 11 matrices (Eq. 37's z_i).
-//  k_absmax, k_validate, k_scan_rows, k_gather, k_identity: plumbing.
+//  k_absmax, k_validate, k_copy_rows, k_scan_rows, k_gather, k_identity:
+//                 plumbing.
 #include <atomic>
 #include <climits>
 
@@ -212,19 +213,19 @@ __device__ __forceinline__ int count_marks(int wlen, int lane, const ProdSmem<fa
 // Number the marked columns of [0, wlen) in ascending order and fill
 // colbuf.  Only the first kAccCap get a slot; returns their count and sets
 // *cut to the offset of the first column without one (wlen if all fit).
-__device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<true>& S, int* cut) {
+__device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSmem<true>& S, int* cut) {
     int run = 0, cutoff = wlen;
     for (int i0 = 0; i0 < wlen; i0 += 32) {
         const int i = i0 + lane;
         const bool f = i < wlen && S.tab[i] != 0;
         const unsigned m = __ballot_sync(kFull, f);
         const int slot = run + __popc(m & lanemask_lt());
-        if (f && slot < kAccCap) {
+        if (f && slot < cap) {
             S.tab[i] = (unsigned short)slot;
             S.colbuf[slot] = (unsigned short)i;
         }
-        if (run <= kAccCap && run + __popc(m) > kAccCap) {
-            const unsigned fo = __ballot_sync(kFull, f && slot == kAccCap);
+        if (run <= cap && run + __popc(m) > cap) {
+            const unsigned fo = __ballot_sync(kFull, f && slot == cap);
             cutoff = i0 + __ffs(fo) - 1;
         }
         run += __popc(m);
@@ -232,9 +233,9 @@ __device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<true>& 
     }
     __syncwarp();
     *cut = cutoff;
-    return min(run, kAccCap);
+    return min(run, cap);
 }
-__device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<false>& S, int* cut) {
+__device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSmem<false>& S, int* cut) {
     constexpr int per = kBmWords / 32;
     const int nw = (wlen + 31) >> 5;
     const int base = lane * per;
@@ -252,13 +253,13 @@ __device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<false>&
     }
     __syncwarp();
     int cutoff = wlen;
-    if (total > kAccCap) {
+    if (total > cap) {
         int found = INT_MAX;
         for (int w = lane; w < nw; w += 32) {
             const int pc = __popc(S.pm[w].y), pre = (int)S.pm[w].x;
-            if (pre <= kAccCap && kAccCap < pre + pc) {
+            if (pre <= cap && cap < pre + pc) {
                 unsigned bits = S.pm[w].y;
-                for (int i = 0; i < kAccCap - pre; ++i) bits &= bits - 1u;  // drop the lowest ones
+                for (int i = 0; i < cap - pre; ++i) bits &= bits - 1u;  // drop the lowest ones
                 found = w * 32 + (__ffs(bits) - 1);
             }
         }
@@ -276,7 +277,7 @@ __device__ __forceinline__ int assign_slots(int wlen, int lane, ProdSmem<false>&
     }
     __syncwarp();
     *cut = cutoff;
-    return min(total, kAccCap);
+    return min(total, cap);
 }
 
 // The 128 entries [off, off + 128) of B row kk of the segment, four 32-entry
@@ -389,7 +390,9 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
 template <bool TAB>
 __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_product(ProductArgs P) {
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
-    constexpr int kCols = ProdSmem<TAB>::kCols;
+    // columns and slots of one chunk (lowered only to exercise chunking)
+    const int kCols = P.chunk_cols > 0 && P.chunk_cols < ProdSmem<TAB>::kCols ? P.chunk_cols : ProdSmem<TAB>::kCols;
+    const int kSlots = P.chunk_slots > 0 && P.chunk_slots < kAccCap ? P.chunk_slots : kAccCap;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
     ProdSmem<TAB>* warps = reinterpret_cast<ProdSmem<TAB>*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
@@ -463,12 +466,12 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
                 total += count_marks(cend - (int)c0, lane, S);
             }
         }
-        const long long base = arena_take(arena, (unsigned long long)((total + 3) & ~3LL), P.ctl, lane);
+        const long long base = arena_take(arena, (unsigned long long)((total + 3) & ~3LL), P.arena, P.ctl, P.pool_val, lane);
         if (base < 0) {
             if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
             continue;
         }
-        const bool single = reuse && total <= kAccCap;
+        const bool single = reuse && total <= kSlots;
         int written = 0;
         int c0 = lo;
         while (c0 <= hi) {
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
             if (!reuse) build_map<TAB>(P, add, nadd, r, c0, cend, pa0, pa1, false, lane, S);
             reuse = false;
             int cut;
-            const int cnt = assign_slots(cend - c0, lane, S, &cut);
+            const int cnt = assign_slots(cend - c0, kSlots, lane, S, &cut);
             const int c1 = c0 + cut;
             for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
             __syncwarp();
@@ -538,12 +541,17 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
             __syncwarp();
             c0 = c1;
         }
+        // the row's unused reserved slots read as exact zeros (never candidates)
+        const long long rend = base + ((total + 3) & ~3LL);
+        for (long long q = base + written + lane; q < rend; q += 32) P.pool_val[q] = 0.0;
         if (lane == 0) {
             P.out_rb[r] = (int)base;
             P.out_re[r] = (int)(base + written);
             my_written += (unsigned long long)written;
         }
     }
+    // the unused end of this warp's arena reads as exact zeros too
+    arena_close(arena, P.pool_val, lane);
     // ---- block totals for the step statistics
     my_cand = (unsigned long long)warp_sum((int)my_cand);
     my_absmax = warp_max_u64(my_absmax);
@@ -563,447 +571,6 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
             if (blk_cand) atomicAdd(&P.stat->ncand, blk_cand);
         }
         if (P.absmax_slot && blk_absmax) atomicMax(&P.absmax_slot->absmax, blk_absmax);
-    }
-}
-
-// ---------------------------------------------------------------- k_product_win
-// Row-group kernel with a dense column-window accumulator.  A group of G
-// threads (G = 32..256, 256 / G groups per block) computes one output row at
-// a time: acc[c - c0] holds column c of the chunk [c0, c0 + cap) of the row's
-// column window, so no symbolic pass and no slot lookup is needed.
-//
-// The row is a sequence of items, each a coefficient and a row of a pooled
-// matrix: first the addends alpha_t M_t (t ascending; the identity is an item
-// without a row), then a_rk B_k for k of A's row ascending.  Every output
-// entry is folded as acc = fma(coef, m, acc) item after item, with a group
-// barrier between items: exactly the fixed rounding order of the product.
-//
-// Item rows reach shared memory by TMA bulk copies (cp.async.bulk) into a
-// kTmaStages-deep ring of stages; one thread of the group issues the copies
-// kTmaStages pieces ahead, completion is tracked by one mbarrier per stage,
-// and the group barrier after each piece releases its stage.  Pool rows start
-// at multiples of 4 entries and own a multiple of 4 slots, so every copy is
-// 16-byte aligned and sized.  A row whose window exceeds `cap` is processed in
-// several column chunks (its pool space is reserved up front from an upper
-// bound); other rows reserve their exact entry count after accumulation.
-constexpr int kWinThreads = 256;
-constexpr int kTmaStages = 4;
-constexpr unsigned long long kWaitBudgetNs = 2000000000ull;  // 2 s
-
-struct Item {
-    double a;  // coefficient
-    int b, e;  // row range [b, e) in the pool; b < 0 marks the identity
-};
-
-template <int G>
-struct WinCfg {
-    static constexpr int NG = kWinThreads / G;
-    static constexpr int NW = G / 32;
-    static constexpr int SENT = 4 * G;  // entries per stage
-};
-
-// per-group shared memory after acc[cap]
-template <int G>
-struct WinGroup {
-    int sc[kTmaStages][WinCfg<G>::SENT];
-    double sv[kTmaStages][WinCfg<G>::SENT];
-    unsigned long long bar[kTmaStages];
-    Item items[G];
-    long long red[WinCfg<G>::NW];
-    int misc[4];
-};
-
-template <int G>
-__host__ __device__ size_t win_group_bytes(int cap) {
-    return ((size_t)cap * sizeof(double) + sizeof(WinGroup<G>) + 127) & ~(size_t)127;
-}
-
-constexpr size_t kWinHeader = (sizeof(AddTerm) * kMaxAdd + 127) & ~(size_t)127;
-
-template <int G>
-__host__ __device__ size_t win_smem_bytes(int cap) {
-    return kWinHeader + win_group_bytes<G>(cap) * WinCfg<G>::NG;
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// wait for the phase of `bar` with the given parity; false after kWaitBudgetNs
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitBudgetNs) return false;
-    return true;
-}
-__device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-template <int G>
-__device__ __forceinline__ void group_sync(int g) {
-    if constexpr (G == 32) {
-        __syncwarp();
-    } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "n"(G) : "memory");
-    }
-}
-
-// group-wide reductions through the per-group scratch (all G threads call)
-template <int G, class T, class Op>
-__device__ __forceinline__ T group_reduce(T v, Op op, WinGroup<G>& S, int g, int gt) {
-    for (int o = 16; o; o >>= 1) v = op(v, (T)__shfl_xor_sync(kFull, v, o));
-    if constexpr (G == 32) {
-        return v;
-    } else {
-        group_sync<G>(g);
-        if ((gt & 31) == 0) S.red[gt >> 5] = (long long)v;
-        group_sync<G>(g);
-        T t = (T)S.red[0];
-#pragma unroll
-        for (int w = 1; w < WinCfg<G>::NW; ++w) t = op(t, (T)S.red[w]);
-        return t;
-    }
-}
-
-// Piece cursor over the items [0, cnt) of a segment: item i, offset `off`
-// (entries from the 4-aligned start of its range).  Identity items are one
-// piece without data.
-template <int G>
-__device__ __forceinline__ void piece_first(const WinGroup<G>& S, int cnt, int& i, int& off) {
-    i = 0;
-    off = 0;
-    while (i < cnt && S.items[i].b >= 0 && S.items[i].e <= S.items[i].b) ++i;
-}
-template <int G>
-__device__ __forceinline__ void piece_next(const WinGroup<G>& S, int cnt, int& i, int& off) {
-    const Item& it = S.items[i];
-    if (it.b >= 0) {
-        off += WinCfg<G>::SENT;
-        if ((it.b & ~3) + off < it.e) return;
-    }
-    off = 0;
-    do {
-        ++i;
-    } while (i < cnt && S.items[i].b >= 0 && S.items[i].e <= S.items[i].b);
-}
-
-// Issue the TMA copies of piece (i, off) into ring slot `slot` (one thread).
-template <int G>
-__device__ __forceinline__ void piece_issue(const int* col, const double* val, WinGroup<G>& S, int i, int off,
-                                            int slot) {
-    const Item& it = S.items[i];
-    const int ab = it.b & ~3;
-    const int p0 = ab + off;
-    const int p1 = min(it.e, p0 + WinCfg<G>::SENT);
-    const unsigned cnt4 = (unsigned)((p1 - p0 + 3) & ~3);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&S.bar[slot], cnt4 * (unsigned)(sizeof(int) + sizeof(double)));
-    tma_load(&S.sc[slot][0], col + p0, cnt4 * (unsigned)sizeof(int), &S.bar[slot]);
-    tma_load(&S.sv[slot][0], val + p0, cnt4 * (unsigned)sizeof(double), &S.bar[slot]);
-}
-
-template <int G>
-__global__ void __launch_bounds__(kWinThreads) k_product_win(ProductArgs P, int cap) {
-    constexpr int NG = WinCfg<G>::NG;
-    constexpr int NW = WinCfg<G>::NW;
-    constexpr int SENT = WinCfg<G>::SENT;
-    extern __shared__ __align__(16) unsigned char smem_win[];
-    const int g = threadIdx.x / G, gt = threadIdx.x % G, lane = threadIdx.x & 31, gw = gt >> 5;
-    AddTerm* add = reinterpret_cast<AddTerm*>(smem_win);
-    unsigned char* gbase = smem_win + kWinHeader + win_group_bytes<G>(cap) * g;
-    double* acc = reinterpret_cast<double*>(gbase);
-    WinGroup<G>& S = *reinterpret_cast<WinGroup<G>*>(gbase + (size_t)cap * sizeof(double));
-    const int nadd = P.nadd;
-    for (int t = threadIdx.x; t < nadd; t += blockDim.x) add[t] = P.add[t];
-    if (gt == 0) {
-        for (int s = 0; s < kTmaStages; ++s) mbar_init(&S.bar[s], 1);
-        S.misc[2] = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
-    unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
-    unsigned consumed = 0, issued = 0;  // pieces through the ring (group-uniform)
-    bool alive = true;
-    // every item row (B rows and addend rows) is a row of the pool
-    const int* pcol = P.pool_col;
-    const double* pval = P.pool_val;
-
-    for (int r = blockIdx.x * NG + g; r < P.n && alive; r += gridDim.x * NG) {
-        // ---- window [lo, hi] of row r and its multiply-add count
-        int lo = INT_MAX, hi = -1;
-        long long ub = 0;  // entry upper bound: products plus addend entries
-        for (int t = gt; t < nadd; t += G) {
-            const AddTerm& T = add[t];
-            if (!T.rb) {
-                lo = min(lo, r);
-                hi = max(hi, r);
-                ub += 1;
-            } else {
-                int s = T.rb[r], e = T.re[r];
-                ub += e - s;
-                if (s < e) {
-                    lo = min(lo, T.col[s]);
-                    hi = max(hi, T.col[e - 1]);
-                }
-            }
-        }
-        int pa0 = 0, pa1 = 0;
-        if (P.A.rb) {
-            pa0 = P.A.rb[r];
-            pa1 = P.A.re[r];
-        }
-        for (int p = pa0 + gt; p < pa1; p += G) {
-            int k = P.A.col[p];
-            int s = P.B.rb[k], e = P.B.re[k];
-            ub += e - s;
-            if (s < e) {
-                lo = min(lo, P.B.col[s]);
-                hi = max(hi, P.B.col[e - 1]);
-            }
-        }
-        lo = group_reduce<G, int>(lo, [](int x, int y) { return min(x, y); }, S, g, gt);
-        hi = group_reduce<G, int>(hi, [](int x, int y) { return max(x, y); }, S, g, gt);
-        ub = group_reduce<G, long long>(ub, [](long long x, long long y) { return x + y; }, S, g, gt);
-        if (gt == 0) my_fma += (unsigned long long)ub;
-        if (hi < lo) {
-            if (gt == 0) P.out_rb[r] = P.out_re[r] = 0;
-            group_sync<G>(g);
-            continue;
-        }
-        const long long W = (long long)hi - lo + 1;
-        const bool single = W <= cap;
-        long long base = 0;
-        bool ok = true;
-        if (!single) {
-            // reserve the upper bound min(W, products + addend entries) now
-            long long need = (min(W, ub) + 3) & ~3LL;
-            if (gt == 0) {
-                unsigned long long b = atomicAdd(&P.ctl->pool_used, (unsigned long long)need);
-                bool fits = b + (unsigned long long)need <= P.ctl->pool_cap;
-                if (!fits) atomicOr(&P.ctl->status, kDevPoolFull);
-                S.misc[0] = fits ? 1 : 0;
-                S.misc[1] = (int)(b & 0x7fffffff);
-            }
-            group_sync<G>(g);
-            ok = S.misc[0] != 0;
-            base = S.misc[1];
-            group_sync<G>(g);
-        }
-        long long written = 0;
-        const int ntot = nadd + (pa1 - pa0);
-        for (long long c0l = lo; c0l <= hi && ok && alive; c0l += cap) {
-            const int c0 = (int)c0l;
-            const int wlen = (int)min((long long)cap, (long long)hi - c0 + 1);
-            const int c1 = c0 + wlen;
-            for (int i = gt; i < wlen; i += G) acc[i] = 0.0;
-            for (int seg = 0; seg < ntot && alive; seg += G) {
-                // ---- items of this segment: addends first, then A's row
-                const int cnt = min(G, ntot - seg);
-                group_sync<G>(g);  // previous segment's items fully consumed
-                if (gt < cnt) {
-                    int idx = seg + gt;
-                    Item it;
-                    int b, e;
-                    if (idx < nadd) {
-                        const AddTerm& T = add[idx];
-                        it.a = T.alpha;
-                        if (!T.rb) {
-                            b = -1;
-                            e = 0;
-                        } else {
-                            b = T.rb[r];
-                            e = T.re[r];
-                        }
-                    } else {
-                        int p = pa0 + idx - nadd;
-                        int k = P.A.col[p];
-                        it.a = P.A.val[p];
-                        b = P.B.rb[k];
-                        e = P.B.re[k];
-                    }
-                    if (b >= 0 && !single) {
-                        int b2 = lower_bound_col(pcol, b, e, c0);
-                        e = lower_bound_col(pcol, b2, e, c1);
-                        b = b2;
-                    }
-                    it.b = b;
-                    it.e = e;
-                    S.items[gt] = it;
-                }
-                group_sync<G>(g);
-                // ---- pieces through the TMA ring
-                int ci, coff, ii, ioff;
-                piece_first<G>(S, cnt, ci, coff);
-                ii = ci;
-                ioff = coff;
-                // prologue: fill the ring up to kTmaStages pieces ahead
-                while (ii < cnt && issued - consumed < (unsigned)kTmaStages) {
-                    if (S.items[ii].b >= 0) {
-                        if (gt == 0) piece_issue<G>(pcol, pval, S, ii, ioff, (int)(issued % kTmaStages));
-                        ++issued;
-                    }
-                    piece_next<G>(S, cnt, ii, ioff);
-                }
-                while (ci < cnt) {
-                    const Item it = S.items[ci];
-                    if (it.b < 0) {
-                        // identity item: acc[r] = fma(alpha, 1, acc[r])
-                        if (gt == 0 && r >= c0 && r < c1) acc[r - c0] = __fma_rn(it.a, 1.0, acc[r - c0]);
-                    } else {
-                        const int slot = (int)(consumed % kTmaStages);
-                        const bool got = mbar_wait(&S.bar[slot], (consumed / kTmaStages) & 1u);
-                        if (!got) {
-                            atomicOr(&P.ctl->status, kDevTimeout);
-                            S.misc[2] = 1;
-                        }
-                        const int ab = it.b & ~3;
-                        const int p0 = ab + coff;
-                        const int lo_i = max(it.b, p0) - p0, hi_i = min(it.e, p0 + SENT) - p0;
-                        for (int i = lo_i + gt; i < hi_i; i += G) {
-                            int c = S.sc[slot][i];
-                            double v = S.sv[slot][i];
-                            acc[c - c0] = __fma_rn(it.a, v, acc[c - c0]);
-                        }
-                        ++consumed;
-                    }
-                    piece_next<G>(S, cnt, ci, coff);
-                    group_sync<G>(g);  // item done: order of the fma chain, stage released
-                    if (S.misc[2]) {
-                        alive = false;
-                        break;
-                    }
-                    while (ii < cnt && issued - consumed < (unsigned)kTmaStages) {
-                        if (S.items[ii].b >= 0) {
-                            if (gt == 0) piece_issue<G>(pcol, pval, S, ii, ioff, (int)(issued % kTmaStages));
-                            ++issued;
-                        }
-                        piece_next<G>(S, cnt, ii, ioff);
-                    }
-                }
-            }
-            if (!alive) break;
-            group_sync<G>(g);
-            // ---- write-back: each warp sweeps a contiguous part of the window
-            const int part = ((wlen + NW * 32 - 1) / (NW * 32)) * 32;
-            const int q0 = gw * part, q1 = min(wlen, q0 + part);
-            int mycount = 0;
-            for (int i0 = q0; i0 < q1; i0 += 32) {
-                int i = i0 + lane;
-                bool nz = i < q1 && mag_bits(acc[i]) != 0ull;
-                mycount += __popc(__ballot_sync(kFull, nz));
-            }
-            int before = 0, total = mycount;
-            if constexpr (G > 32) {
-                if (lane == 0) S.red[gw] = mycount;
-                group_sync<G>(g);
-                total = 0;
-                for (int w = 0; w < NW; ++w) {
-                    int cw = (int)S.red[w];
-                    if (w < gw) before += cw;
-                    total += cw;
-                }
-                group_sync<G>(g);
-            }
-            if (single) {
-                if (gt == 0) {
-                    unsigned long long need = (unsigned long long)((total + 3) & ~3);
-                    unsigned long long b = atomicAdd(&P.ctl->pool_used, need);
-                    bool fits = b + need <= P.ctl->pool_cap;
-                    if (!fits) atomicOr(&P.ctl->status, kDevPoolFull);
-                    S.misc[0] = fits ? 1 : 0;
-                    S.misc[1] = (int)(b & 0x7fffffff);
-                }
-                group_sync<G>(g);
-                ok = S.misc[0] != 0;
-                base = S.misc[1];
-                group_sync<G>(g);
-                if (!ok) break;
-            }
-            long long pos0 = base + written + before;
-            for (int i0 = q0; i0 < q1; i0 += 32) {
-                int i = i0 + lane;
-                double x = i < q1 ? acc[i] : 0.0;
-                unsigned long long xb = mag_bits(x);
-                bool nz = i < q1 && xb != 0ull;
-                unsigned m = __ballot_sync(kFull, nz);
-                if (nz) {
-                    long long pos = pos0 + __popc(m & lanemask_lt());
-                    int c = c0 + i;
-                    P.pool_col[pos] = c;
-                    P.pool_val[pos] = x;
-                    my_absmax = xb > my_absmax ? xb : my_absmax;
-                    if (P.filtering && xb <= eps_bits) {
-                        exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, P.e_lsb);
-                        ++my_cand;
-                    }
-                }
-                pos0 += __popc(m);
-            }
-            written += total;
-        }
-        if (gt == 0) {
-            if (ok && alive) {
-                P.out_rb[r] = (int)base;
-                P.out_re[r] = (int)(base + written);
-                my_written += (unsigned long long)written;
-            } else {
-                P.out_rb[r] = P.out_re[r] = 0;
-            }
-        }
-        group_sync<G>(g);
-    }
-    if (!alive && gt == 0) {
-        // bounded drain of the copies still in flight before the block exits
-        while (consumed < issued) {
-            mbar_wait(&S.bar[consumed % kTmaStages], (consumed / kTmaStages) & 1u);
-            ++consumed;
-        }
-    }
-    // ---- block totals for the step statistics
-    __shared__ unsigned long long blk[4];
-    if (threadIdx.x < 4) blk[threadIdx.x] = 0ull;
-    __syncthreads();
-    my_cand = (unsigned long long)warp_sum((int)my_cand);
-    my_absmax = warp_max_u64(my_absmax);
-    for (int o = 16; o; o >>= 1) {
-        my_fma += __shfl_xor_sync(kFull, my_fma, o);
-        my_written += __shfl_xor_sync(kFull, my_written, o);
-    }
-    if (lane == 0) {
-        if (my_fma) atomicAdd(&blk[0], my_fma);
-        if (my_written) atomicAdd(&blk[1], my_written);
-        if (my_cand) atomicAdd(&blk[2], my_cand);
-        if (my_absmax) atomicMax(&blk[3], my_absmax);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (blk[0]) atomicAdd(&P.ctl->fma_total, blk[0]);
-        if (P.stat) {
-            if (blk[0]) atomicAdd(&P.stat->fma, blk[0]);
-            if (blk[1]) atomicAdd(&P.stat->nnz_pre, blk[1]);
-            if (blk[2]) atomicAdd(&P.stat->ncand, blk[2]);
-        }
-        if (P.absmax_slot && blk[3]) atomicMax(&P.absmax_slot->absmax, blk[3]);
     }
 }
 
@@ -1028,6 +595,13 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     double eps_f = A.eps_g, c = 0.0;
     int it = 0;
     bool alive = true;
+    // the step's pool range; the counter runs past the capacity on overflow
+    const unsigned long long p0 = min(__ldcg(&A.stat->pool_start), A.ctl->pool_cap);
+    const unsigned long long p1 = min(__ldcg(&A.ctl->pool_used), A.ctl->pool_cap);
+    // a phase whose pool overflowed is discarded: its pool range is not
+    // complete, so there is nothing to filter (every block reads the same
+    // status, set by an earlier launch)
+    if (__ldcg(&A.ctl->status) & kDevPoolFull) return;
     if (__ldcg(&A.stat->ncand) == 0ull) {
         // the product left no entry with |x| <= eps_g: the first pass finds an
         // empty candidate matrix (c = 0), nothing is dropped
@@ -1072,14 +646,20 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         }
         eps_f = A.eps_g / m;
         const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
-        // accumulate the entries still below the threshold
-        for (int r = gw; r < A.n; r += nwarps) {
-            int s = A.rb[r], e = A.re[r];
-            for (int q = s + lane; q < e; q += 32) {
-                unsigned long long xb = mag_bits(A.val[q]);
-                if (xb <= fb) {
-                    int col = A.col[q];
-                    exact_add(A.words + col, n, A.sticky + col, xb, A.e_lsb);
+        // accumulate the entries still below the threshold: one streaming
+        // pass over the step's pool range (its gaps hold exact zeros)
+        for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
+            unsigned long long xb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long q = q0 + (unsigned long long)u * nthreads;
+                xb[u] = q < p1 ? mag_bits(__ldcg(A.val + q)) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (xb[u] != 0ull && xb[u] <= fb) {
+                    const int col = A.col[q0 + (unsigned long long)u * nthreads];
+                    exact_add_checked(A.words, A.sticky, col, A.n, xb[u], A.e_lsb, A.ctl);
                 }
             }
         }
@@ -1116,6 +696,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
             w += __popc(m);
             __syncwarp();
         }
+        for (int q = w + lane; q < e; q += 32) A.val[q] = 0.0;  // dropped tail reads as zeros
         if (lane == 0) {
             A.re[r] = w;
             kept += (unsigned long long)(w - s);
@@ -1136,22 +717,36 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
 constexpr int kNormThreads = 256;
 
 __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
     const size_t n = (size_t)A.n;
-    for (long long u = gw; u < (long long)A.count * A.n; u += nwarps) {
-        int mi = (int)(u / A.n), r = (int)(u % A.n);
-        const RowView& M = A.m[mi];
-        int lsb = lsb_for_bound(A.slots[mi].absmax);
+    // a phase whose pool overflowed is discarded (all blocks read the same
+    // status, set by an earlier launch)
+    if (__ldcg(&A.ctl->status) & kDevPoolFull) return;
+    // every |x| of every matrix into per-column fixed-point sums: streaming
+    // passes over the matrices' pool ranges
+    for (int mi = 0; mi < A.count; ++mi) {
+        // the counter keeps counting past the capacity when the pool overflows
+        const unsigned long long cap = A.ctl->pool_cap;
+        const unsigned long long p0 = min(__ldcg(&A.ctl->mark[mi]), cap);
+        const unsigned long long p1 = min(__ldcg(&A.ctl->mark[mi + 1]), cap);
+        const int lsb = lsb_for_bound(A.slots[mi].absmax);
         unsigned long long* words = A.words + (size_t)mi * kChunks * n;
         unsigned* sticky = A.sticky + (size_t)mi * n;
-        int s = M.rb[r], e = M.re[r];
-        for (int q = s + lane; q < e; q += 32) {
-            int c = M.col[q];
-            exact_add(words + c, n, sticky + c, mag_bits(M.val[q]), lsb);
+        for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
+            unsigned long long xb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long q = q0 + (unsigned long long)u * nthreads;
+                xb[u] = q < p1 ? mag_bits(A.pool_val[q]) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (xb[u] != 0ull) {
+                    const int c = A.pool_col[q0 + (unsigned long long)u * nthreads];
+                    exact_add_checked(words, sticky, c, A.n, xb[u], lsb, A.ctl);
+                }
+            }
         }
     }
     if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
@@ -1166,16 +761,17 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
 }
 
 // ---------------------------------------------------------------- plumbing
-__global__ void k_absmax(int n, RowView M, NormSlot* slot) {
+// max |x| over the pool entries [mark[i], mark[i+1])
+__global__ void k_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot) {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned long long cap = ctl->pool_cap;  // counters may run past it on overflow
+    const unsigned long long p0 = min(__ldcg(&ctl->mark[i]), cap), p1 = min(__ldcg(&ctl->mark[i + 1]), cap);
     unsigned long long mx = 0ull;
-    for (int r = gw; r < n; r += nwarps)
-        for (int q = M.rb[r] + lane; q < M.re[r]; q += 32) {
-            unsigned long long b = mag_bits(M.val[q]);
-            mx = b > mx ? b : mx;
-        }
+    for (unsigned long long q = p0 + blockIdx.x * blockDim.x + threadIdx.x; q < p1;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long b = mag_bits(pool_val[q]);
+        mx = b > mx ? b : mx;
+    }
     mx = warp_max_u64(mx);
     if (lane == 0 && mx) atomicMax(&slot->absmax, mx);
 }
@@ -1259,27 +855,29 @@ __global__ void k_gather(int n, RowView src, const int* rowptr, int* col, double
 // Copy a canonical CSR matrix into the pool: each row gets a 4-entry aligned
 // slot of round-up(len, 4) entries (the layout the TMA copies rely on).
 __global__ void k_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
-                            int* pool_col, double* pool_val, Ctl* ctl) {
+                            int* pool_col, double* pool_val, Ctl* ctl, unsigned long long arena_size) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     Arena arena;
     for (int r = gw; r < n; r += nwarps) {
         int s = rowptr[r], e = rowptr[r + 1];
-        const long long base = arena_take(arena, (unsigned long long)((e - s + 3) & ~3), ctl, lane);
+        const long long base = arena_take(arena, (unsigned long long)((e - s + 3) & ~3), arena_size, ctl, pool_val, lane);
         if (base < 0) {
             if (lane == 0) rb[r] = re[r] = 0;
             continue;
         }
-        for (int q = lane; q < e - s; q += 32) {
-            pool_col[base + q] = col[s + q];
-            pool_val[base + q] = val[s + q];
+        const int padded = (e - s + 3) & ~3;
+        for (int q = lane; q < padded; q += 32) {
+            pool_col[base + q] = q < e - s ? col[s + q] : 0;
+            pool_val[base + q] = q < e - s ? val[s + q] : 0.0;
         }
         if (lane == 0) {
             rb[r] = (int)base;
             re[r] = (int)base + (e - s);
         }
     }
+    arena_close(arena, pool_val, lane);
 }
 
 __global__ void k_identity(int n, double alpha, int* rowptr, int* col, double* val) {
@@ -1306,53 +904,6 @@ static std::atomic<long long> g_launches{0};
 
 long long launch_count() { return g_launches.load(); }
 
-// smem budget of one k_product_win block: two blocks fit on one SM
-constexpr size_t kWinBlockBudget = 112 * 1024;
-
-template <int G>
-static int win_cap() {
-    int cap = 32 * G;
-    while (cap > 64 && win_smem_bytes<G>(cap) > kWinBlockBudget) cap -= 32;
-    return cap;
-}
-
-template <int G>
-static cudaError_t win_init() {
-    return cudaFuncSetAttribute(k_product_win<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)win_smem_bytes<G>(win_cap<G>()));
-}
-
-template <int G>
-static cudaError_t win_launch(const ProductArgs& P, int cap_limit, cudaStream_t st) {
-    const int full = win_cap<G>();
-    const int cap = (cap_limit > 0 && cap_limit < full) ? cap_limit : full;
-    long long blocks = ((long long)P.n + WinCfg<G>::NG - 1) / WinCfg<G>::NG;
-    const long long maxb = (long long)g_sms * 2 * 8;
-    if (blocks > maxb) blocks = maxb;
-    k_product_win<G><<<(unsigned)blocks, kWinThreads, win_smem_bytes<G>(full), st>>>(P, cap);
-    ++g_launches;
-    return cudaGetLastError();
-}
-
-int product_win_cap(int group) {
-    switch (group) {
-        case 32: return win_cap<32>();
-        case 64: return win_cap<64>();
-        case 128: return win_cap<128>();
-        default: return win_cap<256>();
-    }
-}
-
-cudaError_t launch_product_win(const ProductArgs& P, int group, int cap_limit, cudaStream_t st) {
-    if (P.n <= 0) return cudaSuccess;
-    switch (group) {
-        case 32: return win_launch<32>(P, cap_limit, st);
-        case 64: return win_launch<64>(P, cap_limit, st);
-        case 128: return win_launch<128>(P, cap_limit, st);
-        default: return win_launch<256>(P, cap_limit, st);
-    }
-}
-
 cudaError_t kernels_init() {
     if (g_sms) return cudaSuccess;
     int dev = 0;
@@ -1366,10 +917,6 @@ cudaError_t kernels_init() {
     err = cudaFuncSetAttribute(k_product<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)prod_smem_bytes<false>());
     if (err != cudaSuccess) return err;
-    if ((err = win_init<32>()) != cudaSuccess) return err;
-    if ((err = win_init<64>()) != cudaSuccess) return err;
-    if ((err = win_init<128>()) != cudaSuccess) return err;
-    if ((err = win_init<256>()) != cudaSuccess) return err;
     int per = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
@@ -1419,11 +966,8 @@ cudaError_t launch_norms(const NormArgs& A, cudaStream_t st) {
                                        0, st);
 }
 
-cudaError_t launch_absmax(int n, const RowView& M, NormSlot* slot, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    int blocks = (n + 7) / 8;
-    if (blocks > g_sms * 8) blocks = g_sms * 8;
-    k_absmax<<<blocks, 256, 0, st>>>(n, M, slot);
+cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st) {
+    k_absmax<<<g_sms * 4, 256, 0, st>>>(pool_val, ctl, i, slot);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -1459,11 +1003,12 @@ cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* 
 }
 
 cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
-                             int* pool_col, double* pool_val, Ctl* ctl, cudaStream_t st) {
+                             int* pool_col, double* pool_val, Ctl* ctl, unsigned long long arena_size,
+                             cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    int blocks = (n + 7) / 8;
-    if (blocks > g_sms * 4) blocks = g_sms * 4;
-    k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl);
+    int blocks = (n + 63) / 64;
+    if (blocks > g_sms) blocks = g_sms;
+    k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl, arena_size);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -14,11 +14,9 @@ size_t product_smem_bytes();
 int product_warps_per_block();
 
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st);
-cudaError_t launch_product_win(const ProductArgs& P, int group, int cap_limit, cudaStream_t st);
-int product_win_cap(int group);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
 cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
-cudaError_t launch_absmax(int n, const RowView& M, NormSlot* slot, cudaStream_t st);
+cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st);
 cudaError_t launch_validate(int n, int nnz, const int* rowptr, const int* col, const double* val, Ctl* ctl,
                             cudaStream_t st);
 cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, Ctl* ctl, cudaStream_t st);
@@ -26,7 +24,8 @@ cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col
                           cudaStream_t st);
 cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* val, cudaStream_t st);
 cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
-                             int* pool_col, double* pool_val, Ctl* ctl, cudaStream_t st);
+                             int* pool_col, double* pool_val, Ctl* ctl, unsigned long long arena_size,
+                             cudaStream_t st);
 cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
 
 }  // namespace psf

@@ -20,10 +20,10 @@ pytestmark = pytest.mark.gpu
 psf = pytest.importorskip("paper_2208_05683_gb300")
 
 
-def run_both(Z, a, tol, kernel="auto", window_cap=0, **kw):
+def run_both(Z, a, tol, kernel="auto", chunk_cols=0, chunk_slots=0, **kw):
     got = psf.Series(a, tol, poly=kw.get("poly", False), filtered=kw.get("filtered", True),
                      submult=kw.get("submult", False), s=kw.get("s", 0), kernel=kernel,
-                     window_cap=window_cap).eval(dev(Z))
+                     chunk_cols=chunk_cols, chunk_slots=chunk_slots).eval(dev(Z))
     ref = psscf(Z, a, tol, **kw)
     return got, ref
 
@@ -63,22 +63,25 @@ def test_lap2d_32_bitwise(kind):
     check_same(got, ref, kind)
 
 
-@pytest.mark.parametrize("kernel,window_cap", [("window", 0), ("bitmap", 0), ("window", 256), ("window", 64)])
-def test_product_kernels_agree_bitwise(kernel, window_cap):
-    # both product kernels, and the window kernel with rows split into
-    # several column chunks, give the oracle's result bit for bit
+@pytest.mark.parametrize("kernel,cols,slots", [("table", 0, 0), ("bitmap", 0, 0), ("table", 96, 0),
+                                               ("bitmap", 64, 0), ("table", 0, 40), ("bitmap", 0, 33),
+                                               ("table", 40, 37)])
+def test_slot_maps_and_row_chunking_bitwise(kernel, cols, slots):
+    # both slot maps of the product kernel, and rows split into several column
+    # chunks (by width or by accumulator slots), give the oracle's result bit
+    # for bit
     Z = ocsr(syn.laplacian_2d(24))
     for kind in ("exp", "cos"):
-        got, ref = run_both(Z, syn.coeffs(kind), 1e-12, kernel=kernel, window_cap=window_cap)
-        check_same(got, ref, f"{kernel} cap {window_cap} {kind}")
+        got, ref = run_both(Z, syn.coeffs(kind), 1e-12, kernel=kernel, chunk_cols=cols, chunk_slots=slots)
+        check_same(got, ref, f"{kernel} {cols}/{slots} {kind}")
     Zb = ocsr(syn.banded_random(700, 6, 3, 2.0))
-    got, ref = run_both(Zb, syn.coeffs("exp"), 1e-12, kernel=kernel, window_cap=window_cap)
-    check_same(got, ref, f"{kernel} cap {window_cap} banded")
+    got, ref = run_both(Zb, syn.coeffs("exp"), 1e-12, kernel=kernel, chunk_cols=cols, chunk_slots=slots)
+    check_same(got, ref, f"{kernel} {cols}/{slots} banded")
 
 
-def test_group_sizes_follow_previous_evaluation():
-    # the second evaluation of a series uses the row lengths of the first to
-    # pick its thread-group sizes; the result must not change
+def test_second_evaluation_uses_first_as_hints():
+    # the second evaluation of a series sizes its pool and picks its slot maps
+    # from the first one's statistics; the result must not change
     Z = ocsr(syn.laplacian_2d(40))
     s = psf.Series(syn.coeffs("exp"), 1e-12)
     r1 = s.eval(dev(Z))
