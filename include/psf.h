@@ -173,6 +173,32 @@ PSF_API int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t n
 PSF_API int psf_norm1(const psf_csr_t* M, void* stream, double* out);
 
 /*
+ * psf_norm1_noalloc: the same exact ||M||_1 as psf_norm1 (bit for bit),
+ * computed without allocating any memory.  The paper has no counterpart: it
+ * is an operational variant for callers that must not allocate, e.g. a
+ * serving loop whose device memory is already committed to admitted
+ * requests (an allocation could fail or evict them), or code that overlaps
+ * work on other streams and cannot afford the device-wide synchronisation
+ * that freeing device memory implies.
+ *
+ * Instead of a workspace per call, it uses one scratch region compiled into
+ * the library (a static device array of about 4.3 MB: the fixed-point column
+ * sums of PSF_NORM1_NOALLOC_MAX_N columns and a control block), and it reads
+ * M's entries in place.
+ *  - M: device CSR, n <= PSF_NORM1_NOALLOC_MAX_N (else PSF_ETOOBIG, nothing
+ *    is launched); malformed input gives PSF_EINVAL as for psf_norm1.
+ *  - out: host pointer, receives the norm; the call synchronizes `stream`.
+ *  - The first call on a device (with that device current) looks up the
+ *    scratch region's address and configures the kernels; make it before any
+ *    stream capture.  Later calls only launch kernels and copy 12 bytes back.
+ *  - The scratch region is shared: calls that overlap in time on one device
+ *    (several threads, or several streams without ordering between them)
+ *    race on it and give wrong results.  Serialize them.
+ */
+#define PSF_NORM1_NOALLOC_MAX_N 65536
+PSF_API int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out);
+
+/*
  * Host-only planner: from coefficients, tol, flags, the block-size override
  * s and the norms z_0..z_10 (||Z^i||_1, or only z_0 = 1, z_1 = ||Z||_1 with
  * PSF_Z_SUBMULT), fill N, q, b, g, products, z, alpha10, trunc, budget, and

@@ -10,6 +10,7 @@ pointers and columns, float64 values, torch tensors on a CUDA device).
     eval_batch([...series], [...Z])         many instances at once
     product_filter(A, B, addends, thr)      one filtered product (Eq. 11/14 + Alg. 1)
     norm1(M)                                exact ||M||_1
+    norm1_noalloc(M)                        the same, without allocating device memory
     plan(coeffs, tol, norms, ...)           the a-priori analysis (host only)
 
 The library is loaded from ``paper_2208_05683_gb300/_build/libpsf.so``; if it
@@ -24,11 +25,12 @@ from dataclasses import dataclass, field
 from . import _build
 from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_SUBMULT, PSF_PARAM_ALG1_MAXIT,
                    PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS,
-                   PSF_PARAM_CHUNK_SLOTS, PSF_MAX_Q,
+                   PSF_PARAM_CHUNK_SLOTS, PSF_MAX_Q, PSF_NORM1_NOALLOC_MAX_N,
                    PsfError, CSRStruct, InfoStruct, StepStruct, lib, check)
 
 __all__ = [
-    "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "plan", "PsfError",
+    "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "norm1_noalloc", "plan",
+    "PsfError",
     "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_MAX_Q", "build", "lib",
 ]
 
@@ -220,6 +222,15 @@ def norm1(M: DeviceCSR, stream=None) -> float:
     out = ctypes.c_double()
     ms = M._struct()
     check(lib().psf_norm1(ctypes.byref(ms), _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def norm1_noalloc(M: DeviceCSR, stream=None) -> float:
+    """||M||_1 as norm1, in the library's static scratch region (no device
+    allocation; n <= PSF_NORM1_NOALLOC_MAX_N; overlapping calls race)."""
+    out = ctypes.c_double()
+    ms = M._struct()
+    check(lib().psf_norm1_noalloc(ctypes.byref(ms), _stream_ptr(stream), ctypes.byref(out)))
     return out.value
 
 

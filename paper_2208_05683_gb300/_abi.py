@@ -12,6 +12,7 @@ PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT = 0, 1, 2, 4
 PSF_PARAM_ER, PSF_PARAM_ALG1_MAXIT, PSF_PARAM_POOL_ENTRIES = 1, 2, 3
 PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
 PSF_MAX_Q = 23
+PSF_NORM1_NOALLOC_MAX_N = 65536
 
 ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG"}
 
@@ -19,6 +20,7 @@ ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT
 EXPORTS = [
     "psf_version", "psf_last_error", "psf_series_create", "psf_series_set_param",
     "psf_series_destroy", "psf_eval", "psf_eval_batch", "psf_product_filter", "psf_norm1",
+    "psf_norm1_noalloc",
     "psf_plan", "psf_result_csr", "psf_result_copy", "psf_result_info", "psf_result_step",
     "psf_result_destroy", "psf_launch_count", "psf_profile", "psf_profile_read",
 ]
@@ -97,6 +99,7 @@ def _declare(h: ctypes.CDLL) -> None:
     h.psf_product_filter.argtypes = [csrp, csrp, i32, ctypes.POINTER(f64), ctypes.POINTER(csrp), f64, f64,
                                      i32, vp, ctypes.POINTER(vp)]
     h.psf_norm1.argtypes = [csrp, vp, ctypes.POINTER(f64)]
+    h.psf_norm1_noalloc.argtypes = [csrp, vp, ctypes.POINTER(f64)]
     h.psf_plan.argtypes = [ctypes.POINTER(f64), i64, i32, f64, ctypes.c_uint32, ctypes.POINTER(f64),
                            ctypes.POINTER(InfoStruct), ctypes.POINTER(f64), ctypes.POINTER(f64)]
     h.psf_result_csr.argtypes = [vp, csrp]

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1055,3 +1056,93 @@ int psf_result_destroy(psf_result_t r) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- norm without allocation
+// psf_norm1_noalloc works in one scratch region compiled into the library
+// instead of a per-call workspace: some callers cannot allocate at the moment
+// they need a norm (their device memory is committed to other work, or the
+// implicit device-wide synchronisation of freeing memory would stall their
+// other streams).  The region holds the control block, the norm slot and the
+// fixed-point column sums of up to PSF_NORM1_NOALLOC_MAX_N columns; the
+// matrix's own (col, val) arrays serve as the flat entry range the norm
+// kernels scan, so nothing is copied.
+namespace {
+
+constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kNaMaxN = PSF_NORM1_NOALLOC_MAX_N;
+constexpr size_t kNaCtl = 0;
+constexpr size_t kNaSlot = kNaCtl + round256(sizeof(Ctl));
+constexpr size_t kNaSticky = kNaSlot + round256(sizeof(NormSlot));
+constexpr size_t kNaWords = kNaSticky + round256(sizeof(unsigned) * kNaMaxN);
+constexpr size_t kNaBytes = kNaWords + sizeof(unsigned long long) * kChunks * kNaMaxN;
+
+static __device__ __align__(256) unsigned char g_norm1_scratch[kNaBytes];
+
+// Device address of the scratch region, looked up once per device (with
+// that device current) and kept; the lookup is the call that may initialise
+// the module, which is why the first call belongs before any stream capture.
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+void* g_na_ptr[kNaMaxDevices] = {};
+
+int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNaMaxDevices) return fail(PSF_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        CU(cudaGetSymbolAddress(&p, g_norm1_scratch));
+        if (!p) return fail(PSF_ECUDA, "scratch region has no device address");
+        g_na_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_na_ptr[dev]);
+    return PSF_OK;
+}
+
+}  // namespace
+
+extern "C" int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out) {
+    if (!M || !out) return fail(PSF_EINVAL, "null argument");
+    int rc = check_csr(M, M->n, "M");
+    if (rc) return rc;
+    if ((size_t)M->n > kNaMaxN)
+        return fail(PSF_ETOOBIG, "psf_norm1_noalloc: n = %d exceeds its static scratch limit of %d columns", M->n,
+                    (int)kNaMaxN);
+    if (M->n == 0) {
+        *out = 0.0;
+        return PSF_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(kernels_init());
+    unsigned char* base = nullptr;
+    if ((rc = noalloc_scratch(&base))) return rc;
+    Ctl* ctl = reinterpret_cast<Ctl*>(base + kNaCtl);
+    NormSlot* slot = reinterpret_cast<NormSlot*>(base + kNaSlot);
+    unsigned* sticky = reinterpret_cast<unsigned*>(base + kNaSticky);
+    unsigned long long* words = reinterpret_cast<unsigned long long*>(base + kNaWords);
+    // clear what must start at zero, check the input (its verdict is read
+    // with the result; the norm kernels never index with a column outside
+    // [0, n)), then max |x| and the exact column sums over M's entries
+    CU(launch_norm_scratch_init(ctl, slot, words, sticky, M->n, M->nnz, st));
+    CU(launch_validate(M->n, M->nnz, M->rowptr, M->col, M->val, ctl, st));
+    CU(launch_absmax(M->val, ctl, 0, slot, st));
+    NormArgs na{};
+    na.n = M->n;
+    na.count = 1;
+    na.pool_col = M->col;
+    na.pool_val = M->val;
+    na.slots = slot;
+    na.words = words;
+    na.sticky = sticky;
+    na.ctl = ctl;
+    CU(launch_norms(na, st));
+    int status = 0;
+    unsigned long long bits = 0ull;
+    CU(cudaMemcpyAsync(&status, &ctl->status, sizeof status, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&bits, &slot->result, sizeof bits, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if ((rc = status_to_code(status))) return rc;
+    std::memcpy(out, &bits, sizeof bits);
+    return PSF_OK;
+}

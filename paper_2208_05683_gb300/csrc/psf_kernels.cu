@@ -880,6 +880,27 @@ __global__ void k_copy_rows(int n, const int* rowptr, const int* col, const doub
     arena_close(arena, pool_val, lane);
 }
 
+// Reset a caller-provided norm workspace for one matrix of n columns and
+// nnz entries read in place: clear the control block, the norm slot and the
+// column-sum words, and let the matrix's entries [0, nnz) be norm matrix 0.
+__global__ void k_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long long* words, unsigned* sticky, int n,
+                                    long long nnz) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    for (long long i = t; i < (long long)kChunks * n; i += nt) words[i] = 0ull;
+    for (long long i = t; i < n; i += nt) sticky[i] = 0u;
+    if (t == 0) {
+        Ctl c{};
+        c.pool_cap = (unsigned long long)nnz;
+        c.pool_used = (unsigned long long)nnz;
+        c.mark[0] = 0ull;
+        c.mark[1] = (unsigned long long)nnz;
+        *ctl = c;
+        slot->absmax = 0ull;
+        slot->result = 0ull;
+    }
+}
+
 __global__ void k_identity(int n, double alpha, int* rowptr, int* col, double* val) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) {
@@ -1009,6 +1030,16 @@ cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const dou
     int blocks = (n + 63) / 64;
     if (blocks > g_sms) blocks = g_sms;
     k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl, arena_size);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long long* words, unsigned* sticky, int n,
+                                     long long nnz, cudaStream_t st) {
+    int blocks = (int)(((long long)kChunks * n + 255) / 256);
+    if (blocks < 1) blocks = 1;
+    if (blocks > g_sms * 4) blocks = g_sms * 4;
+    k_norm_scratch_init<<<blocks, 256, 0, st>>>(ctl, slot, words, sticky, n, nnz);
     ++g_launches;
     return cudaGetLastError();
 }

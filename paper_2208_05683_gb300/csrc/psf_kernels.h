@@ -26,6 +26,8 @@ cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* 
 cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
                              int* pool_col, double* pool_val, Ctl* ctl, unsigned long long arena_size,
                              cudaStream_t st);
+cudaError_t launch_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long long* words, unsigned* sticky, int n,
+                                     long long nnz, cudaStream_t st);
 cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
 
 }  // namespace psf
