@@ -18,16 +18,17 @@
 #include <string>
 #include <vector>
 
-#include "../../include/psf.h"
-#include "psf_kernels.h"
-#include "psf_plan.h"
+#include "psf_internal.h"
 
 using namespace psf;
+using namespace psf::host;
 
 // ---------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
 
-static int fail(int code, const char* fmt, ...) {
+namespace psf {
+namespace host {
+int fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -37,78 +38,7 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-#define CU(expr)                                                                             \
-    do {                                                                                     \
-        cudaError_t e_ = (expr);                                                             \
-        if (e_ != cudaSuccess)                                                               \
-            return fail(e_ == cudaErrorMemoryAllocation ? PSF_ENOMEM : PSF_ECUDA, "%s: %s (%s:%d)", \
-                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
-    } while (0)
-
-// ---------------------------------------------------------------- objects
-struct psf_series_s {
-    std::vector<double> a;
-    double tol = 0.0;
-    uint32_t flags = 0;
-    int s = 0;
-    double e_r = 0.1;
-    int maxit = 1000;
-    unsigned long long pool_hint = 0;  // user-set initial capacity (entries)
-    unsigned long long z_need = 0;     // largest pool the norm phase has needed
-    unsigned long long ps_need = 0;    // largest pool the PS phase has needed
-    // B-operand mean row lengths seen by the previous evaluation, per step:
-    // they pick the thread-group size of the product kernel (tuning only)
-    std::vector<double> len_z, len_baby, len_giant;
-    int kernel = 0;       // PSF_PARAM_KERNEL
-    int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
-    int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS
-};
-
-struct psf_result_s {
-    int n = 0;
-    long long nnz = 0;
-    int* rowptr = nullptr;
-    int* col = nullptr;
-    double* val = nullptr;
-    cudaStream_t stream = nullptr;
-    psf_info_t info{};
-    std::vector<psf_step_info_t> steps;
-};
-
-namespace {
-
-// Stream-ordered device buffer released on the stream it was made on.
-struct DevBuf {
-    void* p = nullptr;
-    cudaStream_t st = nullptr;
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { release(); }
-    cudaError_t alloc(size_t bytes, cudaStream_t s) {
-        release();
-        st = s;
-        if (bytes == 0) bytes = 16;
-        return cudaMallocAsync(&p, bytes, s);
-    }
-    void release() {
-        if (p) cudaFreeAsync(p, st);
-        p = nullptr;
-    }
-    template <class T>
-    T* as() const {
-        return static_cast<T*>(p);
-    }
-};
-
 bool g_pool_configured = false;
-
-// Optional event timing of the product kernel (psf_profile).
-struct Profile {
-    bool on = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    double fma = 0.0;
-};
 Profile g_prof;
 
 cudaError_t configure_mempool() {
@@ -144,69 +74,6 @@ int check_csr(const psf_csr_t* m, int n, const char* what) {
         return fail(PSF_EINVAL, "%s: null device array", what);
     return PSF_OK;
 }
-
-// Device workspace shared by the phases of one evaluation.
-struct Work {
-    int n = 0;
-    cudaStream_t st = nullptr;
-    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val;
-    unsigned long long cap = 0;
-    std::vector<DevBuf*> rows;  // 2n ints each: rb then re
-    int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
-    int chunk_cols = 0, chunk_slots = 0;
-
-    ~Work() {
-        for (DevBuf* b : rows) delete b;
-    }
-    Ctl* C() const { return ctl.as<Ctl>(); }
-    int init(int n_, cudaStream_t s, int nstats) {
-        n = n_;
-        st = s;
-        CU(ctl.alloc(sizeof(Ctl), st));
-        CU(cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st));
-        CU(stats.alloc(sizeof(StepStat) * (size_t)(nstats > 0 ? nstats : 1), st));
-        CU(slots.alloc(sizeof(NormSlot) * kMaxNorms, st));
-        CU(cudaMemsetAsync(slots.p, 0, sizeof(NormSlot) * kMaxNorms, st));
-        size_t nn = (size_t)(n > 0 ? n : 1);
-        CU(words.alloc(sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
-        CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
-        CU(sticky.alloc(sizeof(unsigned) * nn * kMaxNorms, st));
-        CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
-        return PSF_OK;
-    }
-    // (re)allocate the entry pool and reset the device control block
-    int reset_pool(unsigned long long entries) {
-        if (entries > (unsigned long long)INT32_MAX) return fail(PSF_ETOOBIG, "pool of %llu entries exceeds 2^31", entries);
-        if (entries > cap) {
-            CU(pool_col.alloc(sizeof(int) * entries, st));
-            CU(pool_val.alloc(sizeof(double) * entries, st));
-            cap = entries;
-        }
-        Ctl h{};
-        h.pool_cap = cap;
-        CU(cudaMemcpyAsync(ctl.p, &h, offsetof(Ctl, bar_count), cudaMemcpyHostToDevice, st));
-        return PSF_OK;
-    }
-    // Column-sum accumulators are zero between steps; a phase cut short by a
-    // pool overflow can leave some set, so they are cleared before its retry.
-    int clear_sums() {
-        size_t nn = (size_t)(n > 0 ? n : 1);
-        CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
-        CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
-        return PSF_OK;
-    }
-    // row arrays of matrix slot i
-    int rows_for(size_t i, int** rb, int** re) {
-        while (rows.size() <= i) rows.push_back(new DevBuf());
-        if (!rows[i]->p) CU(rows[i]->alloc(sizeof(int) * 2 * (size_t)(n > 0 ? n : 1), st));
-        *rb = rows[i]->as<int>();
-        *re = *rb + n;
-        return PSF_OK;
-    }
-    RowView pooled(int* rb, int* re) const { return RowView{rb, re, pool_col.as<int>(), pool_val.as<double>()}; }
-    int* pcol() const { return pool_col.as<int>(); }
-    double* pval() const { return pool_val.as<double>(); }
-};
 
 // Host copy of the control block (only the fields read back).
 struct CtlHost {
@@ -389,6 +256,10 @@ int finish_result(Work& w, const RowView& M, psf_result_s* r, unsigned long long
 
 void destroy_result(psf_result_s* r) {
     if (!r) return;
+    if (r->owner) {  // views into a batch's storage, freed with its last result
+        delete r;
+        return;
+    }
     if (r->rowptr) cudaFreeAsync(r->rowptr, r->stream);
     if (r->col) cudaFreeAsync(r->col, r->stream);
     if (r->val) cudaFreeAsync(r->val, r->stream);
@@ -402,7 +273,10 @@ int prepare(cudaStream_t st) {
     return PSF_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace psf
+
+using namespace psf::host;
 
 // ---------------------------------------------------------------- ABI
 extern "C" {
@@ -965,23 +839,6 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     inf.fma = (int64_t)eval_fma;
     if (g_prof.on) g_prof.fma += (double)eval_fma;
     *out = handle;
-    return PSF_OK;
-}
-
-int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, int32_t count, void* stream,
-                   psf_result_t* outs) {
-    if (count < 0 || (count > 0 && (!series || !Zs || !outs))) return fail(PSF_EINVAL, "bad batch arguments");
-    for (int i = 0; i < count; ++i) outs[i] = nullptr;
-    for (int i = 0; i < count; ++i) {
-        int rc = psf_eval(series[i], &Zs[i], stream, &outs[i]);
-        if (rc) {
-            for (int j = 0; j < i; ++j) {
-                psf_result_destroy(outs[j]);
-                outs[j] = nullptr;
-            }
-            return rc;
-        }
-    }
     return PSF_OK;
 }
 

@@ -70,6 +70,26 @@ struct AddTerm {
     double alpha;
 };
 
+// A batch of instances is one block-diagonal matrix: instance i owns the
+// rows and columns [off_i, off_i + n_i).  What a step does to an instance's
+// rows is one of these modes.
+enum : int {
+    kBatchSkip = 0,     // no output rows
+    kBatchProduct = 1,  // sum of the addends + A B (and Algorithm 1 pass 1)
+    kBatchPass = 2,     // rows of B passed through unchanged (no work)
+    kBatchAddOnly = 3,  // sum of the addends only
+};
+
+// Per-instance parameters of one batched step.
+struct BatchStep {
+    double eps_g;  // > 0: Algorithm 1 on this instance with eps_g and bound
+    double bound;  // eps_g (1 + e_r)
+    int e_lsb;     // LSB exponent of the column-sum fixed point
+    int maxit;     // Algorithm 1 pass cap
+    int mode;
+    int pad;
+};
+
 // C = sum_t add[t].alpha * M_t + A * B, rows written to the pool.
 struct ProductArgs {
     int n;
@@ -92,6 +112,41 @@ struct ProductArgs {
     int chunk_cols;             // > 0: fewer columns per chunk (exercises chunking)
     int chunk_slots;            // > 0: fewer accumulator slots per chunk
     unsigned long long arena;   // pool entries a warp takes at a time (multiple of 4)
+    // batch (inst == nullptr: one instance, the fields above apply to all rows)
+    const int* inst;            // instance of each row, n entries
+    const BatchStep* bstep;     // per instance
+    const double* alpha_tab;    // [t * ninst + i]: coefficient of term t for instance i (+0: absent)
+    int ninst;
+    int absmax_stride;          // absmax slot of instance i: absmax_slot + i * absmax_stride
+    StepStat* stat_tab;         // per instance (nullptr: no statistics)
+};
+
+// Algorithm 1 passes 2, 3, ... and compaction for every filtered instance of
+// a batched step.
+struct Alg1BatchArgs {
+    int n;  // rows = columns of the block-diagonal batch
+    int ninst;
+    const int* inst;
+    const BatchStep* bstep;
+    int* rb;
+    int* re;
+    int* col;
+    double* val;
+    unsigned long long* words;
+    unsigned* sticky;
+    unsigned long long* cslot;             // 2 * ninst column-sum maxima (bits)
+    const unsigned long long* pool_start;  // pool counter before the step's product
+    Ctl* ctl;
+    StepStat* stat_tab;  // per instance
+};
+
+// One input matrix of a batch (device CSR, 0-based local columns).
+struct BatchSrc {
+    const int* rowptr;
+    const int* col;
+    const double* val;
+    int n;
+    int off;  // first global row / column
 };
 
 struct Alg1Args {
@@ -115,10 +170,12 @@ struct NormArgs {
     int count;  // matrices
     const int* pool_col;
     const double* pool_val;
-    NormSlot* slots;            // count
+    NormSlot* slots;            // count (instance i of a batch: slots + i * slot_stride)
     unsigned long long* words;  // count * kChunks * n
     unsigned* sticky;           // count * n
     Ctl* ctl;
+    const int* inst;            // batch: instance of each column (nullptr: one instance)
+    int slot_stride;
 };
 
 // ---------------------------------------------------------------- helpers

@@ -1,0 +1,169 @@
+// psf_internal.h -- host-side internals shared by the translation units of
+// the library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <utility>
+#include <vector>
+
+#include "../../include/psf.h"
+#include "psf_kernels.h"
+#include "psf_plan.h"
+
+// ---------------------------------------------------------------- objects
+struct psf_series_s {
+    std::vector<double> a;
+    double tol = 0.0;
+    uint32_t flags = 0;
+    int s = 0;
+    double e_r = 0.1;
+    int maxit = 1000;
+    unsigned long long pool_hint = 0;  // user-set initial capacity (entries)
+    unsigned long long z_need = 0;     // largest pool the norm phase has needed
+    unsigned long long ps_need = 0;    // largest pool the PS phase has needed
+    // B-operand mean row lengths seen by the previous evaluation, per step:
+    // they pick the thread-group size of the product kernel (tuning only)
+    std::vector<double> len_z, len_baby, len_giant;
+    int kernel = 0;       // PSF_PARAM_KERNEL
+    int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
+    int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS
+};
+
+struct psf_result_s {
+    int n = 0;
+    long long nnz = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+    cudaStream_t stream = nullptr;
+    psf_info_t info{};
+    std::vector<psf_step_info_t> steps;
+    // set when rowptr/col/val point into storage shared by several results
+    // (a batch); the storage is released with the last of them
+    std::shared_ptr<void> owner;
+};
+
+namespace psf {
+namespace host {
+
+// Record a failure message for psf_last_error and return `code`.
+int fail(int code, const char* fmt, ...);
+
+#define CU(expr)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? PSF_ENOMEM : PSF_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+// Stream-ordered device buffer released on the stream it was made on.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t alloc(size_t bytes, cudaStream_t s) {
+        release();
+        st = s;
+        if (bytes == 0) bytes = 16;
+        return cudaMallocAsync(&p, bytes, s);
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+// Optional event timing of the product kernel (psf_profile).
+struct Profile {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    double fma = 0.0;
+};
+extern Profile g_prof;
+
+// Device workspace shared by the phases of one evaluation.
+struct Work {
+    int n = 0;
+    cudaStream_t st = nullptr;
+    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val;
+    unsigned long long cap = 0;
+    std::vector<DevBuf*> rows;  // 2n ints each: rb then re
+    int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
+    int chunk_cols = 0, chunk_slots = 0;
+
+    ~Work() {
+        for (DevBuf* b : rows) delete b;
+    }
+    Ctl* C() const { return ctl.as<Ctl>(); }
+    int init(int n_, cudaStream_t s, int nstats) {
+        n = n_;
+        st = s;
+        CU(ctl.alloc(sizeof(Ctl), st));
+        CU(cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st));
+        CU(stats.alloc(sizeof(StepStat) * (size_t)(nstats > 0 ? nstats : 1), st));
+        CU(slots.alloc(sizeof(NormSlot) * kMaxNorms, st));
+        CU(cudaMemsetAsync(slots.p, 0, sizeof(NormSlot) * kMaxNorms, st));
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        CU(words.alloc(sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
+        CU(sticky.alloc(sizeof(unsigned) * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
+        return PSF_OK;
+    }
+    // (re)allocate the entry pool and reset the device control block
+    int reset_pool(unsigned long long entries) {
+        if (entries > (unsigned long long)INT32_MAX) return fail(PSF_ETOOBIG, "pool of %llu entries exceeds 2^31", entries);
+        if (entries > cap) {
+            CU(pool_col.alloc(sizeof(int) * entries, st));
+            CU(pool_val.alloc(sizeof(double) * entries, st));
+            cap = entries;
+        }
+        Ctl h{};
+        h.pool_cap = cap;
+        CU(cudaMemcpyAsync(ctl.p, &h, offsetof(Ctl, bar_count), cudaMemcpyHostToDevice, st));
+        return PSF_OK;
+    }
+    // Column-sum accumulators are zero between steps; a phase cut short by a
+    // pool overflow can leave some set, so they are cleared before its retry.
+    int clear_sums() {
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
+        CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
+        return PSF_OK;
+    }
+    // row arrays of matrix slot i
+    int rows_for(size_t i, int** rb, int** re) {
+        while (rows.size() <= i) rows.push_back(new DevBuf());
+        if (!rows[i]->p) CU(rows[i]->alloc(sizeof(int) * 2 * (size_t)(n > 0 ? n : 1), st));
+        *rb = rows[i]->as<int>();
+        *re = *rb + n;
+        return PSF_OK;
+    }
+    RowView pooled(int* rb, int* re) const { return RowView{rb, re, pool_col.as<int>(), pool_val.as<double>()}; }
+    int* pcol() const { return pool_col.as<int>(); }
+    double* pval() const { return pool_val.as<double>(); }
+};
+
+int lsb_for_bound_host(double x);
+RowView view_of(const psf_csr_t& m);
+int check_csr(const psf_csr_t* m, int n, const char* what);
+int read_back(Work& w, Ctl& c, NormSlot* slots);
+int status_to_code(int st);
+unsigned long long arena_for(double row_len);
+int mark_pool(Work& w, int i);
+void destroy_result(psf_result_s* r);
+int prepare(cudaStream_t st);
+
+}  // namespace host
+}  // namespace psf

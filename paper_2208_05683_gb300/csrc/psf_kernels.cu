@@ -174,11 +174,12 @@ __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false>& S
 
 // Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
 template <bool TAB>
-__device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, int r, int c0, int cend,
-                                          int pa0, int pa1, bool whole, int lane, ProdSmem<TAB>& S) {
+__device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
+                                          int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB>& S) {
     clear_map(cend - c0, lane, S);
     __syncwarp();
     for (int t = 0; t < nadd; ++t) {
+        if (!((tmask >> t) & 1u)) continue;
         const AddTerm& T = add[t];
         if (!T.rb) {
             if (lane == 0 && r >= c0 && r < cend) mark_one(r - c0, S);
@@ -387,7 +388,29 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
     }
 }
 
-template <bool TAB>
+// Statistics of one row of a batched step, added to its instance's record:
+// multiply-adds (per-lane partial counts), Algorithm 1 candidates (per lane),
+// entries written and the largest |x| (per lane).
+__device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, unsigned long long fma,
+                                                unsigned long long cand, int written, unsigned long long absmax,
+                                                int lane) {
+    for (int o = 16; o; o >>= 1) {
+        fma += __shfl_xor_sync(kFull, fma, o);
+        cand += __shfl_xor_sync(kFull, cand, o);
+    }
+    absmax = warp_max_u64(absmax);
+    if (lane == 0) {
+        if (P.stat_tab) {
+            StepStat* st = P.stat_tab + inst;
+            if (fma) atomicAdd(&st->fma, fma);
+            if (written) atomicAdd(&st->nnz_pre, (unsigned long long)written);
+            if (cand) atomicAdd(&st->ncand, cand);
+        }
+        if (P.absmax_slot && absmax) atomicMax(&(P.absmax_slot + (size_t)inst * P.absmax_stride)->absmax, absmax);
+    }
+}
+
+template <bool TAB, bool BATCH>
 __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_product(ProductArgs P) {
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
     // columns and slots of one chunk (lowered only to exercise chunking)
@@ -413,9 +436,37 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
     Arena arena;
 
     for (int r = blockIdx.x * kWarps + wib; r < P.n; r += gridDim.x * kWarps) {
+        // ---- the row's terms: single instance, every term and the product;
+        // batch, what the row's instance does in this step
+        bool prod = P.A.rb != nullptr;
+        unsigned tmask = kFull;  // terms present in this row (batch: coefficient != 0)
+        double my_alpha = 0.0;   // batch: coefficient of term `lane` for this row
+        unsigned long long r_eps = eps_bits;
+        int r_lsb = P.e_lsb;
+        bool r_filt = P.filtering != 0;
+        int r_inst = 0;
+        if constexpr (BATCH) {
+            r_inst = P.inst[r];
+            const BatchStep bs = P.bstep[r_inst];
+            if (bs.mode == kBatchSkip || bs.mode == kBatchPass) {
+                if (lane == 0) {
+                    P.out_rb[r] = bs.mode == kBatchPass ? P.B.rb[r] : 0;
+                    P.out_re[r] = bs.mode == kBatchPass ? P.B.re[r] : 0;
+                }
+                continue;
+            }
+            prod = bs.mode == kBatchProduct;
+            my_alpha = lane < nadd ? P.alpha_tab[(size_t)lane * P.ninst + r_inst] : 0.0;
+            tmask = __ballot_sync(kFull, __double_as_longlong(my_alpha) != 0ll);
+            r_filt = bs.eps_g > 0.0;
+            r_eps = (unsigned long long)__double_as_longlong(bs.eps_g);
+            r_lsb = bs.e_lsb;
+        }
+        const unsigned long long fma0 = my_fma, cand0 = my_cand;
         // ---- column window of row r and the row's multiply-add count
         int lo = INT_MAX, hi = -1;
         for (int t = 0; t < nadd; ++t) {
+            if (!((tmask >> t) & 1u)) continue;
             const AddTerm& T = add[t];
             if (!T.rb) {
                 lo = min(lo, r);
@@ -429,7 +480,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
             }
         }
         int pa0 = 0, pa1 = 0;
-        if (P.A.rb) {
+        if (prod) {
             pa0 = P.A.rb[r];
             pa1 = P.A.re[r];
         }
@@ -444,11 +495,12 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
         }
         if (lane == 0)
             for (int t = 0; t < nadd; ++t)
-                my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
+                if ((tmask >> t) & 1u) my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
         lo = warp_min(lo);
         hi = warp_max(hi);
         if (hi < lo) {
             if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
+            if constexpr (BATCH) row_stats_batch(P, r_inst, my_fma - fma0, 0ull, 0, 0ull, lane);
             continue;
         }
 
@@ -456,13 +508,13 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
         long long total = 0;
         bool reuse = false;
         if (hi - lo + 1 <= kCols) {
-            build_map<TAB>(P, add, nadd, r, lo, hi + 1, pa0, pa1, true, lane, S);
+            build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S);
             total = count_marks(hi - lo + 1, lane, S);
             reuse = true;
         } else {
             for (long long c0 = lo; c0 <= hi; c0 += kCols) {
                 int cend = (int)min((long long)hi + 1, c0 + kCols);
-                build_map<TAB>(P, add, nadd, r, (int)c0, cend, pa0, pa1, false, lane, S);
+                build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S);
                 total += count_marks(cend - (int)c0, lane, S);
             }
         }
@@ -476,7 +528,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
         int c0 = lo;
         while (c0 <= hi) {
             int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
-            if (!reuse) build_map<TAB>(P, add, nadd, r, c0, cend, pa0, pa1, false, lane, S);
+            if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S);
             reuse = false;
             int cut;
             const int cnt = assign_slots(cend - c0, kSlots, lane, S, &cut);
@@ -486,8 +538,9 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
 
             // ---- weighted sum of the addends, t ascending
             for (int t = 0; t < nadd; ++t) {
+                if (!((tmask >> t) & 1u)) continue;
                 const AddTerm& T = add[t];
-                const double alpha = T.alpha;
+                const double alpha = BATCH ? __shfl_sync(kFull, my_alpha, t) : T.alpha;
                 if (!T.rb) {
                     if (lane == 0 && r >= c0 && r < c1) {
                         int i = slot_lookup(S, r - c0);
@@ -531,8 +584,8 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
                     P.pool_col[pos] = c;
                     P.pool_val[pos] = x;
                     my_absmax = xb > my_absmax ? xb : my_absmax;
-                    if (P.filtering && xb <= eps_bits) {
-                        exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, P.e_lsb);
+                    if (r_filt && xb <= r_eps) {
+                        exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, r_lsb);
                         ++my_cand;
                     }
                 }
@@ -547,11 +600,17 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
         if (lane == 0) {
             P.out_rb[r] = (int)base;
             P.out_re[r] = (int)(base + written);
+        }
+        if constexpr (BATCH) {
+            row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane);
+            my_absmax = 0ull;
+        } else if (lane == 0) {
             my_written += (unsigned long long)written;
         }
     }
     // the unused end of this warp's arena reads as exact zeros too
     arena_close(arena, P.pool_val, lane);
+    if constexpr (BATCH) return;
     // ---- block totals for the step statistics
     my_cand = (unsigned long long)warp_sum((int)my_cand);
     my_absmax = warp_max_u64(my_absmax);
@@ -710,6 +769,166 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     }
 }
 
+// ---------------------------------------------------------------- k_alg1_batch
+// Algorithm 1 for every filtered instance of a batched step, one cooperative
+// launch.  The instances run the recurrence of k_alg1 side by side: column
+// sums belong to the instance owning the column, each instance has its own
+// c, eps_f and pass count, and a pass streams the step's whole pool range
+// once for all instances still iterating.  Every block keeps the per-instance
+// state in shared memory and updates it from the same global column-sum
+// maxima, so all blocks take the same decisions.
+constexpr int kMaxBatch = 1024;  // instances of one batched launch
+
+__global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const size_t n = (size_t)A.n;
+    __shared__ double s_eps[kMaxBatch];  // eps_f
+    __shared__ int s_it[kMaxBatch];
+    __shared__ unsigned char s_state[kMaxBatch];  // 0 iterating, 1 finished, 2 not filtered here
+    __shared__ int s_left;
+    if (__ldcg(&A.ctl->status) & kDevPoolFull) return;  // discarded phase (same for all blocks)
+    if (threadIdx.x == 0) s_left = 0;
+    __syncthreads();
+    int left = 0;
+    for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) {
+        const BatchStep bs = A.bstep[i];
+        const bool filt = (bs.mode == kBatchProduct || bs.mode == kBatchAddOnly) && bs.eps_g > 0.0;
+        s_eps[i] = bs.eps_g;
+        s_it[i] = 0;
+        // an instance without candidates finds c = 0 in its first pass
+        const bool empty = filt && __ldcg(&A.stat_tab[i].ncand) == 0ull;
+        s_state[i] = !filt ? 2 : (empty ? 1 : 0);
+        if (empty) s_it[i] = 1;
+        left += (filt && !empty) ? 1 : 0;
+    }
+    atomicAdd(&s_left, left);
+    __syncthreads();
+    const unsigned long long cap = A.ctl->pool_cap;
+    const unsigned long long p0 = min(__ldcg(A.pool_start), cap);
+    const unsigned long long p1 = min(__ldcg(&A.ctl->pool_used), cap);
+    bool alive = true;
+    int pass = 0;
+    while (s_left > 0) {
+        // finalize the column sums of the iterating instances
+        for (int j = gt; j < A.n; j += nthreads) {
+            const int i = A.inst[j];
+            if (s_state[i] != 0) continue;
+            double v = chunk_round(A.words + j, n, A.sticky + j, A.bstep[i].e_lsb);
+            unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+            if (vb) atomicMax(&A.cslot[2 * i + (pass & 1)], vb);
+        }
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) A.cslot[2 * i + ((pass + 1) & 1)] = 0ull;
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+            alive = false;
+            break;
+        }
+        // the recurrence of every iterating instance (identical in all blocks)
+        __syncthreads();
+        if (threadIdx.x == 0) s_left = 0;
+        __syncthreads();
+        left = 0;
+        for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) {
+            if (s_state[i] != 0) continue;
+            const BatchStep bs = A.bstep[i];
+            const double c = __longlong_as_double((long long)__ldcg(&A.cslot[2 * i + (pass & 1)]));
+            const double m = c / s_eps[i];
+            const int it = ++s_it[i];
+            if (!(c > bs.bound)) {
+                s_state[i] = 1;
+                if (blockIdx.x == 0) A.stat_tab[i].dropped = c;
+            } else if (it >= bs.maxit) {
+                s_state[i] = 1;
+                if (blockIdx.x == 0) {
+                    A.stat_tab[i].dropped = c;
+                    atomicOr(&A.ctl->status, kDevNotConv);
+                }
+            } else {
+                s_eps[i] = bs.eps_g / m;
+                ++left;
+            }
+        }
+        atomicAdd(&s_left, left);
+        __syncthreads();
+        if (s_left == 0) break;
+        // accumulate the entries still below their instance's threshold
+        for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
+            unsigned long long xb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long q = q0 + (unsigned long long)u * nthreads;
+                xb[u] = q < p1 ? mag_bits(__ldcg(A.val + q)) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (xb[u] == 0ull) continue;
+                const int col = A.col[q0 + (unsigned long long)u * nthreads];
+                if ((unsigned)col >= (unsigned)A.n) {
+                    atomicOr(&A.ctl->status, kDevInternal);
+                    continue;
+                }
+                const int i = A.inst[col];
+                if (s_state[i] != 0) continue;
+                if (xb[u] <= (unsigned long long)__double_as_longlong(s_eps[i]))
+                    exact_add(A.words + col, n, A.sticky + col, xb[u], A.bstep[i].e_lsb);
+            }
+        }
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+            alive = false;
+            break;
+        }
+        ++pass;
+    }
+    if (!alive) return;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) {
+            if (s_state[i] == 2) continue;
+            A.stat_tab[i].eps_f = s_eps[i];
+            A.stat_tab[i].iters = s_it[i];
+            if (s_it[i] == 1 && __ldcg(&A.stat_tab[i].ncand) == 0ull) {
+                A.stat_tab[i].dropped = 0.0;
+                A.stat_tab[i].nnz_post = __ldcg(&A.stat_tab[i].nnz_pre);
+            }
+        }
+    // compaction: keep |x| > eps_f of the row's instance, in place
+    for (int r = gw; r < A.n; r += nwarps) {
+        const int i = A.inst[r];
+        if (s_state[i] != 1 || __ldcg(&A.stat_tab[i].ncand) == 0ull) continue;
+        const unsigned long long fb = (unsigned long long)__double_as_longlong(s_eps[i]);
+        int s = A.rb[r], e = A.re[r];
+        int w = s;
+        for (int q0 = s; q0 < e; q0 += 32) {
+            int q = q0 + lane;
+            int col = 0;
+            double x = 0.0;
+            bool keep = false;
+            if (q < e) {
+                col = A.col[q];
+                x = A.val[q];
+                keep = mag_bits(x) > fb;
+            }
+            __syncwarp();
+            unsigned m = __ballot_sync(kFull, keep);
+            if (keep) {
+                int pos = w + __popc(m & lanemask_lt());
+                A.col[pos] = col;
+                A.val[pos] = x;
+            }
+            w += __popc(m);
+            __syncwarp();
+        }
+        for (int q = w + lane; q < e; q += 32) A.val[q] = 0.0;
+        if (lane == 0) {
+            A.re[r] = w;
+            if (w > s) atomicAdd(&A.stat_tab[i].nnz_post, (unsigned long long)(w - s));
+        }
+    }
+}
+
 // ---------------------------------------------------------------- k_norms
 // Exact ||M||_1 of up to kMaxNorms matrices whose max |x| is already in
 // slots[i].absmax: accumulate every |x| into per-column fixed-point sums,
@@ -730,9 +949,24 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
         const unsigned long long cap = A.ctl->pool_cap;
         const unsigned long long p0 = min(__ldcg(&A.ctl->mark[mi]), cap);
         const unsigned long long p1 = min(__ldcg(&A.ctl->mark[mi + 1]), cap);
-        const int lsb = lsb_for_bound(A.slots[mi].absmax);
         unsigned long long* words = A.words + (size_t)mi * kChunks * n;
         unsigned* sticky = A.sticky + (size_t)mi * n;
+        if (A.inst) {
+            // batch: the fixed point of each column follows its instance's max |x|
+            for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
+                const unsigned long long xb = mag_bits(A.pool_val[q]);
+                if (xb == 0ull) continue;
+                const int c = A.pool_col[q];
+                if ((unsigned)c >= (unsigned)A.n) {
+                    atomicOr(&A.ctl->status, kDevInternal);
+                    continue;
+                }
+                const int lsb = lsb_for_bound(A.slots[(size_t)A.inst[c] * A.slot_stride + mi].absmax);
+                exact_add(words + c, n, sticky + c, xb, lsb);
+            }
+            continue;
+        }
+        const int lsb = lsb_for_bound(A.slots[mi].absmax);
         for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
             unsigned long long xb[4];
 #pragma unroll
@@ -752,11 +986,12 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
     if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
     for (long long u = gt; u < (long long)A.count * A.n; u += nthreads) {
         int mi = (int)(u / A.n), j = (int)(u % A.n);
-        int lsb = lsb_for_bound(A.slots[mi].absmax);
+        NormSlot* slot = A.inst ? A.slots + (size_t)A.inst[j] * A.slot_stride + mi : A.slots + mi;
+        int lsb = lsb_for_bound(slot->absmax);
         unsigned long long* words = A.words + (size_t)mi * kChunks * n;
         double sum = chunk_round(words + j, n, A.sticky + (size_t)mi * n + j, lsb);
         unsigned long long sb = (unsigned long long)__double_as_longlong(sum);
-        if (sb) atomicMax(&A.slots[mi].result, sb);
+        if (sb) atomicMax(&slot->result, sb);
     }
 }
 
@@ -901,6 +1136,131 @@ __global__ void k_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long long
     }
 }
 
+// ---- batches: the instance of every row (binary search over the row
+// offsets off[0..ninst], off[ninst] = n)
+__global__ void k_inst_table(int n, int ninst, const int* off, int* inst) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int lo = 0, hi = ninst - 1;  // largest i with off[i] <= r
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    inst[r] = lo;
+}
+
+// Check every input of a batch like k_validate: thread per global row.
+__global__ void k_validate_batch(int n, const int* inst, const BatchSrc* src, const int* nnz, Ctl* ctl) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int i = inst[r];
+    const BatchSrc S = src[i];
+    const int l = r - S.off;
+    bool bad = false;
+    const int s = S.rowptr[l], e = S.rowptr[l + 1];
+    if (l == 0 && s != 0) bad = true;
+    if (l == S.n - 1 && e != nnz[i]) bad = true;
+    if (s > e || s < 0 || e > nnz[i]) {
+        bad = true;
+    } else {
+        int prev = -1;
+        for (int q = s; q < e; ++q) {
+            const int c = S.col[q];
+            const bool finite = (mag_bits(S.val[q]) >> 52) != 0x7ffull;
+            if (c <= prev || c >= S.n || !finite) {
+                bad = true;
+                break;
+            }
+            prev = c;
+        }
+    }
+    if (bad) atomicOr(&ctl->status, kDevBadInput);
+}
+
+// Copy the inputs of a batch into the pool as the block-diagonal matrix
+// (columns shifted to global), rows padded to 4 entries; records each
+// instance's max |x| in absmax[i * stride].
+__global__ void k_copy_rows_batch(int n, const int* inst, const BatchSrc* src, int* rb, int* re, int* pool_col,
+                                  double* pool_val, Ctl* ctl, unsigned long long arena_size, NormSlot* absmax,
+                                  int stride) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    Arena arena;
+    for (int r = gw; r < n; r += nwarps) {
+        const int i = inst[r];
+        const BatchSrc S = src[i];
+        const int l = r - S.off;
+        const int s = S.rowptr[l], e = S.rowptr[l + 1];
+        const long long base = arena_take(arena, (unsigned long long)((e - s + 3) & ~3), arena_size, ctl, pool_val, lane);
+        if (base < 0) {
+            if (lane == 0) rb[r] = re[r] = 0;
+            continue;
+        }
+        const int padded = (e - s + 3) & ~3;
+        unsigned long long mx = 0ull;
+        for (int q = lane; q < padded; q += 32) {
+            const bool in = q < e - s;
+            const double v = in ? S.val[s + q] : 0.0;
+            pool_col[base + q] = in ? S.col[s + q] + S.off : 0;
+            pool_val[base + q] = v;
+            const unsigned long long b = mag_bits(v);
+            mx = b > mx ? b : mx;
+        }
+        mx = warp_max_u64(mx);
+        if (lane == 0) {
+            rb[r] = (int)base;
+            re[r] = (int)base + (e - s);
+            if (absmax && mx) atomicMax(&absmax[(size_t)i * stride].absmax, mx);
+        }
+    }
+    arena_close(arena, pool_val, lane);
+}
+
+// out rows <- the rows of matrix sel[inst[r]] of a table of row arrays.
+struct RowTable {
+    const int* rb[kMaxAdd + 2];
+    const int* re[kMaxAdd + 2];
+};
+__global__ void k_compose_rows(int n, const int* inst, const int* sel, RowTable T, int* out_rb, int* out_re) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int k = sel[inst[r]];
+    out_rb[r] = T.rb[k][r];
+    out_re[r] = T.re[k][r];
+}
+
+// Split the block-diagonal result (global row pointers rowptr) into the
+// instances' CSR: instance i's row pointers start at out_rp + off_i + i
+// (n_i + 1 entries, rebased to 0), its entries at rowptr[off_i] with local
+// columns.
+__global__ void k_gather_batch(int n, int ninst, const int* inst, const int* off, RowView src, const int* rowptr,
+                               int* out_rp, int* col, double* val) {
+    const int lane = threadIdx.x & 31;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gw = gt >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = gt; i < ninst; i += gridDim.x * blockDim.x)
+        out_rp[off[i + 1] + i] = rowptr[off[i + 1]] - rowptr[off[i]];
+    for (int r = gw; r < n; r += nwarps) {
+        const int i = inst[r];
+        const int o = off[i];
+        const int s = src.rb[r], e = src.re[r], d = rowptr[r];
+        if (lane == 0) out_rp[r + i] = d - rowptr[o];
+        for (int q = lane; q < e - s; q += 32) {
+            col[d + q] = src.col[s + q] - o;
+            val[d + q] = src.val[s + q];
+        }
+    }
+}
+
+// bounds[i] = rowptr[off[i]], i = 0..ninst
+__global__ void k_bounds(int ninst, const int* off, const int* rowptr, int* bounds) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= ninst) bounds[i] = rowptr[off[i]];
+}
+
 __global__ void k_identity(int n, double alpha, int* rowptr, int* col, double* val) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) {
@@ -920,7 +1280,7 @@ __global__ void k_csr_to_rows(int n, const int* rowptr, int* rb, int* re) {
 }
 
 // ---------------------------------------------------------------- launchers
-static int g_sms = 0, g_alg1_blocks = 0, g_norm_blocks = 0;
+static int g_sms = 0, g_alg1_blocks = 0, g_alg1b_blocks = 0, g_norm_blocks = 0;
 static std::atomic<long long> g_launches{0};
 
 long long launch_count() { return g_launches.load(); }
@@ -932,26 +1292,31 @@ cudaError_t kernels_init() {
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_product<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)prod_smem_bytes<true>());
-    if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_product<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)prod_smem_bytes<false>());
-    if (err != cudaSuccess) return err;
+    const void* prods[4] = {(const void*)k_product<true, false>, (const void*)k_product<false, false>,
+                            (const void*)k_product<true, true>, (const void*)k_product<false, true>};
+    const int psmem[4] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
+                          (int)prod_smem_bytes<false>()};
+    for (int i = 0; i < 4; ++i) {
+        err = cudaFuncSetAttribute(prods[i], cudaFuncAttributeMaxDynamicSharedMemorySize, psmem[i]);
+        if (err != cudaSuccess) return err;
+    }
     int per = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
     g_alg1_blocks = g_sms * (per < 2 ? per : 2);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1_batch, kAlg1Threads, 0);
+    if (err != cudaSuccess) return err;
+    g_alg1b_blocks = g_sms * (per < 2 ? per : 2);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_norms, kNormThreads, 0);
     if (err != cudaSuccess) return err;
     g_norm_blocks = g_sms * (per < 2 ? per : 2);
-    if (g_alg1_blocks <= 0 || g_norm_blocks <= 0) return cudaErrorInvalidConfiguration;
+    if (g_alg1_blocks <= 0 || g_alg1b_blocks <= 0 || g_norm_blocks <= 0) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
 }
 
 int num_sms() { return g_sms; }
 
-template <bool TAB>
+template <bool TAB, bool BATCH>
 static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
     // one wave of resident blocks, rows strided over the warps (each warp
@@ -959,14 +1324,15 @@ static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     long long blocks = ((long long)P.n + kWarps - 1) / kWarps;
     const long long cap = (long long)g_sms * (TAB ? 7 : 6);
     if (blocks > cap) blocks = cap;
-    k_product<TAB><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
+    k_product<TAB, BATCH><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
     ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st) {
     if (P.n <= 0) return cudaSuccess;
-    return table ? prod_launch<true>(P, st) : prod_launch<false>(P, st);
+    if (P.inst) return table ? prod_launch<true, true>(P, st) : prod_launch<false, true>(P, st);
+    return table ? prod_launch<true, false>(P, st) : prod_launch<false, false>(P, st);
 }
 
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {
@@ -1040,6 +1406,74 @@ cudaError_t launch_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long lon
     if (blocks < 1) blocks = 1;
     if (blocks > g_sms * 4) blocks = g_sms * 4;
     k_norm_scratch_init<<<blocks, 256, 0, st>>>(ctl, slot, words, sticky, n, nnz);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alg1_batch(const Alg1BatchArgs& A, cudaStream_t st) {
+    if (A.ninst > kMaxBatch) return cudaErrorInvalidValue;
+    cudaError_t err = cudaMemsetAsync(A.cslot, 0, sizeof(unsigned long long) * 2 * (size_t)A.ninst, st);
+    if (err != cudaSuccess) return err;
+    Alg1BatchArgs a = A;
+    void* args[] = {&a};
+    ++g_launches;
+    return cudaLaunchCooperativeKernel((const void*)k_alg1_batch, dim3(g_alg1b_blocks), dim3(kAlg1Threads), args,
+                                       0, st);
+}
+
+cudaError_t launch_inst_table(int n, int ninst, const int* off, int* inst, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_inst_table<<<(n + 255) / 256, 256, 0, st>>>(n, ninst, off, inst);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_batch(int n, const int* inst, const BatchSrc* src, const int* nnz, Ctl* ctl,
+                                  cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_validate_batch<<<(n + 255) / 256, 256, 0, st>>>(n, inst, src, nnz, ctl);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows_batch(int n, const int* inst, const BatchSrc* src, int* rb, int* re, int* pool_col,
+                                   double* pool_val, Ctl* ctl, unsigned long long arena_size, NormSlot* absmax,
+                                   int stride, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int blocks = (n + 7) / 8;
+    if (blocks > g_sms * 8) blocks = g_sms * 8;
+    k_copy_rows_batch<<<blocks, 256, 0, st>>>(n, inst, src, rb, re, pool_col, pool_val, ctl, arena_size, absmax,
+                                              stride);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compose_rows(int n, const int* inst, const int* sel, const int* const* rbs, const int* const* res,
+                                int count, int* out_rb, int* out_re, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (count > kMaxAdd + 2) return cudaErrorInvalidValue;
+    RowTable T{};
+    for (int k = 0; k < count; ++k) {
+        T.rb[k] = rbs[k];
+        T.re[k] = res[k];
+    }
+    k_compose_rows<<<(n + 255) / 256, 256, 0, st>>>(n, inst, sel, T, out_rb, out_re);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* off, const RowView& src,
+                                const int* rowptr, int* out_rp, int* col, double* val, cudaStream_t st) {
+    int blocks = (n + 7) / 8;
+    if (blocks < 1) blocks = 1;
+    if (blocks > g_sms * 16) blocks = g_sms * 16;
+    k_gather_batch<<<blocks, 256, 0, st>>>(n, ninst, inst, off, src, rowptr, out_rp, col, val);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st) {
+    k_bounds<<<(ninst + 1 + 255) / 256, 256, 0, st>>>(ninst, off, rowptr, bounds);
     ++g_launches;
     return cudaGetLastError();
 }

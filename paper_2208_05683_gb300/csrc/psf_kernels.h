@@ -28,6 +28,20 @@ cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const dou
                              cudaStream_t st);
 cudaError_t launch_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long long* words, unsigned* sticky, int n,
                                      long long nnz, cudaStream_t st);
+// batches (block-diagonal matrix of instances)
+constexpr int kMaxBatchInst = 1024;
+cudaError_t launch_alg1_batch(const Alg1BatchArgs& A, cudaStream_t st);
+cudaError_t launch_inst_table(int n, int ninst, const int* off, int* inst, cudaStream_t st);
+cudaError_t launch_validate_batch(int n, const int* inst, const BatchSrc* src, const int* nnz, Ctl* ctl,
+                                  cudaStream_t st);
+cudaError_t launch_copy_rows_batch(int n, const int* inst, const BatchSrc* src, int* rb, int* re, int* pool_col,
+                                   double* pool_val, Ctl* ctl, unsigned long long arena_size, NormSlot* absmax,
+                                   int stride, cudaStream_t st);
+cudaError_t launch_compose_rows(int n, const int* inst, const int* sel, const int* const* rbs, const int* const* res,
+                                int count, int* out_rb, int* out_re, cudaStream_t st);
+cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* off, const RowView& src,
+                                const int* rowptr, int* out_rp, int* col, double* val, cudaStream_t st);
+cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st);
 cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
 
 }  // namespace psf

@@ -162,3 +162,47 @@ def workload(name: str):
     if name == "banded_n65536_hbw5":
         return banded_random(65536, 5, seed=0, target_norm1=2.0), "exp", 1e-12
     raise KeyError(name)
+
+
+# ------------------------------------------------------- instance mixtures
+def _scaled(csr, target):
+    nrm = norm1(csr)
+    return scale(csr, target / nrm) if nrm > 0 else csr
+
+
+def mixed_instance(seed: int, n_lo: int, n_hi: int, kinds=("exp", "cosh"), tols=(1e-12,)):
+    """One instance of a size mixture: (Z, coefficient kind, tol).
+
+    n = round(exp(U[ln n_lo, ln n_hi])); the type is uniform over the 1D
+    Laplacian, the 2D Laplacian (n rounded to a square m^2) and the banded
+    random matrix of half-bandwidth 5; ||Z||_1 ~ U[1, 4]; the series kind and
+    the tolerance are drawn uniformly from ``kinds`` and ``tols``.  Everything
+    follows from ``seed``.
+    """
+    rng = np.random.default_rng([seed, 2208])
+    n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    typ = int(rng.integers(0, 3))
+    target = float(rng.uniform(1.0, 4.0))
+    kind = kinds[int(rng.integers(0, len(kinds)))]
+    tol = tols[int(rng.integers(0, len(tols)))]
+    if typ == 0:
+        Z = _scaled(laplacian_1d(max(n, 2)), target)
+    elif typ == 1:
+        m = max(2, int(round(math.sqrt(n))))
+        Z = _scaled(laplacian_2d(m), target)
+    else:
+        Z = banded_random(max(n, 6), 5, seed=seed, target_norm1=target)
+    return Z, kind, tol
+
+
+def batch_instances(count: int = 512, seed0: int = 0):
+    """The batched workload: ``count`` instances (seeds seed0..), n
+    log-uniform in [64, 4096], exp or cosh, tol 1e-12."""
+    return [mixed_instance(seed0 + i, 64, 4096) for i in range(count)]
+
+
+def serving_requests(count: int, seed0: int = 0, n_lo: int = 256, n_hi: int = 65536):
+    """Serving mixture: n log-uniform in [n_lo, n_hi], exp/cos/sinh, tol from
+    {1e-8, 1e-10, 1e-12}."""
+    return [mixed_instance(seed0 + i, n_lo, n_hi, kinds=("exp", "cos", "sinh"), tols=(1e-8, 1e-10, 1e-12))
+            for i in range(count)]

@@ -38,3 +38,22 @@ def rel_fro(gpu_csr, ref: CSR) -> float:
     G = sp.csr_matrix((val, col, rp), shape=(ref.n, ref.n))
     R = ref.to_scipy()
     return float(sp.linalg.norm(G - R) / sp.linalg.norm(R))
+
+
+def check_same(got, ref, what=""):
+    info = got.info
+    p = ref.plan
+    assert (info["N"], info["q"], info["b"], info["g"]) == (p.N, p.q, p.b, p.g), what
+    assert info["z"] == ref.norms[:11] or info["z"] == p.z[:11], what
+    assert_csr_bitwise(got.csr, ref.F, what)
+    if ref.F.nnz:
+        assert rel_fro(got.csr, ref.F) <= 1e-12
+    # per-step Algorithm 1 decisions (S_0 and the g = 1 add are kind "add")
+    gsteps = [s for s in got.steps if s["kind"] != "add"]
+    osteps = [s for s in ref.steps if not (s.kind == "giant" and s.threshold == 0.0 and s.iters == 0
+                                           and p.g == 1 and s.index == 1)]
+    assert len(gsteps) == len(osteps), what
+    for g, o in zip(gsteps, osteps):
+        assert g["nnz_pre"] == o.nnz_pre and g["nnz_post"] == o.nnz_post, (what, g, o)
+        if o.threshold > 0:
+            assert g["eps_f"] == o.eps_f and g["iters"] == o.iters and g["dropped"] == o.c, (what, g, o)

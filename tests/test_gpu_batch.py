@@ -1,0 +1,130 @@
+"""psf_eval_batch through the C ABI: many (series, Z) instances evaluated as
+one block-diagonal batch.
+
+Every instance's result must be bit for bit the oracle's filtered PS result
+(and the result of evaluating it alone with psf_eval), with the same plan and
+the same per-step Algorithm 1 decisions, whatever else is in the batch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from gpu_helpers import assert_csr_bitwise, check_same, dev, ocsr
+from oracle import CSR, psscf
+
+pytestmark = pytest.mark.gpu
+
+psf = pytest.importorskip("paper_2208_05683_gb300")
+
+
+def series_of(a, tol, **kw):
+    return psf.Series(a, tol, poly=kw.get("poly", False), filtered=kw.get("filtered", True),
+                      submult=kw.get("submult", False), s=kw.get("s", 0))
+
+
+def mixed_cases():
+    """(name, oracle CSR, coefficients, tol, options) covering the modes."""
+    poly_a = [(-1.0) ** i / math.factorial(i) for i in range(5)]
+    diag = np.zeros((40, 40))
+    diag[np.arange(0, 40, 3), np.arange(0, 40, 3)] = np.linspace(-2, 1, 14)
+    return [
+        ("lap1d exp", ocsr(syn.laplacian_1d(256)), syn.coeffs("exp"), 1e-12, {}),
+        ("lap2d cos", ocsr(syn.laplacian_2d(24)), syn.coeffs("cos"), 1e-12, {}),
+        ("banded sinh", ocsr(syn.banded_random(700, 6, 3, 2.0)), syn.coeffs("sinh"), 1e-10, {}),
+        ("lap2d cosh", ocsr(syn.laplacian_2d(20)), syn.coeffs("cosh"), 1e-12, {}),
+        ("poly N=5", ocsr(syn.banded_random(500, 2, 5, 1.5)), poly_a, 1e-11, {"poly": True}),
+        ("submult", ocsr(syn.laplacian_1d(300)), syn.coeffs("exp"), 1e-12, {"submult": True}),
+        ("unfiltered", ocsr(syn.laplacian_1d(128)), syn.coeffs("exp"), 1e-12, {"filtered": False}),
+        ("s=2", ocsr(syn.laplacian_1d(200)), syn.coeffs("exp"), 1e-12, {"s": 2}),
+        ("zero matrix", CSR.empty(64), syn.coeffs("cos"), 1e-12, {}),
+        ("n=1", CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([0.5])),
+         syn.coeffs("exp"), 1e-12, {}),
+        ("diag", CSR.from_dense(diag), syn.coeffs("exp"), 1e-12, {}),
+        ("nilpotent", CSR.from_dense(np.diag(np.full(20, 0.75), 1)), syn.coeffs("exp"), 1e-14, {}),
+        ("tol 1e-8", ocsr(syn.banded_random(900, 5, 7, 2.0)), syn.coeffs("exp"), 1e-8, {}),
+    ]
+
+
+def test_mixed_batch_bitwise_vs_oracle_and_single():
+    cases = mixed_cases()
+    series = [series_of(a, tol, **kw) for _, _, a, tol, kw in cases]
+    got = psf.eval_batch(series, [dev(Z) for _, Z, _, _, _ in cases])
+    assert len(got) == len(cases)
+    for (name, Z, a, tol, kw), g in zip(cases, got):
+        ref = psscf(Z, a, tol, **kw)
+        check_same(g, ref, name)
+        alone = series_of(a, tol, **kw).eval(dev(Z))
+        assert alone.steps == g.steps, name
+        for key in ("N", "q", "b", "g", "products", "z", "trunc", "budget", "nnz"):
+            assert alone.info[key] == g.info[key], (name, key)
+
+
+def test_batch_order_does_not_matter():
+    # the same instances in reverse order give the same results
+    cases = mixed_cases()[:8]
+    series = [series_of(a, tol, **kw) for _, _, a, tol, kw in cases]
+    Zs = [dev(Z) for _, Z, _, _, _ in cases]
+    fwd = psf.eval_batch(series, Zs)
+    rev = psf.eval_batch(series[::-1], Zs[::-1])[::-1]
+    for (name, *_), f, r in zip(cases, fwd, rev):
+        for x, y in zip(f.csr.to_host(), r.csr.to_host()):
+            assert np.array_equal(x, y), name
+        assert f.steps == r.steps, name
+
+
+def test_batched_workload_512_instances_sampled_against_oracle():
+    # the batched workload at full size (512 instances, n in [64, 4096]);
+    # a seeded sample of instances is checked against the oracle one by one
+    inst = syn.batch_instances(512)
+    series = [psf.Series(syn.coeffs(k), tol) for _, k, tol in inst]
+    got = psf.eval_batch(series, [dev(Z) for Z, _, _ in inst])
+    rng = np.random.default_rng(5)
+    sample = sorted(set(rng.choice(512, 20, replace=False).tolist()) | {int(np.argmax([len(Z[0]) for Z, _, _ in inst]))})
+    for i in sample:
+        Z, k, tol = inst[i]
+        check_same(got[i], psscf(ocsr(Z), syn.coeffs(k), tol), f"instance {i}")
+    # every instance: the result's row count and a valid CSR
+    for (Z, _, _), g in zip(inst, got):
+        rp, col, val = g.csr.to_host()
+        assert len(rp) == len(Z[0]) and rp[0] == 0 and rp[-1] == len(col)
+
+
+def test_more_instances_than_one_launch_holds():
+    # 1100 tiny instances: split into several launch groups
+    inst = [syn.mixed_instance(9000 + i, 2, 12) for i in range(1100)]
+    series = [psf.Series(syn.coeffs(k), tol) for _, k, tol in inst]
+    got = psf.eval_batch(series, [dev(Z) for Z, _, _ in inst])
+    for i in (0, 1, 511, 1023, 1024, 1025, 1099):
+        Z, k, tol = inst[i]
+        check_same(got[i], psscf(ocsr(Z), syn.coeffs(k), tol), f"instance {i}")
+
+
+def test_batch_edge_cases():
+    # a single instance, an empty (n = 0) instance, and an all-trivial batch
+    Z = ocsr(syn.laplacian_1d(100))
+    one = psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12)], [dev(Z)])
+    assert_csr_bitwise(one[0].csr, psscf(Z, syn.coeffs("exp"), 1e-12).F, "single")
+    empty = dev((np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0)))
+    res = psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12)] * 3, [dev(Z), empty, dev(Z)])
+    assert res[1].csr.n == 0 and res[1].csr.nnz == 0
+    assert_csr_bitwise(res[2].csr, psscf(Z, syn.coeffs("exp"), 1e-12).F, "after empty")
+    zeros = [CSR.empty(n) for n in (5, 17, 64)]
+    res = psf.eval_batch([psf.Series(syn.coeffs("cos"), 1e-12) for _ in zeros], [dev(z) for z in zeros])
+    for z, r in zip(zeros, res):
+        check_same(r, psscf(z, syn.coeffs("cos"), 1e-12), "zero")
+    assert psf.eval_batch([], []) == []
+
+
+def test_batch_errors_fail_the_whole_batch():
+    good = dev(ocsr(syn.laplacian_1d(50)))
+    bad = dev((np.array([0, 1, 1, 1, 1, 1], np.int32), np.array([7], np.int32), np.array([1.0])))
+    with pytest.raises(psf.PsfError) as e:
+        psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12)] * 2, [good, bad])
+    assert e.value.code == 1
+    # a series too short for its tolerance: Eq. (34) finds no truncation length
+    with pytest.raises(psf.PsfError) as e:
+        psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12), psf.Series(syn.coeffs("exp", 5), 1e-12)],
+                       [good, good])
+    assert e.value.code == 4

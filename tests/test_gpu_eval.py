@@ -12,7 +12,7 @@ import pytest
 
 import synthetic as syn
 from closed_forms import fun_lap1d, norm1_dense
-from gpu_helpers import assert_csr_bitwise, dev, ocsr, rel_fro
+from gpu_helpers import assert_csr_bitwise, check_same, dev, ocsr, rel_fro
 from oracle import CSR, psscf
 
 pytestmark = pytest.mark.gpu
@@ -26,25 +26,6 @@ def run_both(Z, a, tol, kernel="auto", chunk_cols=0, chunk_slots=0, **kw):
                      chunk_cols=chunk_cols, chunk_slots=chunk_slots).eval(dev(Z))
     ref = psscf(Z, a, tol, **kw)
     return got, ref
-
-
-def check_same(got, ref, what=""):
-    info = got.info
-    p = ref.plan
-    assert (info["N"], info["q"], info["b"], info["g"]) == (p.N, p.q, p.b, p.g), what
-    assert info["z"] == ref.norms[:11] or info["z"] == p.z[:11], what
-    assert_csr_bitwise(got.csr, ref.F, what)
-    if ref.F.nnz:
-        assert rel_fro(got.csr, ref.F) <= 1e-12
-    # per-step Algorithm 1 decisions (S_0 and the g = 1 add are kind "add")
-    gsteps = [s for s in got.steps if s["kind"] != "add"]
-    osteps = [s for s in ref.steps if not (s.kind == "giant" and s.threshold == 0.0 and s.iters == 0
-                                           and p.g == 1 and s.index == 1)]
-    assert len(gsteps) == len(osteps), what
-    for g, o in zip(gsteps, osteps):
-        assert g["nnz_pre"] == o.nnz_pre and g["nnz_post"] == o.nnz_post, (what, g, o)
-        if o.threshold > 0:
-            assert g["eps_f"] == o.eps_f and g["iters"] == o.iters and g["dropped"] == o.c, (what, g, o)
 
 
 def test_exp_lap1d_n256_bitwise_and_closed_form():
