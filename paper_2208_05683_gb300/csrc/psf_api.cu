@@ -154,6 +154,12 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     P.chunk_cols = w.chunk_cols;
     P.chunk_slots = w.chunk_slots;
     P.arena = arena_for(alen > 0.0 ? alen * (blen > 1.0 ? blen : 1.0) : 8.0 * (add.size() + 1));
+    if (filt) {
+        P.cand_col = w.cand_col.as<int>();
+        P.cand_x = w.cand_x.as<unsigned long long>();
+        P.cand_cap = w.ccap;
+        P.cand_chunk = w.cand_chunk();
+    }
     if (P.stat) CU(cudaMemcpyAsync(&P.stat->pool_start, &w.C()->pool_used, sizeof(unsigned long long),
                                    cudaMemcpyDeviceToDevice, w.st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -184,6 +190,8 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
         a.sticky = P.sticky;
         a.ctl = w.C();
         a.stat = P.stat;
+        a.cand_col = P.cand_col;
+        a.cand_x = P.cand_x;
         CU(launch_alg1(a, w.st));
     }
     *out = w.pooled(rb, re);

@@ -468,6 +468,12 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             P.stat_tab = d_stat.as<StepStat>() + si * (size_t)count;
             P.chunk_cols = w.chunk_cols;
             P.chunk_slots = w.chunk_slots;
+            if (T.any_filter) {
+                P.cand_col = w.cand_col.as<int>();
+                P.cand_x = w.cand_x.as<unsigned long long>();
+                P.cand_cap = w.ccap;
+                P.cand_chunk = w.cand_chunk();
+            }
             const double fma_row = T.work_rows > 0.0 ? T.work_fma / T.work_rows : 8.0 * (T.nadd + 1);
             P.arena = arena_for(fma_row);
             CU(cudaMemcpyAsync(d_pstart.as<unsigned long long>() + si, &w.C()->pool_used, sizeof(unsigned long long),
@@ -500,6 +506,8 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 a.pool_start = d_pstart.as<unsigned long long>() + si;
                 a.ctl = w.C();
                 a.stat_tab = P.stat_tab;
+                a.cand_col = P.cand_col;
+                a.cand_x = P.cand_x;
                 CU(launch_alg1_batch(a, st));
             }
             const RowView out = w.pooled(rb, re);

@@ -32,6 +32,12 @@ struct Ctl {
     unsigned long long nnz_total;  // row-length scan result
     int maxwin;                    // widest row (last - first column + 1) of validated inputs
     int status;
+    // Algorithm 1 candidate lists (two buffers of cand_cap entries): entry
+    // counts, and a flag set when the product's list overflowed
+    unsigned long long cand_cnt[2];
+    unsigned long long cand_cap;
+    int cand_over;
+    unsigned cand_chunk;  // entries a warp reserves at a time (32..128)
     unsigned bar_count;  // fields from here on survive a pool reset
     unsigned bar_gen;
     int pad;
@@ -112,6 +118,11 @@ struct ProductArgs {
     int chunk_cols;             // > 0: fewer columns per chunk (exercises chunking)
     int chunk_slots;            // > 0: fewer accumulator slots per chunk
     unsigned long long arena;   // pool entries a warp takes at a time (multiple of 4)
+    // Algorithm 1 candidates (0 < |x| <= eps_g) appended to list 0 (nullptr: none)
+    int* cand_col;
+    unsigned long long* cand_x;  // |x| bits
+    unsigned long long cand_cap;
+    unsigned cand_chunk;
     // batch (inst == nullptr: one instance, the fields above apply to all rows)
     const int* inst;            // instance of each row, n entries
     const BatchStep* bstep;     // per instance
@@ -138,6 +149,8 @@ struct Alg1BatchArgs {
     const unsigned long long* pool_start;  // pool counter before the step's product
     Ctl* ctl;
     StepStat* stat_tab;  // per instance
+    int* cand_col;       // two candidate lists of ctl->cand_cap entries each
+    unsigned long long* cand_x;
 };
 
 // One input matrix of a batch (device CSR, 0-based local columns).
@@ -161,6 +174,8 @@ struct Alg1Args {
     unsigned* sticky;
     Ctl* ctl;
     StepStat* stat;
+    int* cand_col;               // two candidate lists of ctl->cand_cap entries each
+    unsigned long long* cand_x;
 };
 
 // Matrix i of the norm kernel occupies the pool entries [mark[i], mark[i+1])
@@ -369,6 +384,52 @@ __device__ __forceinline__ void exact_add_checked(unsigned long long* words, uns
     } else {
         atomicOr(&ctl->status, kDevInternal);
     }
+}
+
+// Candidate lists of Algorithm 1.  A list holds the entries that can still
+// be dropped: pass 1 (in the product's write-back) appends every entry with
+// 0 < |x| <= eps_g; a later pass with threshold eps_f keeps the entries with
+// |x| <= eps_f (an entry above it stays in the matrix for good, since eps_f
+// only decreases) and adds them to the exact column sums.  A warp reserves
+// list space `chunk` entries at a time (one atomic per chunk, so the counter
+// is not contended) and clears the unused end of a chunk when it takes the
+// next one or finishes: a list entry with |x| bits 0 is a hole.  A list that
+// runs out of space sets the overflow flag; its consumer then scans the
+// step's pool range instead.
+
+struct CandArena {
+    unsigned long long next = 0, end = 0;
+};
+
+__device__ __forceinline__ void cand_close(CandArena& a, unsigned long long* out_x, int lane) {
+    for (unsigned long long q = a.next + lane; q < a.end; q += 32) out_x[q] = 0ull;
+    a.next = a.end = 0;
+}
+
+__device__ __forceinline__ void cand_push(CandArena& a, bool keep, int col, unsigned long long xb, int* out_col,
+                                          unsigned long long* out_x, unsigned long long* counter,
+                                          unsigned long long cap, unsigned chunk, int* over, int lane) {
+    const unsigned km = __ballot_sync(kFull, keep);
+    if (!km) return;
+    const unsigned k = (unsigned)__popc(km);
+    if (a.next + k > a.end) {
+        cand_close(a, out_x, lane);
+        unsigned long long b = 0ull;
+        if (lane == 0) b = atomicAdd(counter, (unsigned long long)chunk);
+        b = __shfl_sync(kFull, b, 0);
+        if (b + chunk > cap) {  // full: the consumer scans the pool instead
+            if (lane == 0) *over = 1;
+            return;
+        }
+        a.next = b;
+        a.end = b + chunk;
+    }
+    if (keep) {
+        const unsigned long long i = a.next + (unsigned)__popc(km & lanemask_lt());
+        out_col[i] = col;
+        out_x[i] = xb;
+    }
+    a.next += k;
 }
 
 // Grid-wide barrier for cooperative launches, with a bounded wait: after

@@ -96,8 +96,8 @@ extern Profile g_prof;
 struct Work {
     int n = 0;
     cudaStream_t st = nullptr;
-    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val;
-    unsigned long long cap = 0;
+    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val, cand_col, cand_x;
+    unsigned long long cap = 0, ccap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
     int chunk_cols = 0, chunk_slots = 0;
@@ -128,11 +128,25 @@ struct Work {
             CU(pool_col.alloc(sizeof(int) * entries, st));
             CU(pool_val.alloc(sizeof(double) * entries, st));
             cap = entries;
+            // two Algorithm 1 candidate lists of half the pool each (a step
+            // whose candidates do not fit falls back to full scans)
+            ccap = cap / 2 > 1024 ? cap / 2 : 1024;
+            CU(cand_col.alloc(sizeof(int) * 2 * ccap, st));
+            CU(cand_x.alloc(sizeof(unsigned long long) * 2 * ccap, st));
         }
         Ctl h{};
         h.pool_cap = cap;
+        h.cand_cap = ccap;
+        h.cand_chunk = cand_chunk();
         CU(cudaMemcpyAsync(ctl.p, &h, offsetof(Ctl, bar_count), cudaMemcpyHostToDevice, st));
         return PSF_OK;
+    }
+    // Entries a warp reserves in a candidate list at a time: up to 128, so
+    // that about 12k warps' unused chunk ends take at most a quarter of it.
+    unsigned cand_chunk() const {
+        unsigned long long c = ccap / (4ull * 12288ull);
+        c = c < 32ull ? 32ull : (c > 128ull ? 128ull : c);
+        return (unsigned)(c & ~31ull);
     }
     // Column-sum accumulators are zero between steps; a phase cut short by a
     // pool overflow can leave some set, so they are cleared before its retry.

@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
     const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
     unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
     Arena arena;
+    CandArena carena;
 
     for (int r = blockIdx.x * kWarps + wib; r < P.n; r += gridDim.x * kWarps) {
         // ---- the row's terms: single instance, every term and the product;
@@ -579,16 +580,20 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
                 unsigned long long xb = mag_bits(x);
                 bool nz = i < cnt && xb != 0ull;
                 unsigned m = __ballot_sync(kFull, nz);
+                const bool cand = nz && r_filt && xb <= r_eps;
                 if (nz) {
                     long long pos = (long long)base + written + __popc(m & lanemask_lt());
                     P.pool_col[pos] = c;
                     P.pool_val[pos] = x;
                     my_absmax = xb > my_absmax ? xb : my_absmax;
-                    if (r_filt && xb <= r_eps) {
+                    if (cand) {
                         exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, r_lsb);
                         ++my_cand;
                     }
                 }
+                if (P.cand_col)
+                    cand_push(carena, cand, c, xb, P.cand_col, P.cand_x, &P.ctl->cand_cnt[0], P.cand_cap,
+                              P.cand_chunk, &P.ctl->cand_over, lane);
                 written += __popc(m);
             }
             __syncwarp();
@@ -608,8 +613,10 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_pro
             my_written += (unsigned long long)written;
         }
     }
-    // the unused end of this warp's arena reads as exact zeros too
+    // the unused end of this warp's arena reads as exact zeros too, and the
+    // unused end of its candidate chunk as holes
     arena_close(arena, P.pool_val, lane);
+    if (P.cand_col) cand_close(carena, P.cand_x, lane);
     if constexpr (BATCH) return;
     // ---- block totals for the step statistics
     my_cand = (unsigned long long)warp_sum((int)my_cand);
@@ -661,6 +668,9 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     // complete, so there is nothing to filter (every block reads the same
     // status, set by an earlier launch)
     if (__ldcg(&A.ctl->status) & kDevPoolFull) return;
+    bool over = __ldcg(&A.ctl->cand_over) != 0 || A.cand_col == nullptr;
+    const unsigned long long ccap = A.ctl->cand_cap;
+    const unsigned cchunk = A.ctl->cand_chunk;
     if (__ldcg(&A.stat->ncand) == 0ull) {
         // the product left no entry with |x| <= eps_g: the first pass finds an
         // empty candidate matrix (c = 0), nothing is dropped
@@ -688,7 +698,10 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
             v = warp_max_u64(v);
             if (threadIdx.x == 0) {
                 if (v) atomicMax(&A.ctl->cslot[it & 1], v);
-                if (blockIdx.x == 0) A.ctl->cslot[(it + 1) & 1] = 0ull;
+                if (blockIdx.x == 0) {
+                    A.ctl->cslot[(it + 1) & 1] = 0ull;
+                    A.ctl->cand_cnt[(it + 1) & 1] = 0ull;  // the next rescan's output list
+                }
             }
         }
         if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
@@ -705,6 +718,33 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         }
         eps_f = A.eps_g / m;
         const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
+        if (!over) {
+            // rescan the candidates of the previous pass (list (it-1)&1) into list it&1
+            const int bi = (it - 1) & 1, bo = it & 1;
+            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), ccap);
+            const int* ic = A.cand_col + (size_t)bi * ccap;
+            const unsigned long long* ix = A.cand_x + (size_t)bi * ccap;
+            CandArena ca;
+            for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += (unsigned long long)nthreads) {
+                const unsigned long long q = q0 + (unsigned long long)lane;
+                const bool in = q < cnt;
+                const unsigned long long xb = in ? __ldcg(ix + q) : 0ull;
+                const int col = in && xb ? __ldcg(ic + q) : 0;
+                const bool keep = in && xb != 0ull && xb <= fb;
+                if (keep) exact_add_checked(A.words, A.sticky, col, A.n, xb, A.e_lsb, A.ctl);
+                cand_push(ca, keep, col, xb, A.cand_col + (size_t)bo * ccap, A.cand_x + (size_t)bo * ccap,
+                          &A.ctl->cand_cnt[bo], ccap, cchunk, &A.ctl->cand_over, lane);
+            }
+            cand_close(ca, A.cand_x + (size_t)bo * ccap, lane);
+            if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+                alive = false;
+                break;
+            }
+            // a list that overflowed is incomplete: scan the pool from now on
+            // (the flag is read after the barrier, so every block agrees)
+            over = __ldcg(&A.ctl->cand_over) != 0;
+            continue;
+        }
         // accumulate the entries still below the threshold: one streaming
         // pass over the step's pool range (its gaps hold exact zeros)
         for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
@@ -728,6 +768,20 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         }
     }
     if (!alive) return;
+    if (gt == 0) {  // the lists are empty for the next step
+        A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = 0ull;
+        A.ctl->cand_over = 0;
+    }
+    if (!(c > 0.0)) {
+        // nothing was dropped: the matrix stays as the product wrote it
+        if (gt == 0) {
+            A.stat->eps_f = eps_f;
+            A.stat->iters = it;
+            A.stat->dropped = c;
+            A.stat->nnz_post = __ldcg(&A.stat->nnz_pre);
+        }
+        return;
+    }
 
     // compaction: keep |x| > eps_f, in place, column order preserved
     const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
@@ -787,6 +841,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
     const int nthreads = gridDim.x * blockDim.x;
     const size_t n = (size_t)A.n;
     __shared__ double s_eps[kMaxBatch];  // eps_f
+    __shared__ double s_c[kMaxBatch];    // last column-sum maximum c
     __shared__ int s_it[kMaxBatch];
     __shared__ unsigned char s_state[kMaxBatch];  // 0 iterating, 1 finished, 2 not filtered here
     __shared__ int s_left;
@@ -798,6 +853,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         const BatchStep bs = A.bstep[i];
         const bool filt = (bs.mode == kBatchProduct || bs.mode == kBatchAddOnly) && bs.eps_g > 0.0;
         s_eps[i] = bs.eps_g;
+        s_c[i] = 0.0;
         s_it[i] = 0;
         // an instance without candidates finds c = 0 in its first pass
         const bool empty = filt && __ldcg(&A.stat_tab[i].ncand) == 0ull;
@@ -810,6 +866,9 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
     const unsigned long long cap = A.ctl->pool_cap;
     const unsigned long long p0 = min(__ldcg(A.pool_start), cap);
     const unsigned long long p1 = min(__ldcg(&A.ctl->pool_used), cap);
+    bool over = __ldcg(&A.ctl->cand_over) != 0 || A.cand_col == nullptr;
+    const unsigned long long ccap = A.ctl->cand_cap;
+    const unsigned cchunk = A.ctl->cand_chunk;
     bool alive = true;
     int pass = 0;
     while (s_left > 0) {
@@ -821,8 +880,10 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
             unsigned long long vb = (unsigned long long)__double_as_longlong(v);
             if (vb) atomicMax(&A.cslot[2 * i + (pass & 1)], vb);
         }
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
             for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) A.cslot[2 * i + ((pass + 1) & 1)] = 0ull;
+            if (threadIdx.x == 0) A.ctl->cand_cnt[(pass + 1) & 1] = 0ull;  // the next rescan's output list
+        }
         if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
             alive = false;
             break;
@@ -838,15 +899,12 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
             const double c = __longlong_as_double((long long)__ldcg(&A.cslot[2 * i + (pass & 1)]));
             const double m = c / s_eps[i];
             const int it = ++s_it[i];
+            s_c[i] = c;
             if (!(c > bs.bound)) {
                 s_state[i] = 1;
-                if (blockIdx.x == 0) A.stat_tab[i].dropped = c;
             } else if (it >= bs.maxit) {
                 s_state[i] = 1;
-                if (blockIdx.x == 0) {
-                    A.stat_tab[i].dropped = c;
-                    atomicOr(&A.ctl->status, kDevNotConv);
-                }
+                if (blockIdx.x == 0) atomicOr(&A.ctl->status, kDevNotConv);
             } else {
                 s_eps[i] = bs.eps_g / m;
                 ++left;
@@ -855,6 +913,40 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         atomicAdd(&s_left, left);
         __syncthreads();
         if (s_left == 0) break;
+        if (!over) {
+            // rescan the candidates of the previous pass into the other list
+            const int bi = pass & 1, bo = (pass + 1) & 1;
+            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), ccap);
+            const int* ic = A.cand_col + (size_t)bi * ccap;
+            const unsigned long long* ix = A.cand_x + (size_t)bi * ccap;
+            CandArena ca;
+            for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += (unsigned long long)nthreads) {
+                const unsigned long long q = q0 + (unsigned long long)lane;
+                const bool in = q < cnt;
+                const unsigned long long xb = in ? __ldcg(ix + q) : 0ull;
+                const int col = in && xb ? __ldcg(ic + q) : 0;
+                bool keep = false;
+                if (in && xb) {
+                    if ((unsigned)col >= (unsigned)A.n) {
+                        atomicOr(&A.ctl->status, kDevInternal);
+                    } else {
+                        const int i = A.inst[col];
+                        keep = s_state[i] == 0 && xb <= (unsigned long long)__double_as_longlong(s_eps[i]);
+                        if (keep) exact_add(A.words + col, n, A.sticky + col, xb, A.bstep[i].e_lsb);
+                    }
+                }
+                cand_push(ca, keep, col, xb, A.cand_col + (size_t)bo * ccap, A.cand_x + (size_t)bo * ccap,
+                          &A.ctl->cand_cnt[bo], ccap, cchunk, &A.ctl->cand_over, lane);
+            }
+            cand_close(ca, A.cand_x + (size_t)bo * ccap, lane);
+            if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+                alive = false;
+                break;
+            }
+            over = __ldcg(&A.ctl->cand_over) != 0;  // read after the barrier: every block agrees
+            ++pass;
+            continue;
+        }
         // accumulate the entries still below their instance's threshold
         for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
             unsigned long long xb[4];
@@ -884,20 +976,23 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         ++pass;
     }
     if (!alive) return;
+    if (gt == 0) {  // the lists are empty for the next step
+        A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = 0ull;
+        A.ctl->cand_over = 0;
+    }
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) {
             if (s_state[i] == 2) continue;
             A.stat_tab[i].eps_f = s_eps[i];
             A.stat_tab[i].iters = s_it[i];
-            if (s_it[i] == 1 && __ldcg(&A.stat_tab[i].ncand) == 0ull) {
-                A.stat_tab[i].dropped = 0.0;
-                A.stat_tab[i].nnz_post = __ldcg(&A.stat_tab[i].nnz_pre);
-            }
+            A.stat_tab[i].dropped = s_c[i];
+            if (!(s_c[i] > 0.0)) A.stat_tab[i].nnz_post = __ldcg(&A.stat_tab[i].nnz_pre);  // nothing dropped
         }
-    // compaction: keep |x| > eps_f of the row's instance, in place
+    // compaction of the instances that dropped entries: keep |x| > eps_f of
+    // the row's instance, in place
     for (int r = gw; r < A.n; r += nwarps) {
         const int i = A.inst[r];
-        if (s_state[i] != 1 || __ldcg(&A.stat_tab[i].ncand) == 0ull) continue;
+        if (s_state[i] != 1 || !(s_c[i] > 0.0)) continue;
         const unsigned long long fb = (unsigned long long)__double_as_longlong(s_eps[i]);
         int s = A.rb[r], e = A.re[r];
         int w = s;
