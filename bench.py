@@ -309,6 +309,11 @@ def run_psf(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(rp, col, val)
+    batched = serving = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = measure_batched(args, dev, flush)
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = measure_serving(args, dev)
 
     if rank == 0:
         lat_sorted = sorted(lat)
@@ -328,10 +333,134 @@ def run_psf(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "dense_ps": dense,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_batched(args, dev, flush):
+    """The batched workload: 512 instances (n log-uniform in [64, 4096], 1D/2D
+    Laplacian or banded, ||Z||_1 in [1, 4], exp or cosh, tol 1e-12) in one
+    psf_eval_batch call, against the same instances evaluated one by one."""
+    import ctypes
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    from paper_2208_05683_gb300 import _abi
+    L = psf.lib()
+    stream = torch.cuda.current_stream()
+    inst = syn.batch_instances(512)
+    series = [psf.Series(syn.coeffs(k), tol) for _, k, tol in inst]
+    Zs = [psf.DeviceCSR.from_host(*Z, device=dev) for Z, _, _ in inst]
+    count = len(Zs)
+    sh = (ctypes.c_void_p * count)(*[x._h.value for x in series])
+    zs = (_abi.CSRStruct * count)(*[z._struct() for z in Zs])
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def once():
+        outs = (ctypes.c_void_p * count)()
+        _abi.check(L.psf_eval_batch(sh, zs, count, sp, outs))
+        for i in range(count):
+            _abi.check(L.psf_result_destroy(ctypes.c_void_p(outs[i])))
+
+    for _ in range(3):
+        once()
+    reps, ms = 5, []
+    c0 = ctypes_i64(L.psf_launch_count)
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        once()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = (ctypes_i64(L.psf_launch_count) - c0) / reps
+    _abi.check(L.psf_profile(1))
+    once()
+    torch.cuda.synchronize()
+    nl, pms, fma = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _abi.check(L.psf_profile_read(ctypes.byref(nl), ctypes.byref(pms), ctypes.byref(fma), 1))
+    _abi.check(L.psf_profile(0))
+    # the same instances one psf_eval at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for x, z in zip(series, Zs):
+        _abi.check(L.psf_result_destroy(x.eval_handle(z, stream)))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    med = statistics.median(ms)
+    return {"instances": count, "rows": int(sum(z.n for z in Zs)), "nnz": int(sum(z.nnz for z in Zs)),
+            "inst_per_s": count / (med / 1e3), "ms_per_batch": med, "launches_per_batch": launches,
+            "product_tflops": 2.0 * fma.value / (pms.value / 1e3) / 1e12 if pms.value > 0 else None,
+            "algorithmic_fma": fma.value,
+            "sequential_inst_per_s": count / t_seq, "speedup_vs_sequential": (count / (med / 1e3)) / (count / t_seq),
+            "how": "median of 5 event-timed psf_eval_batch calls (L2 flushed before each), inputs resident"}
+
+
+def measure_serving(args, dev):
+    """Serving: a Poisson stream of requests (n log-uniform in [256, 65536],
+    1D/2D Laplacian or banded, exp/cos/sinh, tol from {1e-8, 1e-10, 1e-12})
+    through the library's server at 0.7x its measured saturated rate."""
+    import numpy as np
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    count = args.serving_requests
+    reqs = syn.serving_requests(count, seed0=0)
+    series = [psf.Series(syn.coeffs(k), tol) for _, k, tol in reqs]
+    Zs = [psf.DeviceCSR.from_host(*Z, device=dev) for Z, _, _ in reqs]
+    workers, max_batch = 4, 16
+    srv = psf.Server(workers=workers, max_batch=max_batch)
+    try:
+        def drain(k):
+            got = []
+            while len(got) < k:
+                got += srv.poll(256, 100, take=False)
+            return got
+
+        for i in range(min(24, count)):  # warm-up: pool sizes, kernels
+            srv.submit(series[i], Zs[i], i)
+        drain(min(24, count))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(count):
+            srv.submit(series[i], Zs[i], i)
+        drain(count)
+        sat = count / (time.perf_counter() - t0)
+        rate = 0.7 * sat
+        rng = np.random.default_rng(1)
+        gaps = rng.exponential(1.0 / rate, count)
+        done = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for i in range(count):
+            t_next += gaps[i]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                done += srv.poll(256, int(max(0.0, (t_next - now) * 1e3)), take=False)
+            srv.submit(series[i], Zs[i], count + i)
+        done += drain(count - len(done))
+        t_end = time.perf_counter()
+        stats = srv.stats()
+    finally:
+        srv.close()
+    lat = sorted(c["latency_ms"] for c in done)
+    return {"requests": count, "rate_per_s": rate, "evals_per_s": count / (t_end - t_start),
+            "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "saturated_evals_per_s": sat, "mean_batch": float(np.mean([c["batch_size"] for c in done])),
+            "max_concurrent": stats["max_concurrent"], "failed": stats["failed"], "workers": workers,
+            "max_batch": max_batch,
+            "sample": f"{count} requests (seeds 0..{count - 1}) of the serving mixture; Poisson arrivals at 0.7x "
+                      "the saturated rate measured on the same requests",
+            "latency": "host clock, submit to result available"}
 
 
 def ctypes_i64(fn) -> int:
@@ -369,6 +498,9 @@ def main():
     ap.add_argument("--impl", choices=["psf", "reference"], default="psf")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense FP64 PS baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=300, help="requests of the serving measurement")
     args = ap.parse_args()
     if args.case:
         run_case(args)

@@ -145,13 +145,81 @@ PSF_API int psf_series_destroy(psf_series_t series);
 PSF_API int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t* out);
 
 /*
- * Evaluate `count` independent instances Zs[i] with series[i] in one pass:
- * each PS stage of all instances runs as one kernel launch over the union of
- * their rows.  Results are bitwise identical to psf_eval on each instance.
- * outs[i] receives each result.  Synchronizes `stream` twice.
+ * Evaluate `count` independent instances Zs[i] (each square, any size n_i)
+ * with series[i] (Algorithm 2 each).  The instances are laid out as one
+ * block-diagonal matrix, so every stage (each of Z^2..Z^10, each baby step,
+ * S_0, each giant step) of all instances runs as one launch of the product
+ * kernel and, where filtered, one launch of the Algorithm 1 kernel; the
+ * number of launches depends on the largest q_i and b_i, not on `count`.
+ * Instances differ per stage only in small device tables (what the stage
+ * does to the instance, its coefficients and Algorithm 1 threshold).
+ * Results are bitwise identical to psf_eval on each instance, whatever else
+ * is in the batch; outs[i] receives instance i's result (all results of a
+ * batch share one device allocation, released with the last of them).
+ * Slot-map and chunking parameters are taken from series[0].
+ * Synchronizes `stream` three times (validation, norms, result sizes).
+ * Instances are processed in groups of at most 1024 instances and 2^24 rows.
+ * Errors: any instance's error fails the whole call (outs[i] all NULL);
+ * the message names the instance where it is known.
  */
 PSF_API int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, int32_t count, void* stream,
                    psf_result_t* outs);
+
+/*
+ * Serving loop with continuous batching (no counterpart in the paper, which
+ * evaluates one matrix at a time).
+ *
+ * `workers` host threads each own a CUDA stream.  A worker that is free
+ * admits the oldest waiting requests, as many as fit both `max_batch` and
+ * the device-memory budget (each request's footprint is predicted from its
+ * n and nnz), and evaluates them together as one psf_eval_batch on its
+ * stream.  Requests that arrive while other batches are running are admitted
+ * by the next free worker as soon as memory allows, so their work overlaps
+ * on the device with the batches in flight.  A request that would not fit
+ * the budget even alone is admitted when nothing else is in flight.  If a
+ * batch fails, its requests are evaluated again one by one, so a bad request
+ * fails alone.  Results are bitwise identical to psf_eval.
+ *
+ * psf_server_submit: Z (device CSR) must stay valid, and neither the series
+ *   nor Z may be changed or destroyed, until the request's completion has been
+ *   polled.  `tag` is returned with the completion.  Thread-safe.
+ * psf_server_poll: up to `max` completions, waiting up to `wait_ms` (-1:
+ *   until at least one is available or nothing is pending) for the first;
+ *   *got receives the number returned.  Each completion owns its result
+ *   (destroy it with psf_result_destroy before psf_server_destroy).
+ * psf_server_destroy: waits for the requests in flight and drops the
+ *   completions not polled (their results are destroyed).
+ */
+typedef struct psf_server_s* psf_server_t;
+
+typedef struct {
+    int32_t workers;      /* host threads = concurrent batches (default 4) */
+    int32_t max_batch;    /* requests per batch (default 64, <= 1024) */
+    int64_t hbm_budget;   /* bytes of device memory for requests in flight (0: half the free memory) */
+} psf_server_config_t;
+
+typedef struct {
+    uint64_t tag;         /* as submitted */
+    int32_t status;       /* PSF_OK or the request's error code */
+    int32_t batch_size;   /* requests evaluated together with this one (itself included) */
+    psf_result_t result;  /* NULL unless status == PSF_OK */
+    double queue_ms;      /* submit -> admission */
+    double latency_ms;    /* submit -> result available */
+} psf_completion_t;
+
+typedef struct {
+    int64_t submitted, completed, failed, batches;
+    int32_t max_concurrent;  /* most batches in flight at once */
+    int32_t pending;         /* waiting for admission */
+    int64_t budget_peak;     /* most predicted bytes in flight at once */
+} psf_server_stats_t;
+
+PSF_API int psf_server_create(const psf_server_config_t* config, psf_server_t* out);
+PSF_API int psf_server_submit(psf_server_t server, psf_series_t series, const psf_csr_t* Z, uint64_t tag);
+PSF_API int psf_server_poll(psf_server_t server, psf_completion_t* out, int32_t max, int32_t wait_ms,
+                            int32_t* got);
+PSF_API int psf_server_stats(psf_server_t server, psf_server_stats_t* stats);
+PSF_API int psf_server_destroy(psf_server_t server);
 
 /*
  * One filtered product, the building block of every PS step:

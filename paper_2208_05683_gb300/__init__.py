@@ -7,7 +7,8 @@ library.  Matrices are square CSR on the GPU (``DeviceCSR``: int32 row
 pointers and columns, float64 values, torch tensors on a CUDA device).
 
     Series(coeffs, tol, ...).eval(Z)        Algorithm 2 (filtered PS)
-    eval_batch([...series], [...Z])         many instances at once
+    eval_batch([...series], [...Z])         many instances at once (one block-diagonal batch)
+    Server(...).submit / poll               serving loop with continuous batching
     product_filter(A, B, addends, thr)      one filtered product (Eq. 11/14 + Alg. 1)
     norm1(M)                                exact ||M||_1
     norm1_noalloc(M)                        the same, without allocating device memory
@@ -26,11 +27,11 @@ from . import _build
 from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_SUBMULT, PSF_PARAM_ALG1_MAXIT,
                    PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS,
                    PSF_PARAM_CHUNK_SLOTS, PSF_MAX_Q, PSF_NORM1_NOALLOC_MAX_N,
-                   PsfError, CSRStruct, InfoStruct, StepStruct, lib, check)
+                   PsfError, CSRStruct, InfoStruct, StepStruct, ServerConfig, Completion, ServerStats, lib, check)
 
 __all__ = [
     "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "norm1_noalloc", "plan",
-    "PsfError",
+    "Server", "PsfError",
     "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_MAX_Q", "build", "lib",
 ]
 
@@ -192,6 +193,67 @@ def eval_batch(series, Zs, stream=None):
     outs = (ctypes.c_void_p * count)()
     check(L.psf_eval_batch(sh, zs, count, st, outs))
     return [_take_result(ctypes.c_void_p(outs[i]), st) for i in range(count)]
+
+
+class Server:
+    """Serving loop of the library (psf_server_*): requests are admitted by
+    worker threads as workers and device memory free up, evaluated in
+    batches, and overlap on the GPU.  ``submit`` keeps the series and Z
+    alive until the request's completion has been polled."""
+
+    def __init__(self, workers: int = 4, max_batch: int = 64, hbm_budget: int = 0):
+        cfg = ServerConfig(int(workers), int(max_batch), int(hbm_budget))
+        h = ctypes.c_void_p()
+        check(lib().psf_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, series: Series, Z: DeviceCSR, tag: int) -> None:
+        zs = Z._struct()
+        check(lib().psf_server_submit(self._h, series._h, ctypes.byref(zs), ctypes.c_uint64(int(tag))))
+        self._keep[int(tag)] = (series, Z)
+
+    def poll(self, max_items: int = 64, wait_ms: int = -1, take: bool = True):
+        """Completed requests: dicts with tag, status, batch_size, queue_ms,
+        latency_ms and result (a Result, or None if the request failed or
+        ``take`` is False, in which case the result is released unread)."""
+        torch = _torch()
+        buf = (Completion * max(1, max_items))()
+        got = ctypes.c_int32()
+        check(lib().psf_server_poll(self._h, buf, int(max_items), int(wait_ms), ctypes.byref(got)))
+        out = []
+        for i in range(got.value):
+            c = buf[i]
+            res = None
+            if c.status == PSF_OK and c.result and not take:
+                check(lib().psf_result_destroy(ctypes.c_void_p(c.result)))
+            elif c.status == PSF_OK and c.result:
+                st = torch.cuda.current_stream()
+                res = _take_result(ctypes.c_void_p(c.result), _stream_ptr(st), keep=True)
+                st.synchronize()  # the copy is done before the result is freed on its own stream
+                check(lib().psf_result_destroy(ctypes.c_void_p(c.result)))
+            self._keep.pop(int(c.tag), None)
+            out.append({"tag": int(c.tag), "status": int(c.status), "batch_size": int(c.batch_size),
+                        "queue_ms": c.queue_ms, "latency_ms": c.latency_ms, "result": res})
+        return out
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(lib().psf_server_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().psf_server_destroy(h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def product_filter(A: DeviceCSR | None, B: DeviceCSR | None, addends=(), threshold: float = 0.0,

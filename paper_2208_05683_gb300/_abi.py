@@ -20,7 +20,8 @@ ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT
 EXPORTS = [
     "psf_version", "psf_last_error", "psf_series_create", "psf_series_set_param",
     "psf_series_destroy", "psf_eval", "psf_eval_batch", "psf_product_filter", "psf_norm1",
-    "psf_norm1_noalloc",
+    "psf_norm1_noalloc", "psf_server_create", "psf_server_submit", "psf_server_poll", "psf_server_stats",
+    "psf_server_destroy",
     "psf_plan", "psf_result_csr", "psf_result_copy", "psf_result_info", "psf_result_step",
     "psf_result_destroy", "psf_launch_count", "psf_profile", "psf_profile_read",
 ]
@@ -35,6 +36,24 @@ class PsfError(RuntimeError):
 class CSRStruct(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("rowptr", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("result", ctypes.c_void_p), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("max_concurrent", ctypes.c_int32), ("pending", ctypes.c_int32),
+                ("budget_peak", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class InfoStruct(ctypes.Structure):
@@ -100,6 +119,11 @@ def _declare(h: ctypes.CDLL) -> None:
                                      i32, vp, ctypes.POINTER(vp)]
     h.psf_norm1.argtypes = [csrp, vp, ctypes.POINTER(f64)]
     h.psf_norm1_noalloc.argtypes = [csrp, vp, ctypes.POINTER(f64)]
+    h.psf_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    h.psf_server_submit.argtypes = [vp, vp, csrp, ctypes.c_uint64]
+    h.psf_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32, i32, ctypes.POINTER(i32)]
+    h.psf_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    h.psf_server_destroy.argtypes = [vp]
     h.psf_plan.argtypes = [ctypes.POINTER(f64), i64, i32, f64, ctypes.c_uint32, ctypes.POINTER(f64),
                            ctypes.POINTER(InfoStruct), ctypes.POINTER(f64), ctypes.POINTER(f64)]
     h.psf_result_csr.argtypes = [vp, csrp]
