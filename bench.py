@@ -483,7 +483,8 @@ def run_case(args):
     res = psf.Series(syn.coeffs(args.kind), TOL, pool_entries=200_000_000, kernel=args.kernel).eval(Z)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "kind": args.kind, "nnz": res.csr.nnz, "N": res.info["N"],
-                      "fma": res.info["fma"]}))
+                      "fma": res.info["fma"], "step_fma": [s["fma"] for s in res.steps],
+                      "step_kind": [s["kind"] for s in res.steps]}))
 
 
 def main():

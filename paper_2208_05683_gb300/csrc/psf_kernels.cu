@@ -377,12 +377,23 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
     for (int kk = 0; kk < cnt; ++kk) {
-        if (S.kl[kk] == 0) continue;
+        const int len = S.kl[kk];
+        if (len == 0) continue;
         const double a = S.ka[kk];
-        for (int off = 0; off < S.kl[kk]; off += 128) {
-            Chunk ch;
-            chunk_load<false>(bcol, bval, S, kk, off, lane, ch);
-            chunk_fold<false>(S, ch, a, c0);
+        if (len <= 32) {
+            // a short B row fills one piece: fold only that one (a DFMA
+            // occupies the FP64 pipe for the whole warp, active lanes or not)
+            if (lane < len) {
+                const int q = S.kb[kk] + lane;
+                const int i = slot_lookup(S, bcol[q] - c0);
+                S.acc[i] = __fma_rn(a, bval[q], S.acc[i]);
+            }
+        } else {
+            for (int off = 0; off < len; off += 128) {
+                Chunk ch;
+                chunk_load<false>(bcol, bval, S, kk, off, lane, ch);
+                chunk_fold<false>(S, ch, a, c0);
+            }
         }
         __syncwarp();
     }
