@@ -252,16 +252,18 @@ __device__ __forceinline__ unsigned long long mag_bits(double x) {
 
 // Exact column sums with deferred carries.  A column's fixed-point value is
 //   sum_c  w[c] * 2^(32 c + e_lsb),  c = 0 .. kChunks-1,
-// where every 64-bit word w[c] only ever receives addends below 2^32.  A
-// word therefore absorbs 2^31 additions without overflow, additions need no
-// carry handling and are fire-and-forget reductions; carries are propagated
-// once, when the column is read (chunk_round).
+// where every 64-bit word w[c] only ever receives addends of magnitude below
+// 2^32, added or subtracted (two's complement): a word absorbs 2^31
+// operations without overflow, operations need no carry handling and are
+// fire-and-forget reductions; carries are propagated once, when the column
+// is read (chunk_round).  Bits below 2^e_lsb are truncated; *sticky counts
+// the summands whose truncated part is nonzero (it is decremented when such
+// a summand is subtracted), so the remainder is zero iff the count is.
 
-// Add v (0 <= v < 2^(e_lsb + kWindow)) to the column whose chunk 0 is at w
-// (chunk stride `stride`).  Bits below 2^e_lsb are truncated and recorded in
-// *sticky.
-__device__ __forceinline__ void exact_add(unsigned long long* w, size_t stride, unsigned* sticky,
-                                          unsigned long long vbits, int e_lsb) {
+// Split v (0 <= v < 2^(e_lsb + kWindow)) into its chunk pieces: returns the
+// first chunk index, and the three 32-bit pieces (possibly 0).
+__device__ __forceinline__ int exact_split(unsigned long long vbits, int e_lsb, unsigned long long& p0,
+                                           unsigned long long& p1, unsigned long long& p2, bool& lost) {
     int E = (int)(vbits >> 52);
     unsigned long long M = vbits & ((1ull << 52) - 1);
     int e;
@@ -271,42 +273,67 @@ __device__ __forceinline__ void exact_add(unsigned long long* w, size_t stride, 
     } else {
         e = -1074;
     }
-    if (M == 0ull) return;
+    p0 = p1 = p2 = 0ull;
+    lost = false;
+    if (M == 0ull) return 0;
     int o = e - e_lsb;
     if (o < 0) {
         int sh = -o;
-        unsigned long long lost = sh >= 64 ? M : (M & ((1ull << sh) - 1));
+        lost = (sh >= 64 ? M : (M & ((1ull << sh) - 1))) != 0ull;
         M = sh >= 64 ? 0ull : (M >> sh);
-        if (lost) atomicOr(sticky, 1u);
-        if (M == 0ull) return;
+        if (M == 0ull) return 0;
         o = 0;
     }
-    int L = o >> 5, s = o & 31;
-    unsigned long long lo = M << s;                      // bits [0, 64) of M * 2^s
-    unsigned long long hi = s ? (M >> (64 - s)) : 0ull;  // bits [64, 85)
-    unsigned long long c0 = lo & 0xffffffffull, c1 = lo >> 32;
-    if (c0) atomicAdd(w + (size_t)L * stride, c0);
-    if (c1) atomicAdd(w + (size_t)(L + 1) * stride, c1);
-    if (hi) atomicAdd(w + (size_t)(L + 2) * stride, hi);
+    const int L = o >> 5, s = o & 31;
+    const unsigned long long lo = M << s;  // bits [0, 64) of M * 2^s
+    p0 = lo & 0xffffffffull;
+    p1 = lo >> 32;
+    p2 = s ? (M >> (64 - s)) : 0ull;  // bits [64, 85)
+    return L;
+}
+
+// Add v to the column whose chunk 0 is at w (chunk stride `stride`).
+__device__ __forceinline__ void exact_add(unsigned long long* w, size_t stride, unsigned* sticky,
+                                          unsigned long long vbits, int e_lsb) {
+    unsigned long long p0, p1, p2;
+    bool lost;
+    const int L = exact_split(vbits, e_lsb, p0, p1, p2, lost);
+    if (lost) atomicAdd(sticky, 1u);
+    if (p0) atomicAdd(w + (size_t)L * stride, p0);
+    if (p1) atomicAdd(w + (size_t)(L + 1) * stride, p1);
+    if (p2) atomicAdd(w + (size_t)(L + 2) * stride, p2);
+}
+
+// Subtract v (added before with the same e_lsb) from the column.
+__device__ __forceinline__ void exact_sub(unsigned long long* w, size_t stride, unsigned* sticky,
+                                          unsigned long long vbits, int e_lsb) {
+    unsigned long long p0, p1, p2;
+    bool lost;
+    const int L = exact_split(vbits, e_lsb, p0, p1, p2, lost);
+    if (lost) atomicSub(sticky, 1u);
+    if (p0) atomicAdd(w + (size_t)L * stride, 0ull - p0);
+    if (p1) atomicAdd(w + (size_t)(L + 1) * stride, 0ull - p1);
+    if (p2) atomicAdd(w + (size_t)(L + 2) * stride, 0ull - p2);
 }
 
 // Read a column's chunks (L2 reads: they were written by other SMs'
-// reductions), clear them, propagate the carries and round the value to the
-// nearest double, ties to even (a truncated positive remainder, flagged by
-// `sticky`, breaks ties upward).
-__device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stride, unsigned* sticky,
-                                              int e_lsb) {
+// reductions), clear them if `clear`, propagate the (signed) carries and
+// round the non-negative value to the nearest double, ties to even (a
+// truncated positive remainder, flagged by a nonzero sticky count, breaks
+// ties upward).
+__device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stride, unsigned* sticky, int e_lsb,
+                                              bool clear = true) {
     unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
-    unsigned long long carry = 0ull;
+    long long carry = 0;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
-        unsigned long long t = __ldcg(w + (size_t)c * stride) + carry;
-        w[(size_t)c * stride] = 0ull;
-        limb[c >> 1] |= (t & 0xffffffffull) << (32 * (c & 1));
+        const long long t = (long long)__ldcg(w + (size_t)c * stride) + carry;
+        if (clear) w[(size_t)c * stride] = 0ull;
+        limb[c >> 1] |= ((unsigned long long)t & 0xffffffffull) << (32 * (c & 1));
         carry = t >> 32;
     }
     bool st = __ldcg(sticky) != 0u;
-    *sticky = 0u;
+    if (clear) *sticky = 0u;
     int top = -1;
     for (int i = 3; i >= 0; --i)
         if (limb[i]) {
@@ -374,6 +401,16 @@ __device__ __forceinline__ long long arena_take(Arena& a, unsigned long long nee
     return (long long)r;
 }
 
+// Clear the column sums of columns [j0, n) with stride `step` (all chunks
+// and the sticky count).
+__device__ __forceinline__ void clear_sums(unsigned long long* words, unsigned* sticky, int n, int j0, int step) {
+    for (int j = j0; j < n; j += step) {
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) words[(size_t)c * n + j] = 0ull;
+        sticky[j] = 0u;
+    }
+}
+
 // Column sums of a flat scan: an entry whose column lies outside [0, n)
 // cannot come from a correct pool; it is skipped and flagged, never used as
 // an index.
@@ -385,12 +422,21 @@ __device__ __forceinline__ void exact_add_checked(unsigned long long* words, uns
         atomicOr(&ctl->status, kDevInternal);
     }
 }
+__device__ __forceinline__ void exact_sub_checked(unsigned long long* words, unsigned* sticky, int col, int n,
+                                                  unsigned long long vbits, int e_lsb, Ctl* ctl) {
+    if ((unsigned)col < (unsigned)n) {
+        exact_sub(words + col, (size_t)n, sticky + col, vbits, e_lsb);
+    } else {
+        atomicOr(&ctl->status, kDevInternal);
+    }
+}
 
 // Candidate lists of Algorithm 1.  A list holds the entries that can still
-// be dropped: pass 1 (in the product's write-back) appends every entry with
+// be dropped, and the exact column sums hold exactly the list's entries:
+// pass 1 (in the product's write-back) appends and adds every entry with
 // 0 < |x| <= eps_g; a later pass with threshold eps_f keeps the entries with
-// |x| <= eps_f (an entry above it stays in the matrix for good, since eps_f
-// only decreases) and adds them to the exact column sums.  A warp reserves
+// |x| <= eps_f and subtracts the others from the sums (an entry above eps_f
+// stays in the matrix for good, since eps_f only decreases).  A warp reserves
 // list space `chunk` entries at a time (one atomic per chunk, so the counter
 // is not contended) and clears the unused end of a chunk when it takes the
 // next one or finishes: a list entry with |x| bits 0 is a hole.  A list that

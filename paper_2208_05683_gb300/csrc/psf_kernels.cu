@@ -693,11 +693,14 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         }
         return;
     }
+    bool dirty = false;  // the column sums were left in place by the last finalize
     for (;;) {
-        // finalize: round each column sum, clear the accumulator, max
+        // finalize: round each column sum, take the max.  The sums are kept
+        // for an incremental (list) pass and cleared for a full pool scan.
         unsigned long long local = 0ull;
+        dirty = !over;
         for (int j = gt; j < A.n; j += nthreads) {
-            double s = chunk_round(A.words + j, n, A.sticky + j, A.e_lsb);
+            double s = chunk_round(A.words + j, n, A.sticky + j, A.e_lsb, over);
             unsigned long long sb = (unsigned long long)__double_as_longlong(s);
             local = sb > local ? sb : local;
         }
@@ -742,7 +745,8 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
                 const unsigned long long xb = in ? __ldcg(ix + q) : 0ull;
                 const int col = in && xb ? __ldcg(ic + q) : 0;
                 const bool keep = in && xb != 0ull && xb <= fb;
-                if (keep) exact_add_checked(A.words, A.sticky, col, A.n, xb, A.e_lsb, A.ctl);
+                // an entry that leaves the list leaves the column sums
+                if (in && xb != 0ull && !keep) exact_sub_checked(A.words, A.sticky, col, A.n, xb, A.e_lsb, A.ctl);
                 cand_push(ca, keep, col, xb, A.cand_col + (size_t)bo * ccap, A.cand_x + (size_t)bo * ccap,
                           &A.ctl->cand_cnt[bo], ccap, cchunk, &A.ctl->cand_over, lane);
             }
@@ -783,6 +787,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = 0ull;
         A.ctl->cand_over = 0;
     }
+    if (dirty) clear_sums(A.words, A.sticky, A.n, gt, nthreads);  // zero for the next step
     if (!(c > 0.0)) {
         // nothing was dropped: the matrix stays as the product wrote it
         if (gt == 0) {
@@ -881,13 +886,16 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
     const unsigned long long ccap = A.ctl->cand_cap;
     const unsigned cchunk = A.ctl->cand_chunk;
     bool alive = true;
+    bool dirty = false;  // some column sums were left in place
     int pass = 0;
     while (s_left > 0) {
-        // finalize the column sums of the iterating instances
+        // finalize the column sums of the iterating instances (kept for an
+        // incremental list pass, cleared for a full pool scan)
+        if (!over) dirty = true;
         for (int j = gt; j < A.n; j += nthreads) {
             const int i = A.inst[j];
             if (s_state[i] != 0) continue;
-            double v = chunk_round(A.words + j, n, A.sticky + j, A.bstep[i].e_lsb);
+            double v = chunk_round(A.words + j, n, A.sticky + j, A.bstep[i].e_lsb, over);
             unsigned long long vb = (unsigned long long)__double_as_longlong(v);
             if (vb) atomicMax(&A.cslot[2 * i + (pass & 1)], vb);
         }
@@ -942,8 +950,11 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
                         atomicOr(&A.ctl->status, kDevInternal);
                     } else {
                         const int i = A.inst[col];
-                        keep = s_state[i] == 0 && xb <= (unsigned long long)__double_as_longlong(s_eps[i]);
-                        if (keep) exact_add(A.words + col, n, A.sticky + col, xb, A.bstep[i].e_lsb);
+                        if (s_state[i] == 0) {
+                            keep = xb <= (unsigned long long)__double_as_longlong(s_eps[i]);
+                            // an entry that leaves the list leaves the column sums
+                            if (!keep) exact_sub(A.words + col, n, A.sticky + col, xb, A.bstep[i].e_lsb);
+                        }
                     }
                 }
                 cand_push(ca, keep, col, xb, A.cand_col + (size_t)bo * ccap, A.cand_x + (size_t)bo * ccap,
@@ -991,6 +1002,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = 0ull;
         A.ctl->cand_over = 0;
     }
+    if (dirty) clear_sums(A.words, A.sticky, A.n, gt, nthreads);  // zero for the next step
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) {
             if (s_state[i] == 2) continue;
