@@ -166,6 +166,34 @@ __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int
     }
     if (mask) atomicOr(&S.pm[curw].y, mask);
 }
+// Short B rows (at most 32 entries each): lane i marks the segment's B row i,
+// so the rows' column loads are in flight together instead of one row after
+// the other.
+__device__ __forceinline__ void mark_rows_short(const int* __restrict__ col, int cnt, int c0, int cend, int lane,
+                                                ProdSmem<false>& S) {
+    if (lane >= cnt) return;
+    const int s = S.kb[lane], e = s + S.kl[lane];
+    unsigned curw = 0xffffffffu, mask = 0u;
+#pragma unroll 2
+    for (int q = s; q < e; q += 4) {
+        int cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cs[u] = q + u < e ? col[q + u] : INT_MIN;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = cs[u];
+            if (c < c0 || c >= cend) continue;
+            const unsigned off = (unsigned)(c - c0), w = off >> 5;
+            if (w != curw) {
+                if (mask) atomicOr(&S.pm[curw].y, mask);
+                curw = w;
+                mask = 0u;
+            }
+            mask |= 1u << (off & 31);
+        }
+    }
+    if (mask) atomicOr(&S.pm[curw].y, mask);
+}
 __device__ __forceinline__ void mark_one(int o, ProdSmem<false>& S) { atomicOr(&S.pm[o >> 5].y, 1u << (o & 31)); }
 __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false>& S) {
     const int nw = (wlen + 31) >> 5;
@@ -190,6 +218,13 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
     for (int seg = pa0; seg < pa1; seg += 32) {
         const int cnt = min(32, pa1 - seg);
         load_segment<TAB>(P, seg, cnt, whole, c0, cend, lane, S);
+        if constexpr (!TAB) {
+            if (warp_max(lane < cnt ? S.kl[lane] : 0) <= 32) {
+                mark_rows_short(P.B.col, cnt, c0, cend, lane, S);
+                __syncwarp();
+                continue;
+            }
+        }
         for (int i = 0; i < cnt; ++i) mark_row(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
         __syncwarp();
     }
@@ -372,10 +407,56 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
     }
     __syncwarp();
 }
+// One 32-lane piece of short B row kk (at most 32 entries): column -1 where
+// there is none.
+__device__ __forceinline__ void short_load(const int* __restrict__ bcol, const double* __restrict__ bval,
+                                           const ProdSmem<false>& S, int cnt, int kk, int lane, int& c, double& v) {
+    c = -1;
+    v = 0.0;
+    if (kk < cnt && lane < S.kl[kk]) {
+        const int q = S.kb[kk] + lane;
+        c = bcol[q];
+        v = bval[q];
+    }
+}
+__device__ __forceinline__ void short_fold(ProdSmem<false>& S, int c, double v, double a, int c0) {
+    if (c >= 0) {
+        const int i = slot_lookup(S, c - c0);
+        S.acc[i] = __fma_rn(a, v, S.acc[i]);
+    }
+}
+
 __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane,
                                                    ProdSmem<false>& S) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
+    if (warp_max(lane < cnt ? S.kl[lane] : 0) <= 32) {
+        // every B row is one piece: the pieces of the next three rows are
+        // loaded while one is folded (rows in k order, a warp barrier between)
+        int ca, cb, cc, cd;
+        double va, vb, vc, vd;
+        short_load(bcol, bval, S, cnt, 0, lane, ca, va);
+        short_load(bcol, bval, S, cnt, 1, lane, cb, vb);
+        short_load(bcol, bval, S, cnt, 2, lane, cc, vc);
+        for (int kk = 0; kk < cnt; kk += 4) {
+            short_load(bcol, bval, S, cnt, kk + 3, lane, cd, vd);
+            short_fold(S, ca, va, S.ka[kk], c0);
+            __syncwarp();
+            if (kk + 1 >= cnt) break;
+            short_load(bcol, bval, S, cnt, kk + 4, lane, ca, va);
+            short_fold(S, cb, vb, S.ka[kk + 1], c0);
+            __syncwarp();
+            if (kk + 2 >= cnt) break;
+            short_load(bcol, bval, S, cnt, kk + 5, lane, cb, vb);
+            short_fold(S, cc, vc, S.ka[kk + 2], c0);
+            __syncwarp();
+            if (kk + 3 >= cnt) break;
+            short_load(bcol, bval, S, cnt, kk + 6, lane, cc, vc);
+            short_fold(S, cd, vd, S.ka[kk + 3], c0);
+            __syncwarp();
+        }
+        return;
+    }
     for (int kk = 0; kk < cnt; ++kk) {
         const int len = S.kl[kk];
         if (len == 0) continue;
