@@ -309,7 +309,9 @@ def run_psf(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(rp, col, val)
-    batched = serving = None
+    batched = serving = sweep = None
+    if rank == 0 and world == 1 and args.sweep:
+        sweep = measure_tol_sweep(args, dev)
     if rank == 0 and world == 1 and not args.no_batched:
         batched = measure_batched(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_serving:
@@ -335,6 +337,7 @@ def run_psf(args):
             "dense_ps": dense,
             "batched": batched,
             "serving": serving,
+            "tol_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -463,6 +466,49 @@ def measure_serving(args, dev):
             "latency": "host clock, submit to result available"}
 
 
+def measure_tol_sweep(args, dev):
+    """The banded workload (n = 65536, half-bandwidth 5, ||Z||_1 = 2, exp)
+    over tolerances 1e-8..1e-14: time, result density and products per
+    evaluation, against dense FP64 PS on the same GPU (products x one
+    measured n x n float64 matmul, projected from n = 8192 by n^3 since
+    three dense 65536^2 matrices would hold 100 GB)."""
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    rp, col, val = syn.banded_random(65536, 5, 0, 2.0)
+    n = len(rp) - 1
+    Z = psf.DeviceCSR.from_host(rp, col, val, device=dev)
+    m = 8192
+    A = torch.randn(m, m, dtype=torch.float64, device=dev)
+    torch.matmul(A, A)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    torch.matmul(A, A)
+    e1.record()
+    e1.synchronize()
+    t_gemm = e0.elapsed_time(e1) / 1e3 * (n / m) ** 3
+    del A
+    torch.cuda.empty_cache()
+    rows = []
+    for tol in (1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-13, 1e-14):
+        s = psf.Series(syn.coeffs("exp"), tol)
+        for _ in range(2):
+            s.eval(Z)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            r = s.eval(Z)
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) / reps
+        info = r.info
+        rows.append({"tol": tol, "ms": t * 1e3, "N": info["N"], "products": info["products"],
+                     "density": info["nnz"] / n / n, "fma": info["fma"],
+                     "dense_ms": info["products"] * t_gemm * 1e3})
+    return {"workload": "banded_n65536_hbw5 exp", "dense_dgemm_s_projected": t_gemm, "rows": rows}
+
+
 def ctypes_i64(fn) -> int:
     import ctypes
     v = ctypes.c_int64()
@@ -502,6 +548,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=300, help="requests of the serving measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="add the tolerance sweep of the banded n = 65536 workload against dense PS")
     args = ap.parse_args()
     if args.case:
         run_case(args)
