@@ -278,6 +278,27 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
              const double* norms, psf_info_t* info, double* zeta, double* sigma);
 
 /*
+ * Tuning, process-wide (no counterpart in the paper).
+ * PSF_TUNE_TABLE_CROSSOVER: products per output row (mean over a step's
+ *   rows, from the previous evaluation's or the norm phase's statistics)
+ *   from which the product kernel uses its column-table slot map instead of
+ *   the bitmap map (default: never, the bitmap map measured faster on the
+ *   2D Laplacian and banded workloads).  Both maps give bitwise identical
+ *   results; the choice only changes speed.
+ * psf_autotune: evaluate `series` at Z once with each slot map (after one
+ *   warm-up evaluation), time every product launch, and set the crossover
+ *   that minimises the summed product time; returns it, and the time it
+ *   saves against the previous setting (ms per evaluation) if `saved_ms` is
+ *   not NULL.  Synchronizes `stream`.  Not thread-safe with evaluations that
+ *   run concurrently on other threads (they may see either setting).
+ */
+#define PSF_TUNE_TABLE_CROSSOVER 1
+PSF_API int psf_tune_set(int32_t key, double value);
+PSF_API int psf_tune_get(int32_t key, double* value);
+PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,
+                         double* saved_ms);
+
+/*
  * Instrumentation.  psf_launch_count: kernels this library has launched in
  * this process.  psf_profile(1) makes every later product-kernel launch
  * record a CUDA event pair on its stream; psf_profile_read waits for the

@@ -31,7 +31,7 @@ from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_SUBMULT, PS
 
 __all__ = [
     "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "norm1_noalloc", "plan",
-    "Server", "PsfError",
+    "Server", "autotune", "tune_get", "tune_set", "PsfError",
     "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_MAX_Q", "build", "lib",
 ]
 
@@ -294,6 +294,25 @@ def norm1_noalloc(M: DeviceCSR, stream=None) -> float:
     ms = M._struct()
     check(lib().psf_norm1_noalloc(ctypes.byref(ms), _stream_ptr(stream), ctypes.byref(out)))
     return out.value
+
+
+def autotune(series: "Series", Z: DeviceCSR, stream=None):
+    """psf_autotune: time both slot maps on this evaluation and keep the
+    faster crossover; returns (crossover, ms saved per evaluation)."""
+    c, saved = ctypes.c_double(), ctypes.c_double()
+    zs = Z._struct()
+    check(lib().psf_autotune(series._h, ctypes.byref(zs), _stream_ptr(stream), ctypes.byref(c), ctypes.byref(saved)))
+    return c.value, saved.value
+
+
+def tune_get(key: int = 1) -> float:
+    v = ctypes.c_double()
+    check(lib().psf_tune_get(int(key), ctypes.byref(v)))
+    return v.value
+
+
+def tune_set(key: int, value: float) -> None:
+    check(lib().psf_tune_set(int(key), float(value)))
 
 
 def plan(coeffs, tol: float, norms, *, poly: bool = False, submult: bool = False, s: int = 0):

@@ -13,6 +13,7 @@ PSF_PARAM_ER, PSF_PARAM_ALG1_MAXIT, PSF_PARAM_POOL_ENTRIES = 1, 2, 3
 PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
 PSF_MAX_Q = 23
 PSF_NORM1_NOALLOC_MAX_N = 65536
+PSF_TUNE_TABLE_CROSSOVER = 1
 
 ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG"}
 
@@ -21,7 +22,7 @@ EXPORTS = [
     "psf_version", "psf_last_error", "psf_series_create", "psf_series_set_param",
     "psf_series_destroy", "psf_eval", "psf_eval_batch", "psf_product_filter", "psf_norm1",
     "psf_norm1_noalloc", "psf_server_create", "psf_server_submit", "psf_server_poll", "psf_server_stats",
-    "psf_server_destroy",
+    "psf_server_destroy", "psf_tune_set", "psf_tune_get", "psf_autotune",
     "psf_plan", "psf_result_csr", "psf_result_copy", "psf_result_info", "psf_result_step",
     "psf_result_destroy", "psf_launch_count", "psf_profile", "psf_profile_read",
 ]
@@ -124,6 +125,9 @@ def _declare(h: ctypes.CDLL) -> None:
     h.psf_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32, i32, ctypes.POINTER(i32)]
     h.psf_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     h.psf_server_destroy.argtypes = [vp]
+    h.psf_tune_set.argtypes = [i32, f64]
+    h.psf_tune_get.argtypes = [i32, ctypes.POINTER(f64)]
+    h.psf_autotune.argtypes = [vp, csrp, vp, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     h.psf_plan.argtypes = [ctypes.POINTER(f64), i64, i32, f64, ctypes.c_uint32, ctypes.POINTER(f64),
                            ctypes.POINTER(InfoStruct), ctypes.POINTER(f64), ctypes.POINTER(f64)]
     h.psf_result_csr.argtypes = [vp, csrp]

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -40,6 +41,12 @@ int fail(int code, const char* fmt, ...) {
 
 bool g_pool_configured = false;
 Profile g_prof;
+// Default: the bitmap map for every step.  psf_autotune measured it faster
+// than the column table on the 2D Laplacian (exp, cos) and banded workloads,
+// giant steps included, where its 24 resident warps per SM hide the gather
+// latency better than the table map's 14.
+std::atomic<double> g_table_crossover{1e300};
+thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
     if (g_pool_configured) return cudaSuccess;
@@ -163,17 +170,24 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     if (P.stat) CU(cudaMemcpyAsync(&P.stat->pool_start, &w.C()->pool_used, sizeof(unsigned long long),
                                    cudaMemcpyDeviceToDevice, w.st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (g_prof.on) {
+    const bool timed = g_prof.on || g_tune_rec;
+    if (timed) {
         CU(cudaEventCreate(&e0));
         CU(cudaEventCreate(&e1));
         CU(cudaEventRecord(e0, w.st));
     }
-    // table map when a row folds many products per window column
-    const bool table = w.slot_map == 1 || (w.slot_map == 0 && alen * blen >= 2048.0);
+    // table map when a row folds many products (the crossover is tunable)
+    const double work = alen > 0.0 ? alen * blen : 0.0;
+    const bool table = use_table(w.slot_map, work);
     CU(launch_product(P, table, w.st));
-    if (g_prof.on) {
+    if (timed) {
         CU(cudaEventRecord(e1, w.st));
-        g_prof.ev.emplace_back(e0, e1);
+        if (g_tune_rec) {
+            g_tune_rec->work.push_back(work);
+            g_tune_rec->ev.emplace_back(e0, e1);
+        } else {
+            g_prof.ev.emplace_back(e0, e1);
+        }
     }
     if (filt) {
         Alg1Args a{};
@@ -847,6 +861,86 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     inf.fma = (int64_t)eval_fma;
     if (g_prof.on) g_prof.fma += (double)eval_fma;
     *out = handle;
+    return PSF_OK;
+}
+
+int psf_tune_set(int32_t key, double value) {
+    switch (key) {
+        case PSF_TUNE_TABLE_CROSSOVER:
+            if (!(value >= 0.0)) return fail(PSF_EINVAL, "crossover must be >= 0");
+            g_table_crossover.store(value);
+            return PSF_OK;
+        default:
+            return fail(PSF_EINVAL, "unknown tuning key %d", key);
+    }
+}
+
+int psf_tune_get(int32_t key, double* value) {
+    if (!value) return fail(PSF_EINVAL, "null argument");
+    switch (key) {
+        case PSF_TUNE_TABLE_CROSSOVER:
+            *value = g_table_crossover.load();
+            return PSF_OK;
+        default:
+            return fail(PSF_EINVAL, "unknown tuning key %d", key);
+    }
+}
+
+// Evaluate the series once with each slot map, timing every product launch,
+// and keep the crossover (work per row) that minimises the summed time: the
+// launches are the same in both runs (same plan, same steps), only the map
+// differs, and both maps give bitwise identical results.
+int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover, double* saved_ms) {
+    if (!series || !Z || !crossover) return fail(PSF_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    psf_result_t r = nullptr;
+    int rc = psf_eval(series, Z, stream, &r);  // warm-up: pool sizes are learnt
+    if (rc) return rc;
+    psf_result_destroy(r);
+    const int saved_map = series->kernel;
+    std::vector<double> work[2];
+    std::vector<double> ms[2];
+    for (int m = 0; m < 2; ++m) {
+        TuneRecorder rec;
+        series->kernel = m == 0 ? 1 : 2;
+        g_tune_rec = &rec;
+        rc = psf_eval(series, Z, stream, &r);
+        g_tune_rec = nullptr;
+        series->kernel = saved_map;
+        if (rc == PSF_OK) {
+            psf_result_destroy(r);
+            if (cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PSF_ECUDA, "autotune sync");
+        }
+        for (auto& pr : rec.ev) {
+            float t = 0.0f;
+            if (rc == PSF_OK && cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess)
+                rc = fail(PSF_ECUDA, "autotune timing");
+            ms[m].push_back(t);
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        work[m] = rec.work;
+        if (rc) return rc;
+    }
+    if (work[0] != work[1]) return fail(PSF_ECUDA, "autotune: the two runs launched different products");
+    // candidate crossovers: every work level, plus "never table"
+    std::vector<double> cand(work[0]);
+    cand.push_back(std::numeric_limits<double>::infinity());
+    double best_t = std::numeric_limits<double>::infinity(), best_c = g_table_crossover.load(), cur_t = 0.0;
+    const double cur_c = g_table_crossover.load();
+    for (size_t i = 0; i < work[0].size(); ++i) cur_t += work[0][i] >= cur_c ? ms[0][i] : ms[1][i];
+    for (double c : cand) {
+        double t = 0.0;
+        for (size_t i = 0; i < work[0].size(); ++i) t += work[0][i] >= c ? ms[0][i] : ms[1][i];
+        if (t < best_t || (t == best_t && c > best_c)) {
+            best_t = t;
+            best_c = c;
+        }
+    }
+    if (std::isinf(best_c)) best_c = 1e300;
+    g_table_crossover.store(best_c);
+    *crossover = best_c;
+    if (saved_ms) *saved_ms = cur_t - best_t;
     return PSF_OK;
 }
 

@@ -214,7 +214,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                     P.chunk_slots = w.chunk_slots;
                     const double blen = zlen_all * (k - 1) * (k - 1);
                     P.arena = arena_for(zlen_all * blen);
-                    const bool table = w.slot_map == 1 || (w.slot_map == 0 && zlen_all * blen >= 2048.0);
+                    const bool table = use_table(w.slot_map, zlen_all * blen);
                     CU(launch_product(P, table, st));
                     if ((rc = mark_pool(w, k))) return rc;
                     prev = w.pooled(rb, re);
@@ -478,7 +478,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             P.arena = arena_for(fma_row);
             CU(cudaMemcpyAsync(d_pstart.as<unsigned long long>() + si, &w.C()->pool_used, sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, st));
-            const bool table = w.slot_map == 1 || (w.slot_map == 0 && fma_row >= 2048.0);
+            const bool table = use_table(w.slot_map, fma_row);
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (g_prof.on) {
                 CU(cudaEventCreate(&e0));

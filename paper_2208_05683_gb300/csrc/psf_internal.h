@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <memory>
 #include <utility>
@@ -168,6 +169,22 @@ struct Work {
     int* pcol() const { return pool_col.as<int>(); }
     double* pval() const { return pool_val.as<double>(); }
 };
+
+// Process-wide tuning (psf_tune_*, psf_autotune): the products per output
+// row from which the product kernel uses the column-table slot map.
+extern std::atomic<double> g_table_crossover;
+// slot_map 1: table, 2: bitmap, 0: by the work per row and the crossover
+inline bool use_table(int slot_map, double work_per_row) {
+    return slot_map == 1 || (slot_map == 0 && work_per_row >= g_table_crossover.load(std::memory_order_relaxed));
+}
+
+// Recorder of product launches for psf_autotune (set on the calling thread
+// only): each launch's work per row and its event pair.
+struct TuneRecorder {
+    std::vector<double> work;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+};
+extern thread_local TuneRecorder* g_tune_rec;
 
 int lsb_for_bound_host(double x);
 RowView view_of(const psf_csr_t& m);

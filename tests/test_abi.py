@@ -108,3 +108,18 @@ def test_host_planner_not_converged():
     with pytest.raises(psf.PsfError) as e:
         psf.plan(syn.coeffs("exp", 6), 1e-12, [1.0] + [10.0 ** i for i in range(1, 11)])
     assert e.value.code == _abi.PSF_ENOTCONV
+
+
+def test_tuning_keys_are_checked_on_the_host():
+    old = psf.tune_get(_abi.PSF_TUNE_TABLE_CROSSOVER)
+    try:
+        psf.tune_set(_abi.PSF_TUNE_TABLE_CROSSOVER, 512.0)
+        assert psf.tune_get(_abi.PSF_TUNE_TABLE_CROSSOVER) == 512.0
+        with pytest.raises(psf.PsfError):
+            psf.tune_set(_abi.PSF_TUNE_TABLE_CROSSOVER, -1.0)
+        with pytest.raises(psf.PsfError):
+            psf.tune_set(99, 1.0)
+        with pytest.raises(psf.PsfError):
+            psf.tune_get(99)
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_TABLE_CROSSOVER, old)
