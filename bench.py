@@ -48,6 +48,18 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def job_rate(units_per_rank: float, local_ms: float, world: int, device=None):
+    """Whole-job rate over replicas: the units all ranks processed divided by
+    the slowest rank's time (max over ranks); returns (rate, max ms)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return world * units_per_rank / (local_ms / 1e3), local_ms
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -236,13 +248,8 @@ def run_psf(args):
     barrier()
     clocks.stop()
     launches = ctypes_i64(L.psf_launch_count) - cnt0
-    total_ms = sum(lat)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     evals = args.steps * len(KINDS)
-    value = world * evals / (total_ms / 1e3)
+    value, total_ms = job_rate(evals, sum(lat), world, dev)
 
     # ---- roofline of the product kernel (event-timed launches, separate pass)
     import ctypes
@@ -289,7 +296,7 @@ def run_psf(args):
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
             d2h = sum(t.numel() * t.element_size() for out in host_out for t in out)
-    e2e_value = world * len(KINDS) * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    e2e_value, _ = job_rate(len(KINDS) * len(e2e_ms), sum(e2e_ms), world, dev)
 
     # ---- dense FP64 PS on the same GPU: product count x measured DGEMM time
     dense = None
