@@ -39,7 +39,10 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-bool g_pool_configured = false;
+// the device memory pool's release threshold is raised once per device
+constexpr int kMaxPoolDevices = 64;
+bool g_pool_configured[kMaxPoolDevices] = {};
+std::mutex g_pool_mu;
 Profile g_prof;
 // Default: the bitmap map for every step.  psf_autotune measured it faster
 // than the column table on the 2D Laplacian (exp, cos) and banded workloads,
@@ -49,17 +52,19 @@ std::atomic<double> g_table_crossover{1e300};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
-    if (g_pool_configured) return cudaSuccess;
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool_configured[dev]) return cudaSuccess;
     cudaMemPool_t pool;
     err = cudaDeviceGetDefaultMemPool(&pool, dev);
     if (err != cudaSuccess) return err;
     unsigned long long thr = ~0ull;  // keep freed blocks for reuse
     err = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (err != cudaSuccess) return err;
-    g_pool_configured = true;
+    g_pool_configured[dev] = true;
     return cudaSuccess;
 }
 

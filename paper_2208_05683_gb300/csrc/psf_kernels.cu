@@ -13,6 +13,7 @@
 //                 plumbing.
 #include <atomic>
 #include <climits>
+#include <mutex>
 
 #include "psf_device.cuh"
 #include "psf_kernels.h"
@@ -1479,17 +1480,38 @@ __global__ void k_csr_to_rows(int n, const int* rowptr, int* rb, int* re) {
 }
 
 // ---------------------------------------------------------------- launchers
-static int g_sms = 0, g_alg1_blocks = 0, g_alg1b_blocks = 0, g_norm_blocks = 0;
+// Launch configuration, per device (set up once by kernels_init, guarded by
+// a mutex; a device's entry is published through `ready`).
+struct DevCfg {
+    int sms = 0, alg1_blocks = 0, alg1b_blocks = 0, norm_blocks = 0;
+    std::atomic<bool> ready{false};
+};
+constexpr int kMaxDevices = 64;
+static DevCfg g_dev[kMaxDevices];
+static std::mutex g_init_mu;
 static std::atomic<long long> g_launches{0};
 
 long long launch_count() { return g_launches.load(); }
 
+static const DevCfg& dcfg();
+static int sms_now();
+static const DevCfg& dcfg() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    return g_dev[dev];
+}
+
 cudaError_t kernels_init() {
-    if (g_sms) return cudaSuccess;
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    DevCfg& c = g_dev[dev];
+    if (c.ready.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_init_mu);
+    if (c.ready.load(std::memory_order_acquire)) return cudaSuccess;
+    int sms = 0;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     const void* prods[4] = {(const void*)k_product<true, false>, (const void*)k_product<false, false>,
                             (const void*)k_product<true, true>, (const void*)k_product<false, true>};
@@ -1502,18 +1524,21 @@ cudaError_t kernels_init() {
     int per = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
-    g_alg1_blocks = g_sms * (per < 2 ? per : 2);
+    c.alg1_blocks = sms * (per < 2 ? per : 2);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1_batch, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
-    g_alg1b_blocks = g_sms * (per < 2 ? per : 2);
+    c.alg1b_blocks = sms * (per < 2 ? per : 2);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_norms, kNormThreads, 0);
     if (err != cudaSuccess) return err;
-    g_norm_blocks = g_sms * (per < 2 ? per : 2);
-    if (g_alg1_blocks <= 0 || g_alg1b_blocks <= 0 || g_norm_blocks <= 0) return cudaErrorInvalidConfiguration;
+    c.norm_blocks = sms * (per < 2 ? per : 2);
+    if (c.alg1_blocks <= 0 || c.alg1b_blocks <= 0 || c.norm_blocks <= 0) return cudaErrorInvalidConfiguration;
+    c.sms = sms;
+    c.ready.store(true, std::memory_order_release);
     return cudaSuccess;
 }
 
-int num_sms() { return g_sms; }
+int num_sms() { return dcfg().sms; }
+static int sms_now() { return dcfg().sms; }
 
 template <bool TAB, bool BATCH>
 static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
@@ -1521,7 +1546,7 @@ static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     // one wave of resident blocks, rows strided over the warps (each warp
     // keeps one pool arena)
     long long blocks = ((long long)P.n + kWarps - 1) / kWarps;
-    const long long cap = (long long)g_sms * (TAB ? 7 : 6);
+    const long long cap = (long long)sms_now() * (TAB ? 7 : 6);
     if (blocks > cap) blocks = cap;
     k_product<TAB, BATCH><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
     ++g_launches;
@@ -1540,7 +1565,7 @@ cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {
     Alg1Args a = A;
     void* args[] = {&a};
     ++g_launches;
-    return cudaLaunchCooperativeKernel((const void*)k_alg1, dim3(g_alg1_blocks), dim3(kAlg1Threads), args,
+    return cudaLaunchCooperativeKernel((const void*)k_alg1, dim3(dcfg().alg1_blocks), dim3(kAlg1Threads), args,
                                        0, st);
 }
 
@@ -1548,12 +1573,12 @@ cudaError_t launch_norms(const NormArgs& A, cudaStream_t st) {
     NormArgs a = A;
     void* args[] = {&a};
     ++g_launches;
-    return cudaLaunchCooperativeKernel((const void*)k_norms, dim3(g_norm_blocks), dim3(kNormThreads), args,
+    return cudaLaunchCooperativeKernel((const void*)k_norms, dim3(dcfg().norm_blocks), dim3(kNormThreads), args,
                                        0, st);
 }
 
 cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st) {
-    k_absmax<<<g_sms * 4, 256, 0, st>>>(pool_val, ctl, i, slot);
+    k_absmax<<<sms_now() * 4, 256, 0, st>>>(pool_val, ctl, i, slot);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -1576,7 +1601,7 @@ cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col
                           cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int blocks = (n + 7) / 8;
-    if (blocks > g_sms * 16) blocks = g_sms * 16;
+    if (blocks > sms_now() * 16) blocks = sms_now() * 16;
     k_gather<<<blocks, 256, 0, st>>>(n, src, rowptr, col, val);
     ++g_launches;
     return cudaGetLastError();
@@ -1593,7 +1618,7 @@ cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const dou
                              cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int blocks = (n + 63) / 64;
-    if (blocks > g_sms) blocks = g_sms;
+    if (blocks > sms_now()) blocks = sms_now();
     k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl, arena_size);
     ++g_launches;
     return cudaGetLastError();
@@ -1603,7 +1628,7 @@ cudaError_t launch_norm_scratch_init(Ctl* ctl, NormSlot* slot, unsigned long lon
                                      long long nnz, cudaStream_t st) {
     int blocks = (int)(((long long)kChunks * n + 255) / 256);
     if (blocks < 1) blocks = 1;
-    if (blocks > g_sms * 4) blocks = g_sms * 4;
+    if (blocks > sms_now() * 4) blocks = sms_now() * 4;
     k_norm_scratch_init<<<blocks, 256, 0, st>>>(ctl, slot, words, sticky, n, nnz);
     ++g_launches;
     return cudaGetLastError();
@@ -1616,7 +1641,7 @@ cudaError_t launch_alg1_batch(const Alg1BatchArgs& A, cudaStream_t st) {
     Alg1BatchArgs a = A;
     void* args[] = {&a};
     ++g_launches;
-    return cudaLaunchCooperativeKernel((const void*)k_alg1_batch, dim3(g_alg1b_blocks), dim3(kAlg1Threads), args,
+    return cudaLaunchCooperativeKernel((const void*)k_alg1_batch, dim3(dcfg().alg1b_blocks), dim3(kAlg1Threads), args,
                                        0, st);
 }
 
@@ -1640,7 +1665,7 @@ cudaError_t launch_copy_rows_batch(int n, const int* inst, const BatchSrc* src, 
                                    int stride, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int blocks = (n + 7) / 8;
-    if (blocks > g_sms * 8) blocks = g_sms * 8;
+    if (blocks > sms_now() * 8) blocks = sms_now() * 8;
     k_copy_rows_batch<<<blocks, 256, 0, st>>>(n, inst, src, rb, re, pool_col, pool_val, ctl, arena_size, absmax,
                                               stride);
     ++g_launches;
@@ -1665,7 +1690,7 @@ cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* of
                                 const int* rowptr, int* out_rp, int* col, double* val, cudaStream_t st) {
     int blocks = (n + 7) / 8;
     if (blocks < 1) blocks = 1;
-    if (blocks > g_sms * 16) blocks = g_sms * 16;
+    if (blocks > sms_now() * 16) blocks = sms_now() * 16;
     k_gather_batch<<<blocks, 256, 0, st>>>(n, ninst, inst, off, src, rowptr, out_rp, col, val);
     ++g_launches;
     return cudaGetLastError();

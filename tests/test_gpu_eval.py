@@ -141,10 +141,12 @@ def test_lap2d_128x128_full_size_bitwise(kind):
 
 
 @pytest.mark.slow
-def test_banded_n65536_full_size_bitwise():
+@pytest.mark.parametrize("tol", [1e-8, 1e-12, 1e-14])
+def test_banded_n65536_full_size_bitwise(tol):
+    # the banded workload at full size, across its tolerance sweep
     Z = ocsr(syn.banded_random(65536, 5, 0, 2.0))
-    got, ref = run_both(Z, syn.coeffs("exp"), 1e-12)
-    check_same(got, ref, "banded 65536")
+    got, ref = run_both(Z, syn.coeffs("exp"), tol)
+    check_same(got, ref, f"banded 65536 tol {tol}")
 
 
 @pytest.mark.slow
