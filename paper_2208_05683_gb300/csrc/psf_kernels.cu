@@ -46,7 +46,7 @@ namespace psf {
 constexpr int kTabCap = 4160;  // columns of the table map
 constexpr int kBmWords = 160;  // bitmap words of the bitmap map
 constexpr int kBmBits = kBmWords * 32;
-constexpr int kAccCap = 672;
+constexpr int kAccCap = 600;  // with 7 bitmap blocks of 4 warps per SM, shared memory is full
 
 template <bool TAB>
 struct ProdSmem;
@@ -55,6 +55,7 @@ template <>
 struct ProdSmem<true> {
     static constexpr int kCols = kTabCap;
     static constexpr int kWarps = 2;
+    static constexpr int kBlocksPerSm = 7;
     unsigned short tab[kTabCap];
     double acc[kAccCap];
     double ka[32];
@@ -67,6 +68,7 @@ template <>
 struct ProdSmem<false> {
     static constexpr int kCols = kBmBits;
     static constexpr int kWarps = 4;
+    static constexpr int kBlocksPerSm = 7;  // 28 warps: registers (72) and shared memory
     uint2 pm[kBmWords];  // .x = set bits before the word, .y = bitmap word
     double acc[kAccCap];
     double ka[32];
@@ -504,7 +506,7 @@ __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, 
 }
 
 template <bool TAB, bool BATCH>
-__global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, TAB ? 7 : 6) k_product(ProductArgs P) {
+__global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBlocksPerSm) k_product(ProductArgs P) {
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
     // columns and slots of one chunk (lowered only to exercise chunking)
     const int kCols = P.chunk_cols > 0 && P.chunk_cols < ProdSmem<TAB>::kCols ? P.chunk_cols : ProdSmem<TAB>::kCols;
@@ -1546,7 +1548,7 @@ static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     // one wave of resident blocks, rows strided over the warps (each warp
     // keeps one pool arena)
     long long blocks = ((long long)P.n + kWarps - 1) / kWarps;
-    const long long cap = (long long)sms_now() * (TAB ? 7 : 6);
+    const long long cap = (long long)sms_now() * ProdSmem<TAB>::kBlocksPerSm;
     if (blocks > cap) blocks = cap;
     k_product<TAB, BATCH><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
     ++g_launches;
