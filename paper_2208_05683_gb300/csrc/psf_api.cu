@@ -251,7 +251,7 @@ int make_result(Work& w, const RowView& M, psf_result_t* out, psf_result_s** mad
             break;
         }
         if (w.n > 0) {
-            e = launch_scan_rows(w.n, M.rb, M.re, r->rowptr, w.C(), w.st);
+            e = launch_scan_rows(w.n, M.rb, M.re, r->rowptr, w.C(), w.scan.as<long long>(), w.st);
         } else {
             e = cudaMemsetAsync(r->rowptr, 0, sizeof(int), w.st);
         }

@@ -515,7 +515,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             else S = out;
         }
         F = S;
-        CU(launch_scan_rows(n, F.rb, F.re, d_rowptr.as<int>(), w.C(), st));
+        CU(launch_scan_rows(n, F.rb, F.re, d_rowptr.as<int>(), w.C(), w.scan.as<long long>(), st));
         CU(launch_bounds(count, d_off.as<int>(), d_rowptr.as<int>(), d_bounds.as<int>(), st));
         CU(cudaMemcpyAsync(bounds.data(), d_bounds.p, sizeof(int) * bounds.size(), cudaMemcpyDeviceToHost, st));
         CU(cudaMemcpyAsync(pst.data(), d_stat.p, sizeof(StepStat) * pst.size(), cudaMemcpyDeviceToHost, st));

@@ -97,7 +97,7 @@ extern Profile g_prof;
 struct Work {
     int n = 0;
     cudaStream_t st = nullptr;
-    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val, cand_col, cand_x;
+    DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val, cand_col, cand_x, scan;
     unsigned long long cap = 0, ccap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
@@ -120,6 +120,7 @@ struct Work {
         CU(cudaMemsetAsync(words.p, 0, sizeof(unsigned long long) * kChunks * nn * kMaxNorms, st));
         CU(sticky.alloc(sizeof(unsigned) * nn * kMaxNorms, st));
         CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
+        CU(scan.alloc(sizeof(long long) * scan_scratch_len(n_), st));
         return PSF_OK;
     }
     // (re)allocate the entry pool and reset the device control block

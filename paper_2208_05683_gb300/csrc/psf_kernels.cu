@@ -9,7 +9,7 @@
 //  k_alg1         the remaining passes of Algorithm 1 (Sec. 3.1.1) and the
 //                 final in-place compaction, one cooperative launch.
 //  k_norms        exact 1-norms of up to 11 matrices (Eq. 37's z_i).
-//  k_absmax, k_validate, k_copy_rows, k_scan_rows, k_gather, k_identity:
+//  k_absmax, k_validate, k_copy_rows, k_scan_*, k_gather, k_identity:
 //                 plumbing.
 #include <atomic>
 #include <climits>
@@ -1154,17 +1154,34 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
         unsigned long long* words = A.words + (size_t)mi * kChunks * n;
         unsigned* sticky = A.sticky + (size_t)mi * n;
         if (A.inst) {
-            // batch: the fixed point of each column follows its instance's max |x|
-            for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
-                const unsigned long long xb = mag_bits(A.pool_val[q]);
-                if (xb == 0ull) continue;
-                const int c = A.pool_col[q];
-                if ((unsigned)c >= (unsigned)A.n) {
-                    atomicOr(&A.ctl->status, kDevInternal);
-                    continue;
+            // batch: the fixed point of each column follows its instance's max
+            // |x|; four entries per thread at a time, so that their dependent
+            // loads (column, instance, max) overlap
+            for (unsigned long long q0 = p0 + (unsigned long long)gt; q0 < p1; q0 += 4ull * nthreads) {
+                unsigned long long xb[4];
+                int c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long q = q0 + (unsigned long long)u * nthreads;
+                    xb[u] = q < p1 ? mag_bits(A.pool_val[q]) : 0ull;
+                    c[u] = xb[u] ? A.pool_col[q] : 0;
                 }
-                const int lsb = lsb_for_bound(A.slots[(size_t)A.inst[c] * A.slot_stride + mi].absmax);
-                exact_add(words + c, n, sticky + c, xb, lsb);
+                int lsb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    lsb[u] = 0;
+                    if (xb[u] && (unsigned)c[u] < (unsigned)A.n)
+                        lsb[u] = lsb_for_bound(A.slots[(size_t)A.inst[c[u]] * A.slot_stride + mi].absmax);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!xb[u]) continue;
+                    if ((unsigned)c[u] >= (unsigned)A.n) {
+                        atomicOr(&A.ctl->status, kDevInternal);
+                        continue;
+                    }
+                    exact_add(words + c[u], n, sticky + c[u], xb[u], lsb[u]);
+                }
             }
             continue;
         }
@@ -1245,35 +1262,75 @@ __global__ void k_validate(int n, int nnz, const int* rowptr, const int* col, co
     if (bad) atomicOr(&ctl->status, kDevBadInput);
 }
 
-// Exclusive scan of row lengths re - rb into rowptr (n + 1 entries); one
-// block of kScanThreads threads, each owning a contiguous range of rows.
-constexpr int kScanThreads = 1024;
+// Exclusive scan of row lengths re - rb into rowptr (n + 1 entries), in
+// three launches over tiles of kScanTile rows: tile sums, a scan of the tile
+// sums (one block), and the scan inside each tile plus its tile's offset.
+// `sums` holds ceil(n / kScanTile) + 1 values.
+constexpr int kScanTile = 1024;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_rows(int n, const int* rb, const int* re,
-                                                             int* rowptr, Ctl* ctl) {
-    __shared__ long long part[kScanThreads];
-    const int t = threadIdx.x;
-    const long long per = ((long long)n + kScanThreads - 1) / kScanThreads;
-    const long long r0 = t * per, r1 = min((long long)n, r0 + per);
-    long long s = 0;
-    for (long long r = r0; r < r1; ++r) s += re[r] - rb[r];
-    part[t] = s;
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* part, long long* total) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) part[wid] = x;
     __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        long long v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (wid == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        long long p = lane < nw ? part[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, p, o);
+            if (lane >= o) p += y;
+        }
+        if (lane < nw) part[lane] = p;  // inclusive warp totals
     }
-    long long run = part[t] - s;
-    for (long long r = r0; r < r1; ++r) {
-        rowptr[r] = (int)run;
-        run += re[r] - rb[r];
+    __syncthreads();
+    const long long before = wid ? part[wid - 1] : 0;
+    *total = part[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_tile_sums(int n, const int* rb, const int* re, long long* sums) {
+    __shared__ long long part[32];
+    const long long r = (long long)blockIdx.x * kScanTile + threadIdx.x;
+    const long long len = r < n ? (long long)(re[r] - rb[r]) : 0;
+    long long total;
+    block_excl_scan(len, part, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_tiles(int ntiles, long long* sums, Ctl* ctl) {
+    __shared__ long long part[32];
+    // each thread owns a contiguous run of tiles
+    const int per = (ntiles + kScanTile - 1) / kScanTile;
+    const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
+    long long s = 0;
+    for (int t = t0; t < t1; ++t) s += sums[t];
+    long long total;
+    long long run = block_excl_scan(s, part, &total);
+    for (int t = t0; t < t1; ++t) {
+        const long long v = sums[t];
+        sums[t] = run;
+        run += v;
     }
-    if (t == kScanThreads - 1) {
-        rowptr[n] = (int)part[t];
-        ctl->nnz_total = (unsigned long long)part[t];
+    if (threadIdx.x == 0) {
+        sums[ntiles] = total;
+        ctl->nnz_total = (unsigned long long)total;
     }
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_apply(int n, const int* rb, const int* re, const long long* sums,
+                                                           int* rowptr) {
+    __shared__ long long part[32];
+    const long long r = (long long)blockIdx.x * kScanTile + threadIdx.x;
+    const long long len = r < n ? (long long)(re[r] - rb[r]) : 0;
+    long long total;
+    const long long ex = block_excl_scan(len, part, &total) + sums[blockIdx.x];
+    if (r < n) rowptr[r] = (int)ex;  // the host rejects totals of 2^31 and more
+    if (r == n - 1 || (n == 0 && r == 0)) rowptr[n] = (int)sums[gridDim.x];
 }
 
 __global__ void k_gather(int n, RowView src, const int* rowptr, int* col, double* val) {
@@ -1593,8 +1650,21 @@ cudaError_t launch_validate(int n, int nnz, const int* rowptr, const int* col, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, Ctl* ctl, cudaStream_t st) {
-    k_scan_rows<<<1, kScanThreads, 0, st>>>(n, rb, re, rowptr, ctl);
+size_t scan_scratch_len(int n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 2; }
+
+cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, Ctl* ctl, long long* sums,
+                             cudaStream_t st) {
+    const int ntiles = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
+    if (n > 0) {
+        k_scan_tile_sums<<<ntiles, kScanTile, 0, st>>>(n, rb, re, sums);
+        ++g_launches;
+    } else {
+        cudaError_t err = cudaMemsetAsync(sums, 0, sizeof(long long), st);
+        if (err != cudaSuccess) return err;
+    }
+    k_scan_tiles<<<1, kScanTile, 0, st>>>(ntiles, sums, ctl);
+    ++g_launches;
+    k_scan_apply<<<ntiles, kScanTile, 0, st>>>(n, rb, re, sums, rowptr);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -19,7 +19,9 @@ cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
 cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st);
 cudaError_t launch_validate(int n, int nnz, const int* rowptr, const int* col, const double* val, Ctl* ctl,
                             cudaStream_t st);
-cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, Ctl* ctl, cudaStream_t st);
+size_t scan_scratch_len(int n);  // long longs of scratch launch_scan_rows needs
+cudaError_t launch_scan_rows(int n, const int* rb, const int* re, int* rowptr, Ctl* ctl, long long* sums,
+                             cudaStream_t st);
 cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col, double* val,
                           cudaStream_t st);
 cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* val, cudaStream_t st);
