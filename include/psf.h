@@ -87,9 +87,12 @@ typedef struct {
     double trunc;       /* truncation bound sum_{i>=N} |a_i| z_i (0 for polynomials) */
     double budget;      /* filtering budget: tol - trunc (Eq. 35) or tol (Eq. 27) */
     int64_t nnz;        /* entries of the result */
-    int64_t fma;        /* algorithmic multiply-adds of every product and sum of the
-                           evaluation (norm powers included): sum over output rows r
-                           of sum_{k in A_r} nnz(B_k) plus the addend entries */
+    int64_t fma;        /* multiply-adds the product kernel executed in the evaluation
+                           (norm powers included): sum over output rows r of
+                           sum_{k in A_r} nnz(B_k) plus the addend entries; a baby
+                           step equal to a power already computed (nothing dropped
+                           before it) is not executed again and not counted here,
+                           its step record still lists its product's count */
 } psf_info_t;
 
 /* Statistics of one filtered product (Alg. 2 l.5-6 or l.11-12). */

@@ -134,9 +134,13 @@ unsigned long long arena_for(double row_len) {
 
 // Launch one product step into matrix slot `slot`, with Algorithm 1 when
 // threshold > 0.
+// reuse_k > 0: the step is baby step k and row slot `slot` still holds the
+// norm phase's Z^k; while no entry has been dropped (a device flag), the
+// product is skipped and k_reuse_pass1 does the step on those rows.
 int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
              double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
-             NormSlot* absmax_slot = nullptr, double blen = 0.0, double alen = 0.0) {
+             NormSlot* absmax_slot = nullptr, double blen = 0.0, double alen = 0.0, int reuse_k = 0,
+             unsigned long long reuse_fma = 0) {
     if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
@@ -184,7 +188,29 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     // table map when a row folds many products (the crossover is tunable)
     const double work = alen > 0.0 ? alen * blen : 0.0;
     const bool table = use_table(w.slot_map, work);
+    if (reuse_k > 0) P.skip_unless = &w.C()->dropped;
     CU(launch_product(P, table, w.st));
+    if (reuse_k > 0) {
+        ReuseArgs R{};
+        R.n = w.n;
+        R.rb = rb;
+        R.re = re;
+        R.col = w.pcol();
+        R.val = w.pval();
+        R.k = reuse_k;
+        R.eps_g = eps_g;
+        R.e_lsb = P.e_lsb;
+        R.fma = reuse_fma;
+        R.words = P.words;
+        R.sticky = P.sticky;
+        R.cand_col = P.cand_col;
+        R.cand_x = P.cand_x;
+        R.cand_cap = P.cand_cap;
+        R.cand_chunk = P.cand_chunk;
+        R.ctl = w.C();
+        R.stat = P.stat;
+        CU(launch_reuse_pass1(R, w.st));
+    }
     if (timed) {
         CU(cudaEventRecord(e1, w.st));
         if (g_tune_rec) {
@@ -578,6 +604,13 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     unsigned long long zcap = series->pool_hint;
     if (zcap < series->z_need + series->z_need / 8) zcap = series->z_need + series->z_need / 8;
     unsigned long long z_used = 0, z_fma = 0;
+    // Once the series knows what its PS phase needs, the pool holds both
+    // phases: the PS phase continues after the powers Z^2..Z^10, whose
+    // leading ones double as baby steps while nothing is dropped.
+    const unsigned long long ps_reserve =
+        (series->ps_need > 0 && !submult && n > 0) ? series->ps_need + series->ps_need / 8 + 4096 : 0;
+    RowView zp{};
+    unsigned long long zfma[kMaxNorms] = {0ull};  // multiply-adds of Z^i in the norm phase
     {
         unsigned long long est = (unsigned long long)Z->nnz * 256ull + (unsigned long long)n * 64ull + 4096ull;
         if (series->z_need == 0 && zcap < est) zcap = est;
@@ -594,11 +627,12 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             na.ctl = w.C();
             na.count = 1;
             if (n > 0) {
-                if ((rc = w.reset_pool(zcap))) return rc;
+                unsigned long long total = zcap + ps_reserve;
+                if (total > (unsigned long long)INT32_MAX) total = INT32_MAX;
+                if ((rc = w.reset_pool(total))) return rc;
                 na.pool_col = w.pcol();
                 na.pool_val = w.pval();
                 CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * 16, st));
-                RowView zp;
                 if ((rc = mark_pool(w, 0)) || (rc = pool_copy(w, *Z, kSlotZp, &zp)) || (rc = mark_pool(w, 1)))
                     return rc;
                 CU(launch_absmax(w.pval(), w.C(), 0, slots + 1, st));
@@ -641,6 +675,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 series->len_z.assign(9, 0.0);
                 for (int i = 2; i <= 10; ++i) {
                     znnz[i] = (double)zs[i - 2].nnz_pre;
+                    zfma[i] = zs[i - 2].fma;
                     series->len_z[(size_t)(i - 2)] = znnz[i - 1] / n;
                 }
             }
@@ -696,12 +731,20 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
         if (series->ps_need == 0 && cap < est) cap = est;
         if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
-            if ((rc = w.reset_pool(cap))) return rc;
+            // attempt 0 continues in the norm phase's pool when it reserved
+            // room; a retry after an overflow starts from an empty pool
+            const bool reuse = attempt == 0 && ps_reserve > 0;
+            const unsigned long long used_before = reuse ? z_used : 0ull;
+            if (!reuse && (rc = w.reset_pool(cap))) return rc;
             CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * (size_t)stat_cap, st));
             steps.clear();
             int si = 0;
             std::vector<RowView> Zh((size_t)q + 1);
-            if ((rc = pool_copy(w, *Z, kSlotZp, &Zh[1]))) return rc;  // Z-hat_(1) = Z, pooled
+            if (reuse) {
+                Zh[1] = zp;  // Z-hat_(1) = Z, pooled by the norm phase
+            } else if ((rc = pool_copy(w, *Z, kSlotZp, &Zh[1]))) {
+                return rc;
+            }
             size_t slot = 0;
             // baby steps: Z-hat_(k+1) = filter(Z Z-hat_(k)), threshold zeta_{k+1}
             for (int k = 1; k < q; ++k) {
@@ -709,8 +752,10 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 double blen = (size_t)(k - 1) < series->len_baby.size()
                                   ? series->len_baby[(size_t)(k - 1)]
                                   : (k <= 10 && znnz[k] > 0.0 ? znnz[k] / n : zlen * k * k);
+                // baby step k + 1 writes row slot k - 1, the slot of the norm phase's Z^(k+1)
+                const int rk = (reuse && k + 1 <= 10 && slot == (size_t)(k - 1)) ? k + 1 : 0;
                 if ((rc = run_step(w, &vz, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
-                                   &Zh[(size_t)k + 1], nullptr, blen, zlen)))
+                                   &Zh[(size_t)k + 1], nullptr, blen, zlen, rk, rk ? zfma[rk] : 0ull)))
                     return rc;
                 psf_step_info_t s{};
                 s.kind = 0;
@@ -846,7 +891,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 return rc;
             }
             eval_fma = c.fma_total;
-            if (c.pool_used > series->ps_need) series->ps_need = c.pool_used;
+            if (c.pool_used - used_before > series->ps_need) series->ps_need = c.pool_used - used_before;
             break;
         }
     }

@@ -38,6 +38,8 @@ struct Ctl {
     unsigned long long cand_cap;
     int cand_over;
     unsigned cand_chunk;  // entries a warp reserves at a time (32..128)
+    int dropped;          // set once Algorithm 1 has dropped an entry (baby steps reuse powers until then)
+    int pad1;
     unsigned bar_count;  // fields from here on survive a pool reset
     unsigned bar_gen;
     int pad;
@@ -48,6 +50,7 @@ struct Ctl {
 // Device half of psf_step_info_t.
 struct StepStat {
     unsigned long long pool_start;  // pool counter before the step's product
+    unsigned long long pool_end;    // 0: the step's entries end at the pool counter
     unsigned long long nnz_pre, nnz_post, ncand, fma;
     double eps_f, dropped;
     int iters, pad;
@@ -123,6 +126,7 @@ struct ProductArgs {
     unsigned long long* cand_x;  // |x| bits
     unsigned long long cand_cap;
     unsigned cand_chunk;
+    const int* skip_unless;     // non-null: the launch does nothing while *skip_unless == 0
     // batch (inst == nullptr: one instance, the fields above apply to all rows)
     const int* inst;            // instance of each row, n entries
     const BatchStep* bstep;     // per instance
@@ -176,6 +180,28 @@ struct Alg1Args {
     StepStat* stat;
     int* cand_col;               // two candidate lists of ctl->cand_cap entries each
     unsigned long long* cand_x;
+};
+
+// Arguments of k_reuse_pass1 (a baby step that equals a power of the norm
+// phase).
+struct ReuseArgs {
+    int n;
+    const int* rb;
+    const int* re;
+    const int* col;
+    const double* val;
+    int k;  // power
+    double eps_g;
+    int e_lsb;
+    unsigned long long fma;  // the power's multiply-adds in the norm phase
+    unsigned long long* words;
+    unsigned* sticky;
+    int* cand_col;
+    unsigned long long* cand_x;
+    unsigned long long cand_cap;
+    unsigned cand_chunk;
+    Ctl* ctl;
+    StepStat* stat;
 };
 
 // Matrix i of the norm kernel occupies the pool entries [mark[i], mark[i+1])

@@ -507,6 +507,9 @@ __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, 
 
 template <bool TAB, bool BATCH>
 __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBlocksPerSm) k_product(ProductArgs P) {
+    // a baby step whose product equals an already computed power (no entry
+    // dropped so far) is done by k_reuse_pass1 instead (same value in all blocks)
+    if (P.skip_unless && __ldcg(P.skip_unless) == 0) return;
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
     // columns and slots of one chunk (lowered only to exercise chunking)
     const int kCols = P.chunk_cols > 0 && P.chunk_cols < ProdSmem<TAB>::kCols ? P.chunk_cols : ProdSmem<TAB>::kCols;
@@ -735,6 +738,55 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
     }
 }
 
+// ---------------------------------------------------------------- k_reuse_pass1
+// A baby step Z-hat_(k) = filter(Z Z-hat_(k-1)) while no earlier step has
+// dropped an entry: Z-hat_(k-1) is then the power Z^(k-1) of the norm phase,
+// so the product is that phase's Z^k, entry for entry, and its rows are kept
+// as they are.  What the product's write-back would have done remains:
+// Algorithm 1's first pass (exact column sums and the candidate list of the
+// entries 0 < |x| <= eps_g) and the step statistics.  The power's pool range
+// is [mark[k-1], mark[k]).  Does nothing once an entry has been dropped (the
+// product kernel then runs instead).
+
+__global__ void __launch_bounds__(256) k_reuse_pass1(ReuseArgs R) {
+    if (__ldcg(&R.ctl->dropped) != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned long long eb = (unsigned long long)__double_as_longlong(R.eps_g);
+    unsigned long long nnz = 0ull, cand = 0ull;
+    CandArena ca;
+    for (int r = gw; r < R.n; r += nwarps) {
+        const int s = R.rb[r], e = R.re[r];
+        for (int q0 = s; q0 < e; q0 += 32) {
+            const int q = q0 + lane;
+            const bool in = q < e;
+            const unsigned long long xb = in ? mag_bits(R.val[q]) : 0ull;
+            const int c = in ? R.col[q] : 0;
+            const bool is_cand = xb != 0ull && xb <= eb;
+            if (is_cand) {
+                exact_add_checked(R.words, R.sticky, c, R.n, xb, R.e_lsb, R.ctl);
+                ++cand;
+            }
+            if (xb) ++nnz;
+            cand_push(ca, is_cand, c, xb, R.cand_col, R.cand_x, &R.ctl->cand_cnt[0], R.cand_cap, R.cand_chunk,
+                      &R.ctl->cand_over, lane);
+        }
+    }
+    cand_close(ca, R.cand_x, lane);
+    nnz = (unsigned long long)warp_sum((int)nnz);
+    cand = (unsigned long long)warp_sum((int)cand);
+    if (lane == 0) {
+        if (nnz) atomicAdd(&R.stat->nnz_pre, nnz);
+        if (cand) atomicAdd(&R.stat->ncand, cand);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        R.stat->fma = R.fma;
+        R.stat->pool_start = R.ctl->mark[R.k - 1];
+        R.stat->pool_end = R.ctl->mark[R.k];
+    }
+}
+
 // ---------------------------------------------------------------- k_alg1
 // Passes 2, 3, ... of Algorithm 1 and the compaction, as one cooperative
 // launch.  On entry the column sums of pass 1 (entries |x| <= eps_g) are in
@@ -758,7 +810,8 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     bool alive = true;
     // the step's pool range; the counter runs past the capacity on overflow
     const unsigned long long p0 = min(__ldcg(&A.stat->pool_start), A.ctl->pool_cap);
-    const unsigned long long p1 = min(__ldcg(&A.ctl->pool_used), A.ctl->pool_cap);
+    const unsigned long long pe = __ldcg(&A.stat->pool_end);
+    const unsigned long long p1 = min(pe ? pe : __ldcg(&A.ctl->pool_used), A.ctl->pool_cap);
     // a phase whose pool overflowed is discarded: its pool range is not
     // complete, so there is nothing to filter (every block reads the same
     // status, set by an earlier launch)
@@ -883,6 +936,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         return;
     }
 
+    if (gt == 0) A.ctl->dropped = 1;
     // compaction: keep |x| > eps_f, in place, column order preserved
     const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
     unsigned long long kept = 0ull;
@@ -1770,6 +1824,15 @@ cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* of
 
 cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st) {
     k_bounds<<<(ninst + 1 + 255) / 256, 256, 0, st>>>(ninst, off, rowptr, bounds);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st) {
+    if (R.n <= 0) return cudaSuccess;
+    int blocks = (R.n + 7) / 8;
+    if (blocks > sms_now() * 8) blocks = sms_now() * 8;
+    k_reuse_pass1<<<blocks, 256, 0, st>>>(R);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ cudaError_t launch_compose_rows(int n, const int* inst, const int* sel, const in
 cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* off, const RowView& src,
                                 const int* rowptr, int* out_rp, int* col, double* val, cudaStream_t st);
 cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st);
+cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st);
 cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
 
 }  // namespace psf

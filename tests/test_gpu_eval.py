@@ -72,6 +72,32 @@ def test_second_evaluation_uses_first_as_hints():
     assert_csr_bitwise(r2.csr, ref.F, "second")
 
 
+@pytest.mark.parametrize("case", ["lap2d_exp", "lap2d_cos", "banded_drop", "banded_1e-12", "unfiltered", "poly"])
+def test_repeated_evaluation_reuses_powers_bitwise(case):
+    # from its second evaluation on, a series keeps the norm phase's powers
+    # and uses them as baby steps until an entry is dropped; the results and
+    # step records must equal the oracle's either way (the loose tolerance
+    # makes baby steps drop entries)
+    Z, a, tol, kw = {
+        "lap2d_exp": (syn.laplacian_2d(40), syn.coeffs("exp"), 1e-12, {}),
+        "lap2d_cos": (syn.laplacian_2d(40), syn.coeffs("cos"), 1e-12, {}),
+        # baby step 3 drops entries: baby step 4 is a product again
+        "banded_drop": (syn.banded_random(3000, 5, 7, 4.0), syn.coeffs("exp"), 1e-6, {}),
+        "banded_1e-12": (syn.banded_random(3000, 5, 7, 2.0), syn.coeffs("exp"), 1e-12, {}),
+        "unfiltered": (syn.laplacian_1d(300), syn.coeffs("exp"), 1e-12, {"filtered": False}),
+        "poly": (syn.banded_random(500, 2, 5, 1.5), [(-1.0) ** i / math.factorial(i) for i in range(17)], 1e-11,
+                 {"poly": True}),
+    }[case]
+    Z = ocsr(Z)
+    s = psf.Series(a, tol, poly=kw.get("poly", False), filtered=kw.get("filtered", True))
+    ref = psscf(Z, a, tol, **kw)
+    first = s.eval(dev(Z))
+    for _ in range(2):
+        again = s.eval(dev(Z))
+        check_same(again, ref, case)
+        assert again.steps == first.steps, case
+
+
 @pytest.mark.parametrize("seed,n,hbw", [(0, 1000, 5), (1, 777, 3), (2, 4099, 2)])
 def test_banded_random_bitwise(seed, n, hbw):
     Z = ocsr(syn.banded_random(n, hbw, seed, 2.0))
