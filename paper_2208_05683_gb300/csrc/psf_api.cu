@@ -597,6 +597,11 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     double znnz[kMaxNorms] = {0.0};  // nnz(Z^i) of this evaluation
     znnz[1] = (double)Z->nnz;
     NormSlot* slots = w.slots.as<NormSlot>();
+    if (n > 0) {
+        const size_t nb = sizeof(unsigned long long) * (size_t)kNormPieces * (size_t)n * 10;
+        CU(w.nwords.alloc(nb, st));
+        CU(cudaMemsetAsync(w.nwords.p, 0, nb, st));
+    }
 
     // ---- Alg. 2 step 1: norms ||Z^i||_1, i <= 10 (Eq. 37)
     double norms[kMaxNorms];
@@ -617,25 +622,28 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
         if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
         for (int attempt = 0;; ++attempt) {
             CU(cudaMemsetAsync(slots, 0, sizeof(NormSlot) * kMaxNorms, st));
-            // matrices of the norm kernel: the pooled Z, then Z^2 .. Z^10, each
-            // delimited in the pool by counter snapshots
-            NormArgs na{};
-            na.n = n;
-            na.slots = slots + 1;
-            na.words = w.words.as<unsigned long long>();
-            na.sticky = w.sticky.as<unsigned>();
-            na.ctl = w.C();
-            na.count = 1;
+            // the pooled Z and Z^2 .. Z^10, each delimited in the pool by counter
+            // snapshots (the marks also give baby steps their powers' ranges)
             if (n > 0) {
                 unsigned long long total = zcap + ps_reserve;
                 if (total > (unsigned long long)INT32_MAX) total = INT32_MAX;
                 if ((rc = w.reset_pool(total))) return rc;
-                na.pool_col = w.pcol();
-                na.pool_val = w.pval();
                 CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * 16, st));
                 if ((rc = mark_pool(w, 0)) || (rc = pool_copy(w, *Z, kSlotZp, &zp)) || (rc = mark_pool(w, 1)))
                     return rc;
                 CU(launch_absmax(w.pval(), w.C(), 0, slots + 1, st));
+                // norms by row tiles: matrix 0 is the pooled Z, matrix i-1 is Z^i
+                NormRowsArgs nr{};
+                nr.n = n;
+                nr.count = 1;
+                nr.rb[0] = zp.rb;
+                nr.re[0] = zp.re;
+                nr.col = w.pcol();
+                nr.val = w.pval();
+                nr.slots = slots + 1;
+                nr.words = w.nwords.as<unsigned long long>();
+                nr.sticky = w.sticky.as<unsigned>();
+                nr.ctl = w.C();
                 if (!submult) {
                     RowView prev = zp;
                     for (int i = 2; i <= 10; ++i) {
@@ -646,11 +654,13 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                                            slots + i, blen, zlen)))
                             return rc;
                         if ((rc = mark_pool(w, i))) return rc;
+                        nr.rb[i - 1] = cur.rb;
+                        nr.re[i - 1] = cur.re;
                         prev = cur;
                     }
-                    na.count = 10;
+                    nr.count = 10;
                 }
-                CU(launch_norms(na, st));
+                CU(launch_norms_rows(nr, st));
             }
             Ctl c;
             NormSlot hs[kMaxNorms];

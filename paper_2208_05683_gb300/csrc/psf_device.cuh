@@ -204,6 +204,22 @@ struct ReuseArgs {
     StepStat* stat;
 };
 
+// Exact ||M_i||_1 of up to kMaxNorms matrices given by their rows (row r of
+// matrix i spans [rb[i][r], re[i][r]) of col/val); max |x| of matrix i is in
+// slots[i].absmax.
+struct NormRowsArgs {
+    int n;
+    int count;
+    const int* rb[kMaxNorms];
+    const int* re[kMaxNorms];
+    const int* col;
+    const double* val;
+    NormSlot* slots;
+    unsigned long long* words;  // count * kNormPieces * n, zero on entry
+    unsigned* sticky;           // count * n, zero on entry
+    Ctl* ctl;
+};
+
 // Matrix i of the norm kernel occupies the pool entries [mark[i], mark[i+1])
 // (gaps read as exact zeros).
 struct NormArgs {
@@ -342,24 +358,10 @@ __device__ __forceinline__ void exact_sub(unsigned long long* w, size_t stride, 
     if (p2) atomicAdd(w + (size_t)(L + 2) * stride, 0ull - p2);
 }
 
-// Read a column's chunks (L2 reads: they were written by other SMs'
-// reductions), clear them if `clear`, propagate the (signed) carries and
-// round the non-negative value to the nearest double, ties to even (a
-// truncated positive remainder, flagged by a nonzero sticky count, breaks
-// ties upward).
-__device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stride, unsigned* sticky, int e_lsb,
-                                              bool clear = true) {
-    unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
-    long long carry = 0;
-#pragma unroll
-    for (int c = 0; c < kChunks; ++c) {
-        const long long t = (long long)__ldcg(w + (size_t)c * stride) + carry;
-        if (clear) w[(size_t)c * stride] = 0ull;
-        limb[c >> 1] |= ((unsigned long long)t & 0xffffffffull) << (32 * (c & 1));
-        carry = t >> 32;
-    }
-    bool st = __ldcg(sticky) != 0u;
-    if (clear) *sticky = 0u;
+// Round the non-negative integer limb[0..3] (256 bits, little endian) times
+// 2^e_lsb to the nearest double, ties to even; `st` flags a positive
+// remainder below the LSB (it breaks ties upward).
+__device__ __forceinline__ double round_limbs(const unsigned long long limb[4], bool st, int e_lsb) {
     int top = -1;
     for (int i = 3; i >= 0; --i)
         if (limb[i]) {
@@ -388,6 +390,85 @@ __device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stri
         }
     }
     return ldexp((double)M, shift + e_lsb);
+}
+
+// Read a column's chunks (L2 reads: they were written by other SMs'
+// reductions), clear them if `clear`, propagate the (signed) carries and
+// round the non-negative value to the nearest double, ties to even (a
+// truncated positive remainder, flagged by a nonzero sticky count, breaks
+// ties upward).
+__device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stride, unsigned* sticky, int e_lsb,
+                                              bool clear = true) {
+    unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
+    long long carry = 0;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        const long long t = (long long)__ldcg(w + (size_t)c * stride) + carry;
+        if (clear) w[(size_t)c * stride] = 0ull;
+        limb[c >> 1] |= ((unsigned long long)t & 0xffffffffull) << (32 * (c & 1));
+        carry = t >> 32;
+    }
+    const bool st = __ldcg(sticky) != 0u;
+    if (clear) *sticky = 0u;
+    return round_limbs(limb, st, e_lsb);
+}
+
+// Column sums of the norm kernel in 24-bit pieces: a column's value is
+//   sum_p w[p] * 2^(24 p + e_lsb),  p = 0 .. kNormPieces-1  (240 bits),
+// each word receiving addends below 2^32 (a tile's shared-memory piece, or
+// one 24-bit piece of a summand).  Summands are below 2^(e_lsb + kWindow).
+constexpr int kNormPieces = 10;
+
+// Split v into 24-bit pieces at offset e_lsb: returns the first piece index;
+// p[0..3] are the pieces (possibly 0); `lost` flags truncated nonzero bits.
+__device__ __forceinline__ int split24(unsigned long long vbits, int e_lsb, unsigned p[4], bool& lost) {
+    int E = (int)(vbits >> 52);
+    unsigned long long M = vbits & ((1ull << 52) - 1);
+    int e;
+    if (E) {
+        M |= (1ull << 52);
+        e = E - 1075;
+    } else {
+        e = -1074;
+    }
+    p[0] = p[1] = p[2] = p[3] = 0u;
+    lost = false;
+    if (M == 0ull) return 0;
+    int o = e - e_lsb;
+    if (o < 0) {
+        const int sh = -o;
+        lost = (sh >= 64 ? M : (M & ((1ull << sh) - 1))) != 0ull;
+        M = sh >= 64 ? 0ull : (M >> sh);
+        if (M == 0ull) return 0;
+        o = 0;
+    }
+    const int L = o / 24, s = o - L * 24;
+    const unsigned long long lo = M << s;                 // bits [0, 64) of M * 2^s
+    const unsigned long long hi = s ? (M >> (64 - s)) : 0ull;  // bits [64, 77)
+    p[0] = (unsigned)(lo & 0xffffffull);
+    p[1] = (unsigned)((lo >> 24) & 0xffffffull);
+    p[2] = (unsigned)(((lo >> 48) | (hi << 16)) & 0xffffffull);
+    p[3] = (unsigned)((hi >> 8) & 0xffffffull);
+    return L;
+}
+
+// Read, clear and round a column of 24-bit pieces.
+__device__ __forceinline__ double round24(unsigned long long* w, size_t stride, unsigned* sticky, int e_lsb) {
+    unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
+    unsigned long long carry = 0ull;
+#pragma unroll
+    for (int p = 0; p < kNormPieces; ++p) {
+        const unsigned long long t = __ldcg(w + (size_t)p * stride) + carry;
+        w[(size_t)p * stride] = 0ull;
+        const unsigned long long piece = t & 0xffffffull;
+        carry = t >> 24;
+        const int bit = 24 * p, li = bit >> 6, sh = bit & 63;
+        limb[li] |= piece << sh;
+        if (sh > 40) limb[li + 1] |= piece >> (64 - sh);
+    }
+    const bool st = __ldcg(sticky) != 0u;
+    *sticky = 0u;
+    return round_limbs(limb, st, e_lsb);
 }
 
 // Per-warp sub-allocator of the entry pool: a warp takes `size` entries (or

@@ -98,6 +98,7 @@ struct Work {
     int n = 0;
     cudaStream_t st = nullptr;
     DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val, cand_col, cand_x, scan;
+    DevBuf nwords;  // 24-bit-piece column sums of the norm phase (zero between uses)
     unsigned long long cap = 0, ccap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap

@@ -1257,14 +1257,152 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
         }
     }
     if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
-    for (long long u = gt; u < (long long)A.count * A.n; u += nthreads) {
-        int mi = (int)(u / A.n), j = (int)(u % A.n);
-        NormSlot* slot = A.inst ? A.slots + (size_t)A.inst[j] * A.slot_stride + mi : A.slots + mi;
-        int lsb = lsb_for_bound(slot->absmax);
+    const int lane = threadIdx.x & 31;
+    for (int mi = 0; mi < A.count; ++mi) {
         unsigned long long* words = A.words + (size_t)mi * kChunks * n;
-        double sum = chunk_round(words + j, n, A.sticky + (size_t)mi * n + j, lsb);
-        unsigned long long sb = (unsigned long long)__double_as_longlong(sum);
-        if (sb) atomicMax(&slot->result, sb);
+        unsigned long long mx = 0ull;
+        for (int j = gt; j < A.n; j += nthreads) {
+            NormSlot* slot = A.inst ? A.slots + (size_t)A.inst[j] * A.slot_stride + mi : A.slots + mi;
+            const int lsb = lsb_for_bound(slot->absmax);
+            const double sum = chunk_round(words + j, n, A.sticky + (size_t)mi * n + j, lsb);
+            const unsigned long long sb = (unsigned long long)__double_as_longlong(sum);
+            if (A.inst) {
+                if (sb) atomicMax(&slot->result, sb);  // columns of one warp may belong to several instances
+            } else {
+                mx = sb > mx ? sb : mx;
+            }
+        }
+        if (!A.inst) {
+            mx = warp_max_u64(mx);  // one reduction per warp, not per column
+            if (lane == 0 && mx) atomicMax(&A.slots[mi].result, mx);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- k_norms_rows
+// The same norms, by tiles of consecutive rows: for banded and grid matrices
+// a tile's entries fall in a narrow window of columns, so a block sums its
+// tile exactly in shared memory (24-bit pieces in 32-bit words: a tile of at
+// most 255 rows cannot overflow them) and adds the window to the global sums
+// once, instead of one global reduction per piece of every entry.  A tile
+// whose window is wider than kNormWin takes the global path entry by entry.
+// One block per (tile, matrix); k_norms_finish rounds and takes the maxima.
+constexpr int kNormTile = 128;
+constexpr int kNormWin = 3072;
+constexpr int kNormRowsThreads = 1024;
+static_assert(kNormTile <= 255, "shared 24-bit pieces of a tile must not overflow");
+
+size_t norms_rows_smem_bytes() { return sizeof(unsigned) * (size_t)(kNormPieces + 1) * kNormWin; }
+
+__global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A) {
+    extern __shared__ unsigned nsm[];  // [kNormPieces][kNormWin] pieces, then [kNormWin] sticky counts
+    __shared__ int s_lo[kNormRowsThreads / 32], s_hi[kNormRowsThreads / 32];
+    if (__ldcg(&A.ctl->status) & kDevPoolFull) return;  // discarded phase
+    const int mi = blockIdx.y;
+    const int n = A.n;
+    const int r0 = blockIdx.x * kNormTile, r1 = min(n, r0 + kNormTile);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int* rb = A.rb[mi];
+    const int* re = A.re[mi];
+    const int lsb = lsb_for_bound(A.slots[mi].absmax);
+    unsigned long long* words = A.words + (size_t)mi * kNormPieces * n;
+    unsigned* sticky = A.sticky + (size_t)mi * n;
+    // the tile's column window (rows are sorted)
+    int lo = INT_MAX, hi = -1;
+    for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) {
+        const int s = rb[r], e = re[r];
+        if (s < e) {
+            lo = min(lo, A.col[s]);
+            hi = max(hi, A.col[e - 1]);
+        }
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if (lane == 0) {
+        s_lo[wid] = lo;
+        s_hi[wid] = hi;
+    }
+    __syncthreads();
+    lo = INT_MAX;
+    hi = -1;
+    for (int i = 0; i < nw; ++i) {
+        lo = min(lo, s_lo[i]);
+        hi = max(hi, s_hi[i]);
+    }
+    if (hi < lo) return;  // an empty tile (same in all threads)
+    if (lo < 0 || hi >= n) {
+        if (threadIdx.x == 0) atomicOr(&A.ctl->status, kDevInternal);
+        return;
+    }
+    const int wlen = hi - lo + 1;
+    const bool local = wlen <= kNormWin;
+    unsigned* wst = nsm + (size_t)kNormPieces * kNormWin;
+    if (local) {
+        for (int i = threadIdx.x; i < wlen; i += blockDim.x) {
+#pragma unroll
+            for (int p = 0; p < kNormPieces; ++p) nsm[p * kNormWin + i] = 0u;
+            wst[i] = 0u;
+        }
+        __syncthreads();
+    }
+    for (int r = r0 + wid; r < r1; r += nw) {
+        const int s = rb[r], e = re[r];
+        for (int q = s + lane; q < e; q += 32) {
+            const unsigned long long xb = mag_bits(A.val[q]);
+            if (xb == 0ull) continue;
+            const int c = A.col[q];
+            if ((unsigned)c >= (unsigned)n) {
+                atomicOr(&A.ctl->status, kDevInternal);
+                continue;
+            }
+            unsigned pc[4];
+            bool lost;
+            const int L = split24(xb, lsb, pc, lost);
+            if (local) {
+                const int o = c - lo;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (pc[j]) atomicAdd(&nsm[(L + j) * kNormWin + o], pc[j]);
+                if (lost) atomicAdd(&wst[o], 1u);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (pc[j]) atomicAdd(&words[(size_t)(L + j) * n + c], (unsigned long long)pc[j]);
+                if (lost) atomicAdd(&sticky[c], 1u);
+            }
+        }
+    }
+    if (!local) return;
+    __syncthreads();
+    for (int i = threadIdx.x; i < wlen; i += blockDim.x) {
+#pragma unroll
+        for (int p = 0; p < kNormPieces; ++p) {
+            const unsigned v = nsm[p * kNormWin + i];
+            if (v) atomicAdd(&words[(size_t)p * n + lo + i], (unsigned long long)v);
+        }
+        if (wst[i]) atomicAdd(&sticky[lo + i], wst[i]);
+    }
+}
+
+__global__ void k_norms_finish(int n, int count, NormSlot* slots, unsigned long long* words, unsigned* sticky,
+                               const Ctl* ctl) {
+    if (__ldcg(&ctl->status) & kDevPoolFull) return;
+    // one thread per (matrix, column); the column count is padded to whole
+    // warps so that a warp's columns belong to one matrix and it reduces
+    // them before the single atomic
+    const long long npad = ((long long)n + 31) & ~31LL;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < (long long)count * npad; u += nt) {
+        const int mi = (int)(u / npad), j = (int)(u % npad);
+        unsigned long long vb = 0ull;
+        if (j < n) {
+            const int lsb = lsb_for_bound(slots[mi].absmax);
+            const double v = round24(words + (size_t)mi * kNormPieces * n + j, (size_t)n, sticky + (size_t)mi * n + j, lsb);
+            vb = (unsigned long long)__double_as_longlong(v);
+        }
+        vb = warp_max_u64(vb);
+        if (lane == 0 && vb) atomicMax(&slots[mi].result, vb);
     }
 }
 
@@ -1634,6 +1772,9 @@ cudaError_t kernels_init() {
         err = cudaFuncSetAttribute(prods[i], cudaFuncAttributeMaxDynamicSharedMemorySize, psmem[i]);
         if (err != cudaSuccess) return err;
     }
+    err = cudaFuncSetAttribute((const void*)k_norms_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)norms_rows_smem_bytes());
+    if (err != cudaSuccess) return err;
     int per = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
@@ -1833,6 +1974,21 @@ cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st) {
     int blocks = (R.n + 7) / 8;
     if (blocks > sms_now() * 8) blocks = sms_now() * 8;
     k_reuse_pass1<<<blocks, 256, 0, st>>>(R);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st) {
+    if (A.n <= 0 || A.count <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((A.n + kNormTile - 1) / kNormTile), (unsigned)A.count);
+    k_norms_rows<<<grid, kNormRowsThreads, norms_rows_smem_bytes(), st>>>(A);
+    ++g_launches;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const long long total = (long long)A.count * (((long long)A.n + 31) & ~31LL);
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > sms_now() * 8) blocks = sms_now() * 8;
+    k_norms_finish<<<blocks, 256, 0, st>>>(A.n, A.count, A.slots, A.words, A.sticky, A.ctl);
     ++g_launches;
     return cudaGetLastError();
 }
