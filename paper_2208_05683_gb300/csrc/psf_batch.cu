@@ -37,6 +37,7 @@ constexpr size_t kRowsZ = 60;        // pooled block-diagonal Z
 constexpr size_t kRowsZq = 61;       // composite Z-hat_(q_i)
 constexpr size_t kRowsBaby = 0;      // + k: baby step k (k = 2..23)
 constexpr size_t kRowsS = 30;        // + (stage & 1): giant-step outputs
+constexpr size_t kRowsPow = 40;      // + k - 2: the norm phase's Z^k (k = 2..10)
 constexpr int kMaxBatchRows = 1 << 24;  // column-sum words: 704 B per row
 
 // Device storage shared by the results of one batch.
@@ -121,6 +122,11 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
     CU(d_nnz.alloc(sizeof(int) * (size_t)count, st));
     CU(d_inst.alloc(sizeof(int) * (size_t)(n > 0 ? n : 1), st));
     CU(d_slots.alloc(sizeof(NormSlot) * kMaxNorms * (size_t)count, st));
+    if (n > 0) {
+        const size_t nb = sizeof(unsigned long long) * (size_t)kNormPieces * (size_t)n * 10;
+        CU(w.nwords.alloc(nb, st));
+        CU(cudaMemsetAsync(w.nwords.p, 0, nb, st));
+    }
     std::vector<BatchSrc> src((size_t)count);
     std::vector<int> nnz((size_t)count);
     for (int i = 0; i < count; ++i) {
@@ -177,22 +183,27 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                                       kMaxNorms, st));
             if ((rc = mark_pool(w, 1))) return rc;
             const RowView zp = w.pooled(zrb, zre);
-            NormArgs na{};
-            na.n = n;
-            na.count = 1;
-            na.pool_col = w.pcol();
-            na.pool_val = w.pval();
-            na.slots = slots + 1;
-            na.slot_stride = kMaxNorms;
-            na.inst = inst;
-            na.words = w.words.as<unsigned long long>();
-            na.sticky = w.sticky.as<unsigned>();
-            na.ctl = w.C();
+            // norms by row tiles: matrix 0 is the pooled Z, matrix k-1 is Z^k
+            NormRowsArgs nr{};
+            nr.n = n;
+            nr.count = 1;
+            nr.rb[0] = zrb;
+            nr.re[0] = zre;
+            nr.col = w.pcol();
+            nr.val = w.pval();
+            nr.slots = slots + 1;
+            nr.slot_stride = kMaxNorms;
+            nr.inst = inst;
+            nr.words = w.nwords.as<unsigned long long>();
+            nr.sticky = w.sticky.as<unsigned>();
+            nr.ctl = w.C();
             if (any_chain) {
                 RowView prev = zp;
                 for (int k = 2; k <= 10; ++k) {
                     int *rb, *re;
-                    if ((rc = w.rows_for(kRowsBaby + (size_t)(k % 2), &rb, &re))) return rc;
+                    if ((rc = w.rows_for(kRowsPow + (size_t)(k - 2), &rb, &re))) return rc;
+                    nr.rb[k - 1] = rb;
+                    nr.re[k - 1] = re;
                     ProductArgs P{};
                     P.n = n;
                     P.A = zp;
@@ -219,9 +230,9 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                     if ((rc = mark_pool(w, k))) return rc;
                     prev = w.pooled(rb, re);
                 }
-                na.count = 10;
+                nr.count = 10;
             }
-            CU(launch_norms(na, st));
+            CU(launch_norms_rows(nr, st));
             Ctl c;
             if ((rc = read_back(w, c, nullptr))) return rc;
             if ((rc = status_to_code(c.status))) return rc;

@@ -218,6 +218,8 @@ struct NormRowsArgs {
     unsigned long long* words;  // count * kNormPieces * n, zero on entry
     unsigned* sticky;           // count * n, zero on entry
     Ctl* ctl;
+    const int* inst;            // batch: instance of each column; matrix i of instance t: slots[t * slot_stride + i]
+    int slot_stride;
 };
 
 // Matrix i of the norm kernel occupies the pool entries [mark[i], mark[i+1])

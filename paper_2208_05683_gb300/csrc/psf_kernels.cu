@@ -1304,7 +1304,7 @@ __global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int* rb = A.rb[mi];
     const int* re = A.re[mi];
-    const int lsb = lsb_for_bound(A.slots[mi].absmax);
+    const int lsb0 = A.inst ? 0 : lsb_for_bound(A.slots[mi].absmax);
     unsigned long long* words = A.words + (size_t)mi * kNormPieces * n;
     unsigned* sticky = A.sticky + (size_t)mi * n;
     // the tile's column window (rows are sorted)
@@ -1355,6 +1355,8 @@ __global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A)
                 atomicOr(&A.ctl->status, kDevInternal);
                 continue;
             }
+            // batch: the fixed point of a column follows its instance's max |x|
+            const int lsb = A.inst ? lsb_for_bound(A.slots[(size_t)A.inst[c] * A.slot_stride + mi].absmax) : lsb0;
             unsigned pc[4];
             bool lost;
             const int L = split24(xb, lsb, pc, lost);
@@ -1385,7 +1387,7 @@ __global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A)
 }
 
 __global__ void k_norms_finish(int n, int count, NormSlot* slots, unsigned long long* words, unsigned* sticky,
-                               const Ctl* ctl) {
+                               const Ctl* ctl, const int* inst, int slot_stride) {
     if (__ldcg(&ctl->status) & kDevPoolFull) return;
     // one thread per (matrix, column); the column count is padded to whole
     // warps so that a warp's columns belong to one matrix and it reduces
@@ -1396,13 +1398,30 @@ __global__ void k_norms_finish(int n, int count, NormSlot* slots, unsigned long 
     for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < (long long)count * npad; u += nt) {
         const int mi = (int)(u / npad), j = (int)(u % npad);
         unsigned long long vb = 0ull;
+        NormSlot* slot = slots + mi;
         if (j < n) {
-            const int lsb = lsb_for_bound(slots[mi].absmax);
+            if (inst) slot = slots + (size_t)inst[j] * slot_stride + mi;
+            const int lsb = lsb_for_bound(slot->absmax);
             const double v = round24(words + (size_t)mi * kNormPieces * n + j, (size_t)n, sticky + (size_t)mi * n + j, lsb);
             vb = (unsigned long long)__double_as_longlong(v);
         }
-        vb = warp_max_u64(vb);
-        if (lane == 0 && vb) atomicMax(&slots[mi].result, vb);
+        if (inst) {
+            // a warp's columns are consecutive, so their instances form
+            // contiguous runs: a segmented reduction leaves each run's
+            // maximum in its first lane
+            const int ti = j < n ? inst[j] : -1;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long w = __shfl_down_sync(kFull, vb, o);
+                const int tj = __shfl_down_sync(kFull, ti, o);
+                if (lane + o < 32 && tj == ti) vb = w > vb ? w : vb;
+            }
+            const int tp = __shfl_up_sync(kFull, ti, 1);
+            const bool first = lane == 0 || tp != ti;
+            if (first && ti >= 0 && vb) atomicMax(&slot->result, vb);
+        } else {
+            vb = warp_max_u64(vb);
+            if (lane == 0 && vb) atomicMax(&slot->result, vb);
+        }
     }
 }
 
@@ -1988,7 +2007,7 @@ cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st) {
     const long long total = (long long)A.count * (((long long)A.n + 31) & ~31LL);
     int blocks = (int)((total + 255) / 256);
     if (blocks > sms_now() * 8) blocks = sms_now() * 8;
-    k_norms_finish<<<blocks, 256, 0, st>>>(A.n, A.count, A.slots, A.words, A.sticky, A.ctl);
+    k_norms_finish<<<blocks, 256, 0, st>>>(A.n, A.count, A.slots, A.words, A.sticky, A.ctl, A.inst, A.slot_stride);
     ++g_launches;
     return cudaGetLastError();
 }
