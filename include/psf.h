@@ -139,9 +139,15 @@ PSF_API int psf_series_destroy(psf_series_t series);
  * Evaluate the series at Z (Algorithm 2): exact ||Z^i||_1 for i <= 10, the
  * plan (Eqs. 6, 24-26, 34-37), baby steps Z-hat_(k+1) = filter(Z Z-hat_(k))
  * and giant steps S-hat_i = filter(B-hat_{b-1-i} + Z-hat_(q) S-hat_{i-1}) with
- * Algorithm 1 after every product.  Synchronizes `stream` twice (after the
- * norms, to plan; at the end, to size the result).  The result CSR is
- * canonical (sorted columns, no stored zeros).
+ * Algorithm 1 after every product.  Synchronizes `stream` three times (input
+ * validation; after the norms, to plan; at the end, to size the result).
+ * The result CSR is canonical (sorted columns, no stored zeros).
+ * The series records sizes seen by the evaluation (pool entries, row
+ * lengths) and sizes the next evaluation's workspace from them; from its
+ * second evaluation on, one pool holds both phases and baby steps reuse the
+ * powers of the norm phase while no entry has been dropped.  Results do not
+ * depend on these records.  Evaluations of one series must not run
+ * concurrently (they update the records); distinct series may.
  * Errors: PSF_EINVAL (malformed Z), PSF_ENOTCONV, PSF_ENOMEM, PSF_ECUDA,
  * PSF_ETIMEOUT, PSF_ETOOBIG.
  */
