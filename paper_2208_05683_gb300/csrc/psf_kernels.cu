@@ -1797,10 +1797,10 @@ cudaError_t kernels_init() {
     int per = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
-    c.alg1_blocks = sms * (per < 2 ? per : 2);
+    c.alg1_blocks = sms * (per < 4 ? per : 4);  // latency-bound phases want warps; barriers want few blocks
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1_batch, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
-    c.alg1b_blocks = sms * (per < 2 ? per : 2);
+    c.alg1b_blocks = sms * (per < 4 ? per : 4);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_norms, kNormThreads, 0);
     if (err != cudaSuccess) return err;
     c.norm_blocks = sms * (per < 2 ? per : 2);
