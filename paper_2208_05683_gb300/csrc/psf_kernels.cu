@@ -738,6 +738,46 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
     }
 }
 
+// Keep the entries of row [s, e) with |x| > fb (bits), in place and in
+// column order; the dropped tail is cleared to exact zeros.  Returns the new
+// end.  Rounds of 128 entries: every lane's four loads are issued before the
+// round's writes (entries only move left, so a round's writes never reach an
+// entry a later round reads).
+__device__ __forceinline__ int compact_row(int* col, double* val, int s, int e, unsigned long long fb, int lane) {
+    int w = s;
+    for (int q0 = s; q0 < e; q0 += 128) {
+        int c[4];
+        double x[4];
+        bool keep[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * 32 + lane;
+            keep[u] = false;
+            c[u] = 0;
+            x[u] = 0.0;
+            if (q < e) {
+                c[u] = col[q];
+                x[u] = val[q];
+                keep[u] = mag_bits(x[u]) > fb;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned m = __ballot_sync(kFull, keep[u]);
+            if (keep[u]) {
+                const int pos = w + __popc(m & lanemask_lt());
+                col[pos] = c[u];
+                val[pos] = x[u];
+            }
+            w += __popc(m);
+        }
+        __syncwarp();
+    }
+    for (int q = w + lane; q < e; q += 32) val[q] = 0.0;
+    return w;
+}
+
 // ---------------------------------------------------------------- k_reuse_pass1
 // A baby step Z-hat_(k) = filter(Z Z-hat_(k-1)) while no earlier step has
 // dropped an entry: Z-hat_(k-1) is then the power Z^(k-1) of the norm phase,
@@ -941,29 +981,8 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
     unsigned long long kept = 0ull;
     for (int r = gw; r < A.n; r += nwarps) {
-        int s = A.rb[r], e = A.re[r];
-        int w = s;
-        for (int q0 = s; q0 < e; q0 += 32) {
-            int q = q0 + lane;
-            int col = 0;
-            double x = 0.0;
-            bool keep = false;
-            if (q < e) {
-                col = A.col[q];
-                x = A.val[q];
-                keep = mag_bits(x) > fb;
-            }
-            __syncwarp();
-            unsigned m = __ballot_sync(kFull, keep);
-            if (keep) {
-                int pos = w + __popc(m & lanemask_lt());
-                A.col[pos] = col;
-                A.val[pos] = x;
-            }
-            w += __popc(m);
-            __syncwarp();
-        }
-        for (int q = w + lane; q < e; q += 32) A.val[q] = 0.0;  // dropped tail reads as zeros
+        const int s = A.rb[r], e = A.re[r];
+        const int w = compact_row(A.col, A.val, s, e, fb, lane);
         if (lane == 0) {
             A.re[r] = w;
             kept += (unsigned long long)(w - s);
@@ -1155,29 +1174,8 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         const int i = A.inst[r];
         if (s_state[i] != 1 || !(s_c[i] > 0.0)) continue;
         const unsigned long long fb = (unsigned long long)__double_as_longlong(s_eps[i]);
-        int s = A.rb[r], e = A.re[r];
-        int w = s;
-        for (int q0 = s; q0 < e; q0 += 32) {
-            int q = q0 + lane;
-            int col = 0;
-            double x = 0.0;
-            bool keep = false;
-            if (q < e) {
-                col = A.col[q];
-                x = A.val[q];
-                keep = mag_bits(x) > fb;
-            }
-            __syncwarp();
-            unsigned m = __ballot_sync(kFull, keep);
-            if (keep) {
-                int pos = w + __popc(m & lanemask_lt());
-                A.col[pos] = col;
-                A.val[pos] = x;
-            }
-            w += __popc(m);
-            __syncwarp();
-        }
-        for (int q = w + lane; q < e; q += 32) A.val[q] = 0.0;
+        const int s = A.rb[r], e = A.re[r];
+        const int w = compact_row(A.col, A.val, s, e, fb, lane);
         if (lane == 0) {
             A.re[r] = w;
             if (w > s) atomicAdd(&A.stat_tab[i].nnz_post, (unsigned long long)(w - s));
