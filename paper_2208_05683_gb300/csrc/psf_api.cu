@@ -87,11 +87,6 @@ int check_csr(const psf_csr_t* m, int n, const char* what) {
     return PSF_OK;
 }
 
-// Host copy of the control block (only the fields read back).
-struct CtlHost {
-    Ctl c;
-    NormSlot s[kMaxNorms];
-};
 
 int read_back(Work& w, Ctl& c, NormSlot* slots) {
     CU(cudaMemcpyAsync(&c, w.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, w.st));
@@ -113,13 +108,12 @@ int status_to_code(int st) {
 
 // Validate input matrices on the device and wait for the verdict: nothing
 // indexes with an input's columns before this returns PSF_OK.
-int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms, int* maxwin = nullptr) {
+int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms) {
     for (const psf_csr_t* m : ms)
         if (m) CU(launch_validate(m->n, m->nnz, m->rowptr, m->col, m->val, w.C(), w.st));
     Ctl c;
     int rc = read_back(w, c, nullptr);
     if (rc) return rc;
-    if (maxwin) *maxwin = c.maxwin;
     return status_to_code(c.status);
 }
 
@@ -486,11 +480,9 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     Work w;
     if ((rc = w.init(n, st, 1))) return rc;
     CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
-    int maxwin = 0;
-    if ((rc = validate_inputs(w, {A, B}, &maxwin))) return rc;
+    if ((rc = validate_inputs(w, {A, B}))) return rc;
     for (int t = 0; t < nadd; ++t)
-        if (addends[t] && (rc = validate_inputs(w, {addends[t]}, &maxwin))) return rc;
-    (void)maxwin;
+        if (addends[t] && (rc = validate_inputs(w, {addends[t]}))) return rc;
     const double blen = B && n > 0 ? (double)B->nnz / n : 0.0;
     unsigned long long est = (unsigned long long)n * 8ull + 16;
     for (int t = 0; t < nadd; ++t)
@@ -587,8 +579,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
 
     Work w;
     if ((rc = w.init(n, st, 16))) return rc;
-    int zwin = 0;
-    if ((rc = validate_inputs(w, {Z}, &zwin))) return rc;
+    if ((rc = validate_inputs(w, {Z}))) return rc;
     w.slot_map = series->kernel;
     w.chunk_cols = series->chunk_cols;
     w.chunk_slots = series->chunk_slots;

@@ -30,8 +30,8 @@ struct Ctl {
     unsigned long long pool_cap;
     unsigned long long cslot[2];   // Algorithm 1 column-sum maxima (bits of doubles >= 0)
     unsigned long long nnz_total;  // row-length scan result
-    int maxwin;                    // widest row (last - first column + 1) of validated inputs
     int status;
+    int pad2;
     // Algorithm 1 candidate lists (two buffers of cand_cap entries): entry
     // counts, and a flag set when the product's list overflowed
     unsigned long long cand_cnt[2];

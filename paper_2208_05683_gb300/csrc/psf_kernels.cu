@@ -5,12 +5,20 @@
 //                 and slot map of each row, exact row reservation in the
 //                 pool, FP64 accumulation in shared memory, write-back of the
 //                 nonzero entries, and the first pass of Algorithm 1 (exact
-//                 column sums of the entries |x| <= eps_g).
+//                 column sums and the candidate list of the entries
+//                 |x| <= eps_g); a batch instantiation reads per-row
+//                 instance parameters.
+//  k_reuse_pass1  a baby step equal to a power of the norm phase: the first
+//                 pass of Algorithm 1 on that power's rows.
 //  k_alg1         the remaining passes of Algorithm 1 (Sec. 3.1.1) and the
-//                 final in-place compaction, one cooperative launch.
-//  k_norms        exact 1-norms of up to 11 matrices (Eq. 37's z_i).
-//  k_absmax, k_validate, k_copy_rows, k_scan_*, k_gather, k_identity:
-//                 plumbing.
+//  k_alg1_batch   final in-place compaction, one cooperative launch (single
+//                 instance, or every filtered instance of a batched step).
+//  k_norms_rows   exact 1-norms of Z^1..Z^10 (Eq. 37's z_i) by row tiles,
+//  k_norms_finish column sums in shared memory; rounding and maxima.
+//  k_norms        exact 1-norms from flat pool ranges (psf_norm1 and its
+//                 allocation-free variant).
+//  k_absmax, k_validate*, k_copy_rows*, k_scan_*, k_gather*, k_identity,
+//  k_inst_table, k_compose_rows, k_bounds: plumbing.
 #include <atomic>
 #include <climits>
 #include <mutex>
@@ -81,8 +89,6 @@ template <bool TAB>
 size_t prod_smem_bytes() {
     return sizeof(ProdSmem<TAB>) * ProdSmem<TAB>::kWarps + sizeof(AddTerm) * kMaxAdd;
 }
-size_t product_smem_bytes() { return prod_smem_bytes<true>(); }
-int product_warps_per_block() { return ProdSmem<true>::kWarps; }
 
 // first position in [s, e) with col >= c (col ascending)
 __device__ __forceinline__ int lower_bound_col(const int* col, int s, int e, int c) {
@@ -1455,7 +1461,6 @@ __global__ void k_validate(int n, int nnz, const int* rowptr, const int* col, co
             bad = true;
         } else {
             int prev = -1;
-            if (s < e) atomicMax(&ctl->maxwin, col[e - 1] - col[s] + 1);
             for (int q = s; q < e; ++q) {
                 int c = col[q];
                 double v = val[q];
@@ -1739,14 +1744,6 @@ __global__ void k_identity(int n, double alpha, int* rowptr, int* col, double* v
     if (r == n) rowptr[n] = n;
 }
 
-__global__ void k_csr_to_rows(int n, const int* rowptr, int* rb, int* re) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) {
-        rb[r] = rowptr[r];
-        re[r] = rowptr[r + 1];
-    }
-}
-
 // ---------------------------------------------------------------- launchers
 // Launch configuration, per device (set up once by kernels_init, guarded by
 // a mutex; a device's entry is published through `ready`).
@@ -2010,11 +2007,5 @@ cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_csr_to_rows<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, rb, re);
-    ++g_launches;
-    return cudaGetLastError();
-}
 
 }  // namespace psf

@@ -10,8 +10,6 @@ namespace psf {
 cudaError_t kernels_init();
 int num_sms();
 long long launch_count();
-size_t product_smem_bytes();
-int product_warps_per_block();
 
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
@@ -46,6 +44,5 @@ cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* of
 cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st);
 cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st);
 cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st);  // then rounds (k_norms_finish)
-cudaError_t launch_csr_to_rows(int n, const int* rowptr, int* rb, int* re, cudaStream_t st);
 
 }  // namespace psf
