@@ -1561,7 +1561,8 @@ __global__ void k_gather(int n, RowView src, const int* rowptr, int* col, double
 }
 
 // Copy a canonical CSR matrix into the pool: each row gets a 4-entry aligned
-// slot of round-up(len, 4) entries (the layout the TMA copies rely on).
+// slot of round-up(len, 4) entries (rows start 16-byte aligned, like the
+// product kernel's rows).
 __global__ void k_copy_rows(int n, const int* rowptr, const int* col, const double* val, int* rb, int* re,
                             int* pool_col, double* pool_val, Ctl* ctl, unsigned long long arena_size) {
     const int lane = threadIdx.x & 31;
