@@ -302,6 +302,9 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
  *   run concurrently on other threads (they may see either setting).
  */
 #define PSF_TUNE_TABLE_CROSSOVER 1
+/* PSF_TUNE_BATCH_GRAPH: 1 (default) runs the PS phase of psf_eval_batch as
+ * one captured CUDA graph, 0 launches its kernels directly (same results). */
+#define PSF_TUNE_BATCH_GRAPH 2
 PSF_API int psf_tune_set(int32_t key, double value);
 PSF_API int psf_tune_get(int32_t key, double* value);
 PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,

@@ -14,6 +14,7 @@ PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
 PSF_MAX_Q = 23
 PSF_NORM1_NOALLOC_MAX_N = 65536
 PSF_TUNE_TABLE_CROSSOVER = 1
+PSF_TUNE_BATCH_GRAPH = 2
 
 ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG"}
 

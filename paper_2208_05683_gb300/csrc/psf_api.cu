@@ -49,6 +49,7 @@ Profile g_prof;
 // giant steps included, where its 24 resident warps per SM hide the gather
 // latency better than the table map's 14.
 std::atomic<double> g_table_crossover{1e300};
+std::atomic<bool> g_batch_graph{true};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
@@ -921,6 +922,10 @@ int psf_tune_set(int32_t key, double value) {
             if (!(value >= 0.0)) return fail(PSF_EINVAL, "crossover must be >= 0");
             g_table_crossover.store(value);
             return PSF_OK;
+        case PSF_TUNE_BATCH_GRAPH:
+            if (!(value == 0.0 || value == 1.0)) return fail(PSF_EINVAL, "batch graph must be 0 or 1");
+            g_batch_graph.store(value != 0.0);
+            return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
     }
@@ -931,6 +936,9 @@ int psf_tune_get(int32_t key, double* value) {
     switch (key) {
         case PSF_TUNE_TABLE_CROSSOVER:
             *value = g_table_crossover.load();
+            return PSF_OK;
+        case PSF_TUNE_BATCH_GRAPH:
+            *value = g_batch_graph.load() ? 1.0 : 0.0;
             return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);

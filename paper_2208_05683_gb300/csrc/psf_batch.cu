@@ -95,6 +95,21 @@ BatchStep step_of(int mode, double thr, double e_r, int maxit) {
     return b;
 }
 
+// A non-blocking stream of the calling thread on the current device, on
+// which batch graphs are recorded (never executed).
+int capture_stream(cudaStream_t* out) {
+    static thread_local cudaStream_t t_stream = nullptr;
+    static thread_local int t_dev = -1;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (!t_stream || t_dev != dev) {
+        CU(cudaStreamCreateWithFlags(&t_stream, cudaStreamNonBlocking));
+        t_dev = dev;
+    }
+    *out = t_stream;
+    return PSF_OK;
+}
+
 int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaStream_t st, psf_result_t* outs) {
     int rc = PSF_OK;
     // ---- offsets of the block-diagonal matrix
@@ -415,9 +430,19 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
     Ctl cfin{};
     for (int attempt = 0;; ++attempt) {
         if ((rc = w.reset_pool(cap))) return rc;
-        CU(cudaMemsetAsync(d_stat.p, 0, sizeof(StepStat) * nst * (size_t)count, st));
         int *zrb, *zre, *qrb, *qre;
         if ((rc = w.rows_for(kRowsZ, &zrb, &zre)) || (rc = w.rows_for(kRowsZq, &qrb, &qre))) return rc;
+        // every row slot of the stages exists before the launches are enqueued
+        // (a captured graph must not allocate)
+        for (size_t si = 0; si < nst; ++si) {
+            int *rb0, *re0;
+            const size_t slot = stages[si].kind == 0 ? kRowsBaby + (size_t)stages[si].index : kRowsS + (si & 1);
+            if ((rc = w.rows_for(slot, &rb0, &re0))) return rc;
+        }
+        // the whole PS phase: pool copy of Z, every stage, the row-length scan
+        auto enqueue = [&](cudaStream_t st) -> int {
+        CU(cudaMemsetAsync(d_stat.p, 0, sizeof(StepStat) * nst * (size_t)count, st));
+
         CU(launch_copy_rows_batch(n, inst, dsrc, zrb, zre, w.pcol(), w.pval(), w.C(), arena_z, nullptr, 0, st));
         const RowView zp = w.pooled(zrb, zre);
         std::vector<RowView> baby((size_t)qmax + 1);
@@ -528,9 +553,44 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         F = S;
         CU(launch_scan_rows(n, F.rb, F.re, d_rowptr.as<int>(), w.C(), w.scan.as<long long>(), st));
         CU(launch_bounds(count, d_off.as<int>(), d_rowptr.as<int>(), d_bounds.as<int>(), st));
+        return PSF_OK;
+        };
+        // captured into a CUDA graph and launched as one unit (no host work
+        // between its ~2 launches per stage); direct launches while the
+        // product kernel is being profiled, or when graphs are switched off
+        const bool use_graph = !g_prof.on && g_batch_graph.load();
+        cudaGraphExec_t exec = nullptr;
+        if (use_graph) {
+            // recorded on a stream of the library (capture is not allowed on
+            // the legacy default stream), launched on the caller's stream
+            cudaStream_t cs = nullptr;
+            if ((rc = capture_stream(&cs))) return rc;
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue(cs);
+            const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+            if (rc == PSF_OK && ec != cudaSuccess) rc = fail(PSF_ECUDA, "batch graph capture: %s", cudaGetErrorString(ec));
+            if (rc == PSF_OK) {
+                const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+                if (ei != cudaSuccess) rc = fail(PSF_ECUDA, "batch graph instantiation: %s", cudaGetErrorString(ei));
+            }
+            if (graph) cudaGraphDestroy(graph);
+            if (rc == PSF_OK) {
+                const cudaError_t el = cudaGraphLaunch(exec, st);
+                if (el != cudaSuccess) rc = fail(PSF_ECUDA, "batch graph launch: %s", cudaGetErrorString(el));
+            }
+            if (rc) {
+                if (exec) cudaGraphExecDestroy(exec);
+                return rc;
+            }
+        } else if ((rc = enqueue(st))) {
+            return rc;
+        }
         CU(cudaMemcpyAsync(bounds.data(), d_bounds.p, sizeof(int) * bounds.size(), cudaMemcpyDeviceToHost, st));
         CU(cudaMemcpyAsync(pst.data(), d_stat.p, sizeof(StepStat) * pst.size(), cudaMemcpyDeviceToHost, st));
-        if ((rc = read_back(w, cfin, nullptr))) return rc;
+        rc = read_back(w, cfin, nullptr);
+        if (exec) cudaGraphExecDestroy(exec);  // the stream has drained
+        if (rc) return rc;
         if ((rc = status_to_code(cfin.status))) return rc;
         if (cfin.status & kDevPoolFull) {
             if ((rc = w.clear_sums())) return rc;

@@ -175,6 +175,8 @@ struct Work {
 // Process-wide tuning (psf_tune_*, psf_autotune): the products per output
 // row from which the product kernel uses the column-table slot map.
 extern std::atomic<double> g_table_crossover;
+// the PS phase of a batch runs as one captured CUDA graph (PSF_TUNE_BATCH_GRAPH)
+extern std::atomic<bool> g_batch_graph;
 // slot_map 1: table, 2: bitmap, 0: by the work per row and the crossover
 inline bool use_table(int slot_map, double work_per_row) {
     return slot_map == 1 || (slot_map == 0 && work_per_row >= g_table_crossover.load(std::memory_order_relaxed));

@@ -128,3 +128,24 @@ def test_batch_errors_fail_the_whole_batch():
         psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12), psf.Series(syn.coeffs("exp", 5), 1e-12)],
                        [good, good])
     assert e.value.code == 4
+
+
+def test_graph_and_direct_launches_agree():
+    # the PS phase of a batch runs as one captured CUDA graph by default;
+    # launching its kernels directly gives the same bits
+    from paper_2208_05683_gb300 import _abi
+    cases = mixed_cases()
+    Zs = [dev(Z) for _, Z, _, _, _ in cases]
+    old = psf.tune_get(_abi.PSF_TUNE_BATCH_GRAPH)
+    try:
+        out = {}
+        for g in (1.0, 0.0):
+            psf.tune_set(_abi.PSF_TUNE_BATCH_GRAPH, g)
+            series = [series_of(a, tol, **kw) for _, _, a, tol, kw in cases]
+            out[g] = psf.eval_batch(series, Zs)
+        for (name, *_), a, b in zip(cases, out[1.0], out[0.0]):
+            for x, y in zip(a.csr.to_host(), b.csr.to_host()):
+                assert np.array_equal(x, y), name
+            assert a.steps == b.steps, name
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_BATCH_GRAPH, old)
