@@ -1351,6 +1351,9 @@ __global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A)
     }
     for (int r = r0 + wid; r < r1; r += nw) {
         const int s = rb[r], e = re[r];
+        // batch: the fixed point of a column follows its instance's max |x|;
+        // a row's columns all belong to the row's instance (block diagonal)
+        const int lsb = A.inst ? lsb_for_bound(A.slots[(size_t)A.inst[r] * A.slot_stride + mi].absmax) : lsb0;
         for (int q = s + lane; q < e; q += 32) {
             const unsigned long long xb = mag_bits(A.val[q]);
             if (xb == 0ull) continue;
@@ -1359,8 +1362,6 @@ __global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A)
                 atomicOr(&A.ctl->status, kDevInternal);
                 continue;
             }
-            // batch: the fixed point of a column follows its instance's max |x|
-            const int lsb = A.inst ? lsb_for_bound(A.slots[(size_t)A.inst[c] * A.slot_stride + mi].absmax) : lsb0;
             unsigned pc[4];
             bool lost;
             const int L = split24(xb, lsb, pc, lost);
@@ -2001,9 +2002,10 @@ cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st) {
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const long long total = (long long)A.count * (((long long)A.n + 31) & ~31LL);
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > sms_now() * 8) blocks = sms_now() * 8;
-    k_norms_finish<<<blocks, 256, 0, st>>>(A.n, A.count, A.slots, A.words, A.sticky, A.ctl, A.inst, A.slot_stride);
+    long long blocks = (total + 255) / 256;  // one (matrix, column) per thread
+    if (blocks > 65535LL * 64) blocks = 65535LL * 64;
+    k_norms_finish<<<(unsigned)blocks, 256, 0, st>>>(A.n, A.count, A.slots, A.words, A.sticky, A.ctl, A.inst,
+                                                     A.slot_stride);
     ++g_launches;
     return cudaGetLastError();
 }
