@@ -305,6 +305,11 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
 /* PSF_TUNE_BATCH_GRAPH: 1 (default) runs the PS phase of psf_eval_batch as
  * one captured CUDA graph, 0 launches its kernels directly (same results). */
 #define PSF_TUNE_BATCH_GRAPH 2
+/* PSF_TUNE_BATCH_REUSE: 1 (default) lets psf_eval_batch take baby step k of
+ * an instance that has dropped no entry yet from the power Z^k its norm
+ * phase computed (k <= 10: the same entries as the product), 0 always runs
+ * the product (same results). */
+#define PSF_TUNE_BATCH_REUSE 3
 PSF_API int psf_tune_set(int32_t key, double value);
 PSF_API int psf_tune_get(int32_t key, double* value);
 PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,

@@ -50,6 +50,7 @@ Profile g_prof;
 // latency better than the table map's 14.
 std::atomic<double> g_table_crossover{1e300};
 std::atomic<bool> g_batch_graph{true};
+std::atomic<bool> g_batch_reuse{true};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
@@ -926,6 +927,10 @@ int psf_tune_set(int32_t key, double value) {
             if (!(value == 0.0 || value == 1.0)) return fail(PSF_EINVAL, "batch graph must be 0 or 1");
             g_batch_graph.store(value != 0.0);
             return PSF_OK;
+        case PSF_TUNE_BATCH_REUSE:
+            if (!(value == 0.0 || value == 1.0)) return fail(PSF_EINVAL, "batch reuse must be 0 or 1");
+            g_batch_reuse.store(value != 0.0);
+            return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
     }
@@ -939,6 +944,9 @@ int psf_tune_get(int32_t key, double* value) {
             return PSF_OK;
         case PSF_TUNE_BATCH_GRAPH:
             *value = g_batch_graph.load() ? 1.0 : 0.0;
+            return PSF_OK;
+        case PSF_TUNE_BATCH_REUSE:
+            *value = g_batch_reuse.load() ? 1.0 : 0.0;
             return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);

@@ -12,7 +12,9 @@
 // Steps of a batch (S = the stage counter):
 //   z chain   Z^2..Z^10 of all instances (exact norms, Eq. 37), then one
 //             norm launch; the host plans every instance (one sync)
-//   baby k    k = 2..max q_i: Z-hat_(k) = filter(Z Z-hat_(k-1)) for q_i >= k
+//   baby k    k = 2..max q_i: Z-hat_(k) = filter(Z Z-hat_(k-1)) for q_i >= k;
+//             an instance that has dropped no entry yet copies its Z^k from
+//             the norm phase instead (the same entries, k <= 10)
 //   S_0       B-hat_{b_i - 1} (addends only) for instances with g_i = 0
 //   giant j   j = 1..max b_i - 1: S-hat_j = filter(B-hat + Z-hat_(q_i) S-hat_{j-1})
 //             for j <= b_i - 1; finished instances pass their rows through
@@ -79,7 +81,9 @@ struct StageTab {
     std::vector<double> alpha;  // [t * ninst + i]
     bool any_filter = false;
     bool any_product = false;
+    bool any_reuse = false;  // some instance may take the norm phase's Z^k
     int nadd = 0;
+    double reuse_rows = 0.0, reuse_nnz = 0.0;  // size of those powers (arena estimate)
     double work_rows = 0.0, work_fma = 0.0;  // estimates for the slot map and arenas
 };
 
@@ -294,6 +298,20 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         }
     }
 
+    // ---- the norm phase's powers stay in their pool for the baby steps: while
+    // an instance has dropped no entry, its baby step k is its Z^k
+    bool keep_powers = false;
+    for (int i = 0; i < count && g_batch_reuse.load(); ++i)
+        if (chain[(size_t)i] && !ip[(size_t)i].trivial && ip[(size_t)i].p.q >= 2) keep_powers = true;
+    DevBuf zk_col, zk_val;  // that pool; the PS phase gets a new one
+    if (keep_powers) {
+        std::swap(zk_col.p, w.pool_col.p);
+        std::swap(zk_col.st, w.pool_col.st);
+        std::swap(zk_val.p, w.pool_val.p);
+        std::swap(zk_val.st, w.pool_val.st);
+        w.cap = 0;
+    }
+
     // ---- stage schedule of the PS phase
     int qmax = 1, bmax = 1;
     for (int i = 0; i < count; ++i)
@@ -350,6 +368,12 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 if (D.index <= p.q) {
                     const double thr = nofilter ? 0.0 : p.zeta[(size_t)D.index];
                     B = step_of(kBatchProduct, thr, S->e_r, S->maxit);
+                    if (keep_powers && chain[(size_t)i] && D.index <= 10) {
+                        B.reuse = 1;
+                        T.any_reuse = true;
+                        T.reuse_rows += ni;
+                        T.reuse_nnz += P.znnz[(size_t)D.index];
+                    }
                     const double bl = P.znnz[(size_t)(D.index - 1)] > 0.0 ? P.znnz[(size_t)(D.index - 1)] / ni
                                                                           : zl * (D.index - 1) * (D.index - 1);
                     T.work_rows += ni;
@@ -387,7 +411,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         }
     }
     // device copies of the stage tables, one upload
-    DevBuf d_tab, d_stat, d_sel, d_cslot, d_pstart;
+    DevBuf d_tab, d_stat, d_sel, d_cslot, d_pstart, d_dropped;
     std::vector<size_t> step_off(nst), alpha_off(nst);
     size_t bytes = 0;
     for (size_t si = 0; si < nst; ++si) {
@@ -408,6 +432,15 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
     CU(d_stat.alloc(sizeof(StepStat) * nst * (size_t)count, st));
     CU(d_cslot.alloc(sizeof(unsigned long long) * 2 * (size_t)count, st));
     CU(d_pstart.alloc(sizeof(unsigned long long) * (nst + 1), st));
+    CU(d_dropped.alloc(sizeof(int) * (size_t)count, st));
+    // the norm phase's Z^k (k = 2..10) in its kept pool
+    RowView zpow[11] = {};
+    if (keep_powers)
+        for (int k = 2; k <= 10; ++k) {
+            int *rb, *re;
+            if ((rc = w.rows_for(kRowsPow + (size_t)(k - 2), &rb, &re))) return rc;
+            zpow[k] = RowView{rb, re, zk_col.as<int>(), zk_val.as<double>()};
+        }
     std::vector<int> sel((size_t)count);
     for (int i = 0; i < count; ++i) sel[(size_t)i] = ip[(size_t)i].trivial ? 1 : ip[(size_t)i].p.q;
     CU(d_sel.alloc(sizeof(int) * (size_t)count, st));
@@ -442,6 +475,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         // the whole PS phase: pool copy of Z, every stage, the row-length scan
         auto enqueue = [&](cudaStream_t st) -> int {
         CU(cudaMemsetAsync(d_stat.p, 0, sizeof(StepStat) * nst * (size_t)count, st));
+        CU(cudaMemsetAsync(d_dropped.p, 0, sizeof(int) * (size_t)count, st));
 
         CU(launch_copy_rows_batch(n, inst, dsrc, zrb, zre, w.pcol(), w.pval(), w.C(), arena_z, nullptr, 0, st));
         const RowView zp = w.pooled(zrb, zre);
@@ -504,6 +538,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             P.stat_tab = d_stat.as<StepStat>() + si * (size_t)count;
             P.chunk_cols = w.chunk_cols;
             P.chunk_slots = w.chunk_slots;
+            P.inst_dropped = d_dropped.as<int>();
             if (T.any_filter) {
                 P.cand_col = w.cand_col.as<int>();
                 P.cand_x = w.cand_x.as<unsigned long long>();
@@ -526,6 +561,12 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 CU(cudaEventRecord(e1, st));
                 g_prof.ev.emplace_back(e0, e1);
             }
+            if (T.any_reuse) {
+                ProductArgs C = P;
+                C.power = zpow[D.index];
+                C.arena = arena_for(T.reuse_nnz / T.reuse_rows);
+                CU(launch_reuse_copy_batch(C, st));
+            }
             if (T.any_filter) {
                 Alg1BatchArgs a{};
                 a.n = n;
@@ -544,6 +585,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 a.stat_tab = P.stat_tab;
                 a.cand_col = P.cand_col;
                 a.cand_x = P.cand_x;
+                a.inst_dropped = d_dropped.as<int>();
                 CU(launch_alg1_batch(a, st));
             }
             const RowView out = w.pooled(rb, re);

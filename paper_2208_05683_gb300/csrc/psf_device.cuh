@@ -10,7 +10,8 @@ namespace psf {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kChunks = 8;    // exact column sums: 8 x 32-bit chunks = 256-bit fixed point
 constexpr int kWindow = 190;  // bits between the fixed point's LSB and 2^E_ref
-constexpr int kMinLsb = -1000;
+constexpr int kMinLsb = -1074;  // the LSB of the subnormals: nothing below it
+constexpr int kExactBits = 96;  // a rounded column sum at or above 2^(e_lsb + 96) is exact
 constexpr int kMaxAdd = 24;   // addend terms of one product (PSF_MAX_Q + 1)
 constexpr int kMaxNorms = 11; // ||Z^i||_1, i = 0..10
 
@@ -96,7 +97,7 @@ struct BatchStep {
     int e_lsb;     // LSB exponent of the column-sum fixed point
     int maxit;     // Algorithm 1 pass cap
     int mode;
-    int pad;
+    int reuse;     // baby step k <= 10 of an instance whose norm phase computed Z^k
 };
 
 // C = sum_t add[t].alpha * M_t + A * B, rows written to the pool.
@@ -134,6 +135,11 @@ struct ProductArgs {
     int ninst;
     int absmax_stride;          // absmax slot of instance i: absmax_slot + i * absmax_stride
     StepStat* stat_tab;         // per instance (nullptr: no statistics)
+    // batched baby steps: instances with bstep.reuse whose flag here is 0
+    // (no entry dropped so far) take their rows from `power` (the norm
+    // phase's Z^k) instead of the product
+    const int* inst_dropped;
+    RowView power;
 };
 
 // Algorithm 1 passes 2, 3, ... and compaction for every filtered instance of
@@ -155,6 +161,7 @@ struct Alg1BatchArgs {
     StepStat* stat_tab;  // per instance
     int* cand_col;       // two candidate lists of ctl->cand_cap entries each
     unsigned long long* cand_x;
+    int* inst_dropped;   // optional: set to 1 for the instances that dropped entries
 };
 
 // One input matrix of a batch (device CSR, 0-based local columns).
@@ -285,6 +292,16 @@ __device__ __forceinline__ int lsb_for_bound(unsigned long long xbits) {
     int eref = E ? E - 1023 + 1 : -1022;
     int lsb = eref - kWindow;
     return lsb < kMinLsb ? kMinLsb : lsb;
+}
+
+// Is a column sum rounded from the fixed point with LSB 2^e_lsb the exact
+// sum rounded?  The truncated remainder is below 2^(e_lsb + 32) (at most
+// 2^31 summands), so it only acts as a sticky bit when the sum's leading bit
+// is 54 + 32 or more bits above the LSB; an LSB at the subnormal LSB
+// truncates nothing.
+__device__ __forceinline__ bool sum_is_exact(double c, int e_lsb) {
+    const int E = (int)(((unsigned long long)__double_as_longlong(c) >> 52) & 0x7ff);
+    return e_lsb <= kMinLsb || (E != 0 && E - 1023 >= e_lsb + kExactBits);
 }
 
 // |x| as the bit pattern of a non-negative double: for such patterns the

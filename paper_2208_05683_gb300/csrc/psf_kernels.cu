@@ -10,6 +10,8 @@
 //                 instance parameters.
 //  k_reuse_pass1  a baby step equal to a power of the norm phase: the first
 //                 pass of Algorithm 1 on that power's rows.
+//  k_reuse_copy_batch  the same for the instances of a batch: those rows
+//                 copied into the step's pool range, with that first pass.
 //  k_alg1         the remaining passes of Algorithm 1 (Sec. 3.1.1) and the
 //  k_alg1_batch   final in-place compaction, one cooperative launch (single
 //                 instance, or every filtered instance of a batched step).
@@ -553,6 +555,8 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
         if constexpr (BATCH) {
             r_inst = P.inst[r];
             const BatchStep bs = P.bstep[r_inst];
+            // the row equals the norm phase's power: k_reuse_copy_batch writes it
+            if (bs.reuse && __ldcg(P.inst_dropped + r_inst) == 0) continue;
             if (bs.mode == kBatchSkip || bs.mode == kBatchPass) {
                 if (lane == 0) {
                     P.out_rb[r] = bs.mode == kBatchPass ? P.B.rb[r] : 0;
@@ -833,6 +837,76 @@ __global__ void __launch_bounds__(256) k_reuse_pass1(ReuseArgs R) {
     }
 }
 
+// ---------------------------------------------------------------- k_reuse_copy_batch
+// Batched baby step k for the instances that have dropped no entry so far:
+// their Z-hat_(k-1) is the norm phase's Z^(k-1), so the product Z Z-hat_(k-1)
+// is that phase's Z^k, entry for entry (the same terms in the same order).
+// Each such row is copied from the norm phase's pool (P.power) into the
+// step's own pool range, and what the product's write-back does besides is
+// done on the way: Algorithm 1's first pass (column sums and candidate list
+// of the entries 0 < |x| <= eps_g) and the row statistics, with the
+// product's multiply-add count (the B row lengths summed over row r of A).
+// The product kernel skips these rows.
+__global__ void __launch_bounds__(256) k_reuse_copy_batch(ProductArgs P) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    Arena arena;
+    CandArena carena;
+    for (int r = gw; r < P.n; r += nwarps) {
+        const int i = P.inst[r];
+        const BatchStep bs = P.bstep[i];
+        if (!bs.reuse || __ldcg(P.inst_dropped + i) != 0) continue;
+        unsigned long long fma = 0ull;
+        for (int p = P.A.rb[r] + lane; p < P.A.re[r]; p += 32) {
+            const int k = P.A.col[p];
+            fma += (unsigned long long)(P.B.re[k] - P.B.rb[k]);
+        }
+        const int s = P.power.rb[r], len = P.power.re[r] - s;
+        if (len <= 0) {
+            if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
+            row_stats_batch(P, i, fma, 0ull, 0, 0ull, lane);
+            continue;
+        }
+        const unsigned long long span = ((unsigned long long)len + 3ull) & ~3ull;
+        const long long base = arena_take(arena, span, P.arena, P.ctl, P.pool_val, lane);
+        if (base < 0) {
+            if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
+            continue;
+        }
+        const bool filt = bs.eps_g > 0.0;
+        const unsigned long long eb = (unsigned long long)__double_as_longlong(bs.eps_g);
+        unsigned long long cand = 0ull;
+        for (int q0 = 0; q0 < len; q0 += 32) {
+            const int q = q0 + lane;
+            const bool in = q < len;
+            const double x = in ? P.power.val[s + q] : 0.0;
+            const int c = in ? P.power.col[s + q] : 0;
+            const unsigned long long xb = mag_bits(x);
+            const bool is_cand = filt && xb != 0ull && xb <= eb;
+            if (in) {
+                P.pool_col[base + q] = c;
+                P.pool_val[base + q] = x;
+            }
+            if (is_cand) {
+                exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, bs.e_lsb);
+                ++cand;
+            }
+            if (P.cand_col)
+                cand_push(carena, is_cand, c, xb, P.cand_col, P.cand_x, &P.ctl->cand_cnt[0], P.cand_cap, P.cand_chunk,
+                          &P.ctl->cand_over, lane);
+        }
+        for (long long q = base + len + lane; q < base + (long long)span; q += 32) P.pool_val[q] = 0.0;
+        if (lane == 0) {
+            P.out_rb[r] = (int)base;
+            P.out_re[r] = (int)(base + len);
+        }
+        row_stats_batch(P, i, fma, cand, len, 0ull, lane);
+    }
+    arena_close(arena, P.pool_val, lane);
+    if (P.cand_col) cand_close(carena, P.cand_x, lane);
+}
+
 // ---------------------------------------------------------------- k_alg1
 // Passes 2, 3, ... of Algorithm 1 and the compaction, as one cooperative
 // launch.  On entry the column sums of pass 1 (entries |x| <= eps_g) are in
@@ -971,6 +1045,41 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         A.ctl->cand_over = 0;
     }
     if (dirty) clear_sums(A.words, A.sticky, A.n, gt, nthreads);  // zero for the next step
+    if (!sum_is_exact(c, A.e_lsb)) {
+        // every candidate is tiny against eps_g and c may have lost bits
+        // below the LSB: count the final candidates again with the LSB of
+        // the largest one.  cslot[it & 1] is 0 (cleared by the last
+        // finalize), cslot[(it - 1) & 1] holds the c every block has read
+        // once all blocks reach the first barrier.
+        const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
+        const int sx = it & 1, sc = (it - 1) & 1;
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (gt == 0) A.ctl->cslot[sc] = 0ull;
+        unsigned long long mx = 0ull;
+        for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
+            const unsigned long long xb = mag_bits(__ldcg(A.val + q));
+            if (xb <= fb && xb > mx) mx = xb;
+        }
+        mx = warp_max_u64(mx);
+        if (lane == 0 && mx) atomicMax(&A.ctl->cslot[sx], mx);
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        const int lsb = lsb_for_bound(__ldcg(&A.ctl->cslot[sx]));
+        for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
+            const unsigned long long xb = mag_bits(__ldcg(A.val + q));
+            if (xb != 0ull && xb <= fb) exact_add_checked(A.words, A.sticky, A.col[q], A.n, xb, lsb, A.ctl);
+        }
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        unsigned long long local = 0ull;
+        for (int j = gt; j < A.n; j += nthreads) {
+            const double s = chunk_round(A.words + j, n, A.sticky + j, lsb, true);
+            const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+            local = sb > local ? sb : local;
+        }
+        local = warp_max_u64(local);
+        if (lane == 0 && local) atomicMax(&A.ctl->cslot[sc], local);
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        c = __longlong_as_double((long long)__ldcg(&A.ctl->cslot[sc]));
+    }
     if (!(c > 0.0)) {
         // nothing was dropped: the matrix stays as the product wrote it
         if (gt == 0) {
@@ -1022,7 +1131,9 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
     __shared__ double s_eps[kMaxBatch];  // eps_f
     __shared__ double s_c[kMaxBatch];    // last column-sum maximum c
     __shared__ int s_it[kMaxBatch];
-    __shared__ unsigned char s_state[kMaxBatch];  // 0 iterating, 1 finished, 2 not filtered here
+    // 0 iterating, 1 finished, 2 not filtered here, 3 finished without
+    // candidates, 4 finished with a c to count again (see below)
+    __shared__ unsigned char s_state[kMaxBatch];
     __shared__ int s_left;
     if (__ldcg(&A.ctl->status) & kDevPoolFull) return;  // discarded phase (same for all blocks)
     if (threadIdx.x == 0) s_left = 0;
@@ -1036,7 +1147,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         s_it[i] = 0;
         // an instance without candidates finds c = 0 in its first pass
         const bool empty = filt && __ldcg(&A.stat_tab[i].ncand) == 0ull;
-        s_state[i] = !filt ? 2 : (empty ? 1 : 0);
+        s_state[i] = !filt ? 2 : (empty ? 3 : 0);
         if (empty) s_it[i] = 1;
         left += (filt && !empty) ? 1 : 0;
     }
@@ -1166,6 +1277,62 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         A.ctl->cand_over = 0;
     }
     if (dirty) clear_sums(A.words, A.sticky, A.n, gt, nthreads);  // zero for the next step
+    // an instance whose candidates are all tiny against its eps_g may have
+    // lost bits of c below the LSB: its final candidates are counted again
+    // with the LSB of its largest one (the same instances in every block)
+    int nfix = 0;
+    for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
+        if (s_state[i] == 1 && !sum_is_exact(s_c[i], A.bstep[i].e_lsb)) {
+            s_state[i] = 4;
+            ++nfix;
+        }
+    if (__syncthreads_or(nfix)) {
+        __shared__ int s_lsb[kMaxBatch];
+        // every block has read the maxima: slot 2i takes the largest
+        // candidate, slot 2i + 1 the new c
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
+                if (s_state[i] == 4) A.cslot[2 * i] = A.cslot[2 * i + 1] = 0ull;
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
+            const unsigned long long xb = mag_bits(__ldcg(A.val + q));
+            if (xb == 0ull) continue;
+            const int col = A.col[q];
+            if ((unsigned)col >= (unsigned)A.n) continue;
+            const int i = A.inst[col];
+            if (s_state[i] == 4 && xb <= (unsigned long long)__double_as_longlong(s_eps[i]))
+                atomicMax(&A.cslot[2 * i], xb);
+        }
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
+            if (s_state[i] == 4) s_lsb[i] = lsb_for_bound(__ldcg(&A.cslot[2 * i]));
+        __syncthreads();
+        for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
+            const unsigned long long xb = mag_bits(__ldcg(A.val + q));
+            if (xb == 0ull) continue;
+            const int col = A.col[q];
+            if ((unsigned)col >= (unsigned)A.n) continue;
+            const int i = A.inst[col];
+            if (s_state[i] == 4 && xb <= (unsigned long long)__double_as_longlong(s_eps[i]))
+                exact_add(A.words + col, n, A.sticky + col, xb, s_lsb[i]);
+        }
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        for (int j = gt; j < A.n; j += nthreads) {
+            const int i = A.inst[j];
+            if (s_state[i] != 4) continue;
+            const double v = chunk_round(A.words + j, n, A.sticky + j, s_lsb[i], true);
+            const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+            if (vb) atomicMax(&A.cslot[2 * i + 1], vb);
+        }
+        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
+            if (s_state[i] == 4) {
+                s_c[i] = __longlong_as_double((long long)__ldcg(&A.cslot[2 * i + 1]));
+                s_state[i] = 1;
+            }
+        __syncthreads();
+    }
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) {
             if (s_state[i] == 2) continue;
@@ -1173,6 +1340,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
             A.stat_tab[i].iters = s_it[i];
             A.stat_tab[i].dropped = s_c[i];
             if (!(s_c[i] > 0.0)) A.stat_tab[i].nnz_post = __ldcg(&A.stat_tab[i].nnz_pre);  // nothing dropped
+            else if (A.inst_dropped) A.inst_dropped[i] = 1;
         }
     // compaction of the instances that dropped entries: keep |x| > eps_f of
     // the row's instance, in place
@@ -1982,6 +2150,15 @@ cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* of
 cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st) {
     k_bounds<<<(ninst + 1 + 255) / 256, 256, 0, st>>>(ninst, off, rowptr, bounds);
     ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reuse_copy_batch(const ProductArgs& P, cudaStream_t st) {
+    if (P.n <= 0) return cudaSuccess;
+    long long blocks = ((long long)P.n + 7) / 8;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    k_reuse_copy_batch<<<(unsigned)blocks, 256, 0, st>>>(P);
     return cudaGetLastError();
 }
 

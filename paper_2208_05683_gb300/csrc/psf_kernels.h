@@ -43,6 +43,7 @@ cudaError_t launch_gather_batch(int n, int ninst, const int* inst, const int* of
                                 const int* rowptr, int* out_rp, int* col, double* val, cudaStream_t st);
 cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bounds, cudaStream_t st);
 cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st);
+cudaError_t launch_reuse_copy_batch(const ProductArgs& P, cudaStream_t st);
 cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st);  // then rounds (k_norms_finish)
 
 }  // namespace psf

@@ -123,3 +123,13 @@ def test_tuning_keys_are_checked_on_the_host():
             psf.tune_get(99)
     finally:
         psf.tune_set(_abi.PSF_TUNE_TABLE_CROSSOVER, old)
+    for key in (_abi.PSF_TUNE_BATCH_GRAPH, _abi.PSF_TUNE_BATCH_REUSE):
+        old = psf.tune_get(key)
+        assert old == 1.0
+        try:
+            psf.tune_set(key, 0.0)
+            assert psf.tune_get(key) == 0.0
+            with pytest.raises(psf.PsfError):
+                psf.tune_set(key, 0.5)
+        finally:
+            psf.tune_set(key, old)

@@ -149,3 +149,40 @@ def test_graph_and_direct_launches_agree():
             assert a.steps == b.steps, name
     finally:
         psf.tune_set(_abi.PSF_TUNE_BATCH_GRAPH, old)
+
+
+def test_baby_steps_from_norm_phase_powers_bitwise():
+    # while an instance has dropped no entry, its batched baby step k <= 10 is
+    # copied from the power Z^k of the norm phase; an instance that drops
+    # entries (loose tolerance), one with q = 12 > 10, a submultiplicative one
+    # (no powers) and an unfiltered one share the batch.  Every result and
+    # step record equals the oracle's and the product-only run's.
+    from paper_2208_05683_gb300 import _abi
+    poly150 = [(-1.0) ** i / math.factorial(i) for i in range(150)]
+    cases = [
+        ("lap2d exp", ocsr(syn.laplacian_2d(40)), syn.coeffs("exp"), 1e-12, {}),
+        ("banded drop", ocsr(syn.banded_random(3000, 5, 7, 4.0)), syn.coeffs("exp"), 1e-6, {}),
+        ("poly q=12", ocsr(syn.banded_random(300, 2, 11, 1.0)), poly150, 1e-11, {"poly": True}),
+        ("submult", ocsr(syn.laplacian_1d(300)), syn.coeffs("exp"), 1e-12, {"submult": True}),
+        ("unfiltered", ocsr(syn.laplacian_1d(200)), syn.coeffs("cos"), 1e-12, {"filtered": False}),
+        ("banded 1e-12", ocsr(syn.banded_random(2000, 5, 8, 2.0)), syn.coeffs("cosh"), 1e-12, {}),
+    ]
+    Zs = [dev(Z) for _, Z, _, _, _ in cases]
+    old = psf.tune_get(_abi.PSF_TUNE_BATCH_REUSE)
+    try:
+        out = {}
+        for reuse in (1.0, 0.0):
+            psf.tune_set(_abi.PSF_TUNE_BATCH_REUSE, reuse)
+            series = [series_of(a, tol, **kw) for _, _, a, tol, kw in cases]
+            out[reuse] = psf.eval_batch(series, Zs)
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_BATCH_REUSE, old)
+    for (name, Z, a, tol, kw), r, p in zip(cases, out[1.0], out[0.0]):
+        ref = psscf(Z, a, tol, **kw)
+        check_same(r, ref, name)
+        for x, y in zip(r.csr.to_host(), p.csr.to_host()):
+            assert np.array_equal(x, y), name
+        assert r.steps == p.steps, name
+    # the poly case really has q > 10, the drop case drops in a baby step
+    assert out[1.0][2].info["q"] == 12
+    assert any(s["kind"] == "baby" and s["nnz_post"] < s["nnz_pre"] for s in out[1.0][1].steps)

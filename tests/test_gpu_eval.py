@@ -98,6 +98,22 @@ def test_repeated_evaluation_reuses_powers_bitwise(case):
         assert again.steps == first.steps, case
 
 
+def test_candidates_far_below_threshold_bitwise():
+    # 150 Taylor terms of exp(-x): q = 12, and the early giant steps only hold
+    # entries near 1e-200 against a threshold near 1e3, far below the column
+    # sums' fixed-point window.  Algorithm 1 must still drop them all and
+    # report the exactly rounded column-sum maximum c, as the oracle does.
+    a = [(-1.0) ** i / math.factorial(i) for i in range(150)]
+    Z = ocsr(syn.banded_random(300, 2, 11, 1.0))
+    ref = psscf(Z, a, 1e-11, poly=True)
+    s = psf.Series(a, 1e-11, poly=True)
+    for _ in range(2):  # the second evaluation takes its baby steps from the norm phase
+        got = s.eval(dev(Z))
+        check_same(got, ref, "poly q=12")
+    assert got.info["q"] == 12
+    assert any(st.c > 0.0 and st.c < 1e-150 for st in ref.steps)
+
+
 @pytest.mark.parametrize("seed,n,hbw", [(0, 1000, 5), (1, 777, 3), (2, 4099, 2)])
 def test_banded_random_bitwise(seed, n, hbw):
     Z = ocsr(syn.banded_random(n, hbw, seed, 2.0))
