@@ -310,6 +310,11 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
  * phase computed (k <= 10: the same entries as the product), 0 always runs
  * the product (same results). */
 #define PSF_TUNE_BATCH_REUSE 3
+/* PSF_TUNE_ALG1_FAR_SHIFT: Algorithm 1's first rescan sets the candidates at
+ * or below eps_g / 2^shift apart; later passes read them again only once
+ * eps_f falls below that bound (default 6; 0 sets every candidate apart,
+ * 2047 none).  An integer in [0, 2047]; results are the same for all. */
+#define PSF_TUNE_ALG1_FAR_SHIFT 4
 PSF_API int psf_tune_set(int32_t key, double value);
 PSF_API int psf_tune_get(int32_t key, double* value);
 PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,

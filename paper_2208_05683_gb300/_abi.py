@@ -16,6 +16,7 @@ PSF_NORM1_NOALLOC_MAX_N = 65536
 PSF_TUNE_TABLE_CROSSOVER = 1
 PSF_TUNE_BATCH_GRAPH = 2
 PSF_TUNE_BATCH_REUSE = 3
+PSF_TUNE_ALG1_FAR_SHIFT = 4
 
 ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG"}
 

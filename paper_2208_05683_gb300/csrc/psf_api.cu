@@ -51,6 +51,7 @@ Profile g_prof;
 std::atomic<double> g_table_crossover{1e300};
 std::atomic<bool> g_batch_graph{true};
 std::atomic<bool> g_batch_reuse{true};
+std::atomic<int> g_far_shift{6};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
@@ -233,6 +234,7 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
         a.stat = P.stat;
         a.cand_col = P.cand_col;
         a.cand_x = P.cand_x;
+        a.far_shift = g_far_shift.load(std::memory_order_relaxed);
         CU(launch_alg1(a, w.st));
     }
     *out = w.pooled(rb, re);
@@ -931,6 +933,11 @@ int psf_tune_set(int32_t key, double value) {
             if (!(value == 0.0 || value == 1.0)) return fail(PSF_EINVAL, "batch reuse must be 0 or 1");
             g_batch_reuse.store(value != 0.0);
             return PSF_OK;
+        case PSF_TUNE_ALG1_FAR_SHIFT:
+            if (!(value >= 0.0 && value <= 2047.0 && value == (double)(int)value))
+                return fail(PSF_EINVAL, "far shift must be an integer in [0, 2047]");
+            g_far_shift.store((int)value);
+            return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
     }
@@ -947,6 +954,9 @@ int psf_tune_get(int32_t key, double* value) {
             return PSF_OK;
         case PSF_TUNE_BATCH_REUSE:
             *value = g_batch_reuse.load() ? 1.0 : 0.0;
+            return PSF_OK;
+        case PSF_TUNE_ALG1_FAR_SHIFT:
+            *value = (double)g_far_shift.load();
             return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);

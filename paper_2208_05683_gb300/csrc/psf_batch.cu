@@ -586,6 +586,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 a.cand_col = P.cand_col;
                 a.cand_x = P.cand_x;
                 a.inst_dropped = d_dropped.as<int>();
+                a.far_shift = g_far_shift.load(std::memory_order_relaxed);
                 CU(launch_alg1_batch(a, st));
             }
             const RowView out = w.pooled(rb, re);

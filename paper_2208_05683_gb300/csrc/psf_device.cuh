@@ -36,6 +36,9 @@ struct Ctl {
     // Algorithm 1 candidate lists (two buffers of cand_cap entries): entry
     // counts, and a flag set when the product's list overflowed
     unsigned long long cand_cnt[2];
+    // entries in the far half of list 1 (candidates below eps_g / 64, set
+    // apart by Algorithm 1's first rescan)
+    unsigned long long cand_far;
     unsigned long long cand_cap;
     int cand_over;
     unsigned cand_chunk;  // entries a warp reserves at a time (32..128)
@@ -162,6 +165,7 @@ struct Alg1BatchArgs {
     int* cand_col;       // two candidate lists of ctl->cand_cap entries each
     unsigned long long* cand_x;
     int* inst_dropped;   // optional: set to 1 for the instances that dropped entries
+    int far_shift;       // as in Alg1Args
 };
 
 // One input matrix of a batch (device CSR, 0-based local columns).
@@ -187,6 +191,7 @@ struct Alg1Args {
     StepStat* stat;
     int* cand_col;               // two candidate lists of ctl->cand_cap entries each
     unsigned long long* cand_x;
+    int far_shift;               // candidates at or below eps_g / 2^far_shift are set apart
 };
 
 // Arguments of k_reuse_pass1 (a baby step that equals a power of the norm
@@ -420,15 +425,23 @@ __device__ __forceinline__ double chunk_round(unsigned long long* w, size_t stri
                                               bool clear = true) {
     unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
     long long carry = 0;
+    // all chunks are loaded before any is cleared, so the loads are in
+    // flight together
+    unsigned long long raw[kChunks];
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) raw[c] = __ldcg(w + (size_t)c * stride);
+    const bool st = __ldcg(sticky) != 0u;
+    if (clear) {
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) w[(size_t)c * stride] = 0ull;
+        *sticky = 0u;
+    }
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
-        const long long t = (long long)__ldcg(w + (size_t)c * stride) + carry;
-        if (clear) w[(size_t)c * stride] = 0ull;
+        const long long t = (long long)raw[c] + carry;
         limb[c >> 1] |= ((unsigned long long)t & 0xffffffffull) << (32 * (c & 1));
         carry = t >> 32;
     }
-    const bool st = __ldcg(sticky) != 0u;
-    if (clear) *sticky = 0u;
     return round_limbs(limb, st, e_lsb);
 }
 
@@ -475,18 +488,24 @@ __device__ __forceinline__ int split24(unsigned long long vbits, int e_lsb, unsi
 __device__ __forceinline__ double round24(unsigned long long* w, size_t stride, unsigned* sticky, int e_lsb) {
     unsigned long long limb[4] = {0ull, 0ull, 0ull, 0ull};
     unsigned long long carry = 0ull;
+    // every piece is loaded before any is cleared: the loads are in flight
+    // together (a store between them would order each after the last)
+    unsigned long long raw[kNormPieces];
+#pragma unroll
+    for (int p = 0; p < kNormPieces; ++p) raw[p] = __ldcg(w + (size_t)p * stride);
+    const bool st = __ldcg(sticky) != 0u;
+#pragma unroll
+    for (int p = 0; p < kNormPieces; ++p) w[(size_t)p * stride] = 0ull;
+    *sticky = 0u;
 #pragma unroll
     for (int p = 0; p < kNormPieces; ++p) {
-        const unsigned long long t = __ldcg(w + (size_t)p * stride) + carry;
-        w[(size_t)p * stride] = 0ull;
+        const unsigned long long t = raw[p] + carry;
         const unsigned long long piece = t & 0xffffffull;
         carry = t >> 24;
         const int bit = 24 * p, li = bit >> 6, sh = bit & 63;
         limb[li] |= piece << sh;
         if (sh > 40) limb[li + 1] |= piece >> (64 - sh);
     }
-    const bool st = __ldcg(sticky) != 0u;
-    *sticky = 0u;
     return round_limbs(limb, st, e_lsb);
 }
 
@@ -602,6 +621,14 @@ __device__ __forceinline__ void cand_push(CandArena& a, bool keep, int col, unsi
         out_x[i] = xb;
     }
     a.next += k;
+}
+
+// Candidates at or below this (bits), eps_g / 2^shift, cannot leave
+// Algorithm 1's list while eps_f stays at or above it (0: none are set
+// apart).  Exact for normal eps_g: only the exponent changes.
+__device__ __forceinline__ unsigned long long far_split(double eps_g, int shift) {
+    const unsigned long long gb = (unsigned long long)__double_as_longlong(eps_g);
+    return (gb >> 52) > (unsigned long long)shift ? gb - ((unsigned long long)shift << 52) : 0ull;
 }
 
 // Grid-wide barrier for cooperative launches, with a bounded wait: after

@@ -750,32 +750,39 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
 
 // Keep the entries of row [s, e) with |x| > fb (bits), in place and in
 // column order; the dropped tail is cleared to exact zeros.  Returns the new
-// end.  Rounds of 128 entries: every lane's four loads are issued before the
-// round's writes (entries only move left, so a round's writes never reach an
-// entry a later round reads).
+// end.  Rounds of 128 entries, software-pipelined: the loads of round i + 1
+// are issued before the writes of round i.  Entries only move left, so the
+// writes of round i stay below its end and never reach round i + 1's
+// entries, which were read before the warp barrier that ends round i.
+__device__ __forceinline__ void compact_load(const int* col, const double* val, int q0, int e, int lane, int c[4],
+                                             double x[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * 32 + lane;
+        c[u] = 0;
+        x[u] = 0.0;
+        if (q < e) {
+            c[u] = col[q];
+            x[u] = val[q];
+        }
+    }
+}
+
 __device__ __forceinline__ int compact_row(int* col, double* val, int s, int e, unsigned long long fb, int lane) {
     int w = s;
+    int c[4];
+    double x[4];
+    compact_load(col, val, s, e, lane, c, x);
     for (int q0 = s; q0 < e; q0 += 128) {
-        int c[4];
-        double x[4];
-        bool keep[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = q0 + u * 32 + lane;
-            keep[u] = false;
-            c[u] = 0;
-            x[u] = 0.0;
-            if (q < e) {
-                c[u] = col[q];
-                x[u] = val[q];
-                keep[u] = mag_bits(x[u]) > fb;
-            }
-        }
+        int cn[4];
+        double xn[4];
+        compact_load(col, val, q0 + 128, e, lane, cn, xn);
         __syncwarp();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const unsigned m = __ballot_sync(kFull, keep[u]);
-            if (keep[u]) {
+            const bool keep = q0 + u * 32 + lane < e && mag_bits(x[u]) > fb;
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (keep) {
                 const int pos = w + __popc(m & lanemask_lt());
                 col[pos] = c[u];
                 val[pos] = x[u];
@@ -783,6 +790,11 @@ __device__ __forceinline__ int compact_row(int* col, double* val, int s, int e, 
             w += __popc(m);
         }
         __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = cn[u];
+            x[u] = xn[u];
+        }
     }
     for (int q = w + lane; q < e; q += 32) val[q] = 0.0;
     return w;
@@ -939,6 +951,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     bool over = __ldcg(&A.ctl->cand_over) != 0 || A.cand_col == nullptr;
     const unsigned long long ccap = A.ctl->cand_cap;
     const unsigned cchunk = A.ctl->cand_chunk;
+    const unsigned long long split = far_split(A.eps_g, A.far_shift);
     if (__ldcg(&A.stat->ncand) == 0ull) {
         // the product left no entry with |x| <= eps_g: the first pass finds an
         // empty candidate matrix (c = 0), nothing is dropped
@@ -990,24 +1003,61 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
         eps_f = A.eps_g / m;
         const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
         if (!over) {
-            // rescan the candidates of the previous pass (list (it-1)&1) into list it&1
+            // rescan the candidates of the previous pass (list (it-1)&1) into
+            // list it&1.  The first rescan sets the candidates at or below
+            // eps_g / 2^far_shift (default 2^6) apart, in the back half of
+            // list 1: they cannot leave while eps_f stays above that, so
+            // later rescans read only the front halves (the near candidates)
+            // and the far half is read again (in place) only once eps_f falls
+            // below it.
             const int bi = (it - 1) & 1, bo = it & 1;
-            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), ccap);
+            const bool first = it == 1;
+            const unsigned long long half = ccap / 2;
+            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), first ? ccap : half);
             const int* ic = A.cand_col + (size_t)bi * ccap;
             const unsigned long long* ix = A.cand_x + (size_t)bi * ccap;
-            CandArena ca;
-            for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += (unsigned long long)nthreads) {
-                const unsigned long long q = q0 + (unsigned long long)lane;
-                const bool in = q < cnt;
-                const unsigned long long xb = in ? __ldcg(ix + q) : 0ull;
-                const int col = in && xb ? __ldcg(ic + q) : 0;
-                const bool keep = in && xb != 0ull && xb <= fb;
-                // an entry that leaves the list leaves the column sums
-                if (in && xb != 0ull && !keep) exact_sub_checked(A.words, A.sticky, col, A.n, xb, A.e_lsb, A.ctl);
-                cand_push(ca, keep, col, xb, A.cand_col + (size_t)bo * ccap, A.cand_x + (size_t)bo * ccap,
-                          &A.ctl->cand_cnt[bo], ccap, cchunk, &A.ctl->cand_over, lane);
+            int* fcol = A.cand_col + ccap + half;
+            unsigned long long* fx = A.cand_x + ccap + half;
+            CandArena ca, cf;
+            // four candidates per thread at a time, all loads issued first
+            const unsigned long long nt = (unsigned long long)nthreads;
+            for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += 4ull * nt) {
+                unsigned long long xb[4];
+                int col[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long q = q0 + (unsigned long long)u * nt + (unsigned long long)lane;
+                    xb[u] = q < cnt ? __ldcg(ix + q) : 0ull;
+                    col[u] = q < cnt ? __ldcg(ic + q) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool keep = xb[u] != 0ull && xb[u] <= fb;
+                    // an entry that leaves the list leaves the column sums
+                    if (xb[u] != 0ull && !keep)
+                        exact_sub_checked(A.words, A.sticky, col[u], A.n, xb[u], A.e_lsb, A.ctl);
+                    const bool far = first && keep && xb[u] <= split;
+                    cand_push(ca, keep && !far, col[u], xb[u], A.cand_col + (size_t)bo * ccap,
+                              A.cand_x + (size_t)bo * ccap, &A.ctl->cand_cnt[bo], half, cchunk, &A.ctl->cand_over,
+                              lane);
+                    if (first)
+                        cand_push(cf, far, col[u], xb[u], fcol, fx, &A.ctl->cand_far, half, cchunk, &A.ctl->cand_over,
+                                  lane);
+                }
             }
             cand_close(ca, A.cand_x + (size_t)bo * ccap, lane);
+            if (first) cand_close(cf, fx, lane);
+            if (!first && fb < split) {
+                // eps_f is below the far candidates' bound: those above it leave
+                const unsigned long long nf = min(__ldcg(&A.ctl->cand_far), half);
+                for (unsigned long long q = (unsigned long long)gt; q < nf; q += nt) {
+                    const unsigned long long xb = __ldcg(fx + q);
+                    if (xb > fb) {
+                        exact_sub_checked(A.words, A.sticky, __ldcg(fcol + q), A.n, xb, A.e_lsb, A.ctl);
+                        fx[q] = 0ull;
+                    }
+                }
+            }
             if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
                 alive = false;
                 break;
@@ -1041,7 +1091,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
     }
     if (!alive) return;
     if (gt == 0) {  // the lists are empty for the next step
-        A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = 0ull;
+        A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = A.ctl->cand_far = 0ull;
         A.ctl->cand_over = 0;
     }
     if (dirty) clear_sums(A.words, A.sticky, A.n, gt, nthreads);  // zero for the next step
@@ -1207,34 +1257,77 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
         __syncthreads();
         if (s_left == 0) break;
         if (!over) {
-            // rescan the candidates of the previous pass into the other list
+            // rescan the candidates of the previous pass into the other list;
+            // the first rescan sets each instance's candidates at or below its
+            // eps_g / 2^far_shift apart in the back half of list 1 (as in k_alg1)
             const int bi = pass & 1, bo = (pass + 1) & 1;
-            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), ccap);
+            const bool first = pass == 0;
+            const unsigned long long half = ccap / 2;
+            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), first ? ccap : half);
             const int* ic = A.cand_col + (size_t)bi * ccap;
             const unsigned long long* ix = A.cand_x + (size_t)bi * ccap;
-            CandArena ca;
-            for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += (unsigned long long)nthreads) {
-                const unsigned long long q = q0 + (unsigned long long)lane;
-                const bool in = q < cnt;
-                const unsigned long long xb = in ? __ldcg(ix + q) : 0ull;
-                const int col = in && xb ? __ldcg(ic + q) : 0;
-                bool keep = false;
-                if (in && xb) {
-                    if ((unsigned)col >= (unsigned)A.n) {
-                        atomicOr(&A.ctl->status, kDevInternal);
-                    } else {
-                        const int i = A.inst[col];
-                        if (s_state[i] == 0) {
-                            keep = xb <= (unsigned long long)__double_as_longlong(s_eps[i]);
-                            // an entry that leaves the list leaves the column sums
-                            if (!keep) exact_sub(A.words + col, n, A.sticky + col, xb, A.bstep[i].e_lsb);
+            int* fcol = A.cand_col + ccap + half;
+            unsigned long long* fx = A.cand_x + ccap + half;
+            CandArena ca, cf;
+            // four candidates per thread at a time, all loads issued first
+            const unsigned long long nt = (unsigned long long)nthreads;
+            for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += 4ull * nt) {
+                unsigned long long xb[4];
+                int col[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long q = q0 + (unsigned long long)u * nt + (unsigned long long)lane;
+                    xb[u] = q < cnt ? __ldcg(ix + q) : 0ull;
+                    col[u] = q < cnt ? __ldcg(ic + q) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    bool keep = false, far = false;
+                    if (xb[u]) {
+                        if ((unsigned)col[u] >= (unsigned)A.n) {
+                            atomicOr(&A.ctl->status, kDevInternal);
+                        } else {
+                            const int i = A.inst[col[u]];
+                            if (s_state[i] == 0) {
+                                keep = xb[u] <= (unsigned long long)__double_as_longlong(s_eps[i]);
+                                // an entry that leaves the list leaves the column sums
+                                if (!keep) exact_sub(A.words + col[u], n, A.sticky + col[u], xb[u], A.bstep[i].e_lsb);
+                                far = first && keep && xb[u] <= far_split(A.bstep[i].eps_g, A.far_shift);
+                            }
                         }
                     }
+                    cand_push(ca, keep && !far, col[u], xb[u], A.cand_col + (size_t)bo * ccap,
+                              A.cand_x + (size_t)bo * ccap, &A.ctl->cand_cnt[bo], half, cchunk, &A.ctl->cand_over,
+                              lane);
+                    if (first)
+                        cand_push(cf, far, col[u], xb[u], fcol, fx, &A.ctl->cand_far, half, cchunk, &A.ctl->cand_over,
+                                  lane);
                 }
-                cand_push(ca, keep, col, xb, A.cand_col + (size_t)bo * ccap, A.cand_x + (size_t)bo * ccap,
-                          &A.ctl->cand_cnt[bo], ccap, cchunk, &A.ctl->cand_over, lane);
             }
             cand_close(ca, A.cand_x + (size_t)bo * ccap, lane);
+            if (first) cand_close(cf, fx, lane);
+            // an instance whose eps_f fell below its far bound: its far
+            // candidates above eps_f leave, in place (the same test in all blocks)
+            int below = 0;
+            if (!first)
+                for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
+                    if (s_state[i] == 0 &&
+                        (unsigned long long)__double_as_longlong(s_eps[i]) < far_split(A.bstep[i].eps_g, A.far_shift))
+                        below = 1;
+            if (__syncthreads_or(below)) {
+                const unsigned long long nf = min(__ldcg(&A.ctl->cand_far), half);
+                for (unsigned long long q = (unsigned long long)gt; q < nf; q += nt) {
+                    const unsigned long long xq = __ldcg(fx + q);
+                    if (xq == 0ull) continue;
+                    const int cq = __ldcg(fcol + q);
+                    if ((unsigned)cq >= (unsigned)A.n) continue;
+                    const int i = A.inst[cq];
+                    if (s_state[i] == 0 && xq > (unsigned long long)__double_as_longlong(s_eps[i])) {
+                        exact_sub(A.words + cq, n, A.sticky + cq, xq, A.bstep[i].e_lsb);
+                        fx[q] = 0ull;
+                    }
+                }
+            }
             if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
                 alive = false;
                 break;
@@ -1273,7 +1366,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
     }
     if (!alive) return;
     if (gt == 0) {  // the lists are empty for the next step
-        A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = 0ull;
+        A.ctl->cand_cnt[0] = A.ctl->cand_cnt[1] = A.ctl->cand_far = 0ull;
         A.ctl->cand_over = 0;
     }
     if (dirty) clear_sums(A.words, A.sticky, A.n, gt, nthreads);  // zero for the next step

@@ -123,6 +123,17 @@ def test_tuning_keys_are_checked_on_the_host():
             psf.tune_get(99)
     finally:
         psf.tune_set(_abi.PSF_TUNE_TABLE_CROSSOVER, old)
+    old = psf.tune_get(_abi.PSF_TUNE_ALG1_FAR_SHIFT)
+    assert old == 6.0
+    try:
+        for v in (0.0, 1.0, 2047.0):
+            psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, v)
+            assert psf.tune_get(_abi.PSF_TUNE_ALG1_FAR_SHIFT) == v
+        for bad in (-1.0, 2.5, 2048.0):
+            with pytest.raises(psf.PsfError):
+                psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, bad)
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, old)
     for key in (_abi.PSF_TUNE_BATCH_GRAPH, _abi.PSF_TUNE_BATCH_REUSE):
         old = psf.tune_get(key)
         assert old == 1.0

@@ -186,3 +186,20 @@ def test_baby_steps_from_norm_phase_powers_bitwise():
     # the poly case really has q > 10, the drop case drops in a baby step
     assert out[1.0][2].info["q"] == 12
     assert any(s["kind"] == "baby" and s["nnz_post"] < s["nnz_pre"] for s in out[1.0][1].steps)
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_batch_far_candidate_split_bitwise(shift):
+    # batched Algorithm 1 with the far candidates set apart per instance at
+    # eps_g / 2^shift: the same bits as the default
+    from paper_2208_05683_gb300 import _abi
+    cases = mixed_cases()
+    Zs = [dev(Z) for _, Z, _, _, _ in cases]
+    old = psf.tune_get(_abi.PSF_TUNE_ALG1_FAR_SHIFT)
+    try:
+        psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, float(shift))
+        got = psf.eval_batch([series_of(a, tol, **kw) for _, _, a, tol, kw in cases], Zs)
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, old)
+    for (name, Z, a, tol, kw), g in zip(cases, got):
+        check_same(g, psscf(Z, a, tol, **kw), f"{name} shift {shift}")

@@ -98,6 +98,32 @@ def test_repeated_evaluation_reuses_powers_bitwise(case):
         assert again.steps == first.steps, case
 
 
+@pytest.mark.parametrize("shift", [0, 1, 2047])
+def test_far_candidate_split_bitwise(shift):
+    # Algorithm 1 sets candidates at or below eps_g / 2^shift apart after its
+    # first pass.  Shift 1 makes later passes reach the set-apart candidates
+    # (eps_f falls 6-27x on these steps), shift 0 sets every candidate apart,
+    # 2047 none; the results and step records are the oracle's in every case.
+    from paper_2208_05683_gb300 import _abi
+    cases = [
+        ("lap2d exp", ocsr(syn.laplacian_2d(48)), syn.coeffs("exp"), 1e-12),
+        ("lap2d cos", ocsr(syn.laplacian_2d(48)), syn.coeffs("cos"), 1e-12),
+        ("banded drop", ocsr(syn.banded_random(3000, 5, 7, 4.0)), syn.coeffs("exp"), 1e-6),
+    ]
+    old = psf.tune_get(_abi.PSF_TUNE_ALG1_FAR_SHIFT)
+    try:
+        psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, float(shift))
+        for name, Z, a, tol in cases:
+            ref = psscf(Z, a, tol)
+            s = psf.Series(a, tol)
+            for _ in range(2):
+                check_same(s.eval(dev(Z)), ref, f"{name} shift {shift}")
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, old)
+    if shift == 1:
+        assert any(st.iters >= 3 and (st.threshold / 1.1) / st.eps_f > 4.0 for st in ref.steps)
+
+
 def test_candidates_far_below_threshold_bitwise():
     # 150 Taylor terms of exp(-x): q = 12, and the early giant steps only hold
     # entries near 1e-200 against a threshold near 1e3, far below the column
