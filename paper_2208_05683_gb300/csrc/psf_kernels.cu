@@ -925,10 +925,11 @@ __global__ void __launch_bounds__(256) k_reuse_copy_batch(ProductArgs P) {
 // the chunk words and both cslot words are 0.  Every block evaluates the same
 // scalar recurrence from the same global values, so all blocks take the same
 // decisions without further communication.
-constexpr int kAlg1Threads = 256;
+constexpr int kAlg1Threads = 1024;  // one block per SM: few grid-barrier arrivals
+constexpr int kAlg1BlocksPerSm = 1;
 constexpr unsigned long long kBarrierBudgetNs = 2000000000ull;  // 2 s
 
-__global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
+__global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Args A) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1171,7 +1172,7 @@ __global__ void __launch_bounds__(kAlg1Threads) k_alg1(Alg1Args A) {
 // maxima, so all blocks take the same decisions.
 constexpr int kMaxBatch = 1024;  // instances of one batched launch
 
-__global__ void __launch_bounds__(kAlg1Threads) k_alg1_batch(Alg1BatchArgs A) {
+__global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(Alg1BatchArgs A) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1615,28 +1616,40 @@ __global__ void __launch_bounds__(kNormRowsThreads) k_norms_rows(NormRowsArgs A)
         // batch: the fixed point of a column follows its instance's max |x|;
         // a row's columns all belong to the row's instance (block diagonal)
         const int lsb = A.inst ? lsb_for_bound(A.slots[(size_t)A.inst[r] * A.slot_stride + mi].absmax) : lsb0;
-        for (int q = s + lane; q < e; q += 32) {
-            const unsigned long long xb = mag_bits(A.val[q]);
-            if (xb == 0ull) continue;
-            const int c = A.col[q];
-            if ((unsigned)c >= (unsigned)n) {
-                atomicOr(&A.ctl->status, kDevInternal);
-                continue;
+        // 128 entries per round, all loads issued first
+        for (int q0 = s; q0 < e; q0 += 128) {
+            unsigned long long xs[4];
+            int cs[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + u * 32 + lane;
+                xs[u] = q < e ? mag_bits(A.val[q]) : 0ull;
+                cs[u] = q < e ? A.col[q] : 0;
             }
-            unsigned pc[4];
-            bool lost;
-            const int L = split24(xb, lsb, pc, lost);
-            if (local) {
-                const int o = c - lo;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (pc[j]) atomicAdd(&nsm[(L + j) * kNormWin + o], pc[j]);
-                if (lost) atomicAdd(&wst[o], 1u);
-            } else {
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long xb = xs[u];
+                if (xb == 0ull) continue;
+                const int c = cs[u];
+                if ((unsigned)c >= (unsigned)n) {
+                    atomicOr(&A.ctl->status, kDevInternal);
+                    continue;
+                }
+                unsigned pc[4];
+                bool lost;
+                const int L = split24(xb, lsb, pc, lost);
+                if (local) {
+                    const int o = c - lo;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (pc[j]) atomicAdd(&words[(size_t)(L + j) * n + c], (unsigned long long)pc[j]);
-                if (lost) atomicAdd(&sticky[c], 1u);
+                    for (int j = 0; j < 4; ++j)
+                        if (pc[j]) atomicAdd(&nsm[(L + j) * kNormWin + o], pc[j]);
+                    if (lost) atomicAdd(&wst[o], 1u);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (pc[j]) atomicAdd(&words[(size_t)(L + j) * n + c], (unsigned long long)pc[j]);
+                    if (lost) atomicAdd(&sticky[c], 1u);
+                }
             }
         }
     }
@@ -2055,7 +2068,7 @@ cudaError_t kernels_init() {
     int per = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
-    c.alg1_blocks = sms * (per < 4 ? per : 4);  // latency-bound phases want warps; barriers want few blocks
+    c.alg1_blocks = sms * (per < kAlg1BlocksPerSm ? per : kAlg1BlocksPerSm);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alg1_batch, kAlg1Threads, 0);
     if (err != cudaSuccess) return err;
     c.alg1b_blocks = sms * (per < 4 ? per : 4);
@@ -2161,9 +2174,11 @@ cudaError_t launch_copy_rows(int n, const int* rowptr, const int* col, const dou
                              int* pool_col, double* pool_val, Ctl* ctl, unsigned long long arena_size,
                              cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    int blocks = (n + 63) / 64;
-    if (blocks > sms_now()) blocks = sms_now();
-    k_copy_rows<<<blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl, arena_size);
+    // about four rows per warp: each row is a dependent load pair, so the
+    // copy is latency-bound and wants many warps in flight
+    long long blocks = ((long long)n + 31) / 32;
+    if (blocks > (long long)sms_now() * 8) blocks = (long long)sms_now() * 8;
+    k_copy_rows<<<(unsigned)blocks, 256, 0, st>>>(n, rowptr, col, val, rb, re, pool_col, pool_val, ctl, arena_size);
     ++g_launches;
     return cudaGetLastError();
 }
