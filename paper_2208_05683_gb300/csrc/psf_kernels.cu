@@ -363,9 +363,11 @@ __device__ __forceinline__ void chunk_next(const ProdSmem<TAB>& S, int cnt, int&
 }
 
 // Fold a chunk in: its columns are distinct, so the four read-modify-writes
-// are independent and are interleaved.
+// are independent and are interleaved.  `np` (the same in every lane) is the
+// number of pieces holding entries: a DFMA occupies the FP64 pipe for the
+// whole warp, so the empty pieces at a row's end are branched over.
 template <bool TAB>
-__device__ __forceinline__ void chunk_fold(ProdSmem<TAB>& S, const Chunk& ch, double a, int c0) {
+__device__ __forceinline__ void chunk_fold(ProdSmem<TAB>& S, const Chunk& ch, double a, int c0, int np = 4) {
     int i[4];
     double x[4];
 #pragma unroll
@@ -374,8 +376,10 @@ __device__ __forceinline__ void chunk_fold(ProdSmem<TAB>& S, const Chunk& ch, do
     for (int u = 0; u < 4; ++u)
         if (i[u] >= 0) x[u] = S.acc[i[u]];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u) {
+        if (u >= np) break;
         if (i[u] >= 0) S.acc[i[u]] = __fma_rn(a, ch.v[u], x[u]);
+    }
 }
 
 // acc[slot(j)] = fma(a_rk, b_kj, acc[slot(j)]) for the segment's k in order.
@@ -484,7 +488,7 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
             for (int off = 0; off < len; off += 128) {
                 Chunk ch;
                 chunk_load<false>(bcol, bval, S, kk, off, lane, ch);
-                chunk_fold<false>(S, ch, a, c0);
+                chunk_fold<false>(S, ch, a, c0, min(4, (len - off + 31) >> 5));
             }
         }
         __syncwarp();
