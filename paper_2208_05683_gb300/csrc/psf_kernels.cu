@@ -551,10 +551,6 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
         // batch, what the row's instance does in this step
         bool prod = P.A.rb != nullptr;
         unsigned tmask = kFull;  // terms present in this row (batch: coefficient != 0)
-        double my_alpha = 0.0;   // batch: coefficient of term `lane` for this row
-        unsigned long long r_eps = eps_bits;
-        int r_lsb = P.e_lsb;
-        bool r_filt = P.filtering != 0;
         int r_inst = 0;
         if constexpr (BATCH) {
             r_inst = P.inst[r];
@@ -569,13 +565,16 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
                 continue;
             }
             prod = bs.mode == kBatchProduct;
-            my_alpha = lane < nadd ? P.alpha_tab[(size_t)lane * P.ninst + r_inst] : 0.0;
-            tmask = __ballot_sync(kFull, __double_as_longlong(my_alpha) != 0ll);
-            r_filt = bs.eps_g > 0.0;
-            r_eps = (unsigned long long)__double_as_longlong(bs.eps_g);
-            r_lsb = bs.e_lsb;
+            const double a_lane = lane < nadd ? P.alpha_tab[(size_t)lane * P.ninst + r_inst] : 0.0;
+            tmask = __ballot_sync(kFull, __double_as_longlong(a_lane) != 0ll);
         }
-        const unsigned long long fma0 = my_fma, cand0 = my_cand;
+        // batch: the counters are per row (reported per instance after each
+        // row); single: running totals, reported per block at the end
+        if constexpr (BATCH) {
+            my_fma = 0ull;
+            my_cand = 0ull;
+        }
+        const unsigned long long fma0 = BATCH ? 0ull : my_fma, cand0 = BATCH ? 0ull : my_cand;
         // ---- column window of row r and the row's multiply-add count
         int lo = INT_MAX, hi = -1;
         for (int t = 0; t < nadd; ++t) {
@@ -653,7 +652,8 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
             for (int t = 0; t < nadd; ++t) {
                 if (!((tmask >> t) & 1u)) continue;
                 const AddTerm& T = add[t];
-                const double alpha = BATCH ? __shfl_sync(kFull, my_alpha, t) : T.alpha;
+                // batch: the row's instance's coefficient (a small, cached table)
+                const double alpha = BATCH ? P.alpha_tab[(size_t)t * P.ninst + r_inst] : T.alpha;
                 if (!T.rb) {
                     if (lane == 0 && r >= c0 && r < c1) {
                         int i = slot_lookup(S, r - c0);
@@ -681,6 +681,17 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
 
             // ---- write back the nonzero entries in column order; the entries
             // with |x| <= eps_g enter the column sums of Algorithm 1's first pass
+            // (batch: the filter of the row's instance, read here rather than
+            // held in registers through the row)
+            unsigned long long r_eps = eps_bits;
+            int r_lsb = P.e_lsb;
+            bool r_filt = P.filtering != 0;
+            if constexpr (BATCH) {
+                const BatchStep& bs = P.bstep[r_inst];
+                r_filt = bs.eps_g > 0.0;
+                r_eps = (unsigned long long)__double_as_longlong(bs.eps_g);
+                r_lsb = bs.e_lsb;
+            }
             for (int i0 = 0; i0 < cnt; i0 += 32) {
                 int i = i0 + lane;
                 double x = 0.0;
