@@ -537,6 +537,91 @@ def measure_tol_sweep(args, dev):
     return {"workload": "banded_n65536_hbw5 exp", "dense_dgemm_s_projected": t_gemm, "rows": rows}
 
 
+def run_e2(args):
+    """The paper's second experiment (Sec. 4, Figs. 1-2) on this GPU: random
+    1000 x 1000 banded matrices, lower = upper bandwidth w = 1..15, N(0, 1)
+    entries, `--e2-seeds` matrices per w, exp and cos at eps_tol = 1e-14.
+    Per w: mean time of filtered PS (PSSCF), unfiltered PS and a dense FP64
+    reference on the same GPU (torch.linalg.matrix_exp; cos(Z) = Re exp(iZ)
+    in complex128), standing in for MATLAB's expm/cosm; the results'
+    densities (nnz / n^2); and the relative errors of Eq. (39) against the
+    dense reference, in the Frobenius norm and the 1-norm.  Times are wall
+    clock through the Python API (one evaluation per matrix, after one
+    untimed evaluation at each w), synchronized on both sides."""
+    import numpy as np
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    n, tol, seeds = 1000, 1e-14, args.e2_seeds
+
+    def dense_of(csr):
+        rp, col, val = (torch.as_tensor(np.asarray(x)).to(dev) for x in csr)
+        rows = torch.repeat_interleave(torch.arange(n, device=dev), (rp[1:] - rp[:-1]).long())
+        X = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        X[rows, col.long()] = val.double()
+        return X
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) * 1e3
+
+    def reference(kind, Zd):
+        if kind == "exp":
+            return torch.linalg.matrix_exp(Zd)
+        return torch.linalg.matrix_exp(1j * Zd.to(torch.complex128)).real.contiguous()
+
+    def errors(res, ref):
+        X = dense_of(res.csr.to_host())
+        D = X - ref
+        fro = float(torch.linalg.norm(D) / torch.linalg.norm(ref))
+        one = float(torch.linalg.matrix_norm(D, ord=1) / torch.linalg.matrix_norm(ref, ord=1))
+        return fro, one
+
+    rows = []
+    for kind in ("exp", "cos"):
+        a = syn.coeffs(kind)
+        filt, unf = psf.Series(a, tol), psf.Series(a, tol, filtered=False)
+        for w in range(1, 16):
+            acc = {k: [] for k in ("psscf_ms", "ps_ms", "ref_ms", "psscf_density", "ps_density", "ref_density",
+                                   "psscf_err_fro", "ps_err_fro", "psscf_err_1", "ps_err_1", "N")}
+            for seed in range(seeds):
+                host = syn.banded_normal(n, w, 1000 * w + seed)
+                Z = psf.DeviceCSR.from_host(*host, device=dev)
+                Zd = dense_of(host)
+                if seed == 0:  # untimed first evaluation at this bandwidth
+                    filt.eval(Z), unf.eval(Z), reference(kind, Zd)
+                rf, tf = timed(lambda: filt.eval(Z))
+                ru, tu = timed(lambda: unf.eval(Z))
+                ref, tr = timed(lambda: reference(kind, Zd))
+                ef, eu = errors(rf, ref), errors(ru, ref)
+                acc["psscf_ms"].append(tf)
+                acc["ps_ms"].append(tu)
+                acc["ref_ms"].append(tr)
+                acc["psscf_density"].append(rf.info["nnz"] / n / n)
+                acc["ps_density"].append(ru.info["nnz"] / n / n)
+                acc["ref_density"].append(float((ref != 0).sum()) / n / n)
+                acc["psscf_err_fro"].append(ef[0])
+                acc["ps_err_fro"].append(eu[0])
+                acc["psscf_err_1"].append(ef[1])
+                acc["ps_err_1"].append(eu[1])
+                acc["N"].append(rf.info["N"])
+            row = {"kind": kind, "w": w}
+            row.update({k: float(np.mean(v)) for k, v in acc.items()})
+            row["psscf_err_fro_max"] = float(np.max(acc["psscf_err_fro"]))
+            rows.append(row)
+            print(f"{kind} w={w:2d}: psscf {row['psscf_ms']:7.2f} ms  ps {row['ps_ms']:7.2f} ms  "
+                  f"dense {row['ref_ms']:7.2f} ms  density {row['psscf_density']:.3f} / {row['ps_density']:.3f}  "
+                  f"err {row['psscf_err_fro']:.2e} / {row['ps_err_fro']:.2e}", file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "banded_normal n=1000, w=1..15, N(0,1), exp and cos, eps_tol=1e-14",
+                      "seeds_per_w": seeds, "reference": "torch.linalg.matrix_exp float64 / complex128 on the GPU",
+                      "timing": "wall clock per evaluation through the Python API, synchronized", "rows": rows}))
+
+
 def ctypes_i64(fn) -> int:
     import ctypes
     v = ctypes.c_int64()
@@ -579,8 +664,13 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=300, help="requests of the serving measurement")
     ap.add_argument("--sweep", action="store_true",
                     help="add the tolerance sweep of the banded n = 65536 workload against dense PS")
+    ap.add_argument("--e2", action="store_true",
+                    help="run the paper's banded N(0,1) experiment (n = 1000, w = 1..15) and exit")
+    ap.add_argument("--e2-seeds", type=int, default=30, help="matrices per bandwidth in --e2")
     args = ap.parse_args()
-    if args.case:
+    if args.e2:
+        run_e2(args)
+    elif args.case:
         run_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -235,3 +235,14 @@ def test_lap2d_full_size_unfiltered_vs_filtered(kind):
     Fu = sp.csr_matrix((val, col, rp), shape=(Z.n, Z.n))
     diff = abs(Ff - Fu).sum(axis=0).max()
     assert diff <= gf.info["budget"]
+
+
+@pytest.mark.parametrize("w", [1, 4, 8, 15])
+@pytest.mark.parametrize("kind", ["exp", "cos"])
+def test_banded_normal_n1000_tol_1e14_bitwise(w, kind):
+    # the paper's second test set (Sec. 4): 1000 x 1000, lower = upper
+    # bandwidth w, N(0, 1) entries, eps_tol = 1e-14.  At w = 15 the result is
+    # about half dense and the products' rows exceed one accumulator chunk.
+    Z = ocsr(syn.banded_normal(1000, w, 11 + w))
+    a = syn.coeffs(kind)
+    check_same(psf.Series(a, 1e-14).eval(dev(Z)), psscf(Z, a, 1e-14), f"w={w} {kind}")
