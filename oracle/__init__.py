@@ -13,6 +13,7 @@ What it computes, with the paper passage each part follows:
   sparse.horner_dense dense Horner (Eq. 1), for small tests
   planner             Eqs. (5), (6), (24)-(28), (34)-(37), Lemma 1
   psscf.psscf         Algorithm 2 (Sec. 3.2.3), filtered and unfiltered
+  normest             deterministic estimates of ||Z^k||_1, k <= 10 (Sec. 3.2.2)
 
 Pinned by ``tests/test_oracle_*.py`` against closed forms, exact rational
 arithmetic, library routines and invariants.  Parity unpinned: Algorithm 1's
@@ -22,9 +23,10 @@ pinned), and the paper's Table 1/2 errors (their matrices are not available).
 from .sparse import CSR, Alg1Result, OracleNotConverged, alg1, axpy, exact_abs_sum, horner_dense, matmul_add, norm1
 from . import planner
 from .psscf import Result, StepStat, block, power_norms, psscf
+from . import normest
 from ._lib import build
 
 __all__ = [
     "CSR", "Alg1Result", "OracleNotConverged", "alg1", "axpy", "exact_abs_sum", "horner_dense",
-    "matmul_add", "norm1", "planner", "Result", "StepStat", "block", "power_norms", "psscf", "build",
+    "matmul_add", "norm1", "planner", "Result", "StepStat", "block", "power_norms", "psscf", "normest", "build",
 ]

@@ -68,3 +68,5 @@ def _declare(h: ctypes.CDLL) -> None:
     h.or_alg1.restype = ctypes.c_int
     h.or_horner_dense.argtypes = [ctypes.c_int32, _f64p, _f64p, ctypes.c_int32, _f64p]
     h.or_horner_dense.restype = ctypes.c_int
+    h.or_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    h.or_spmv.restype = None

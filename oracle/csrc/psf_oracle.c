@@ -441,3 +441,16 @@ int or_horner_dense(int32_t n, const double* Z, const double* a, int32_t N, doub
     free(T);
     return OR_OK;
 }
+
+/*
+ * y = M x for a CSR matrix M (n rows): each y_r is a chain of fma() over
+ * row r's entries in stored order, starting from +0.  The 1-norm estimator
+ * (oracle/normest.py) applies Z^k and its transpose with it.
+ */
+void or_spmv(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, const double* x, double* y) {
+    for (int32_t r = 0; r < n; ++r) {
+        double acc = 0.0;
+        for (int32_t p = rp[r]; p < rp[r + 1]; ++p) acc = fma(v[p], x[ci[p]], acc);
+        y[r] = acc;
+    }
+}
