@@ -54,6 +54,15 @@ extern "C" {
 #define PSF_POLY 1u          /* polynomial of the m given coefficients, thresholds Eq. (28) */
 #define PSF_NOFILTER 2u      /* unfiltered PS scheme (every threshold 0) */
 #define PSF_Z_SUBMULT 4u     /* z_i = ||Z||^i (Sec. 2.2) instead of exact ||Z^i||, i <= 10 */
+/* PSF_Z_ESTIMATE: z_1 = ||Z||_1 exact and z_i, i = 2..10, from a deterministic
+ * estimator instead of the exact norms of the powers (Sec. 3.2.2, Eq. 37:
+ * the paper's normest1, here its single-vector core -- Hager's power
+ * iteration with Higham's stopping rules and alternating test vector, at
+ * most five products with Z^i; every product a fixed fma order, every sum
+ * exact).  Cheaper than the powers Z^2..Z^10; the estimates are lower
+ * bounds.  A column of Z with more than 4096 entries falls back to the exact
+ * norms.  Not with PSF_Z_SUBMULT; psf_eval only (psf_eval_batch rejects it). */
+#define PSF_Z_ESTIMATE 8u
 
 /* ---- tunable parameters (psf_series_set_param) ---- */
 #define PSF_PARAM_ER 1            /* e_r of Algorithm 1 (default 0.1) */

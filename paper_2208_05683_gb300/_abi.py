@@ -8,7 +8,7 @@ import threading
 from . import _build
 
 PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_ENOTCONV, PSF_ETIMEOUT, PSF_ETOOBIG = range(7)
-PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT = 0, 1, 2, 4
+PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT, PSF_Z_ESTIMATE = 0, 1, 2, 4, 8
 PSF_PARAM_ER, PSF_PARAM_ALG1_MAXIT, PSF_PARAM_POOL_ENTRIES = 1, 2, 3
 PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
 PSF_MAX_Q = 23

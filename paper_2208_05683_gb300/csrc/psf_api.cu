@@ -343,7 +343,10 @@ int psf_series_create(const double* coeffs, int64_t m, int32_t s, double tol, ui
     if (!coeffs || m < 1) return fail(PSF_EINVAL, "need at least one coefficient");
     if (m > 100000) return fail(PSF_ETOOBIG, "m = %lld coefficients (max 100000)", (long long)m);
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PSF_EINVAL, "tol must be finite and > 0");
-    if (flags & ~(PSF_POLY | PSF_NOFILTER | PSF_Z_SUBMULT)) return fail(PSF_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(PSF_POLY | PSF_NOFILTER | PSF_Z_SUBMULT | PSF_Z_ESTIMATE))
+        return fail(PSF_EINVAL, "unknown flags 0x%x", flags);
+    if ((flags & PSF_Z_SUBMULT) && (flags & PSF_Z_ESTIMATE))
+        return fail(PSF_EINVAL, "PSF_Z_SUBMULT and PSF_Z_ESTIMATE exclude each other");
     if (s < 0 || s > PSF_MAX_Q) return fail(PSF_EINVAL, "s = %d out of [0, %d]", s, PSF_MAX_Q);
     for (int64_t i = 0; i < m; ++i)
         if (!std::isfinite(coeffs[i])) return fail(PSF_EINVAL, "coefficient %lld is not finite", (long long)i);
@@ -598,9 +601,17 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
         CU(cudaMemsetAsync(w.nwords.p, 0, nb, st));
     }
 
-    // ---- Alg. 2 step 1: norms ||Z^i||_1, i <= 10 (Eq. 37)
+    // ---- Alg. 2 step 1: norms ||Z^i||_1, i <= 10 (Eq. 37): exact (the powers
+    // Z^2..Z^10 are computed), or ||Z||^i, or ||Z||_1 exact and the others
+    // estimated (a column of Z too long for the estimator: exact)
     double norms[kMaxNorms];
     norms[0] = 1.0;
+    bool chain = !submult && n > 0;
+    if ((series->flags & PSF_Z_ESTIMATE) && n > 0) {
+        bool fallback = false;
+        if ((rc = estimate_power_norms(w, *Z, norms, &fallback))) return rc;
+        chain = fallback;
+    }
     unsigned long long zcap = series->pool_hint;
     if (zcap < series->z_need + series->z_need / 8) zcap = series->z_need + series->z_need / 8;
     unsigned long long z_used = 0, z_fma = 0;
@@ -608,7 +619,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     // phases: the PS phase continues after the powers Z^2..Z^10, whose
     // leading ones double as baby steps while nothing is dropped.
     const unsigned long long ps_reserve =
-        (series->ps_need > 0 && !submult && n > 0) ? series->ps_need + series->ps_need / 8 + 4096 : 0;
+        (series->ps_need > 0 && chain) ? series->ps_need + series->ps_need / 8 + 4096 : 0;
     RowView zp{};
     unsigned long long zfma[kMaxNorms] = {0ull};  // multiply-adds of Z^i in the norm phase
     {
@@ -639,7 +650,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 nr.words = w.nwords.as<unsigned long long>();
                 nr.sticky = w.sticky.as<unsigned>();
                 nr.ctl = w.C();
-                if (!submult) {
+                if (chain) {
                     RowView prev = zp;
                     for (int i = 2; i <= 10; ++i) {
                         RowView cur;
@@ -673,7 +684,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             z_used = c.pool_used;
             z_fma = c.fma_total;
             if (z_used > series->z_need) series->z_need = z_used;
-            if (!submult && n > 0) {
+            if (chain) {
                 StepStat zs[9];
                 if (cudaMemcpy(zs, w.stats.p, sizeof zs, cudaMemcpyDeviceToHost) != cudaSuccess)
                     return fail(PSF_ECUDA, "stats read-back");
@@ -684,7 +695,8 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     series->len_z[(size_t)(i - 2)] = znnz[i - 1] / n;
                 }
             }
-            for (int i = 1; i <= 10; ++i) {
+            // ||Z||_1 always; Z^2..Z^10 when the chain ran (else estimated above)
+            for (int i = 1; i <= (chain || submult ? 10 : 1); ++i) {
                 unsigned long long bits = hs[i].result;
                 std::memcpy(&norms[i], &bits, sizeof bits);
             }

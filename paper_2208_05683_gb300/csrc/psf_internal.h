@@ -203,6 +203,9 @@ unsigned long long arena_for(double row_len);
 int mark_pool(Work& w, int i);
 void destroy_result(psf_result_s* r);
 int prepare(cudaStream_t st);
+// Estimates of ||Z^k||_1, k = 2..10, into norms[2..10] (psf_normest.cu);
+// *fallback: a column of Z is too long for the estimator, nothing computed.
+int estimate_power_norms(Work& w, const psf_csr_t& Z, double* norms, bool* fallback);
 
 }  // namespace host
 }  // namespace psf

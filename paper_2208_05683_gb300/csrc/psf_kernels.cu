@@ -2048,6 +2048,7 @@ static std::mutex g_init_mu;
 static std::atomic<long long> g_launches{0};
 
 long long launch_count() { return g_launches.load(); }
+void count_launches(int k) { g_launches += k; }
 
 static const DevCfg& dcfg();
 static int sms_now();

@@ -10,6 +10,7 @@ namespace psf {
 cudaError_t kernels_init();
 int num_sms();
 long long launch_count();
+void count_launches(int k);  // kernels launched by other translation units
 
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);

@@ -144,3 +144,12 @@ def test_tuning_keys_are_checked_on_the_host():
                 psf.tune_set(key, 0.5)
         finally:
             psf.tune_set(key, old)
+
+
+def test_estimate_flag_checked_on_the_host():
+    # the estimator flag is known, and it excludes the submultiplicative bound
+    s = psf.Series(syn.coeffs("exp"), 1e-12, estimate=True)
+    assert s.flags & _abi.PSF_Z_ESTIMATE
+    with pytest.raises(psf.PsfError) as e:
+        psf.Series(syn.coeffs("exp"), 1e-12, submult=True, estimate=True)
+    assert e.value.code == _abi.PSF_EINVAL

@@ -203,3 +203,10 @@ def test_batch_far_candidate_split_bitwise(shift):
         psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, old)
     for (name, Z, a, tol, kw), g in zip(cases, got):
         check_same(g, psscf(Z, a, tol, **kw), f"{name} shift {shift}")
+
+
+def test_batch_rejects_estimated_norms():
+    Z = dev(ocsr(syn.laplacian_1d(50)))
+    with pytest.raises(psf.PsfError) as e:
+        psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12, estimate=True)], [Z])
+    assert e.value.code == 1

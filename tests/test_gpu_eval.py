@@ -246,3 +246,40 @@ def test_banded_normal_n1000_tol_1e14_bitwise(w, kind):
     Z = ocsr(syn.banded_normal(1000, w, 11 + w))
     a = syn.coeffs(kind)
     check_same(psf.Series(a, 1e-14).eval(dev(Z)), psscf(Z, a, 1e-14), f"w={w} {kind}")
+
+
+def estimate_cases():
+    import scipy.sparse as sp
+    n = 5000  # column 0 holds every row: longer than the estimator takes
+    rows = np.concatenate([np.arange(n), np.arange(1, n)])
+    cols = np.concatenate([np.zeros(n, int), np.arange(1, n)])
+    vals = np.concatenate([np.full(n, 1e-4), np.full(n - 1, -0.5)])
+    long_col = CSR.from_scipy(sp.coo_matrix((vals, (rows, cols)), shape=(n, n)))
+    return {
+        "lap2d exp": (ocsr(syn.laplacian_2d(40)), syn.coeffs("exp"), 1e-12),
+        "lap2d cos": (ocsr(syn.laplacian_2d(40)), syn.coeffs("cos"), 1e-12),
+        "banded": (ocsr(syn.banded_random(3000, 5, 7, 2.0)), syn.coeffs("exp"), 1e-12),
+        "banded normal": (ocsr(syn.banded_normal(1000, 4, 5)), syn.coeffs("exp"), 1e-14),
+        "random sparse": (ocsr(syn.random_sparse(700, 0.01, 3, 1.5)), syn.coeffs("cosh"), 1e-10),
+        "n=2": (CSR.from_dense(np.array([[0.5, -1.0], [0.25, 0.75]])), syn.coeffs("exp"), 1e-12),
+        "n=1": (CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([-0.5])),
+                syn.coeffs("exp"), 1e-12),
+        "zero": (CSR.empty(30), syn.coeffs("cos"), 1e-12),
+        "long column": (long_col, syn.coeffs("exp"), 1e-12),
+    }
+
+
+@pytest.mark.parametrize("name", list(estimate_cases()))
+def test_estimated_power_norms_bitwise(name):
+    # PSF_Z_ESTIMATE: z_2..z_10 from the deterministic estimator; the plan and
+    # the result must be the oracle's run with the oracle's estimates (the
+    # long-column case falls back to the exact norms on both sides)
+    from oracle import normest
+    Z, a, tol = estimate_cases()[name]
+    norms = normest.power_norm_estimates(Z)
+    ref = psscf(Z, a, tol, norms=norms)
+    s = psf.Series(a, tol, estimate=True)
+    for _ in range(2):
+        got = s.eval(dev(Z))
+        check_same(got, ref, name)
+        assert got.info["z"][:11] == norms[:11] or got.info["z"][:11] == ref.plan.z[:11], name
