@@ -210,13 +210,13 @@ def run_psf(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def one_step(lat=None):
+    def one_step(lat=None, ser=series):
         out = []
         for k in KINDS:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            h = series[k].eval_handle(Z, stream)
+            h = ser[k].eval_handle(Z, stream)
             e1.record(stream)
             out.append((h, e0, e1))
         for h, e0, e1 in out:
@@ -334,6 +334,28 @@ def run_psf(args):
                  "products_per_eval": prods,
                  "how": "dense FP64 PS time = products x one measured torch.matmul float64 n x n"}
 
+    # ---- the same workload with ||Z^2||..||Z^10|| estimated (PSF_Z_ESTIMATE)
+    # instead of computed from the powers: an option's cost, not the headline
+    est = None
+    if rank == 0 and world == 1:
+        est_series = {k: psf.Series(syn.coeffs(k), TOL, kernel=args.kernel, estimate=True) for k in KINDS}
+        for _ in range(args.warmup):
+            one_step(ser=est_series)
+        elat = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            one_step(elat, ser=est_series)
+        plans, ratios = {}, []
+        for k in KINDS:
+            ie, ix = est_series[k].eval(Z).info, series[k].eval(Z).info
+            plans[k] = {key: [ie[key], ix[key]] for key in ("N", "q", "b", "products")}
+            ratios += [ie["z"][i] / ix["z"][i] for i in range(2, 11) if ix["z"][i] > 0]
+        est = {"evals_per_s": len(elat) / (sum(elat) / 1e3), "p50_ms": statistics.median(elat),
+               "plans_equal": all(v[0] == v[1] for p in plans.values() for v in p.values()),
+               "plans_estimate_vs_exact": plans, "z_estimate_over_exact_min": min(ratios) if ratios else None,
+               "how": "same steps and timing as the headline, series created with estimate=True"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(rp, col, val)
@@ -366,6 +388,7 @@ def run_psf(args):
             "batched": batched,
             "serving": serving,
             "tol_sweep": sweep,
+            "z_estimate": est,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

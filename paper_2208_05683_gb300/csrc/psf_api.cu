@@ -500,7 +500,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     }
     RowView va, vb, res;
     if (A) va = view_of(*A);
-    unsigned long long cap = est;
+    unsigned long long cap = est < kMaxPool ? est : kMaxPool;
     psf_result_s* r = nullptr;
     for (int attempt = 0;; ++attempt) {
         if ((rc = w.reset_pool(cap))) return rc;
@@ -530,8 +530,10 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
         if (c.status & kDevPoolFull) {
             if ((rc = w.clear_sums())) return rc;
             if (attempt > 8) return fail(PSF_ENOMEM, "pool kept overflowing");
+            if (cap >= kMaxPool) return fail(PSF_ETOOBIG, "the step needs more than 2^31 - 2^20 pool entries");
             unsigned long long need = c.pool_used + c.pool_used / 4 + 1024;
             cap = need > 2 * cap ? need : 2 * cap;
+            if (cap > kMaxPool) cap = kMaxPool;
             continue;
         }
         break;
@@ -625,14 +627,14 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     {
         unsigned long long est = (unsigned long long)Z->nnz * 256ull + (unsigned long long)n * 64ull + 4096ull;
         if (series->z_need == 0 && zcap < est) zcap = est;
-        if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
+        if (zcap > kMaxPool) zcap = kMaxPool;
         for (int attempt = 0;; ++attempt) {
             CU(cudaMemsetAsync(slots, 0, sizeof(NormSlot) * kMaxNorms, st));
             // the pooled Z and Z^2 .. Z^10, each delimited in the pool by counter
             // snapshots (the marks also give baby steps their powers' ranges)
             if (n > 0) {
                 unsigned long long total = zcap + ps_reserve;
-                if (total > (unsigned long long)INT32_MAX) total = INT32_MAX;
+                if (total > kMaxPool) total = kMaxPool;
                 if ((rc = w.reset_pool(total))) return rc;
                 CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * 16, st));
                 if ((rc = mark_pool(w, 0)) || (rc = pool_copy(w, *Z, kSlotZp, &zp)) || (rc = mark_pool(w, 1)))
@@ -674,11 +676,11 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             if ((rc = status_to_code(c.status))) return rc;
             if (c.status & kDevPoolFull) {
                 if ((rc = w.clear_sums())) return rc;
-                if (attempt > 8 || zcap >= (unsigned long long)INT32_MAX)
-                    return fail(PSF_ETOOBIG, "the powers Z^2..Z^10 need more than 2^31 entries; use PSF_Z_SUBMULT");
+                if (attempt > 8 || zcap >= kMaxPool)
+                    return fail(PSF_ETOOBIG, "the powers Z^2..Z^10 need more than 2^31 - 2^20 pool entries; use PSF_Z_SUBMULT or PSF_Z_ESTIMATE");
                 unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;
                 zcap = need > 2 * zcap ? need : 2 * zcap;
-                if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
+                if (zcap > kMaxPool) zcap = kMaxPool;
                 continue;
             }
             z_used = c.pool_used;
@@ -746,7 +748,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
         if (cap < series->ps_need + series->ps_need / 8) cap = series->ps_need + series->ps_need / 8;
         unsigned long long est = 4ull * z_used + (unsigned long long)Z->nnz * 64ull + (unsigned long long)n * 64ull;
         if (series->ps_need == 0 && cap < est) cap = est;
-        if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
+        if (cap > kMaxPool) cap = kMaxPool;
         for (int attempt = 0;; ++attempt) {
             // attempt 0 continues in the norm phase's pool when it reserved
             // room; a retry after an overflow starts from an empty pool
@@ -862,11 +864,11 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 destroy_result(r);
                 r = nullptr;
                 if ((rc = w.clear_sums())) return rc;
-                if (attempt > 8 || cap >= (unsigned long long)INT32_MAX)
-                    return fail(PSF_ETOOBIG, "evaluation needs more than 2^31 pool entries");
+                if (attempt > 8 || cap >= kMaxPool)
+                    return fail(PSF_ETOOBIG, "evaluation needs more than 2^31 - 2^20 pool entries");
                 unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;
                 cap = need > 2 * cap ? need : 2 * cap;
-                if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
+                if (cap > kMaxPool) cap = kMaxPool;
                 continue;
             }
             std::vector<StepStat> ss(steps.size());

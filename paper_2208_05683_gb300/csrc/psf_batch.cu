@@ -190,7 +190,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         unsigned long long est = (unsigned long long)nnz_tot * (any_chain ? 128ull : 2ull) + (unsigned long long)n * 8ull +
                                  4096ull * 64ull;
         if (g_z_per_row.load() == 0.0 && zcap < est) zcap = est;
-        if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
+        if (zcap > kMaxPool) zcap = kMaxPool;
         for (int attempt = 0;; ++attempt) {
             CU(cudaMemsetAsync(slots, 0, sizeof(NormSlot) * kMaxNorms * (size_t)count, st));
             CU(cudaMemsetAsync(d_zstat.p, 0, sizeof(StepStat) * 9 * (size_t)count, st));
@@ -257,11 +257,11 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             if ((rc = status_to_code(c.status))) return rc;
             if (c.status & kDevPoolFull) {
                 if ((rc = w.clear_sums())) return rc;
-                if (attempt > 8 || zcap >= (unsigned long long)INT32_MAX)
-                    return fail(PSF_ETOOBIG, "the powers Z^2..Z^10 of the batch need more than 2^31 entries");
+                if (attempt > 8 || zcap >= kMaxPool)
+                    return fail(PSF_ETOOBIG, "the powers Z^2..Z^10 of the batch need more than 2^31 - 2^20 pool entries");
                 unsigned long long need = c.pool_used + c.pool_used / 4 + 4096;
                 zcap = need > 2 * zcap ? need : 2 * zcap;
-                if (zcap > (unsigned long long)INT32_MAX) zcap = INT32_MAX;
+                if (zcap > kMaxPool) zcap = kMaxPool;
                 continue;
             }
             if (n > 0) raise_to(g_z_per_row, (double)c.pool_used / n);
@@ -452,7 +452,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         unsigned long long est = (unsigned long long)nnz_tot * 64ull + (unsigned long long)n * 64ull + 4096ull * 64ull;
         for (int i = 0; i < count; ++i) est += (unsigned long long)(4.0 * ip[(size_t)i].znnz[10]);
         if (g_ps_per_row.load() == 0.0 && cap < est) cap = est;
-        if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
+        if (cap > kMaxPool) cap = kMaxPool;
     }
     DevBuf d_rowptr, d_bounds;
     CU(d_rowptr.alloc(sizeof(int) * ((size_t)n + 1), st));
@@ -637,11 +637,11 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         if ((rc = status_to_code(cfin.status))) return rc;
         if (cfin.status & kDevPoolFull) {
             if ((rc = w.clear_sums())) return rc;
-            if (attempt > 8 || cap >= (unsigned long long)INT32_MAX)
-                return fail(PSF_ETOOBIG, "the batch needs more than 2^31 pool entries");
+            if (attempt > 8 || cap >= kMaxPool)
+                return fail(PSF_ETOOBIG, "the batch needs more than 2^31 - 2^20 pool entries");
             unsigned long long need = cfin.pool_used + cfin.pool_used / 4 + 4096;
             cap = need > 2 * cap ? need : 2 * cap;
-            if (cap > (unsigned long long)INT32_MAX) cap = INT32_MAX;
+            if (cap > kMaxPool) cap = kMaxPool;
             continue;
         }
         if (n > 0) raise_to(g_ps_per_row, (double)cfin.pool_used / n);

@@ -93,6 +93,11 @@ struct Profile {
 };
 extern Profile g_prof;
 
+// Largest entry pool: pool positions are 32-bit in the kernels, and loops
+// step at most a row (plus a few hundred entries) past a row's end, so the
+// capacity stays 2^20 below 2^31 and no position plus offset overflows.
+constexpr unsigned long long kMaxPool = (1ull << 31) - (1ull << 20);
+
 // Device workspace shared by the phases of one evaluation.
 struct Work {
     int n = 0;
@@ -126,7 +131,7 @@ struct Work {
     }
     // (re)allocate the entry pool and reset the device control block
     int reset_pool(unsigned long long entries) {
-        if (entries > (unsigned long long)INT32_MAX) return fail(PSF_ETOOBIG, "pool of %llu entries exceeds 2^31", entries);
+        if (entries > kMaxPool) return fail(PSF_ETOOBIG, "pool of %llu entries exceeds 2^31 - 2^20", entries);
         if (entries > cap) {
             CU(pool_col.alloc(sizeof(int) * entries, st));
             CU(pool_val.alloc(sizeof(double) * entries, st));

@@ -92,10 +92,11 @@ size_t prod_smem_bytes() {
     return sizeof(ProdSmem<TAB>) * ProdSmem<TAB>::kWarps + sizeof(AddTerm) * kMaxAdd;
 }
 
-// first position in [s, e) with col >= c (col ascending)
+// first position in [s, e) with col >= c (col ascending).  Pool positions
+// reach 2^31 - 2^20, so the midpoint is s + (e - s) / 2: s + e would overflow.
 __device__ __forceinline__ int lower_bound_col(const int* col, int s, int e, int c) {
     while (s < e) {
-        int mid = (s + e) >> 1;
+        const int mid = s + ((e - s) >> 1);
         if (col[mid] < c) s = mid + 1;
         else e = mid;
     }

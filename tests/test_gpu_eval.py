@@ -283,3 +283,16 @@ def test_estimated_power_norms_bitwise(name):
         got = s.eval(dev(Z))
         check_same(got, ref, name)
         assert got.info["z"][:11] == norms[:11] or got.info["z"][:11] == ref.plan.z[:11], name
+
+
+def test_extreme_fill_in_fails_cleanly():
+    # an unstructured matrix (n = 200000, about 4 entries per row) whose
+    # powers fill in to dense rows: the pools grow past 2^30 entries, and the
+    # column-chunked rows of the products binary-search positions there,
+    # before the evaluation gives up with PSF_ETOOBIG (a pool is at most
+    # 2^31 - 2^20 entries).  Both norm modes end with the error, not a fault.
+    Z = dev(syn.random_sparse(200000, 2e-5, 1, 2.0))
+    for est in (False, True):
+        with pytest.raises(psf.PsfError) as e:
+            psf.Series(syn.coeffs("exp"), 1e-12, estimate=est).eval(Z)
+        assert e.value.code == 6
