@@ -337,7 +337,7 @@ def run_psf(args):
     # ---- the same workload with ||Z^2||..||Z^10|| estimated (PSF_Z_ESTIMATE)
     # instead of computed from the powers: an option's cost, not the headline
     est = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_estimate:
         est_series = {k: psf.Series(syn.coeffs(k), TOL, kernel=args.kernel, estimate=True) for k in KINDS}
         for _ in range(args.warmup):
             one_step(ser=est_series)
@@ -684,6 +684,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default slot-map crossover")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-estimate", action="store_true", help="skip the estimated-norms (PSF_Z_ESTIMATE) measurement")
     ap.add_argument("--serving-requests", type=int, default=300, help="requests of the serving measurement")
     ap.add_argument("--sweep", action="store_true",
                     help="add the tolerance sweep of the banded n = 65536 workload against dense PS")
