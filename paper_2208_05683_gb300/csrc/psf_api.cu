@@ -137,7 +137,7 @@ unsigned long long arena_for(double row_len) {
 int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
              double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
              NormSlot* absmax_slot = nullptr, double blen = 0.0, double alen = 0.0, int reuse_k = 0,
-             unsigned long long reuse_fma = 0) {
+             unsigned long long reuse_fma = 0, double out_len = 0.0) {
     if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
@@ -186,7 +186,7 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     const double work = alen > 0.0 ? alen * blen : 0.0;
     const bool table = use_table(w.slot_map, work);
     if (reuse_k > 0) P.skip_unless = &w.C()->dropped;
-    CU(launch_product(P, table, w.st));
+    CU(launch_product(P, table, w.st, out_len));
     if (reuse_k > 0) {
         ReuseArgs R{};
         R.n = w.n;
@@ -838,8 +838,10 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                                       ? series->len_giant[(size_t)(i - 1)]
                                       : (znnz[10] > 0.0 ? znnz[10] / n : zlen * 100.0);
                     const double alen = (q <= 10 && znnz[q] > 0.0) ? znnz[q] / n : zlen * q * q;
+                    const double olen =
+                        (size_t)(i - 1) < series->out_giant.size() ? series->out_giant[(size_t)(i - 1)] : 0.0;
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
-                                       &nxt, nullptr, blen, alen)))
+                                       &nxt, nullptr, blen, alen, 0, 0ull, olen)))
                         return rc;
                     s.kind = 1;
                     s.threshold = thr;
@@ -891,6 +893,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             // B-operand row lengths of this evaluation, for the next one
             series->len_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0.0);
             series->len_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
+            series->out_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             {
                 double prev_len = zlen;  // Z-hat_(1) = Z
                 size_t idx = 0;
@@ -902,6 +905,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 if (g == 0) s_len = (double)steps[idx++].nnz_post / n;  // S-hat_0
                 for (int i = 1; i < b; ++i, ++idx) {
                     series->len_giant[(size_t)(i - 1)] = s_len;
+                    series->out_giant[(size_t)(i - 1)] = (double)steps[idx].nnz_pre / n;
                     s_len = (double)steps[idx].nnz_post / n;
                 }
             }

@@ -28,6 +28,9 @@ struct psf_series_s {
     // B-operand mean row lengths seen by the previous evaluation, per step:
     // they pick the thread-group size of the product kernel (tuning only)
     std::vector<double> len_z, len_baby, len_giant;
+    // mean output row length before the filter of each giant step (the
+    // product kernel's accumulator variant for long rows)
+    std::vector<double> out_giant;
     int kernel = 0;       // PSF_PARAM_KERNEL
     int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
     int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS

@@ -54,9 +54,14 @@ namespace psf {
 // A row whose pattern exceeds the chunk (wider than the map or with more
 // than kAccCap entries) is processed in several column chunks.
 constexpr int kTabCap = 4160;  // columns of the table map
-constexpr int kBmWords = 160;  // bitmap words of the bitmap map
+constexpr int kBmWords = 144;  // bitmap words of the bitmap map (4608 columns)
 constexpr int kBmBits = kBmWords * 32;
-constexpr int kAccCap = 600;  // with 7 bitmap blocks of 4 warps per SM, shared memory is full
+// Accumulator slots; with 7 bitmap blocks of 4 warps per SM shared memory is
+// full.  The bitmap map keeps a segment's a_rk in the last 32 slots, so a row
+// has kAccCap - 32 of them; its WIDE instantiation, for steps whose rows are
+// long, reads a_rk from A's row instead and gives a row every slot (a row of
+// up to kAccCap entries then takes one pass, not two column chunks).
+constexpr int kAccCap = 640;
 
 template <bool TAB>
 struct ProdSmem;
@@ -80,8 +85,7 @@ struct ProdSmem<false> {
     static constexpr int kWarps = 4;
     static constexpr int kBlocksPerSm = 7;  // 28 warps: registers (72) and shared memory
     uint2 pm[kBmWords];  // .x = set bits before the word, .y = bitmap word
-    double acc[kAccCap];
-    double ka[32];
+    double acc[kAccCap];  // the last 32 hold a_rk of the segment (not in WIDE)
     int kb[32];
     int kl[32];
     unsigned short colbuf[kAccCap];
@@ -110,11 +114,16 @@ __device__ __forceinline__ int slot_lookup(const ProdSmem<false>& S, int o) {
     return (int)e.x + __popc(e.y & ((1u << (o & 31)) - 1u));
 }
 
-// Load the segment [seg, seg + cnt) of A's row: a_rk and the range of B's row
-// k restricted to columns [c0, c1) (the whole row when `whole`).
+// where a segment's a_rk are kept
+__device__ __forceinline__ double* ka_of(ProdSmem<true>& S) { return S.ka; }
+__device__ __forceinline__ double* ka_of(ProdSmem<false>& S) { return S.acc + (kAccCap - 32); }
+
+// Load the segment [seg, seg + cnt) of A's row: a_rk (unless `store_a` is
+// false) and the range of B's row k restricted to columns [c0, c1) (the
+// whole row when `whole`).
 template <bool TAB>
 __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1,
-                                             int lane, ProdSmem<TAB>& S) {
+                                             int lane, ProdSmem<TAB>& S, bool store_a) {
     if (lane < cnt) {
         int k = P.A.col[seg + lane];
         int b = P.B.rb[k], e = P.B.re[k];
@@ -123,7 +132,7 @@ __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int 
             e = lower_bound_col(P.B.col, b2, e, c1);
             b = b2;
         }
-        S.ka[lane] = P.A.val[seg + lane];
+        if (store_a) ka_of(S)[lane] = P.A.val[seg + lane];
         S.kb[lane] = b;
         S.kl[lane] = e - b;
     }
@@ -215,7 +224,8 @@ __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false>& S
 // Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
 template <bool TAB>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
-                                          int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB>& S) {
+                                          int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB>& S,
+                                          bool store_a) {
     clear_map(cend - c0, lane, S);
     __syncwarp();
     for (int t = 0; t < nadd; ++t) {
@@ -229,7 +239,7 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
     }
     for (int seg = pa0; seg < pa1; seg += 32) {
         const int cnt = min(32, pa1 - seg);
-        load_segment<TAB>(P, seg, cnt, whole, c0, cend, lane, S);
+        load_segment<TAB>(P, seg, cnt, whole, c0, cend, lane, S, store_a);
         if constexpr (!TAB) {
             if (warp_max(lane < cnt ? S.kl[lane] : 0) <= 32) {
                 mark_rows_short(P.B.col, cnt, c0, cend, lane, S);
@@ -284,7 +294,7 @@ __device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSme
     return min(run, cap);
 }
 __device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSmem<false>& S, int* cut) {
-    constexpr int per = kBmWords / 32;
+    constexpr int per = (kBmWords + 31) / 32;  // words per lane (the last lanes' partly past nw)
     const int nw = (wlen + 31) >> 5;
     const int base = lane * per;
     int s = 0;
@@ -388,7 +398,8 @@ __device__ __forceinline__ void chunk_fold(ProdSmem<TAB>& S, const Chunk& ch, do
 // next two are in flight while one is folded in).  Bitmap map (more warps,
 // fewer registers): one chunk at a time.  A warp barrier separates
 // consecutive B rows (the order of the fma chain).
-__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane,
+template <bool WIDE>
+__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int /*seg*/, int cnt, int c0, int lane,
                                                    ProdSmem<true>& S) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
@@ -442,10 +453,15 @@ __device__ __forceinline__ void short_fold(ProdSmem<false>& S, int c, double v, 
     }
 }
 
-__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt, int c0, int lane,
+template <bool WIDE>
+__device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int seg, int cnt, int c0, int lane,
                                                    ProdSmem<false>& S) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
+    const double* ka = ka_of(S);
+    // a_rk of row kk: kept in the accumulator's last slots, or (WIDE) read
+    // from A's row (the same address in every lane)
+    auto a_of = [&](int kk) { return WIDE ? P.A.val[seg + kk] : ka[kk]; };
     if (warp_max(lane < cnt ? S.kl[lane] : 0) <= 32) {
         // every B row is one piece: the pieces of the next three rows are
         // loaded while one is folded (rows in k order, a warp barrier between)
@@ -456,19 +472,19 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
         short_load(bcol, bval, S, cnt, 2, lane, cc, vc);
         for (int kk = 0; kk < cnt; kk += 4) {
             short_load(bcol, bval, S, cnt, kk + 3, lane, cd, vd);
-            short_fold(S, ca, va, S.ka[kk], c0);
+            short_fold(S, ca, va, a_of(kk), c0);
             __syncwarp();
             if (kk + 1 >= cnt) break;
             short_load(bcol, bval, S, cnt, kk + 4, lane, ca, va);
-            short_fold(S, cb, vb, S.ka[kk + 1], c0);
+            short_fold(S, cb, vb, a_of(kk + 1), c0);
             __syncwarp();
             if (kk + 2 >= cnt) break;
             short_load(bcol, bval, S, cnt, kk + 5, lane, cb, vb);
-            short_fold(S, cc, vc, S.ka[kk + 2], c0);
+            short_fold(S, cc, vc, a_of(kk + 2), c0);
             __syncwarp();
             if (kk + 3 >= cnt) break;
             short_load(bcol, bval, S, cnt, kk + 6, lane, cc, vc);
-            short_fold(S, cd, vd, S.ka[kk + 3], c0);
+            short_fold(S, cd, vd, a_of(kk + 3), c0);
             __syncwarp();
         }
         return;
@@ -476,7 +492,7 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int cnt
     for (int kk = 0; kk < cnt; ++kk) {
         const int len = S.kl[kk];
         if (len == 0) continue;
-        const double a = S.ka[kk];
+        const double a = a_of(kk);
         if (len <= 32) {
             // a short B row fills one piece: fold only that one (a DFMA
             // occupies the FP64 pipe for the whole warp, active lanes or not)
@@ -518,7 +534,7 @@ __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, 
     }
 }
 
-template <bool TAB, bool BATCH>
+template <bool TAB, bool BATCH, bool WIDE>
 __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBlocksPerSm) k_product(ProductArgs P) {
     // a baby step whose product equals an already computed power (no entry
     // dropped so far) is done by k_reuse_pass1 instead (same value in all blocks)
@@ -526,7 +542,8 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
     // columns and slots of one chunk (lowered only to exercise chunking)
     const int kCols = P.chunk_cols > 0 && P.chunk_cols < ProdSmem<TAB>::kCols ? P.chunk_cols : ProdSmem<TAB>::kCols;
-    const int kSlots = P.chunk_slots > 0 && P.chunk_slots < kAccCap ? P.chunk_slots : kAccCap;
+    constexpr int kCapN = (TAB || WIDE) ? kAccCap : kAccCap - 32;  // a row's slots
+    const int kSlots = P.chunk_slots > 0 && P.chunk_slots < kCapN ? P.chunk_slots : kCapN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
     ProdSmem<TAB>* warps = reinterpret_cast<ProdSmem<TAB>*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
@@ -621,13 +638,13 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
         long long total = 0;
         bool reuse = false;
         if (hi - lo + 1 <= kCols) {
-            build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S);
+            build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE);
             total = count_marks(hi - lo + 1, lane, S);
             reuse = true;
         } else {
             for (long long c0 = lo; c0 <= hi; c0 += kCols) {
                 int cend = (int)min((long long)hi + 1, c0 + kCols);
-                build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S);
+                build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE);
                 total += count_marks(cend - (int)c0, lane, S);
             }
         }
@@ -641,7 +658,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
         int c0 = lo;
         while (c0 <= hi) {
             int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
-            if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S);
+            if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE);
             reuse = false;
             int cut;
             const int cnt = assign_slots(cend - c0, kSlots, lane, S, &cut);
@@ -676,8 +693,8 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
             // ---- product A B: k of row r ascending
             for (int seg = pa0; seg < pa1; seg += 32) {
                 const int cnt_seg = min(32, pa1 - seg);
-                load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S);
-                accumulate_segment(P, cnt_seg, c0, lane, S);
+                load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S, !WIDE);
+                accumulate_segment<WIDE>(P, seg, cnt_seg, c0, lane, S);
             }
 
             // ---- write back the nonzero entries in column order; the entries
@@ -2071,11 +2088,12 @@ cudaError_t kernels_init() {
     int sms = 0;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    const void* prods[4] = {(const void*)k_product<true, false>, (const void*)k_product<false, false>,
-                            (const void*)k_product<true, true>, (const void*)k_product<false, true>};
-    const int psmem[4] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
-                          (int)prod_smem_bytes<false>()};
-    for (int i = 0; i < 4; ++i) {
+    const void* prods[5] = {(const void*)k_product<true, false, false>, (const void*)k_product<false, false, false>,
+                            (const void*)k_product<true, true, false>, (const void*)k_product<false, true, false>,
+                            (const void*)k_product<false, false, true>};
+    const int psmem[5] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
+                          (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<false>()};
+    for (int i = 0; i < 5; ++i) {
         err = cudaFuncSetAttribute(prods[i], cudaFuncAttributeMaxDynamicSharedMemorySize, psmem[i]);
         if (err != cudaSuccess) return err;
     }
@@ -2101,7 +2119,7 @@ cudaError_t kernels_init() {
 int num_sms() { return dcfg().sms; }
 static int sms_now() { return dcfg().sms; }
 
-template <bool TAB, bool BATCH>
+template <bool TAB, bool BATCH, bool WIDE>
 static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     constexpr int kWarps = ProdSmem<TAB>::kWarps;
     // one wave of resident blocks, rows strided over the warps (each warp
@@ -2109,15 +2127,18 @@ static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     long long blocks = ((long long)P.n + kWarps - 1) / kWarps;
     const long long cap = (long long)sms_now() * ProdSmem<TAB>::kBlocksPerSm;
     if (blocks > cap) blocks = cap;
-    k_product<TAB, BATCH><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
+    k_product<TAB, BATCH, WIDE><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st) {
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len) {
     if (P.n <= 0) return cudaSuccess;
-    if (P.inst) return table ? prod_launch<true, true>(P, st) : prod_launch<false, true>(P, st);
-    return table ? prod_launch<true, false>(P, st) : prod_launch<false, false>(P, st);
+    if (P.inst) return table ? prod_launch<true, true, false>(P, st) : prod_launch<false, true, false>(P, st);
+    if (table) return prod_launch<true, false, false>(P, st);
+    // rows expected near or above the bitmap map's kAccCap - 32 slots: WIDE
+    if (out_len > 0.9 * (kAccCap - 32)) return prod_launch<false, false, true>(P, st);
+    return prod_launch<false, false, false>(P, st);
 }
 
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {

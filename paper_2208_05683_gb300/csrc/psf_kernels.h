@@ -12,7 +12,9 @@ int num_sms();
 long long launch_count();
 void count_launches(int k);  // kernels launched by other translation units
 
-cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st);
+// out_len: the expected mean output row length (0: unknown), which picks the
+// bitmap map's wide-accumulator instantiation for long rows
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len = 0.0);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
 cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
 cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st);

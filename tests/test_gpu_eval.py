@@ -296,3 +296,22 @@ def test_extreme_fill_in_fails_cleanly():
         with pytest.raises(psf.PsfError) as e:
             psf.Series(syn.coeffs("exp"), 1e-12, estimate=est).eval(Z)
         assert e.value.code == 6
+
+
+@pytest.mark.parametrize("case", ["lap2d128 exp", "lap2d128 cos", "banded normal w15"])
+def test_wide_accumulator_rows_bitwise(case):
+    # From the second evaluation on, a giant step whose rows averaged more than
+    # about 550 entries before the filter runs the product kernel's wide
+    # accumulator (every slot to the row, a_rk read from A): the largest giant
+    # step of the 128 x 128 Laplacian has rows of 625-637 entries, the dense
+    # banded matrix rows of up to ~900 (column chunks inside the wide kernel).
+    Z, a, tol = {
+        "lap2d128 exp": (syn.laplacian_2d(128), syn.coeffs("exp"), 1e-12),
+        "lap2d128 cos": (syn.laplacian_2d(128), syn.coeffs("cos"), 1e-12),
+        "banded normal w15": (syn.banded_normal(1000, 15, 4), syn.coeffs("exp"), 1e-14),
+    }[case]
+    Z = ocsr(Z)
+    ref = psscf(Z, a, tol)
+    s = psf.Series(a, tol)
+    for _ in range(3):
+        check_same(s.eval(dev(Z)), ref, case)
