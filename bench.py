@@ -662,7 +662,9 @@ def run_case(args):
     rp, col, val = syn.workload(args.case)[0]
     Z = psf.DeviceCSR.from_host(rp, col, val, device="cuda:0")
     # a pool large enough that no phase is repeated: kernel launch order is fixed
-    res = psf.Series(syn.coeffs(args.kind), TOL, pool_entries=200_000_000, kernel=args.kernel).eval(Z)
+    series = psf.Series(syn.coeffs(args.kind), TOL, pool_entries=200_000_000, kernel=args.kernel)
+    for _ in range(args.repeat):  # later evaluations use the earlier ones' statistics
+        res = series.eval(Z)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "kind": args.kind, "nnz": res.csr.nnz, "N": res.info["N"],
                       "fma": res.info["fma"], "step_fma": [s["fma"] for s in res.steps],
@@ -673,6 +675,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default=None, help="run one evaluation of this workload and exit")
     ap.add_argument("--kind", default="exp")
+    ap.add_argument("--repeat", type=int, default=1, help="with --case: evaluations of the one series")
     ap.add_argument("--kernel", choices=["auto", "table", "bitmap"], default="auto",
                     help="slot map of the product kernel (auto: by products per row)")
     ap.add_argument("--gpus", type=int, default=1)
