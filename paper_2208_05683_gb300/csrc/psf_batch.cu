@@ -100,17 +100,33 @@ BatchStep step_of(int mode, double thr, double e_r, int maxit) {
 }
 
 // A non-blocking stream of the calling thread on the current device, on
-// which batch graphs are recorded (never executed).
+// which batch graphs are recorded (never executed).  It is destroyed when
+// the thread exits (server workers come and go with their servers).
+struct CaptureStream {
+    cudaStream_t stream = nullptr;
+    int dev = -1;
+    ~CaptureStream() {
+        if (stream) cudaStreamDestroy(stream);  // may fail harmlessly at process exit
+    }
+};
+
 int capture_stream(cudaStream_t* out) {
-    static thread_local cudaStream_t t_stream = nullptr;
-    static thread_local int t_dev = -1;
+    static thread_local CaptureStream t;
     int dev = 0;
     CU(cudaGetDevice(&dev));
-    if (!t_stream || t_dev != dev) {
-        CU(cudaStreamCreateWithFlags(&t_stream, cudaStreamNonBlocking));
-        t_dev = dev;
+    if (!t.stream || t.dev != dev) {
+        if (t.stream) {
+            // the previous device's stream: destroyed on that device
+            int cur = dev;
+            CU(cudaSetDevice(t.dev));
+            cudaStreamDestroy(t.stream);
+            t.stream = nullptr;
+            CU(cudaSetDevice(cur));
+        }
+        CU(cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking));
+        t.dev = dev;
     }
-    *out = t_stream;
+    *out = t.stream;
     return PSF_OK;
 }
 
