@@ -65,6 +65,15 @@ def test_banded_random_against_scipy_expm(seed):
     assert norm1_dense(r.F.to_dense() - ref) <= 1e-12 + 1e-14 * norm1_dense(ref)
 
 
+@pytest.mark.parametrize("seed", [0, 3])
+def test_banded_random_cos_against_scipy_cosm(seed):
+    # cos uses the literal series with zero odd coefficients (Eq. 40)
+    Z = csr(syn.banded_random(300, 4, seed, 2.0))
+    r = psscf(Z, syn.coeffs("cos"), 1e-12)
+    ref = scipy.linalg.cosm(Z.to_dense())
+    assert norm1_dense(r.F.to_dense() - ref) <= 1e-12 + 1e-14 * norm1_dense(ref)
+
+
 def test_exp_times_exp_minus_is_identity():
     Z = csr(syn.banded_random(200, 3, 11, 2.0))
     Zm = CSR(Z.n, Z.rowptr, Z.col, -Z.val)
