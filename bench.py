@@ -679,7 +679,7 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "table", "bitmap"], default="auto",
                     help="slot map of the product kernel (auto: by products per row)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)  # 20 evaluations: p50/p99 over >= 20
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["psf", "reference"], default="psf")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense FP64 PS baseline")
