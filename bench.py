@@ -274,42 +274,50 @@ def run_psf(args):
                 "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "launches_timed": nl.value, "kernel_ms": ms.value, "algorithmic_fma": fma.value}
 
-    # ---- end to end: pinned host Z -> device, both evaluations, results -> host
+    # ---- end to end through the C ABI on host buffers: psf_eval_from_host
+    # (pinned host Z copied in by the library) and psf_result_copy into
+    # pinned host arrays, both evaluations, copies inside the timed region
     pin = [torch.as_tensor(x).pin_memory() for x in (np.asarray(rp, np.int32), np.asarray(col, np.int32),
                                                       np.asarray(val, np.float64))]
+    zs_host = _abi.CSRStruct(n, int(len(col)), pin[0].data_ptr(), pin[1].data_ptr(), pin[2].data_ptr())
     h2d = sum(t.numel() * t.element_size() for t in pin)
     e2e_ms, d2h = [], 0
-    # pinned host buffers for the results, allocated in the warm-up steps
-    # (the timed steps copy into them: the D2H copy itself is timed)
+    # pinned host result arrays, allocated in the warm-up steps
     host_buf = {}
 
-    def to_host(k, res):
-        outs = []
-        for name, t in (("rowptr", res.csr.rowptr), ("col", res.csr.col), ("val", res.csr.val)):
+    def host_arrays(k, nnz):
+        want = {"rowptr": (n + 1, torch.int32), "col": (max(nnz, 1), torch.int32), "val": (max(nnz, 1), torch.float64)}
+        for name, (cnt, dt) in want.items():
             b = host_buf.get((k, name))
-            if b is None or b.numel() < t.numel():
-                b = torch.empty(max(t.numel(), 1), dtype=t.dtype, pin_memory=True)
-                host_buf[(k, name)] = b
-            outs.append(b[: t.numel()].copy_(t, non_blocking=True))
-        return outs
+            if b is None or b.numel() < cnt:
+                host_buf[(k, name)] = torch.empty(cnt, dtype=dt, pin_memory=True)
+        return [host_buf[(k, name)] for name in ("rowptr", "col", "val")]
 
+    st_ptr = ctypes.c_void_p(stream.cuda_stream)
     for it in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        dz = [t.to(dev, non_blocking=True) for t in pin]
-        Zd = psf.DeviceCSR(n, *dz)
-        host_out = []
+        handles, copied = [], 0
         for k in KINDS:
-            res = series[k].eval(Zd, stream)
-            host_out.append(to_host(k, res))
+            h = ctypes.c_void_p()
+            _abi.check(L.psf_eval_from_host(series[k]._h, ctypes.byref(zs_host), st_ptr, ctypes.byref(h)))
+            info = _abi.InfoStruct()
+            _abi.check(L.psf_result_info(h, ctypes.byref(info)))
+            hr, hc, hv = host_arrays(k, int(info.nnz))
+            _abi.check(L.psf_result_copy(h, ctypes.c_void_p(hr.data_ptr()), ctypes.c_void_p(hc.data_ptr()),
+                                         ctypes.c_void_p(hv.data_ptr()), st_ptr))
+            copied += (n + 1) * 4 + int(info.nnz) * 12
+            handles.append(h)
         e1.record(stream)
         e1.synchronize()
+        for h in handles:
+            _abi.check(L.psf_result_destroy(h))
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-            d2h = sum(t.numel() * t.element_size() for out in host_out for t in out)
+            d2h = copied
     e2e_value, _ = job_rate(len(KINDS) * len(e2e_ms), sum(e2e_ms), world, dev)
 
     # ---- dense FP64 PS on the same GPU: product count x measured DGEMM time

@@ -163,6 +163,15 @@ PSF_API int psf_series_destroy(psf_series_t series);
 PSF_API int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t* out);
 
 /*
+ * psf_eval on a matrix given in HOST memory (Z's arrays on the host; pinned
+ * memory makes the copies asynchronous): Z is copied into device memory on
+ * `stream`, evaluated, and its copy released after the evaluation's work.
+ * With psf_result_copy into host arrays this is the whole host-to-host
+ * path.  Same errors as psf_eval.
+ */
+PSF_API int psf_eval_from_host(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t* out);
+
+/*
  * Evaluate `count` independent instances Zs[i] (each square, any size n_i)
  * with series[i] (Algorithm 2 each).  The instances are laid out as one
  * block-diagonal matrix, so every stage (each of Z^2..Z^10, each baby step,
@@ -344,7 +353,7 @@ PSF_API int psf_profile_read(int64_t* launches, double* ms, double* fma, int32_t
 /* Read access to a result. */
 PSF_API int psf_result_csr(psf_result_t r, psf_csr_t* view);          /* library-owned device arrays */
 PSF_API int psf_result_copy(psf_result_t r, int32_t* rowptr, int32_t* col, double* val,
-                    void* stream);                            /* device-to-device into caller arrays */
+                    void* stream);  /* into caller arrays, device or host (pinned: asynchronous) */
 PSF_API int psf_result_info(psf_result_t r, psf_info_t* info);
 PSF_API int psf_result_step(psf_result_t r, int32_t i, psf_step_info_t* step);
 PSF_API int psf_result_destroy(psf_result_t r);

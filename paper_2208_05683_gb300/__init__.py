@@ -183,6 +183,38 @@ class Series:
         check(lib().psf_eval(self._h, ctypes.byref(zs), st, ctypes.byref(out)))
         return _take_result(out, st)
 
+    def eval_host(self, rowptr, col, val, stream=None):
+        """psf_eval_from_host on host arrays; returns ((rowptr, col, val) as
+        host numpy arrays, info, steps).  The copies in both directions are
+        the library's (psf_eval_from_host, psf_result_copy into host arrays)."""
+        import numpy as np
+        L = lib()
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col, dtype=np.int32)
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        zs = CSRStruct(len(rp) - 1, len(ci), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        st = _stream_ptr(stream)
+        out = ctypes.c_void_p()
+        check(L.psf_eval_from_host(self._h, ctypes.byref(zs), st, ctypes.byref(out)))
+        try:
+            info = InfoStruct()
+            check(L.psf_result_info(out, ctypes.byref(info)))
+            steps = []
+            for i in range(info.nsteps):
+                s = StepStruct()
+                check(L.psf_result_step(out, i, ctypes.byref(s)))
+                steps.append(s.as_dict())
+            view = CSRStruct()
+            check(L.psf_result_csr(out, ctypes.byref(view)))
+            orp = np.empty(view.n + 1, np.int32)
+            ocol = np.empty(max(view.nnz, 1), np.int32)
+            oval = np.empty(max(view.nnz, 1), np.float64)
+            check(L.psf_result_copy(out, orp.ctypes.data, ocol.ctypes.data, oval.ctypes.data, st))
+            (stream if stream is not None else _torch().cuda.current_stream()).synchronize()
+        finally:
+            L.psf_result_destroy(out)
+        return (orp, ocol[: view.nnz], oval[: view.nnz]), info.as_dict(), steps
+
 
 def eval_batch(series, Zs, stream=None):
     """psf_eval_batch over instances (series[i], Zs[i]); list of Results."""

@@ -23,7 +23,7 @@ ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT
 # Every function the header declares (checked by the tests).
 EXPORTS = [
     "psf_version", "psf_last_error", "psf_series_create", "psf_series_set_param",
-    "psf_series_destroy", "psf_eval", "psf_eval_batch", "psf_product_filter", "psf_norm1",
+    "psf_series_destroy", "psf_eval", "psf_eval_from_host", "psf_eval_batch", "psf_product_filter", "psf_norm1",
     "psf_norm1_noalloc", "psf_server_create", "psf_server_submit", "psf_server_poll", "psf_server_stats",
     "psf_server_destroy", "psf_tune_set", "psf_tune_get", "psf_autotune",
     "psf_plan", "psf_result_csr", "psf_result_copy", "psf_result_info", "psf_result_step",
@@ -118,6 +118,7 @@ def _declare(h: ctypes.CDLL) -> None:
     h.psf_series_set_param.argtypes = [vp, i32, f64]
     h.psf_series_destroy.argtypes = [vp]
     h.psf_eval.argtypes = [vp, csrp, vp, ctypes.POINTER(vp)]
+    h.psf_eval_from_host.argtypes = [vp, csrp, vp, ctypes.POINTER(vp)]
     h.psf_eval_batch.argtypes = [ctypes.POINTER(vp), csrp, i32, vp, ctypes.POINTER(vp)]
     h.psf_product_filter.argtypes = [csrp, csrp, i32, ctypes.POINTER(f64), ctypes.POINTER(csrp), f64, f64,
                                      i32, vp, ctypes.POINTER(vp)]

@@ -1085,10 +1085,33 @@ int psf_result_csr(psf_result_t r, psf_csr_t* view) {
 int psf_result_copy(psf_result_t r, int32_t* rowptr, int32_t* col, double* val, void* stream) {
     if (!r) return fail(PSF_EINVAL, "null result");
     cudaStream_t st = (cudaStream_t)stream;
-    if (rowptr) CU(cudaMemcpyAsync(rowptr, r->rowptr, sizeof(int) * ((size_t)r->n + 1), cudaMemcpyDeviceToDevice, st));
-    if (col && r->nnz) CU(cudaMemcpyAsync(col, r->col, sizeof(int) * (size_t)r->nnz, cudaMemcpyDeviceToDevice, st));
-    if (val && r->nnz) CU(cudaMemcpyAsync(val, r->val, sizeof(double) * (size_t)r->nnz, cudaMemcpyDeviceToDevice, st));
+    // cudaMemcpyDefault: the destination may be device or host memory
+    if (rowptr) CU(cudaMemcpyAsync(rowptr, r->rowptr, sizeof(int) * ((size_t)r->n + 1), cudaMemcpyDefault, st));
+    if (col && r->nnz) CU(cudaMemcpyAsync(col, r->col, sizeof(int) * (size_t)r->nnz, cudaMemcpyDefault, st));
+    if (val && r->nnz) CU(cudaMemcpyAsync(val, r->val, sizeof(double) * (size_t)r->nnz, cudaMemcpyDefault, st));
     return PSF_OK;
+}
+
+int psf_eval_from_host(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t* out) {
+    if (!out) return fail(PSF_EINVAL, "out is null");
+    *out = nullptr;
+    if (!series) return fail(PSF_EINVAL, "null series");
+    int rc = check_csr(Z, Z ? Z->n : 0, "Z");
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = prepare(st))) return rc;
+    // a stream-ordered device copy of Z, released after the evaluation's work
+    DevBuf rp, ci, v;
+    CU(rp.alloc(sizeof(int) * ((size_t)Z->n + 1), st));
+    CU(ci.alloc(sizeof(int) * (size_t)Z->nnz, st));
+    CU(v.alloc(sizeof(double) * (size_t)Z->nnz, st));
+    CU(cudaMemcpyAsync(rp.p, Z->rowptr, sizeof(int) * ((size_t)Z->n + 1), cudaMemcpyDefault, st));
+    if (Z->nnz) {
+        CU(cudaMemcpyAsync(ci.p, Z->col, sizeof(int) * (size_t)Z->nnz, cudaMemcpyDefault, st));
+        CU(cudaMemcpyAsync(v.p, Z->val, sizeof(double) * (size_t)Z->nnz, cudaMemcpyDefault, st));
+    }
+    psf_csr_t Zd{Z->n, Z->nnz, rp.as<int>(), ci.as<int>(), v.as<double>()};
+    return psf_eval(series, &Zd, stream, out);
 }
 
 int psf_result_info(psf_result_t r, psf_info_t* info) {

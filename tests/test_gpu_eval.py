@@ -315,3 +315,21 @@ def test_wide_accumulator_rows_bitwise(case):
     s = psf.Series(a, tol)
     for _ in range(3):
         check_same(s.eval(dev(Z)), ref, case)
+
+
+def test_host_to_host_path_bitwise():
+    # psf_eval_from_host (Z in host memory) and psf_result_copy into host
+    # arrays: the same result as the device path, and as the oracle
+    Z = syn.laplacian_2d(48)
+    s = psf.Series(syn.coeffs("exp"), 1e-12)
+    (rp, col, val), info, steps = s.eval_host(*Z)
+    ref = psscf(ocsr(Z), syn.coeffs("exp"), 1e-12)
+    assert np.array_equal(rp, ref.F.rowptr) and np.array_equal(col, ref.F.col)
+    assert np.array_equal(val.view(np.uint64), np.asarray(ref.F.val).view(np.uint64))
+    dev_res = s.eval(dev(ocsr(Z)))
+    assert dev_res.steps == steps and dev_res.info["nnz"] == info["nnz"]
+    # the zero 5 x 5 matrix through the host path: cos(0) = I
+    (rp0, col0, val0), info0, _ = psf.Series(syn.coeffs("cos"), 1e-12).eval_host(
+        np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert list(rp0) == [0, 1, 2, 3, 4, 5] and list(col0) == [0, 1, 2, 3, 4] and list(val0) == [1.0] * 5
+    assert info0["nnz"] == 5
