@@ -12,7 +12,9 @@ What it computes, with the paper passage each part follows:
   sparse.alg1         Algorithm 1 (Sec. 3.1.1)
   sparse.horner_dense dense Horner (Eq. 1), for small tests
   planner             Eqs. (5), (6), (24)-(28), (34)-(37), Lemma 1
-  psscf.psscf         Algorithm 2 (Sec. 3.2.3), filtered and unfiltered
+  psscf.psscf         Algorithm 2 (Sec. 3.2.3), filtered and unfiltered; with
+                      square=True on W = Z^2 for even or odd series
+                      (planner.split_even_odd, an adjacent variant)
   normest             deterministic estimates of ||Z^k||_1, k <= 10 (Sec. 3.2.2)
 
 Pinned by ``tests/test_oracle_*.py`` against closed forms, exact rational

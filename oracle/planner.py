@@ -127,15 +127,21 @@ def filter_bounds(a, N: int, q: int, b: int, g: int, z, budget: float):
     return d, zeta, sigma
 
 
-def plan(a, tol: float, norms, poly: bool = False, s: int = 0, submult: bool = False) -> Plan:
+def plan(a, tol: float, norms, poly: bool = False, s: int = 0, submult: bool = False,
+         stride: int = 1) -> Plan:
     """Alg. 2 steps 1-3 plus the filtering-norm-thresholds.
 
     Series mode: N = Theta(tol, a, z) (Eq. 34), budget = tol - tail(N)
     (Eq. 35/36).  Polynomial mode: N = len(a), budget = tol (Eq. 27/28).
+
+    ``stride`` = 2 plans the series in W = Z^2 (``split_even_odd``): the
+    norms are still those of Z, and z_i of W is Eq. (37)'s z_{2i} of Z, a
+    bound on ||W^i|| = ||Z^{2i}||.
     """
     a = [float(x) for x in a]
     M = len(a)
-    z = z_sequence(norms, max(M, K_NORMEST + 1), submult)
+    zz = z_sequence(norms, stride * max(M, K_NORMEST + 1), submult)
+    z = zz[::stride]
     if poly:
         N = M
         trunc = 0.0
@@ -151,3 +157,22 @@ def plan(a, tol: float, norms, poly: bool = False, s: int = 0, submult: bool = F
     if N >= 2:
         p.d, p.zeta, p.sigma = filter_bounds(a, N, q, b, g, z, budget)
     return p
+
+
+def split_even_odd(a):
+    """The substitution W = Z^2 for a series with only even or only odd
+    powers (an adjacent variant; the paper evaluates cos with its zero odd
+    coefficients in place, Eq. 40).
+
+    Even: f(Z) = g(Z^2) with c_k = a_{2k}.  Odd: f(Z) = Z g(Z^2) with
+    c_k = a_{2k+1}.  Returns (c, odd); raises ValueError when both parities
+    have nonzero coefficients.  All-zero coefficients count as even.
+    """
+    a = [float(x) for x in a]
+    even_nz = any(x != 0.0 for x in a[0::2])
+    odd_nz = any(x != 0.0 for x in a[1::2])
+    if even_nz and odd_nz:
+        raise ValueError("the series has both even and odd powers")
+    if odd_nz:
+        return a[1::2], True
+    return a[0::2], False

@@ -5,6 +5,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 from . import planner
@@ -13,7 +14,7 @@ from .sparse import CSR, alg1, axpy, matmul_add, norm1
 
 @dataclass
 class StepStat:
-    kind: str  # "baby" (Eq. 11) or "giant" (Eq. 14)
+    kind: str  # "baby" (Eq. 11), "giant" (Eq. 14) or "odd" (F = Z G-hat, square mode)
     index: int  # k of Z-hat_(k) or i of S-hat_i
     threshold: float  # the bound passed to Alg. 2 l.6 / l.12 (0 = unfiltered)
     nnz_pre: int
@@ -63,23 +64,51 @@ def _filter(C: CSR, bound: float, e_r: float, maxit: int):
 
 def psscf(Z: CSR, a, tol: float, *, poly: bool = False, filtered: bool = True, s: int = 0,
           e_r: float = 0.1, maxit: int = 1000, submult: bool = False,
-          norms=None) -> Result:
+          norms=None, square: bool = False) -> Result:
     """f(Z) ~ S-hat_{b-1} by Algorithm 2.
 
     ``filtered=False`` is the unfiltered PS scheme with the same N, q, b: every
     threshold is 0, which keeps every nonzero entry.  ``norms`` may pass
     precomputed ||Z^i||_1, i = 0..10.
+
+    ``square=True`` substitutes W = Z^2 (``planner.split_even_odd``): W = Z Z
+    unfiltered, then Algorithm 2 on g(W) with the norms z_i of W taken as
+    z_{2i} of Z.  An odd series ends with the unfiltered product F = Z G-hat;
+    since ||Z (g(W) - G-hat)|| <= ||Z||_1 ||g(W) - G-hat||, g is evaluated to
+    eps_tol / ||Z||_1 (infinite for Z = 0).
     """
     n = Z.n
     a = [float(x) for x in a]
     if norms is None:
         norms = [1.0, norm1(Z)] if submult else power_norms(Z)  # step 1
-    p = planner.plan(a, tol, norms, poly=poly, s=s, submult=submult)  # steps 2-3
+    if not square:
+        p = planner.plan(a, tol, norms, poly=poly, s=s, submult=submult)  # steps 2-3
+        res = Result(CSR.empty(n), p, list(norms))
+        res.F = _alg2(Z, a, p, res, filtered, e_r, maxit)
+        return res
+    c, odd = planner.split_even_odd(a)
+    tol_g = tol
+    if odd:
+        tol_g = tol / norms[1] if norms[1] != 0.0 else math.inf
+    p = planner.plan(c, tol_g, norms, poly=poly, s=s, submult=submult, stride=2)
     res = Result(CSR.empty(n), p, list(norms))
+    W = matmul_add(Z, Z)
+    res.products += 1
+    G = _alg2(W, c, p, res, filtered, e_r, maxit)
+    if odd:
+        G = matmul_add(Z, G)
+        res.products += 1
+        res.steps.append(StepStat("odd", 1, 0.0, G.nnz, G.nnz, 0.0, 0, 0.0))
+    res.F = G
+    return res
+
+
+def _alg2(Z: CSR, a, p: planner.Plan, res: Result, filtered: bool, e_r: float, maxit: int) -> CSR:
+    """Steps 4-14 of Algorithm 2 with the plan ``p``; appends to ``res.steps``."""
+    n = Z.n
     N, q, b, g = p.N, p.q, p.b, p.g
     if N == 1:
-        res.F = CSR.identity(n, a[0]) if a[0] != 0.0 else CSR.empty(n)
-        return res
+        return CSR.identity(n, a[0]) if a[0] != 0.0 else CSR.empty(n)
 
     # steps 4-7: baby steps Z-hat_(k+1) = filter(Z Z-hat_(k))
     Zh = {1: Z}
@@ -109,5 +138,4 @@ def psscf(Z: CSR, a, tol: float, *, poly: bool = False, filtered: bool = True, s
         f = _filter(St, bound, e_r, maxit)
         S = f.kept
         res.steps.append(StepStat("giant", i, bound, St.nnz, S.nnz, f.eps_f, f.iters, f.c))
-    res.F = S  # step 14
-    return res
+    return S  # step 14
