@@ -364,6 +364,10 @@ def run_psf(args):
                "plans_estimate_vs_exact": plans, "z_estimate_over_exact_min": min(ratios) if ratios else None,
                "how": "same steps and timing as the headline, series created with estimate=True"}
 
+    square = None
+    if rank == 0 and world == 1 and not args.no_square:
+        square = measure_square(args, Z, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(rp, col, val)
@@ -397,6 +401,7 @@ def run_psf(args):
             "serving": serving,
             "tol_sweep": sweep,
             "z_estimate": est,
+            "z_square": square,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -568,6 +573,53 @@ def measure_tol_sweep(args, dev):
     return {"workload": "banded_n65536_hbw5 exp", "dense_dgemm_s_projected": t_gemm, "rows": rows}
 
 
+def measure_square(args, Z, flush):
+    """cos and sinh on the headline workload, directly and with the W = Z^2
+    substitution (PSF_Z_SQUARE): event-timed evaluations with L2 flushed
+    before each, plan sizes, and the 1-norm distance between the two
+    results (each is within tol of f(Z), so at most 2 tol apart)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    from paper_2208_05683_gb300 import _abi
+    L = psf.lib()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for kind in ("cos", "sinh"):
+        row, mats = {}, {}
+        # square_q2: the same with the PS block size q = 2 in W (s override)
+        for mode, opts in (("direct", {}), ("square", {"square": True}), ("square_q2", {"square": True, "s": 2})):
+            s = psf.Series(syn.coeffs(kind), TOL, kernel=args.kernel, **opts)
+            lat = []
+            for it in range(args.warmup + 2 * args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h = s.eval_handle(Z, stream)
+                e1.record(stream)
+                e1.synchronize()
+                _abi.check(L.psf_result_destroy(h))
+                if it >= args.warmup:
+                    lat.append(e0.elapsed_time(e1))
+            r = s.eval(Z)
+            info = r.info
+            rp, col, val = r.csr.to_host()
+            mats[mode] = sp.csr_matrix((val, col, rp), shape=(Z.n, Z.n))
+            row[mode] = {"p50_ms": statistics.median(lat), "evals_per_s": len(lat) / (sum(lat) / 1e3),
+                         "N": info["N"], "q": info["q"], "b": info["b"], "products": info["products"],
+                         "nnz": info["nnz"], "fma": info["fma"]}
+        row["diff_1norm"] = float(abs(mats["direct"] - mats["square"]).sum(axis=0).max())
+        row["diff_1norm_q2"] = float(abs(mats["direct"] - mats["square_q2"]).sum(axis=0).max())
+        row["speedup_p50"] = row["direct"]["p50_ms"] / row["square"]["p50_ms"]
+        row["speedup_p50_q2"] = row["direct"]["p50_ms"] / row["square_q2"]["p50_ms"]
+        out[kind] = row
+    out["how"] = f"{WORKLOAD}, tol {TOL:g}; {2 * args.steps} evaluations per mode after {args.warmup} warm-up"
+    return out
+
+
 def run_e2(args):
     """The paper's second experiment (Sec. 4, Figs. 1-2) on this GPU: random
     1000 x 1000 banded matrices, lower = upper bandwidth w = 1..15, N(0, 1)
@@ -617,15 +669,20 @@ def run_e2(args):
     for kind in ("exp", "cos"):
         a = syn.coeffs(kind)
         filt, unf = psf.Series(a, tol), psf.Series(a, tol, filtered=False)
+        # cos also with the W = Z^2 substitution (PSF_Z_SQUARE)
+        sq = psf.Series(a, tol, square=True) if kind == "cos" else None
         for w in range(1, 16):
             acc = {k: [] for k in ("psscf_ms", "ps_ms", "ref_ms", "psscf_density", "ps_density", "ref_density",
-                                   "psscf_err_fro", "ps_err_fro", "psscf_err_1", "ps_err_1", "N")}
+                                   "psscf_err_fro", "ps_err_fro", "psscf_err_1", "ps_err_1", "N",
+                                   "square_ms", "square_err_fro", "square_density")}
             for seed in range(seeds):
                 host = syn.banded_normal(n, w, 1000 * w + seed)
                 Z = psf.DeviceCSR.from_host(*host, device=dev)
                 Zd = dense_of(host)
                 if seed == 0:  # untimed first evaluation at this bandwidth
                     filt.eval(Z), unf.eval(Z), reference(kind, Zd)
+                    if sq is not None:
+                        sq.eval(Z)
                 rf, tf = timed(lambda: filt.eval(Z))
                 ru, tu = timed(lambda: unf.eval(Z))
                 ref, tr = timed(lambda: reference(kind, Zd))
@@ -641,13 +698,19 @@ def run_e2(args):
                 acc["psscf_err_1"].append(ef[1])
                 acc["ps_err_1"].append(eu[1])
                 acc["N"].append(rf.info["N"])
+                if sq is not None:
+                    rs, ts = timed(lambda: sq.eval(Z))
+                    acc["square_ms"].append(ts)
+                    acc["square_err_fro"].append(errors(rs, ref)[0])
+                    acc["square_density"].append(rs.info["nnz"] / n / n)
             row = {"kind": kind, "w": w}
-            row.update({k: float(np.mean(v)) for k, v in acc.items()})
+            row.update({k: float(np.mean(v)) for k, v in acc.items() if v})
             row["psscf_err_fro_max"] = float(np.max(acc["psscf_err_fro"]))
             rows.append(row)
             print(f"{kind} w={w:2d}: psscf {row['psscf_ms']:7.2f} ms  ps {row['ps_ms']:7.2f} ms  "
                   f"dense {row['ref_ms']:7.2f} ms  density {row['psscf_density']:.3f} / {row['ps_density']:.3f}  "
-                  f"err {row['psscf_err_fro']:.2e} / {row['ps_err_fro']:.2e}", file=sys.stderr, flush=True)
+                  f"err {row['psscf_err_fro']:.2e} / {row['ps_err_fro']:.2e}  "
+                  f"square {row.get('square_ms', float('nan')):7.2f} ms", file=sys.stderr, flush=True)
     print(json.dumps({"experiment": "banded_normal n=1000, w=1..15, N(0,1), exp and cos, eps_tol=1e-14",
                       "seeds_per_w": seeds, "reference": "torch.linalg.matrix_exp float64 / complex128 on the GPU",
                       "timing": "wall clock per evaluation through the Python API, synchronized", "rows": rows}))
@@ -696,6 +759,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-estimate", action="store_true", help="skip the estimated-norms (PSF_Z_ESTIMATE) measurement")
+    ap.add_argument("--no-square", action="store_true",
+                    help="skip the cos/sinh measurement with the W = Z^2 substitution (PSF_Z_SQUARE)")
     ap.add_argument("--serving-requests", type=int, default=300, help="requests of the serving measurement")
     ap.add_argument("--sweep", action="store_true",
                     help="add the tolerance sweep of the banded n = 65536 workload against dense PS")

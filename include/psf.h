@@ -63,6 +63,19 @@ extern "C" {
  * bounds.  A column of Z with more than 4096 entries falls back to the exact
  * norms.  Not with PSF_Z_SUBMULT; psf_eval only (psf_eval_batch rejects it). */
 #define PSF_Z_ESTIMATE 8u
+/* PSF_Z_SQUARE: for a series with only even powers (cos, cosh) or only odd
+ * powers (sin, sinh), run Algorithm 2 on W = Z^2 (an adjacent variant; the
+ * paper evaluates cos with its zero odd coefficients in place, Eq. 40).
+ * Even: f(Z) = g(W), g's coefficients c_k = a_{2k}.  Odd: f(Z) = Z g(W),
+ * c_k = a_{2k+1}, g evaluated to tol / ||Z||_1 and the last product Z G
+ * unfiltered (||Z (g(W) - G)||_1 <= ||Z||_1 ||g(W) - G||_1).  W = Z Z is
+ * unfiltered; the norms of W's powers are z_{2i} of Z (Eq. 37 and Lemma 1 for
+ * Z, or the PSF_Z_SUBMULT / PSF_Z_ESTIMATE variants).  The plan fields N, q,
+ * b, g, trunc, budget and the thresholds are those of g in W; z[] and
+ * alpha10 stay those of Z.  psf_series_create fails with PSF_EINVAL when
+ * both parities have nonzero coefficients.  psf_eval only
+ * (psf_eval_batch and psf_server_submit reject it). */
+#define PSF_Z_SQUARE 16u
 
 /* ---- tunable parameters (psf_series_set_param) ---- */
 #define PSF_PARAM_ER 1            /* e_r of Algorithm 1 (default 0.1) */
@@ -89,7 +102,8 @@ typedef struct {
 typedef struct {
     int32_t N;          /* truncation length (Eq. 34) or m (polynomial) */
     int32_t q, b, g;    /* PS split (Eq. 6) */
-    int32_t products;   /* matrix products in the PS phase (Eq. 5) */
+    int32_t products;   /* matrix products in the PS phase (Eq. 5); with PSF_Z_SQUARE
+                           also W = Z Z and, for an odd series, Z G */
     int32_t nsteps;     /* entries available through psf_result_step */
     double z[11];       /* ||Z^i||_1 (or ||Z||^i), i = 0..10 (Eq. 37) */
     double alpha10;     /* Lemma 1 growth factor */
@@ -106,7 +120,8 @@ typedef struct {
 
 /* Statistics of one filtered product (Alg. 2 l.5-6 or l.11-12). */
 typedef struct {
-    int32_t kind;       /* 0 baby step (Eq. 11), 1 giant step (Eq. 14), 2 plain add */
+    int32_t kind;       /* 0 baby step (Eq. 11), 1 giant step (Eq. 14), 2 plain add,
+                           3 the unfiltered F = Z G of an odd series (PSF_Z_SQUARE) */
     int32_t index;      /* k of Z-hat_(k), or i of S-hat_i */
     double threshold;   /* bound on the dropped 1-norm (zeta_k or sigma_i; 0 = none) */
     int64_t nnz_pre;    /* nonzero entries before the filter */
@@ -129,11 +144,13 @@ PSF_API const char* psf_last_error(void);
  *         clamped to N-1; must be <= PSF_MAX_Q.
  *   tol   eps_tol > 0: the target bound on ||f(Z) - result||_1 (Alg. 2), or the
  *         filtering budget eps of Eq. (27) for PSF_POLY.
- *   flags PSF_SERIES or PSF_POLY, optionally | PSF_NOFILTER | PSF_Z_SUBMULT.
+ *   flags PSF_SERIES or PSF_POLY, optionally | PSF_NOFILTER | PSF_Z_SUBMULT
+ *         (or PSF_Z_ESTIMATE) | PSF_Z_SQUARE.
  * In series mode the coefficients past a_{m-1} are taken as 0; supply enough
  * terms for the tail sum of Eq. (34) to fall below tol/2 before the last one.
- * Errors: PSF_EINVAL (m < 1, tol not finite and > 0, non-finite a_i),
- * PSF_ENOMEM.
+ * Errors: PSF_EINVAL (m < 1, tol not finite and > 0, non-finite a_i, unknown
+ * flags, PSF_Z_SUBMULT with PSF_Z_ESTIMATE, PSF_Z_SQUARE with coefficients of
+ * both parities), PSF_ENOMEM.
  */
 PSF_API int psf_series_create(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
                       psf_series_t* out);
@@ -299,7 +316,9 @@ PSF_API int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out);
  * PSF_Z_SUBMULT), fill N, q, b, g, products, z, alpha10, trunc, budget, and
  * the thresholds zeta[k] (k = 2..q, index k) and sigma[j] (j = 1+g..b-1,
  * index j), each array of length PSF_MAX_Q + 2 (host), entries not defined
- * set to 0.  zeta/sigma may be NULL.
+ * set to 0.  zeta/sigma may be NULL.  With PSF_Z_SQUARE the plan is that of
+ * g in W = Z^2 (see the flag; tol / z_1 for an odd series, infinite when
+ * z_1 = 0); info->z still lists the z_i of Z.
  */
 PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
              const double* norms, psf_info_t* info, double* zeta, double* sigma);

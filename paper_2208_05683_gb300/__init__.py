@@ -24,7 +24,8 @@ import ctypes
 from dataclasses import dataclass, field
 
 from . import _build
-from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_ESTIMATE, PSF_Z_SUBMULT, PSF_PARAM_ALG1_MAXIT,
+from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_ESTIMATE, PSF_Z_SQUARE, PSF_Z_SUBMULT,
+                   PSF_PARAM_ALG1_MAXIT,
                    PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS,
                    PSF_PARAM_CHUNK_SLOTS, PSF_MAX_Q, PSF_NORM1_NOALLOC_MAX_N,
                    PsfError, CSRStruct, InfoStruct, StepStruct, ServerConfig, Completion, ServerStats, lib, check)
@@ -32,7 +33,8 @@ from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_ESTIMATE, P
 __all__ = [
     "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "norm1_noalloc", "plan",
     "Server", "autotune", "tune_get", "tune_set", "PsfError",
-    "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_Z_ESTIMATE", "PSF_MAX_Q", "build", "lib",
+    "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_Z_ESTIMATE", "PSF_Z_SQUARE", "PSF_MAX_Q",
+    "build", "lib",
 ]
 
 
@@ -127,19 +129,23 @@ class Series:
     filtered False gives the unfiltered PS scheme (same N, q, b)
     submult  z_i = ||Z||^i instead of exact ||Z^i||_1 for i <= 10
     estimate z_i, i = 2..10, from the deterministic 1-norm estimator (PSF_Z_ESTIMATE)
+    square   run the scheme on W = Z^2 for a series of only even or only odd
+             powers (PSF_Z_SQUARE)
     s        override of the PS block size q (0 = Eq. 6)
     kernel   slot map of the product kernel: "auto", "table" or "bitmap"
     chunk_cols, chunk_slots  > 0: smaller row chunks (to exercise row chunking)
     """
 
     def __init__(self, coeffs, tol: float, *, poly: bool = False, filtered: bool = True,
-                 submult: bool = False, estimate: bool = False, s: int = 0, e_r: float | None = None,
+                 submult: bool = False, estimate: bool = False, square: bool = False, s: int = 0,
+                 e_r: float | None = None,
                  maxit: int | None = None, pool_entries: int | None = None,
                  kernel: str = "auto", chunk_cols: int = 0, chunk_slots: int = 0):
         L = lib()
         a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
         flags = (PSF_POLY if poly else PSF_SERIES) | (0 if filtered else PSF_NOFILTER) | \
-            (PSF_Z_SUBMULT if submult else 0) | (PSF_Z_ESTIMATE if estimate else 0)
+            (PSF_Z_SUBMULT if submult else 0) | (PSF_Z_ESTIMATE if estimate else 0) | \
+            (PSF_Z_SQUARE if square else 0)
         h = ctypes.c_void_p()
         check(L.psf_series_create(a, len(coeffs), int(s), float(tol), flags, ctypes.byref(h)))
         self._h = h
@@ -348,7 +354,8 @@ def tune_set(key: int, value: float) -> None:
     check(lib().psf_tune_set(int(key), float(value)))
 
 
-def plan(coeffs, tol: float, norms, *, poly: bool = False, submult: bool = False, s: int = 0):
+def plan(coeffs, tol: float, norms, *, poly: bool = False, submult: bool = False, s: int = 0,
+         square: bool = False):
     """The host planner: N, q, b, g, z, truncation bound, budget, zeta, sigma."""
     L = lib()
     a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
@@ -357,7 +364,7 @@ def plan(coeffs, tol: float, norms, *, poly: bool = False, submult: bool = False
     info = InfoStruct()
     zeta = (ctypes.c_double * (PSF_MAX_Q + 2))()
     sigma = (ctypes.c_double * (PSF_MAX_Q + 2))()
-    flags = (PSF_POLY if poly else 0) | (PSF_Z_SUBMULT if submult else 0)
+    flags = (PSF_POLY if poly else 0) | (PSF_Z_SUBMULT if submult else 0) | (PSF_Z_SQUARE if square else 0)
     check(L.psf_plan(a, len(coeffs), int(s), float(tol), flags, nrm, ctypes.byref(info), zeta, sigma))
     d = info.as_dict()
     d["zeta"] = {k: zeta[k] for k in range(2, d["q"] + 1)}

@@ -8,7 +8,7 @@ import threading
 from . import _build
 
 PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_ENOTCONV, PSF_ETIMEOUT, PSF_ETOOBIG = range(7)
-PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT, PSF_Z_ESTIMATE = 0, 1, 2, 4, 8
+PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT, PSF_Z_ESTIMATE, PSF_Z_SQUARE = 0, 1, 2, 4, 8, 16
 PSF_PARAM_ER, PSF_PARAM_ALG1_MAXIT, PSF_PARAM_POOL_ENTRIES = 1, 2, 3
 PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
 PSF_MAX_Q = 23
@@ -78,7 +78,7 @@ class StepStruct(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("dropped", ctypes.c_double), ("fma", ctypes.c_int64)]
 
     def as_dict(self):
-        return {"kind": ("baby", "giant", "add")[self.kind], "index": self.index,
+        return {"kind": ("baby", "giant", "add", "odd")[self.kind], "index": self.index,
                 "threshold": self.threshold, "nnz_pre": self.nnz_pre, "nnz_post": self.nnz_post,
                 "eps_f": self.eps_f, "iters": self.iters, "dropped": self.dropped, "fma": self.fma}
 

@@ -254,6 +254,7 @@ int pool_copy(Work& w, const psf_csr_t& m, size_t slot, RowView* out) {
 }
 
 constexpr size_t kSlotZp = 60;  // row slot of the pooled copy of Z
+constexpr size_t kSlotW = 61;   // row slot of W = Z Z (PSF_Z_SQUARE) when computed in the PS phase
 
 // ctl->mark[i] <- the pool counter, in stream order
 int mark_pool(Work& w, int i) {
@@ -343,7 +344,7 @@ int psf_series_create(const double* coeffs, int64_t m, int32_t s, double tol, ui
     if (!coeffs || m < 1) return fail(PSF_EINVAL, "need at least one coefficient");
     if (m > 100000) return fail(PSF_ETOOBIG, "m = %lld coefficients (max 100000)", (long long)m);
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PSF_EINVAL, "tol must be finite and > 0");
-    if (flags & ~(PSF_POLY | PSF_NOFILTER | PSF_Z_SUBMULT | PSF_Z_ESTIMATE))
+    if (flags & ~(PSF_POLY | PSF_NOFILTER | PSF_Z_SUBMULT | PSF_Z_ESTIMATE | PSF_Z_SQUARE))
         return fail(PSF_EINVAL, "unknown flags 0x%x", flags);
     if ((flags & PSF_Z_SUBMULT) && (flags & PSF_Z_ESTIMATE))
         return fail(PSF_EINVAL, "PSF_Z_SUBMULT and PSF_Z_ESTIMATE exclude each other");
@@ -353,6 +354,10 @@ int psf_series_create(const double* coeffs, int64_t m, int32_t s, double tol, ui
     psf_series_s* p = new (std::nothrow) psf_series_s();
     if (!p) return fail(PSF_ENOMEM, "host allocation");
     p->a.assign(coeffs, coeffs + m);
+    if ((flags & PSF_Z_SQUARE) && split_even_odd(p->a, p->c, p->odd)) {
+        delete p;
+        return fail(PSF_EINVAL, "PSF_Z_SQUARE needs a series of only even or only odd powers");
+    }
     p->tol = tol;
     p->flags = flags;
     p->s = s;
@@ -403,16 +408,25 @@ int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t fl
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PSF_EINVAL, "tol must be finite and > 0");
     if (s < 0 || s > PSF_MAX_Q) return fail(PSF_EINVAL, "s out of range");
     std::vector<double> a(coeffs, coeffs + m);
+    const bool square = flags & PSF_Z_SQUARE;
+    bool odd = false;
+    if (square) {
+        std::vector<double> c;
+        if (split_even_odd(a, c, odd))
+            return fail(PSF_EINVAL, "PSF_Z_SQUARE needs a series of only even or only odd powers");
+        a.swap(c);
+        if (odd) tol = tol / norms[1];  // IEEE: infinite for ||Z||_1 = 0
+    }
     Plan p;
-    if (make_plan(a, tol, flags & PSF_POLY, flags & PSF_Z_SUBMULT, s, norms, p))
-        return fail(PSF_ENOTCONV, "no truncation length within %lld coefficients (Eq. 34)", (long long)m);
+    if (make_plan(a, tol, flags & PSF_POLY, flags & PSF_Z_SUBMULT, s, norms, p, square ? 2 : 1))
+        return fail(PSF_ENOTCONV, "no truncation length within %zu coefficients (Eq. 34)", a.size());
     std::memset(info, 0, sizeof *info);
     info->N = p.N;
     info->q = p.q;
     info->b = p.b;
     info->g = p.g;
-    info->products = p.products;
-    for (int i = 0; i <= 10; ++i) info->z[i] = p.z[(size_t)i];
+    info->products = p.products + (square ? 1 + (int)odd : 0);
+    for (int i = 0; i <= 10; ++i) info->z[i] = p.zz[(size_t)i];
     info->alpha10 = p.alpha10;
     info->trunc = p.trunc;
     info->budget = p.budget;
@@ -584,7 +598,12 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     const bool submult = series->flags & PSF_Z_SUBMULT;
     const bool poly = series->flags & PSF_POLY;
     const bool nofilter = series->flags & PSF_NOFILTER;
-    const std::vector<double>& a = series->a;
+    // PSF_Z_SQUARE: Algorithm 2 runs on W = Z Z with g's coefficients, and an
+    // odd series ends with F = Z G-hat
+    const bool square = series->flags & PSF_Z_SQUARE;
+    const bool odd = square && series->odd;
+    const int stride = square ? 2 : 1;
+    const std::vector<double>& a = square ? series->c : series->a;
 
     Work w;
     if ((rc = w.init(n, st, 16))) return rc;
@@ -622,7 +641,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     // leading ones double as baby steps while nothing is dropped.
     const unsigned long long ps_reserve =
         (series->ps_need > 0 && chain) ? series->ps_need + series->ps_need / 8 + 4096 : 0;
-    RowView zp{};
+    RowView zp{}, zsq{};  // the pooled Z and, when the chain ran, Z^2
     unsigned long long zfma[kMaxNorms] = {0ull};  // multiply-adds of Z^i in the norm phase
     {
         unsigned long long est = (unsigned long long)Z->nnz * 256ull + (unsigned long long)n * 64ull + 4096ull;
@@ -662,6 +681,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                                            slots + i, blen, zlen)))
                             return rc;
                         if ((rc = mark_pool(w, i))) return rc;
+                        if (i == 2) zsq = cur;
                         nr.rb[i - 1] = cur.rb;
                         nr.re[i - 1] = cur.re;
                         prev = cur;
@@ -708,7 +728,9 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
 
     // ---- Alg. 2 steps 2-3 and the thresholds
     Plan p;
-    if (make_plan(a, series->tol, poly, submult, series->s, norms, p))
+    // an odd series: ||f(Z) - Z G-hat||_1 <= ||Z||_1 ||g(W) - G-hat||_1 (IEEE: 1/0 = inf)
+    const double tol_g = odd ? series->tol / norms[1] : series->tol;
+    if (make_plan(a, tol_g, poly, submult, series->s, norms, p, stride))
         return fail(PSF_ENOTCONV, "no truncation length within %zu coefficients (Eq. 34)", a.size());
     if (p.q > PSF_MAX_Q) return fail(PSF_ETOOBIG, "q = %d exceeds %d", p.q, PSF_MAX_Q);
     const int N = p.N, q = p.q, b = p.b, g = p.g;
@@ -721,7 +743,12 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     RowView F;
     std::vector<psf_step_info_t> steps;
     unsigned long long eval_fma = z_fma;
-    if (N == 1 || n == 0) {
+    // mean row length of the k-th power of the matrix the scheme multiplies by
+    auto pow_len = [&](int k) {
+        const int e = k * stride;
+        return (e <= 10 && znnz[e] > 0.0) ? znnz[e] / n : zlen * e * e;
+    };
+    if ((N == 1 && !odd) || n == 0) {
         // f(Z) ~ a_0 I: no product (Eq. 5)
         r = new (std::nothrow) psf_result_s();
         if (!r) return fail(PSF_ENOMEM, "host allocation");
@@ -758,23 +785,34 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat) * (size_t)stat_cap, st));
             steps.clear();
             int si = 0;
-            std::vector<RowView> Zh((size_t)q + 1);
+            std::vector<RowView> Zh((size_t)q + 2);
             if (reuse) {
                 Zh[1] = zp;  // Z-hat_(1) = Z, pooled by the norm phase
             } else if ((rc = pool_copy(w, *Z, kSlotZp, &Zh[1]))) {
                 return rc;
             }
-            size_t slot = 0;
+            // the left factor of the baby steps: Z, or W = Z Z (unfiltered;
+            // the norm phase's Z^2 when this pool still holds it)
+            RowView vm = vz;
+            if (square) {
+                if (reuse) {
+                    vm = zsq;
+                } else if ((rc = run_step(w, &vz, &Zh[1], {}, 0.0, 0.0, 1, -1, kSlotW, &vm, nullptr, zlen, zlen))) {
+                    return rc;
+                }
+                Zh[1] = vm;
+            }
+            // square mode keeps the norm phase's row slots 0..8 (W is slot 0)
+            size_t slot = square ? 9 : 0;
             // baby steps: Z-hat_(k+1) = filter(Z Z-hat_(k)), threshold zeta_{k+1}
             for (int k = 1; k < q; ++k) {
                 double thr = nofilter ? 0.0 : p.zeta[(size_t)k + 1];
-                double blen = (size_t)(k - 1) < series->len_baby.size()
-                                  ? series->len_baby[(size_t)(k - 1)]
-                                  : (k <= 10 && znnz[k] > 0.0 ? znnz[k] / n : zlen * k * k);
+                double blen = (size_t)(k - 1) < series->len_baby.size() ? series->len_baby[(size_t)(k - 1)]
+                                                                         : pow_len(k);
                 // baby step k + 1 writes row slot k - 1, the slot of the norm phase's Z^(k+1)
-                const int rk = (reuse && k + 1 <= 10 && slot == (size_t)(k - 1)) ? k + 1 : 0;
-                if ((rc = run_step(w, &vz, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
-                                   &Zh[(size_t)k + 1], nullptr, blen, zlen, rk, rk ? zfma[rk] : 0ull)))
+                const int rk = (reuse && !square && k + 1 <= 10 && slot == (size_t)(k - 1)) ? k + 1 : 0;
+                if ((rc = run_step(w, &vm, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
+                                   &Zh[(size_t)k + 1], nullptr, blen, pow_len(1), rk, rk ? zfma[rk] : 0ull)))
                     return rc;
                 psf_step_info_t s{};
                 s.kind = 0;
@@ -785,6 +823,11 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             }
             auto block = [&](int i) {
                 std::vector<AddTerm> add;
+                if (q == 0 && coef(0) != 0.0) {  // N = 1 (odd series only): c_0 I
+                    AddTerm T{};
+                    T.alpha = coef(0);
+                    add.push_back(T);
+                }
                 for (int j = 0; j < q; ++j) {
                     double alpha = coef(i * q + j);
                     if (alpha == 0.0) continue;
@@ -837,7 +880,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     double blen = (size_t)(i - 1) < series->len_giant.size()
                                       ? series->len_giant[(size_t)(i - 1)]
                                       : (znnz[10] > 0.0 ? znnz[10] / n : zlen * 100.0);
-                    const double alen = (q <= 10 && znnz[q] > 0.0) ? znnz[q] / n : zlen * q * q;
+                    const double alen = pow_len(q);
                     const double olen =
                         (size_t)(i - 1) < series->out_giant.size() ? series->out_giant[(size_t)(i - 1)] : 0.0;
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
@@ -850,6 +893,18 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 ++si;
                 S = nxt;
                 cur = nslot;
+            }
+            if (odd) {
+                // F = Z G-hat, unfiltered
+                psf_step_info_t s{};
+                s.kind = 3;
+                s.index = 1;
+                RowView G = S;
+                const double glen = series->len_odd > 0.0 ? series->len_odd : pow_len(N - 1);
+                if ((rc = run_step(w, &vz, &G, {}, 0.0, 0.0, 1, si, sslot[cur ^ 1], &S, nullptr, glen, zlen)))
+                    return rc;
+                steps.push_back(s);
+                ++si;
             }
             F = S;
             if ((rc = make_result(w, F, &handle, &r))) return rc;
@@ -895,7 +950,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             series->len_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             series->out_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             {
-                double prev_len = zlen;  // Z-hat_(1) = Z
+                double prev_len = pow_len(1);  // Z-hat_(1) = Z or W
                 size_t idx = 0;
                 for (int k = 1; k < q; ++k, ++idx) {
                     series->len_baby[(size_t)(k - 1)] = prev_len;
@@ -908,6 +963,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     series->out_giant[(size_t)(i - 1)] = (double)steps[idx].nnz_pre / n;
                     s_len = (double)steps[idx].nnz_post / n;
                 }
+                if (odd) series->len_odd = s_len;  // G-hat, the right factor of F = Z G-hat
             }
             if ((rc = finish_result(w, F, r, c.nnz_total))) {
                 destroy_result(r);
@@ -924,9 +980,9 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     inf.q = q;
     inf.b = b;
     inf.g = g;
-    inf.products = p.products;
+    inf.products = p.products + (square ? 1 + (int)odd : 0);
     inf.nsteps = (int32_t)steps.size();
-    for (int i = 0; i <= 10; ++i) inf.z[i] = p.z[(size_t)i];
+    for (int i = 0; i <= 10; ++i) inf.z[i] = p.zz[(size_t)i];
     inf.alpha10 = p.alpha10;
     inf.trunc = p.trunc;
     inf.budget = p.budget;

@@ -743,8 +743,8 @@ extern "C" int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, i
     if (count == 0) return PSF_OK;
     for (int i = 0; i < count; ++i) {
         if (!series[i]) return fail(PSF_EINVAL, "batch instance %d: null series", i);
-        if (series[i]->flags & PSF_Z_ESTIMATE)
-            return fail(PSF_EINVAL, "batch instance %d: PSF_Z_ESTIMATE is for psf_eval only", i);
+        if (series[i]->flags & (PSF_Z_ESTIMATE | PSF_Z_SQUARE))
+            return fail(PSF_EINVAL, "batch instance %d: PSF_Z_ESTIMATE and PSF_Z_SQUARE are for psf_eval only", i);
         int rc = check_csr(&Zs[i], Zs[i].n, "Z");
         if (rc) return rc;
         if (Zs[i].n == 0 && Zs[i].nnz != 0) return fail(PSF_EINVAL, "batch instance %d: n = 0 with entries", i);

@@ -17,6 +17,9 @@
 // ---------------------------------------------------------------- objects
 struct psf_series_s {
     std::vector<double> a;
+    // PSF_Z_SQUARE: the coefficients c_k of g (f(Z) = g(Z^2) or Z g(Z^2))
+    std::vector<double> c;
+    bool odd = false;
     double tol = 0.0;
     uint32_t flags = 0;
     int s = 0;
@@ -31,6 +34,7 @@ struct psf_series_s {
     // mean output row length before the filter of each giant step (the
     // product kernel's accumulator variant for long rows)
     std::vector<double> out_giant;
+    double len_odd = 0.0;  // row length of G-hat in F = Z G-hat (odd series, PSF_Z_SQUARE)
     int kernel = 0;       // PSF_PARAM_KERNEL
     int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
     int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS

@@ -8,6 +8,8 @@
 // Floating-point conventions: plain IEEE FP64, this file is compiled with
 // contraction off; every sum runs left to right in ascending index order as
 // written in the paper; z_i = alpha_10^i above i = 10 (Lemma 1) uses pow().
+// With stride 2 the scheme runs on W = Z^2 (even or odd series, the caller
+// passes the substituted coefficients and tolerance) and z_i of W is z_{2i}.
 #include "psf_plan.h"
 
 #include <cmath>
@@ -47,13 +49,15 @@ double tail_sum(const std::vector<double>& a, const std::vector<double>& z, int 
 }  // namespace
 
 int make_plan(const std::vector<double>& a, double tol, bool poly, bool submult, int s,
-              const double* norms, Plan& p) {
+              const double* norms, Plan& p, int stride) {
     const int M = (int)a.size();
     const int upto = M > kNormest + 1 ? M : kNormest + 1;
-    p.z.assign((size_t)upto + 1, 0.0);
+    const int zlen = stride * upto;
+    std::vector<double>& zz = p.zz;  // Eq. (37) for Z itself
+    zz.assign((size_t)zlen + 1, 0.0);
     if (submult) {
-        p.z[0] = 1.0;
-        for (int i = 1; i <= upto; ++i) p.z[i] = std::pow(norms[1], (double)i);
+        zz[0] = 1.0;
+        for (int i = 1; i <= zlen; ++i) zz[(size_t)i] = std::pow(norms[1], (double)i);
         p.alpha10 = norms[1];
     } else {
         double alpha = 0.0;
@@ -62,8 +66,12 @@ int make_plan(const std::vector<double>& a, double tol, bool poly, bool submult,
             if (k == 5 || r > alpha) alpha = r;
         }
         p.alpha10 = alpha;
-        for (int i = 0; i <= upto; ++i) p.z[i] = i <= kNormest ? norms[i] : std::pow(alpha, (double)i);
+        for (int i = 0; i <= zlen; ++i) zz[(size_t)i] = i <= kNormest ? norms[i] : std::pow(alpha, (double)i);
     }
+    // the matrix whose powers the scheme forms: Z (stride 1) or W = Z^2
+    // (stride 2), whose ||W^i|| = ||Z^{2i}|| is bounded by z_{2i}
+    p.z.assign((size_t)upto + 1, 0.0);
+    for (int i = 0; i <= upto; ++i) p.z[(size_t)i] = zz[(size_t)(stride * i)];
 
     if (poly) {
         p.N = M;
@@ -125,6 +133,17 @@ int make_plan(const std::vector<double>& a, double tol, bool poly, bool submult,
         double den = z[(size_t)(q * (b - 1 - j))] * Mp;
         p.sigma[(size_t)j] = den != 0.0 ? p.budget / den : INFINITY;
     }
+    return 0;
+}
+
+int split_even_odd(const std::vector<double>& a, std::vector<double>& c, bool& odd) {
+    bool even_nz = false, odd_nz = false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (a[i] != 0.0) (i % 2 ? odd_nz : even_nz) = true;
+    if (even_nz && odd_nz) return 1;
+    odd = odd_nz;
+    c.clear();
+    for (size_t i = odd ? 1 : 0; i < a.size(); i += 2) c.push_back(a[i]);
     return 0;
 }
 

@@ -153,3 +153,67 @@ def test_estimate_flag_checked_on_the_host():
     with pytest.raises(psf.PsfError) as e:
         psf.Series(syn.coeffs("exp"), 1e-12, submult=True, estimate=True)
     assert e.value.code == _abi.PSF_EINVAL
+
+
+@pytest.mark.parametrize("kind", ["cos", "cosh", "sinh"])
+@pytest.mark.parametrize("tol", [1e-8, 1e-12, 1e-14])
+@pytest.mark.parametrize("mat", ["lap2d", "banded", "zero"])
+def test_host_planner_square_matches_oracle_bitwise(kind, tol, mat):
+    # PSF_Z_SQUARE: the plan of g in W = Z^2, with z_i of W = z_{2i} of Z and,
+    # for an odd series, the tolerance divided by ||Z||_1
+    if mat == "lap2d":
+        norms = power_norms(CSR(256, *syn.laplacian_2d(16)))
+    elif mat == "banded":
+        norms = power_norms(CSR(200, *syn.banded_random(200, 3, 5, 3.0)))
+    else:
+        norms = [1.0] + [0.0] * 10
+    a = syn.coeffs(kind)
+    c, odd = planner.split_even_odd(a)
+    tol_g = (tol / norms[1] if norms[1] != 0.0 else math.inf) if odd else tol
+    ref = planner.plan(c, tol_g, norms, stride=2)
+    got = psf.plan(a, tol, norms, square=True)
+    assert (got["N"], got["q"], got["b"], got["g"]) == (ref.N, ref.q, ref.b, ref.g)
+    assert got["products"] == planner.mult_count(ref.N) + 1 + int(odd)
+    assert got["trunc"] == ref.trunc and _same(got["budget"], ref.budget)
+    assert got["z"] == planner.z_sequence(norms, 11)[:11]
+    assert set(got["zeta"]) == set(ref.zeta) and set(got["sigma"]) == set(ref.sigma)
+    for k in ref.zeta:
+        assert _same(got["zeta"][k], ref.zeta[k]), k
+    for j in ref.sigma:
+        assert _same(got["sigma"][j], ref.sigma[j]), j
+
+
+@pytest.mark.parametrize("N", range(2, 30))
+def test_host_planner_square_poly_and_submult(N):
+    norms = [1.0] + [1.7 ** i for i in range(1, 11)]
+    for odd in (False, True):
+        a = [0.0] * N
+        for i in range(int(odd), N, 2):
+            a[i] = 1.0 / math.factorial(i)
+        if not any(a):
+            continue
+        c, o = planner.split_even_odd(a)
+        assert o == odd or not any(c)
+        for submult in (False, True):
+            tol_g = 1e-10 / norms[1] if o else 1e-10
+            ref = planner.plan(c, tol_g, norms, poly=True, submult=submult, stride=2)
+            got = psf.plan(a, 1e-10, norms, poly=True, submult=submult, square=True)
+            assert (got["N"], got["q"], got["b"], got["g"]) == (ref.N, ref.q, ref.b, ref.g)
+            assert got["budget"] == ref.budget
+            for k in ref.zeta:
+                assert _same(got["zeta"][k], ref.zeta[k])
+            for j in ref.sigma:
+                assert _same(got["sigma"][j], ref.sigma[j])
+
+
+def test_square_flag_needs_one_parity():
+    s = psf.Series(syn.coeffs("cos"), 1e-12, square=True)
+    assert s.flags & _abi.PSF_Z_SQUARE
+    psf.Series(syn.coeffs("sinh"), 1e-12, square=True, poly=True)
+    for bad in (syn.coeffs("exp"), [1.0, 1.0]):
+        with pytest.raises(psf.PsfError) as e:
+            psf.Series(bad, 1e-12, square=True)
+        assert e.value.code == _abi.PSF_EINVAL
+        with pytest.raises(psf.PsfError) as e:
+            psf.plan(bad, 1e-12, [1.0] + [2.0 ** i for i in range(1, 11)], square=True)
+        assert e.value.code == _abi.PSF_EINVAL

@@ -210,3 +210,10 @@ def test_batch_rejects_estimated_norms():
     with pytest.raises(psf.PsfError) as e:
         psf.eval_batch([psf.Series(syn.coeffs("exp"), 1e-12, estimate=True)], [Z])
     assert e.value.code == 1
+
+
+def test_batch_rejects_the_square_substitution():
+    Z = dev(ocsr(syn.laplacian_1d(50)))
+    with pytest.raises(psf.PsfError) as e:
+        psf.eval_batch([psf.Series(syn.coeffs("cos"), 1e-12, square=True)], [Z])
+    assert e.value.code == 1

@@ -333,3 +333,100 @@ def test_host_to_host_path_bitwise():
         np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
     assert list(rp0) == [0, 1, 2, 3, 4, 5] and list(col0) == [0, 1, 2, 3, 4] and list(val0) == [1.0] * 5
     assert info0["nnz"] == 5
+
+
+def square_cases():
+    return {
+        "lap2d": (ocsr(syn.laplacian_2d(40)), 1e-12),
+        "banded": (ocsr(syn.banded_random(3000, 5, 7, 2.0)), 1e-12),
+        # baby steps in W drop entries
+        "banded loose": (ocsr(syn.banded_random(3000, 5, 7, 4.0)), 1e-6),
+        "random sparse": (ocsr(syn.random_sparse(700, 0.01, 3, 1.5)), 1e-10),
+    }
+
+
+@pytest.mark.parametrize("kind", ["cos", "cosh", "sinh"])
+@pytest.mark.parametrize("mat", list(square_cases()))
+def test_square_mode_bitwise(kind, mat):
+    # PSF_Z_SQUARE: Algorithm 2 on W = Z Z; the second and third evaluations
+    # take W from the norm phase's pool (the same bits as a fresh product)
+    Z, tol = square_cases()[mat]
+    a = syn.coeffs(kind)
+    ref = psscf(Z, a, tol, square=True)
+    s = psf.Series(a, tol, square=True)
+    first = s.eval(dev(Z))
+    check_same(first, ref, f"{kind} {mat}")
+    assert first.info["products"] == ref.products
+    assert first.info["z"] == ref.norms[:11]
+    if kind == "sinh":
+        assert first.steps[-1]["kind"] == "odd"
+    for _ in range(2):
+        again = s.eval(dev(Z))
+        check_same(again, ref, f"{kind} {mat} again")
+        assert again.steps == first.steps
+
+
+@pytest.mark.parametrize("variant", ["unfiltered", "submult", "estimate", "s=2", "poly even", "poly odd"])
+def test_square_mode_variants_bitwise(variant):
+    Z = ocsr(syn.banded_random(1500, 4, 9, 2.5))
+    a, kw, opts = syn.coeffs("cosh"), {}, {}
+    if variant == "unfiltered":
+        kw = opts = {"filtered": False}
+    elif variant == "submult":
+        kw = opts = {"submult": True}
+    elif variant == "estimate":
+        from oracle import normest
+        a = syn.coeffs("sinh")
+        kw, opts = {"norms": normest.power_norm_estimates(Z)}, {"estimate": True}
+    elif variant == "s=2":
+        kw = opts = {"s": 2}
+    elif variant == "poly even":
+        a = [(-1.0) ** (i // 2) / math.factorial(i) if i % 2 == 0 else 0.0 for i in range(23)]
+        kw = opts = {"poly": True}
+    else:
+        a = [1.0 / math.factorial(i) if i % 2 else 0.0 for i in range(20)]
+        kw = opts = {"poly": True}
+    ref = psscf(Z, a, 1e-11, square=True, **kw)
+    got = psf.Series(a, 1e-11, square=True, **opts).eval(dev(Z))
+    check_same(got, ref, variant)
+    assert got.info["products"] == ref.products
+
+
+def test_square_mode_degenerate_cases():
+    cos, sinh = syn.coeffs("cos"), syn.coeffs("sinh")
+    # zero matrix: cos(0) = I, sinh(0) = 0 (g gets an infinite tolerance)
+    Z0 = CSR.empty(50)
+    for a in (cos, sinh):
+        got = psf.Series(a, 1e-12, square=True).eval(dev(Z0))
+        check_same(got, psscf(Z0, a, 1e-12, square=True), "zero")
+    # n = 1
+    Z1 = CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([-0.75]))
+    for a, fn in ((cos, math.cos), (sinh, math.sinh)):
+        got = psf.Series(a, 1e-12, square=True).eval(dev(Z1))
+        check_same(got, psscf(Z1, a, 1e-12, square=True), "n=1")
+        assert abs(got.csr.to_host()[2][0] - fn(-0.75)) <= 1e-12
+    # g truncated to c_0: F = Z (c_0 I), a copy of Z
+    Z = ocsr(syn.banded_random(60, 2, 4, 0.5))
+    got = psf.Series(sinh, 10.0, square=True).eval(dev(Z))
+    ref = psscf(Z, sinh, 10.0, square=True)
+    assert ref.plan.N == 1
+    check_same(got, ref, "N_W = 1")
+    assert_csr_bitwise(got.csr, Z, "copy of Z")
+    # a diagonal with empty rows, and a nilpotent shift (W = Z^2 is a shift by 2)
+    d = np.zeros((40, 40))
+    d[np.arange(0, 40, 3), np.arange(0, 40, 3)] = np.linspace(-2, 1, 14)
+    J = np.diag(np.full(25, 0.75), 1)
+    for M in (d, J):
+        for a in (cos, sinh):
+            got = psf.Series(a, 1e-14, square=True).eval(dev(CSR.from_dense(M)))
+            check_same(got, psscf(CSR.from_dense(M), a, 1e-14, square=True), "structured")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind", ["cos", "sinh"])
+def test_square_mode_lap2d_128x128_bitwise(kind):
+    Z = ocsr(syn.laplacian_2d(128))
+    ref = psscf(Z, syn.coeffs(kind), 1e-12, square=True)
+    s = psf.Series(syn.coeffs(kind), 1e-12, square=True)
+    for _ in range(2):
+        check_same(s.eval(dev(Z)), ref, kind)

@@ -105,3 +105,16 @@ def test_a_bad_request_fails_alone():
     for tag, Z in ((0, good[0]), (2, good[1]), (3, good[2])):
         assert done[tag]["status"] == 0
         assert_csr_bitwise(done[tag]["result"].csr, psscf(Z, syn.coeffs("exp"), 1e-12).F, f"request {tag}")
+
+
+def test_submit_rejects_estimate_and_square():
+    Z = dev(ocsr(syn.laplacian_1d(50)))
+    srv = psf.Server(workers=1, max_batch=4)
+    try:
+        for s in (psf.Series(syn.coeffs("exp"), 1e-12, estimate=True),
+                  psf.Series(syn.coeffs("cos"), 1e-12, square=True)):
+            with pytest.raises(psf.PsfError) as e:
+                srv.submit(s, Z, 7)
+            assert e.value.code == 1
+    finally:
+        srv.close()
