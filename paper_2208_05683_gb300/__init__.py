@@ -72,12 +72,41 @@ class DeviceCSR:
     def to_host(self):
         return (self.rowptr.cpu().numpy(), self.col.cpu().numpy(), self.val.cpu().numpy())
 
+    @staticmethod
+    def from_torch(t, device=None) -> "DeviceCSR":
+        """From a square torch sparse CSR tensor (any index and value dtype;
+        converted to int32 / float64 on ``device``, default the tensor's own
+        device).  Columns must be sorted within each row; the library checks."""
+        torch = _torch()
+        if t.layout != torch.sparse_csr:
+            raise PsfError(1, "expected a torch sparse CSR tensor (torch.sparse_csr layout)")
+        if t.dim() != 2 or t.shape[0] != t.shape[1]:
+            raise PsfError(1, f"expected a square matrix, got shape {tuple(t.shape)}")
+        dev = t.device if device is None else torch.device(device)
+        rp = t.crow_indices().to(device=dev, dtype=torch.int32).contiguous()
+        c = t.col_indices().to(device=dev, dtype=torch.int32).contiguous()
+        v = t.values().to(device=dev, dtype=torch.float64).contiguous()
+        return DeviceCSR(int(t.shape[0]), rp, c, v)
+
+    def to_torch(self):
+        """A torch sparse CSR tensor sharing this matrix's storage."""
+        torch = _torch()
+        return torch.sparse_csr_tensor(self.rowptr, self.col, self.val, size=(self.n, self.n),
+                                       check_invariants=False)
+
     def _struct(self) -> CSRStruct:
         for t in (self.rowptr, self.col, self.val):
             if not t.is_cuda or not t.is_contiguous():
                 raise PsfError(1, "DeviceCSR tensors must be contiguous CUDA tensors")
         return CSRStruct(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
                          self.val.data_ptr())
+
+
+def _as_device_csr(Z) -> "DeviceCSR":
+    """DeviceCSR as given, or converted from a torch sparse CSR tensor."""
+    if isinstance(Z, DeviceCSR):
+        return Z
+    return DeviceCSR.from_torch(Z)
 
 
 def _stream_ptr(stream):
@@ -177,13 +206,16 @@ class Series:
 
     def eval_handle(self, Z: DeviceCSR, stream=None):
         """psf_eval; returns the raw result handle (caller destroys it)."""
-        zs = Z._struct()
+        zs = _as_device_csr(Z)._struct()
         out = ctypes.c_void_p()
         check(lib().psf_eval(self._h, ctypes.byref(zs), _stream_ptr(stream), ctypes.byref(out)))
         return out
 
     def eval(self, Z: DeviceCSR, stream=None) -> Result:
+        """psf_eval on a DeviceCSR or a torch sparse CSR tensor on the GPU;
+        ``Result.csr.to_torch()`` gives the result as a torch sparse CSR tensor."""
         st = _stream_ptr(stream)
+        Z = _as_device_csr(Z)
         zs = Z._struct()
         out = ctypes.c_void_p()
         check(lib().psf_eval(self._h, ctypes.byref(zs), st, ctypes.byref(out)))
@@ -228,6 +260,7 @@ def eval_batch(series, Zs, stream=None):
     count = len(Zs)
     st = _stream_ptr(stream)
     sh = (ctypes.c_void_p * count)(*[s._h.value for s in series])
+    Zs = [_as_device_csr(z) for z in Zs]
     zs = (CSRStruct * count)(*[z._struct() for z in Zs])
     outs = (ctypes.c_void_p * count)()
     check(L.psf_eval_batch(sh, zs, count, st, outs))
@@ -248,6 +281,7 @@ class Server:
         self._keep = {}
 
     def submit(self, series: Series, Z: DeviceCSR, tag: int) -> None:
+        Z = _as_device_csr(Z)
         zs = Z._struct()
         check(lib().psf_server_submit(self._h, series._h, ctypes.byref(zs), ctypes.c_uint64(int(tag))))
         self._keep[int(tag)] = (series, Z)

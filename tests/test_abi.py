@@ -217,3 +217,23 @@ def test_square_flag_needs_one_parity():
         with pytest.raises(psf.PsfError) as e:
             psf.plan(bad, 1e-12, [1.0] + [2.0 ** i for i in range(1, 11)], square=True)
         assert e.value.code == _abi.PSF_EINVAL
+
+
+def test_torch_sparse_csr_round_trip_on_the_host():
+    # the binding's torch interop: a torch sparse CSR tensor in, the same
+    # arrays (int32 / float64) out, and back to a torch tensor
+    import torch
+    rp, col, val = syn.laplacian_2d(6)
+    t = torch.sparse_csr_tensor(torch.tensor(rp, dtype=torch.int64), torch.tensor(col, dtype=torch.int64),
+                                torch.tensor(val, dtype=torch.float32), size=(36, 36))
+    d = psf.DeviceCSR.from_torch(t)
+    assert d.n == 36 and d.rowptr.dtype == torch.int32 and d.val.dtype == torch.float64
+    assert np.array_equal(d.rowptr.numpy(), rp) and np.array_equal(d.col.numpy(), col)
+    assert np.array_equal(d.val.numpy(), np.asarray(val, np.float32).astype(np.float64))
+    back = d.to_torch()
+    assert back.layout == torch.sparse_csr and tuple(back.shape) == (36, 36)
+    assert torch.equal(back.to_dense(), t.to_dense().double())
+    with pytest.raises(psf.PsfError):
+        psf.DeviceCSR.from_torch(torch.zeros(3, 3))
+    with pytest.raises(psf.PsfError):
+        psf.DeviceCSR.from_torch(torch.zeros(3, 4).to_sparse_csr())

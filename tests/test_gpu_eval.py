@@ -430,3 +430,18 @@ def test_square_mode_lap2d_128x128_bitwise(kind):
     s = psf.Series(syn.coeffs(kind), 1e-12, square=True)
     for _ in range(2):
         check_same(s.eval(dev(Z)), ref, kind)
+
+
+def test_torch_sparse_csr_in_and_out():
+    # the binding takes a torch sparse CSR tensor on the GPU (int64 indices
+    # here) and returns one
+    import torch
+    rp, col, val = syn.laplacian_2d(24)
+    t = torch.sparse_csr_tensor(torch.tensor(rp, dtype=torch.int64), torch.tensor(col, dtype=torch.int64),
+                                torch.tensor(val), size=(576, 576)).to("cuda")
+    got = psf.Series(syn.coeffs("exp"), 1e-12).eval(t)
+    ref = psscf(ocsr((rp, col, val)), syn.coeffs("exp"), 1e-12)
+    check_same(got, ref, "torch in")
+    F = got.csr.to_torch()
+    assert F.layout == torch.sparse_csr and F.is_cuda
+    assert np.array_equal(F.to_dense().cpu().numpy(), ref.F.to_dense())
