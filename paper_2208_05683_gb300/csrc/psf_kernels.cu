@@ -162,7 +162,11 @@ __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<true>& S)
 }
 
 // ---- symbolic pass, bitmap map: lane l walks a contiguous slice of the row
-// and ORs whole runs of columns into a bitmap word at a time
+// and ORs whole runs of columns into a bitmap word at a time.  CHK: test
+// each column against [c0, cend); a B row needs no test, since
+// load_segment has already clipped it to that range (or, for a row that
+// takes one chunk, the range spans every B column of the row).
+template <bool CHK>
 __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int e, int c0, int cend, int lane,
                                          ProdSmem<false>& S) {
     const int m = (e - s + 31) >> 5;
@@ -175,7 +179,7 @@ __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int c = cs[u];
-            if (c < c0 || c >= cend) continue;
+            if (CHK ? (c < c0 || c >= cend) : (q + u >= q1)) continue;
             unsigned off = (unsigned)(c - c0), w = off >> 5;
             if (w != curw) {
                 if (mask) atomicOr(&S.pm[curw].y, mask);
@@ -189,7 +193,7 @@ __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int
 }
 // Short B rows (at most 32 entries each): lane i marks the segment's B row i,
 // so the rows' column loads are in flight together instead of one row after
-// the other.
+// the other.  The rows are clipped to [c0, cend) (see mark_row).
 __device__ __forceinline__ void mark_rows_short(const int* __restrict__ col, int cnt, int c0, int cend, int lane,
                                                 ProdSmem<false>& S) {
     if (lane >= cnt) return;
@@ -203,7 +207,7 @@ __device__ __forceinline__ void mark_rows_short(const int* __restrict__ col, int
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int c = cs[u];
-            if (c < c0 || c >= cend) continue;
+            if (q + u >= e) continue;
             const unsigned off = (unsigned)(c - c0), w = off >> 5;
             if (w != curw) {
                 if (mask) atomicOr(&S.pm[curw].y, mask);
@@ -234,7 +238,8 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
         if (!T.rb) {
             if (lane == 0 && r >= c0 && r < cend) mark_one(r - c0, S);
         } else {
-            mark_row(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
+            if constexpr (TAB) mark_row(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
+            else mark_row<true>(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
         }
     }
     for (int seg = pa0; seg < pa1; seg += 32) {
@@ -247,7 +252,10 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
                 continue;
             }
         }
-        for (int i = 0; i < cnt; ++i) mark_row(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+        for (int i = 0; i < cnt; ++i) {
+            if constexpr (TAB) mark_row(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+            else mark_row<false>(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+        }
         __syncwarp();
     }
     __syncwarp();
