@@ -73,8 +73,8 @@ extern "C" {
  * Z, or the PSF_Z_SUBMULT / PSF_Z_ESTIMATE variants).  The plan fields N, q,
  * b, g, trunc, budget and the thresholds are those of g in W; z[] and
  * alpha10 stay those of Z.  psf_series_create fails with PSF_EINVAL when
- * both parities have nonzero coefficients.  psf_eval only
- * (psf_eval_batch and psf_server_submit reject it). */
+ * both parities have nonzero coefficients.  psf_eval, psf_eval_batch and
+ * the server accept it; their results are bitwise the same. */
 #define PSF_Z_SQUARE 16u
 
 /* ---- tunable parameters (psf_series_set_param) ---- */

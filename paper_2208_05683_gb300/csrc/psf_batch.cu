@@ -40,6 +40,8 @@ constexpr size_t kRowsZq = 61;       // composite Z-hat_(q_i)
 constexpr size_t kRowsBaby = 0;      // + k: baby step k (k = 2..23)
 constexpr size_t kRowsS = 30;        // + (stage & 1): giant-step outputs
 constexpr size_t kRowsPow = 40;      // + k - 2: the norm phase's Z^k (k = 2..10)
+constexpr size_t kRowsW = 62;        // W = Z Z of the PSF_Z_SQUARE instances
+constexpr size_t kRowsLeft = 63;     // composite left factor of the baby steps: Z, or W
 constexpr int kMaxBatchRows = 1 << 24;  // column-sum words: 704 B per row
 
 // Device storage shared by the results of one batch.
@@ -65,13 +67,19 @@ void raise_to(std::atomic<double>& a, double v) {
 }
 
 struct InstPlan {
-    bool trivial = false;  // N = 1 (f = a_0 I) or n = 0
+    bool trivial = false;  // N = 1 (f = a_0 I, not an odd series) or n = 0
+    bool sq = false;       // PSF_Z_SQUARE: the scheme runs on W = Z Z
+    bool odd = false;      // ... and ends with F = Z G-hat
     Plan p;
     std::vector<double> znnz;  // nnz(Z^k), k = 0..10 (0 where not computed)
 };
 
+// the coefficients the scheme runs on: a, or g's c_k with PSF_Z_SQUARE
+const std::vector<double>& coeffs_of(const psf_series_s* s) { return (s->flags & PSF_Z_SQUARE) ? s->c : s->a; }
+
 double coef_of(const psf_series_s* s, const Plan& p, int idx) {
-    return (idx < p.N && idx < (int)s->a.size()) ? s->a[(size_t)idx] : 0.0;
+    const std::vector<double>& a = coeffs_of(s);
+    return (idx < p.N && idx < (int)a.size()) ? a[(size_t)idx] : 0.0;
 }
 
 // Host tables of one stage: what every instance does, and the coefficients
@@ -299,11 +307,16 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 std::memcpy(&norms[k], &bits, sizeof bits);
             }
             const bool submult = S->flags & PSF_Z_SUBMULT;
-            if (make_plan(S->a, S->tol, S->flags & PSF_POLY, submult, S->s, norms, P.p))
+            P.sq = S->flags & PSF_Z_SQUARE;
+            P.odd = P.sq && S->odd;
+            // an odd series: ||f(Z) - Z G-hat||_1 <= ||Z||_1 ||g(W) - G-hat||_1 (IEEE: 1/0 = inf)
+            const double tol_g = P.odd ? S->tol / norms[1] : S->tol;
+            if (make_plan(coeffs_of(S), tol_g, S->flags & PSF_POLY, submult, S->s, norms, P.p, P.sq ? 2 : 1))
                 return fail(PSF_ENOTCONV, "batch instance %d: no truncation length within %zu coefficients (Eq. 34)", i,
-                            S->a.size());
+                            coeffs_of(S).size());
             if (P.p.q > PSF_MAX_Q) return fail(PSF_ETOOBIG, "batch instance %d: q = %d exceeds %d", i, P.p.q, PSF_MAX_Q);
-            P.trivial = P.p.N == 1 || Zs[i].n == 0;
+            // an odd series with N = 1 still forms F = Z (c_0 I)
+            P.trivial = (P.p.N == 1 && !P.odd) || Zs[i].n == 0;
             P.znnz.assign(11, 0.0);
             P.znnz[1] = (double)Zs[i].nnz;
             for (int k = 2; k <= 10; ++k) {
@@ -318,7 +331,8 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
     // an instance has dropped no entry, its baby step k is its Z^k
     bool keep_powers = false;
     for (int i = 0; i < count && g_batch_reuse.load(); ++i)
-        if (chain[(size_t)i] && !ip[(size_t)i].trivial && ip[(size_t)i].p.q >= 2) keep_powers = true;
+        if (chain[(size_t)i] && !ip[(size_t)i].trivial && ip[(size_t)i].p.q >= 2 && !ip[(size_t)i].sq)
+            keep_powers = true;
     DevBuf zk_col, zk_val;  // that pool; the PS phase gets a new one
     if (keep_powers) {
         std::swap(zk_col.p, w.pool_col.p);
@@ -338,22 +352,33 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
     const int tz = qmax;          // term index of Z-hat_(q_i)
     const int nadd = qmax + 1;    // addend terms of S_0 and giant stages
     if (nadd > kMaxAdd) return fail(PSF_ETOOBIG, "q = %d exceeds %d", qmax, kMaxAdd - 1);
-    // stage list: baby k = 2..qmax, S_0, giant j = 1..bmax-1
+    // stage list: [W = Z Z], baby k = 2..qmax, S_0, giant j = 1..bmax-1, [F = Z G-hat]
+    bool any_sq = false, any_odd = false;
+    for (int i = 0; i < count; ++i) {
+        any_sq = any_sq || (ip[(size_t)i].sq && !ip[(size_t)i].trivial);
+        any_odd = any_odd || (ip[(size_t)i].odd && !ip[(size_t)i].trivial);
+    }
     struct StageDesc {
-        int kind;   // 0 baby, 2 S_0, 1 giant
+        int kind;   // 0 baby, 2 S_0, 1 giant, 3 W = Z Z, 4 F = Z G-hat (PSF_Z_SQUARE)
         int index;  // k or j
     };
     std::vector<StageDesc> stages;
+    if (any_sq) stages.push_back({3, 0});
     for (int k = 2; k <= qmax; ++k) stages.push_back({0, k});
     stages.push_back({2, 0});
     for (int j = 1; j < bmax; ++j) stages.push_back({1, j});
+    if (any_odd) stages.push_back({4, 1});
+    auto slot_of = [&](size_t si) {
+        const int k = stages[si].kind;
+        return k == 0 ? kRowsBaby + (size_t)stages[si].index : (k == 3 ? kRowsW : kRowsS + (si & 1));
+    };
     const size_t nst = stages.size();
     std::vector<StageTab> tabs(nst);
     for (size_t si = 0; si < nst; ++si) {
         StageTab& T = tabs[si];
         const StageDesc& D = stages[si];
         T.step.resize((size_t)count);
-        T.nadd = D.kind == 0 ? 0 : nadd;
+        T.nadd = (D.kind == 1 || D.kind == 2) ? nadd : 0;  // products alone: baby steps, W, Z G-hat
         T.alpha.assign((size_t)T.nadd * count, 0.0);
         for (int i = 0; i < count; ++i) {
             const psf_series_s* S = series[i];
@@ -374,31 +399,50 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             if (P.trivial) {
                 if (D.kind == 2) {
                     B = step_of(kBatchAddOnly, 0.0, 0.0, 1);
-                    set_alpha(0, S->a[0]);
-                } else if (D.kind == 1) {
+                    set_alpha(0, coeffs_of(S)[0]);
+                } else if (D.kind == 1 || D.kind == 4) {
                     B = step_of(kBatchPass, 0.0, 0.0, 1);
                 }
                 continue;
             }
-            if (D.kind == 0) {
+            if (D.kind == 3) {
+                // W = Z Z, unfiltered (other instances leave the rows empty)
+                if (P.sq) {
+                    B = step_of(kBatchProduct, 0.0, 0.0, 1);
+                    T.work_rows += ni;
+                    T.work_fma += ni * zl * zl;
+                }
+            } else if (D.kind == 4) {
+                // F = Z G-hat of an odd series, unfiltered; the others pass through
+                if (P.odd) {
+                    B = step_of(kBatchProduct, 0.0, 0.0, 1);
+                    T.work_rows += ni;
+                    T.work_fma += ni * zl * (P.znnz[10] > 0.0 ? P.znnz[10] / ni : zl * 100.0);
+                } else {
+                    B = step_of(kBatchPass, 0.0, 0.0, 1);
+                }
+            } else if (D.kind == 0) {
                 if (D.index <= p.q) {
                     const double thr = nofilter ? 0.0 : p.zeta[(size_t)D.index];
                     B = step_of(kBatchProduct, thr, S->e_r, S->maxit);
-                    if (keep_powers && chain[(size_t)i] && D.index <= 10) {
+                    if (keep_powers && chain[(size_t)i] && D.index <= 10 && !P.sq) {
                         B.reuse = 1;
                         T.any_reuse = true;
                         T.reuse_rows += ni;
                         T.reuse_nnz += P.znnz[(size_t)D.index];
                     }
-                    const double bl = P.znnz[(size_t)(D.index - 1)] > 0.0 ? P.znnz[(size_t)(D.index - 1)] / ni
-                                                                          : zl * (D.index - 1) * (D.index - 1);
+                    // the power of the left factor (Z, or W = Z^2) the step multiplies
+                    const int e = (P.sq ? 2 : 1) * (D.index - 1);
+                    const double bl = e <= 10 && P.znnz[(size_t)e] > 0.0 ? P.znnz[(size_t)e] / ni : zl * e * e;
+                    const double al = P.sq && P.znnz[2] > 0.0 ? P.znnz[2] / ni : zl;
                     T.work_rows += ni;
-                    T.work_fma += ni * zl * bl;
+                    T.work_fma += ni * al * bl;
                 }
             } else if (D.kind == 2) {
                 if (p.g == 0) {
                     B = step_of(kBatchAddOnly, 0.0, 0.0, 1);
                     block(p.b - 1);
+                    if (p.q == 0) set_alpha(0, coef_of(S, p, 0));  // N = 1 of an odd series: c_0 I
                 }
             } else {
                 const int j = D.index;
@@ -461,6 +505,14 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
     for (int i = 0; i < count; ++i) sel[(size_t)i] = ip[(size_t)i].trivial ? 1 : ip[(size_t)i].p.q;
     CU(d_sel.alloc(sizeof(int) * (size_t)count, st));
     CU(cudaMemcpyAsync(d_sel.p, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice, st));
+    // the baby steps' left factor per instance: 0 for Z, 1 for W (PSF_Z_SQUARE)
+    DevBuf d_lsel;
+    if (any_sq) {
+        std::vector<int> lsel((size_t)count);
+        for (int i = 0; i < count; ++i) lsel[(size_t)i] = ip[(size_t)i].sq ? 1 : 0;
+        CU(d_lsel.alloc(sizeof(int) * (size_t)count, st));
+        CU(cudaMemcpyAsync(d_lsel.p, lsel.data(), sizeof(int) * lsel.size(), cudaMemcpyHostToDevice, st));
+    }
 
     // ---- PS phase in one pool
     unsigned long long cap = (unsigned long long)(g_ps_per_row.load() * 1.25 * n) + 4096ull;
@@ -485,9 +537,10 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         // (a captured graph must not allocate)
         for (size_t si = 0; si < nst; ++si) {
             int *rb0, *re0;
-            const size_t slot = stages[si].kind == 0 ? kRowsBaby + (size_t)stages[si].index : kRowsS + (si & 1);
-            if ((rc = w.rows_for(slot, &rb0, &re0))) return rc;
+            if ((rc = w.rows_for(slot_of(si), &rb0, &re0))) return rc;
         }
+        int *lrb = nullptr, *lre = nullptr;
+        if (any_sq && (rc = w.rows_for(kRowsLeft, &lrb, &lre))) return rc;
         // the whole PS phase: pool copy of Z, every stage, the row-length scan
         auto enqueue = [&](cudaStream_t st) -> int {
         CU(cudaMemsetAsync(d_stat.p, 0, sizeof(StepStat) * nst * (size_t)count, st));
@@ -497,12 +550,13 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         const RowView zp = w.pooled(zrb, zre);
         std::vector<RowView> baby((size_t)qmax + 1);
         baby[1] = zp;
+        RowView left = zp;  // the baby steps' left factor (Z, or W per instance)
         RowView S{};
         bool zq_done = false;
         for (size_t si = 0; si < nst; ++si) {
             const StageDesc& D = stages[si];
             const StageTab& T = tabs[si];
-            if (D.kind != 0 && !zq_done) {
+            if ((D.kind == 1 || D.kind == 2) && !zq_done) {
                 // Z-hat_(q_i) of every instance, for the giant steps and the g = 1 step
                 const int* rbs[kMaxAdd + 2];
                 const int* res[kMaxAdd + 2];
@@ -514,17 +568,19 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 zq_done = true;
             }
             int *rb, *re;
-            const size_t slot = D.kind == 0 ? kRowsBaby + (size_t)D.index : kRowsS + (si & 1);
-            if ((rc = w.rows_for(slot, &rb, &re))) return rc;
+            if ((rc = w.rows_for(slot_of(si), &rb, &re))) return rc;
             ProductArgs P{};
             P.n = n;
             const RowView zq = w.pooled(qrb, qre);
             if (D.kind == 0) {
-                P.A = zp;
+                P.A = left;
                 P.B = baby[(size_t)D.index - 1];
-            } else if (D.kind == 1) {
-                P.A = zq;
+            } else if (D.kind == 1 || D.kind == 4) {
+                P.A = D.kind == 1 ? zq : zp;  // Z-hat_(q_i) S-hat, or Z G-hat
                 P.B = S;  // also the source of pass-through rows
+            } else if (D.kind == 3) {
+                P.A = zp;
+                P.B = zp;
             }
             P.nadd = T.nadd;
             for (int t = 0; t < T.nadd; ++t) {
@@ -606,8 +662,18 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 CU(launch_alg1_batch(a, st));
             }
             const RowView out = w.pooled(rb, re);
-            if (D.kind == 0) baby[(size_t)D.index] = out;
-            else S = out;
+            if (D.kind == 0) {
+                baby[(size_t)D.index] = out;
+            } else if (D.kind == 3) {
+                // each instance's left factor and Z-hat_(1): Z, or its W
+                const int* rbs[2] = {zp.rb, out.rb};
+                const int* res[2] = {zp.re, out.re};
+                CU(launch_compose_rows(n, inst, d_lsel.as<int>(), rbs, res, 2, lrb, lre, st));
+                left = w.pooled(lrb, lre);
+                baby[1] = left;
+            } else {
+                S = out;
+            }
         }
         F = S;
         CU(launch_scan_rows(n, F.rb, F.re, d_rowptr.as<int>(), w.C(), w.scan.as<long long>(), st));
@@ -696,8 +762,12 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 const BatchStep& B = tabs[si].step[(size_t)i];
                 if (B.mode != kBatchProduct && B.mode != kBatchAddOnly) continue;
                 const StepStat& ss = pst[si * (size_t)count + (size_t)i];
+                if (D.kind == 3) {  // W = Z Z: counted, not a step record (as in psf_eval)
+                    fma += ss.fma;
+                    continue;
+                }
                 psf_step_info_t s{};
-                s.kind = B.mode == kBatchAddOnly ? 2 : (D.kind == 0 ? 0 : 1);
+                s.kind = B.mode == kBatchAddOnly ? 2 : (D.kind == 0 ? 0 : (D.kind == 4 ? 3 : 1));
                 s.index = D.index;
                 const bool filt = B.eps_g > 0.0;
                 s.threshold = filt ? (S->flags & PSF_NOFILTER ? 0.0
@@ -719,9 +789,9 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         inf.q = p.q;
         inf.b = p.b;
         inf.g = p.g;
-        inf.products = P.trivial ? 0 : p.products;
+        inf.products = p.products + (P.sq ? 1 + (int)P.odd : 0);
         inf.nsteps = (int32_t)r->steps.size();
-        for (int k = 0; k <= 10; ++k) inf.z[k] = k < (int)p.z.size() ? p.z[(size_t)k] : 0.0;
+        for (int k = 0; k <= 10; ++k) inf.z[k] = k < (int)p.zz.size() ? p.zz[(size_t)k] : 0.0;
         inf.alpha10 = p.alpha10;
         inf.trunc = p.trunc;
         inf.budget = p.budget;
@@ -743,8 +813,8 @@ extern "C" int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, i
     if (count == 0) return PSF_OK;
     for (int i = 0; i < count; ++i) {
         if (!series[i]) return fail(PSF_EINVAL, "batch instance %d: null series", i);
-        if (series[i]->flags & (PSF_Z_ESTIMATE | PSF_Z_SQUARE))
-            return fail(PSF_EINVAL, "batch instance %d: PSF_Z_ESTIMATE and PSF_Z_SQUARE are for psf_eval only", i);
+        if (series[i]->flags & PSF_Z_ESTIMATE)
+            return fail(PSF_EINVAL, "batch instance %d: PSF_Z_ESTIMATE is for psf_eval only", i);
         int rc = check_csr(&Zs[i], Zs[i].n, "Z");
         if (rc) return rc;
         if (Zs[i].n == 0 && Zs[i].nnz != 0) return fail(PSF_EINVAL, "batch instance %d: n = 0 with entries", i);

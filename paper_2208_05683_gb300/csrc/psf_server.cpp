@@ -193,8 +193,7 @@ int psf_server_create(const psf_server_config_t* config, psf_server_t* out) {
 
 int psf_server_submit(psf_server_t s, psf_series_t series, const psf_csr_t* Z, uint64_t tag) {
     if (!s || !series || !Z) return fail(PSF_EINVAL, "null argument");
-    if (series->flags & (PSF_Z_ESTIMATE | PSF_Z_SQUARE))
-        return fail(PSF_EINVAL, "PSF_Z_ESTIMATE and PSF_Z_SQUARE are for psf_eval only");
+    if (series->flags & PSF_Z_ESTIMATE) return fail(PSF_EINVAL, "PSF_Z_ESTIMATE is for psf_eval only");
     int rc = check_csr(Z, Z->n, "Z");
     if (rc) return rc;
     Request r{series, *Z, tag, Clock::now(), predict_bytes(*Z)};

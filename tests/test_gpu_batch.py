@@ -17,11 +17,12 @@ from oracle import CSR, psscf
 pytestmark = pytest.mark.gpu
 
 psf = pytest.importorskip("paper_2208_05683_gb300")
+_abi = psf._abi
 
 
 def series_of(a, tol, **kw):
     return psf.Series(a, tol, poly=kw.get("poly", False), filtered=kw.get("filtered", True),
-                      submult=kw.get("submult", False), s=kw.get("s", 0))
+                      submult=kw.get("submult", False), s=kw.get("s", 0), square=kw.get("square", False))
 
 
 def mixed_cases():
@@ -212,8 +213,44 @@ def test_batch_rejects_estimated_norms():
     assert e.value.code == 1
 
 
-def test_batch_rejects_the_square_substitution():
-    Z = dev(ocsr(syn.laplacian_1d(50)))
-    with pytest.raises(psf.PsfError) as e:
-        psf.eval_batch([psf.Series(syn.coeffs("cos"), 1e-12, square=True)], [Z])
-    assert e.value.code == 1
+def square_cases():
+    """Instances with the W = Z^2 substitution (PSF_Z_SQUARE)."""
+    cos, cosh, sinh = syn.coeffs("cos"), syn.coeffs("cosh"), syn.coeffs("sinh")
+    odd_poly = [1.0 / math.factorial(i) if i % 2 else 0.0 for i in range(20)]
+    return [
+        ("sq lap2d cos", ocsr(syn.laplacian_2d(24)), cos, 1e-12, {}),
+        ("sq banded sinh", ocsr(syn.banded_random(700, 6, 3, 2.0)), sinh, 1e-10, {}),
+        # baby steps in W drop entries
+        ("sq banded loose cosh", ocsr(syn.banded_random(900, 5, 7, 4.0)), cosh, 1e-6, {}),
+        # g truncated to c_0: F = Z (c_0 I)
+        ("sq sinh N_W=1", ocsr(syn.banded_random(60, 2, 4, 0.5)), sinh, 10.0, {}),
+        ("sq zero sinh", CSR.empty(30), sinh, 1e-12, {}),
+        ("sq zero cos", CSR.empty(12), cos, 1e-12, {}),
+        ("sq n=1 sinh", CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([-0.75])), sinh,
+         1e-12, {}),
+        ("sq s=2 cos", ocsr(syn.laplacian_2d(20)), cos, 1e-12, {"s": 2}),
+        ("sq poly odd", ocsr(syn.banded_random(500, 2, 5, 1.5)), odd_poly, 1e-11, {"poly": True}),
+        ("sq unfiltered", ocsr(syn.laplacian_1d(128)), cosh, 1e-12, {"filtered": False}),
+        ("sq submult", ocsr(syn.laplacian_1d(300)), sinh, 1e-12, {"submult": True}),
+    ]
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_square_instances_in_a_mixed_batch(graph):
+    # square instances (even, odd, trivial, empty) batched with plain ones:
+    # each result is the oracle's and the single evaluation's, bit for bit
+    cases = [(n, Z, a, tol, dict(kw, square=True)) for n, Z, a, tol, kw in square_cases()] + mixed_cases()[:7]
+    series = [series_of(a, tol, **kw) for _, _, a, tol, kw in cases]
+    old = psf.tune_get(_abi.PSF_TUNE_BATCH_GRAPH)
+    psf.tune_set(_abi.PSF_TUNE_BATCH_GRAPH, graph)
+    try:
+        got = psf.eval_batch(series, [dev(Z) for _, Z, _, _, _ in cases])
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_BATCH_GRAPH, old)
+    for (name, Z, a, tol, kw), g in zip(cases, got):
+        ref = psscf(Z, a, tol, **kw)
+        check_same(g, ref, name)
+        alone = series_of(a, tol, **kw).eval(dev(Z))
+        assert alone.steps == g.steps, name
+        for key in ("N", "q", "b", "g", "products", "z", "trunc", "budget", "nnz"):
+            assert alone.info[key] == g.info[key], (name, key)

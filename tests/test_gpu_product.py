@@ -127,10 +127,23 @@ def test_malformed_input_is_rejected():
     bad_order = (np.array([0, 2, 2, 2, 2, 2], np.int32), np.array([3, 1], np.int32), np.array([1.0, 2.0]))
     bad_range = (np.array([0, 1, 1, 1, 1, 1], np.int32), np.array([7], np.int32), np.array([1.0]))
     bad_val = (np.array([0, 1, 1, 1, 1, 1], np.int32), np.array([0], np.int32), np.array([np.nan]))
-    for bad in (bad_order, bad_range, bad_val):
+    # every case below is caught by the validation pass before any kernel
+    # indexes with the input: row pointers first, then the row's columns
+    i32 = lambda *x: np.array(x, np.int32)
+    bad_dup = (i32(0, 2, 2, 2, 2, 2), i32(1, 1), np.array([1.0, 2.0]))          # repeated column
+    bad_neg = (i32(0, 1, 1, 1, 1, 1), i32(-1), np.array([1.0]))                # negative column
+    bad_inf = (i32(0, 1, 1, 1, 1, 1), i32(0), np.array([np.inf]))              # non-finite value
+    bad_dec = (i32(0, 2, 1, 2, 2, 2), i32(0, 1), np.array([1.0, 2.0]))         # decreasing row pointers
+    bad_first = (i32(1, 1, 1, 1, 1, 1), i32(0), np.array([1.0]))               # rowptr[0] != 0
+    bad_last = (i32(0, 1, 1, 1, 1, 0), i32(0), np.array([1.0]))                # rowptr[n] != nnz
+    cases = (bad_order, bad_range, bad_val, bad_dup, bad_neg, bad_inf, bad_dec, bad_first, bad_last)
+    for i, bad in enumerate(cases):
         with pytest.raises(psf.PsfError) as e:
             psf.product_filter(dev(bad), dev(good), [], 0.0)
-        assert e.value.code == 1
+        assert e.value.code == 1, i
         with pytest.raises(psf.PsfError) as e:
             psf.Series(syn.coeffs("exp"), 1e-12).eval(dev(bad))
-        assert e.value.code == 1
+        assert e.value.code == 1, i
+        with pytest.raises(psf.PsfError) as e:
+            psf.Series(syn.coeffs("exp"), 1e-12).eval_host(*bad)
+        assert e.value.code == 1, i

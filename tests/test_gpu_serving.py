@@ -107,14 +107,37 @@ def test_a_bad_request_fails_alone():
         assert_csr_bitwise(done[tag]["result"].csr, psscf(Z, syn.coeffs("exp"), 1e-12).F, f"request {tag}")
 
 
-def test_submit_rejects_estimate_and_square():
+def test_submit_rejects_estimated_norms():
     Z = dev(ocsr(syn.laplacian_1d(50)))
     srv = psf.Server(workers=1, max_batch=4)
     try:
-        for s in (psf.Series(syn.coeffs("exp"), 1e-12, estimate=True),
-                  psf.Series(syn.coeffs("cos"), 1e-12, square=True)):
-            with pytest.raises(psf.PsfError) as e:
-                srv.submit(s, Z, 7)
-            assert e.value.code == 1
+        with pytest.raises(psf.PsfError) as e:
+            srv.submit(psf.Series(syn.coeffs("exp"), 1e-12, estimate=True), Z, 7)
+        assert e.value.code == 1
     finally:
         srv.close()
+
+
+def test_square_requests_in_the_mix():
+    # requests with the W = Z^2 substitution batched with plain ones: each
+    # result is the one it gets alone
+    reqs = syn.serving_requests(24, seed0=300, n_lo=64, n_hi=2048)
+    series = []
+    for i, (_, kind, tol) in enumerate(reqs):
+        sq = kind in ("cos", "sinh") and i % 2 == 0
+        series.append(psf.Series(syn.coeffs(kind), tol, square=sq))
+    assert any(s.flags & 16 for s in series)
+    Zs = [dev(Z) for Z, _, _ in reqs]
+    srv = psf.Server(workers=2, max_batch=8)
+    try:
+        for i in range(len(reqs)):
+            srv.submit(series[i], Zs[i], i)
+        done = drain(srv, len(reqs))
+    finally:
+        srv.close()
+    for i in range(len(reqs)):
+        c = done[i]
+        assert c["status"] == 0, i
+        alone = series[i].eval(Zs[i])
+        same_csr(c["result"].csr, alone.csr, f"request {i}")
+        assert c["result"].steps == alone.steps
