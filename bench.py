@@ -37,6 +37,14 @@ TOL = 1e-12
 # FP64 peak of the GB300 FP64 pipe: 152 SMs x 2 FMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_product_traffic.json")
+
+
+def hbm_peak_gbs() -> float:
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json, when present), else 6800 GB/s."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2208_05683_gb300", "csrc", f)
                   for f in ("psf_kernels.cu", "psf_device.cuh")]
 
@@ -269,8 +277,11 @@ def run_psf(args):
             traffic = prof.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
+    # DRAM rate of the product kernel: ncu bytes per launch x launches / event-timed duration
+    dram_gbs = traffic * nl.value / (ms.value / 1e3) / 1e9 if traffic and ms.value > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_product",
+                "dram_gbs": dram_gbs, "dram_frac_of_hbm": dram_gbs / hbm_peak_gbs() if dram_gbs else None,
                 "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "launches_timed": nl.value, "kernel_ms": ms.value, "algorithmic_fma": fma.value}
 
