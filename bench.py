@@ -84,15 +84,16 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
-        self.rows = []
+        self.rows = []  # (host time of the sample, fields)
         self.proc = None
         self.thread = None
+        self.window = None  # (t0, t1): the timed region
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
@@ -103,7 +104,11 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.perf_counter(), parts))
+
+    def mark(self, t0: float, t1: float):
+        """The timed region, in time.perf_counter() seconds."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is not None:
@@ -116,8 +121,15 @@ class ClockSampler:
             self.thread.join(timeout=5)
 
     def summary(self):
-        if not self.rows:
+        rows = [r for t, r in self.rows]
+        if self.window is not None:
+            # samples taken while the timed region ran (a sample arrives up to
+            # one period after it was taken)
+            t0, t1 = self.window
+            rows = [r for t, r in self.rows if t0 <= t <= t1 + 0.05]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        self_rows = rows
 
         def num(x):
             try:
@@ -125,12 +137,12 @@ class ClockSampler:
             except ValueError:
                 return None
 
-        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
-        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        sm = [num(r[1]) for r in self_rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self_rows if num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in self_rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self_rows)}
 
 
 def make_inputs():
@@ -240,20 +252,24 @@ def run_psf(args):
         c, saved = psf.autotune(series[KINDS[0]], Z)
         tuned = {"table_crossover": c if c < 1e299 else "never", "saved_ms_per_eval": saved}
 
+    # clocks sampled from before the warm-up (nvidia-smi takes a moment to
+    # start); only the samples taken during the timed region are kept
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         one_step()
 
     # ---- timed region: K steps, L2 flushed before each
     cnt0 = ctypes_i64(L.psf_launch_count)
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier()
+    t_region = time.perf_counter()
     lat = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         one_step(lat)
     barrier()
+    clocks.mark(t_region, time.perf_counter())
     clocks.stop()
     launches = ctypes_i64(L.psf_launch_count) - cnt0
     evals = args.steps * len(KINDS)
@@ -761,7 +777,7 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "table", "bitmap"], default="auto",
                     help="slot map of the product kernel (auto: by products per row)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)  # 20 evaluations: p50/p99 over >= 20
+    ap.add_argument("--steps", type=int, default=40)  # 80 evaluations: p50/p99 over >= 20, clocks sampled
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["psf", "reference"], default="psf")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense FP64 PS baseline")
