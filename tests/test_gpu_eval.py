@@ -445,3 +445,48 @@ def test_torch_sparse_csr_in_and_out():
     F = got.csr.to_torch()
     assert F.layout == torch.sparse_csr and F.is_cuda
     assert np.array_equal(F.to_dense().cpu().numpy(), ref.F.to_dense())
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("nb", [1 << 22, 1 << 23])
+def test_lap1d_4m_rows_are_the_small_oracle_rows_shifted(nb):
+    # Z = -0.5 tridiag(-1, 2, -1) is Toeplitz.  Each row of a product of its
+    # powers depends only on the row's distance to the ends, so every row of
+    # the result more than N from both ends is a shift of one interior row,
+    # and the rows near the ends are those of any size >= 2N.  The norms
+    # ||Z^i||_1 = 2^i, the plan and Algorithm 1's column-sum maxima are the
+    # same for n = 256 and n = 2^22, so the large result must equal the
+    # oracle's n = 256 result row by row (shifted), bit for bit: rows, pool
+    # and column sums at 4.2 M and 8.4 M rows checked without running the
+    # oracle there.  At 8.4 M rows the PS phase fills about 1.7e9 of the
+    # 2^31 - 2^20 entries a pool can hold.
+    ns = 256
+    h = ns // 2
+    a = syn.coeffs("exp")
+    ref = psscf(ocsr(syn.laplacian_1d(ns)), a, 1e-12)
+    got = psf.Series(a, 1e-12).eval(dev(syn.laplacian_1d(nb)))
+    p = ref.plan
+    assert (got.info["N"], got.info["q"], got.info["b"], got.info["g"]) == (p.N, p.q, p.b, p.g)
+    assert got.info["z"] == ref.norms[:11]
+    gsteps = [s for s in got.steps if s["kind"] != "add"]
+    osteps = [s for s in ref.steps if not (s.kind == "giant" and s.threshold == 0.0 and p.g == 1 and s.index == 1)]
+    for g, o in zip(gsteps, osteps):
+        if o.threshold > 0:
+            assert g["eps_f"] == o.eps_f and g["iters"] == o.iters and g["dropped"] == o.c, (g, o)
+    srp, scol, sval = ref.F.rowptr, ref.F.col, np.asarray(ref.F.val)
+    len_h = int(srp[h + 1] - srp[h])
+    assert got.csr.nnz == ref.F.nnz + (nb - ns) * len_h
+    rp, col, val = got.csr.to_host()
+    rng = np.random.default_rng(5)
+    rows = list(range(64)) + list(range(nb - 64, nb)) + list(rng.integers(h, nb - h, 3000))
+    for r in rows:
+        if r < h:
+            rs, shift = r, 0
+        elif r >= nb - h:
+            rs, shift = r - (nb - ns), nb - ns
+        else:
+            rs, shift = h, r - h
+        gc, gv = col[rp[r]:rp[r + 1]], val[rp[r]:rp[r + 1]]
+        oc, ov = scol[srp[rs]:srp[rs + 1]] + shift, sval[srp[rs]:srp[rs + 1]]
+        assert np.array_equal(gc, oc), r
+        assert np.array_equal(gv.view(np.uint64), ov.view(np.uint64)), r
