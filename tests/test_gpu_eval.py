@@ -490,3 +490,48 @@ def test_lap1d_4m_rows_are_the_small_oracle_rows_shifted(nb):
         oc, ov = scol[srp[rs]:srp[rs + 1]] + shift, sval[srp[rs]:srp[rs + 1]]
         assert np.array_equal(gc, oc), r
         assert np.array_equal(gv.view(np.uint64), ov.view(np.uint64)), r
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind", ["exp", "cos"])
+def test_lap2d_768x768_rows_are_the_128x128_oracle_rows_shifted(kind):
+    # The 2D Laplacian is translation invariant away from the grid's edges:
+    # a row's pattern and values depend only on the point's distance to each
+    # edge, counted up to the pattern's reach (< 64 here), and the fold order
+    # (row-major order of the 2D offsets) is the same on both grids.  So each
+    # row (i, j) of the 768 x 768 result (n = 589824, 36 times the 128 x 128
+    # workload) is row (is, js) of the 128 x 128 oracle result, its columns
+    # moved by the 2D offset (i - is, j - js); the plan and Algorithm 1's
+    # column-sum maxima agree, since both grids have the same column profiles.
+    M, m = 768, 128
+    a = syn.coeffs(kind)
+    ref = psscf(ocsr(syn.laplacian_2d(m)), a, 1e-12)
+    got = psf.Series(a, 1e-12).eval(dev(syn.laplacian_2d(M)))
+    p = ref.plan
+    assert (got.info["N"], got.info["q"], got.info["b"], got.info["g"]) == (p.N, p.q, p.b, p.g)
+    assert got.info["z"] == ref.norms[:11]
+    gsteps = [s for s in got.steps if s["kind"] != "add"]
+    osteps = [s for s in ref.steps if not (s.kind == "giant" and s.threshold == 0.0 and p.g == 1 and s.index == 1)]
+    for g, o in zip(gsteps, osteps):
+        if o.threshold > 0:
+            assert g["eps_f"] == o.eps_f and g["iters"] == o.iters and g["dropped"] == o.c, (g, o)
+
+    def small(i):  # the small-grid index with the same distances to the edges
+        return i if i < m // 2 else (i - (M - m) if i >= M - m // 2 else m // 2)
+
+    srp, scol, sval = ref.F.rowptr, ref.F.col, np.asarray(ref.F.val)
+    lens = np.diff(srp).reshape(m, m)
+    cnt = np.ones(m, np.int64)
+    cnt[m // 2] = M - m + 1
+    assert got.csr.nnz == int((cnt[:, None] * cnt[None, :] * lens).sum())
+    rp, col, val = got.csr.to_host()
+    rng = np.random.default_rng(9)
+    pts = [(i, j) for i in (0, 1, 63, 64, 700, M - 1) for j in (0, 2, 64, 383, M - 64, M - 1)]
+    pts += [tuple(x) for x in rng.integers(0, M, (2000, 2))]
+    for i, j in pts:
+        r, i_s, j_s = i * M + j, small(i), small(j)
+        rs = i_s * m + j_s
+        oc = scol[srp[rs]:srp[rs + 1]]
+        want = (oc // m + (i - i_s)) * M + (oc % m + (j - j_s))
+        assert np.array_equal(col[rp[r]:rp[r + 1]], want), (i, j)
+        assert np.array_equal(val[rp[r]:rp[r + 1]].view(np.uint64), sval[srp[rs]:srp[rs + 1]].view(np.uint64)), (i, j)
