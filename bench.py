@@ -557,6 +557,53 @@ def measure_serving(args, dev):
             "latency": "host clock, submit to result available"}
 
 
+def run_size_sweep(args):
+    """The bench's 2D Laplacian on larger grids (exp, tol 1e-12): evaluation
+    time (median of 5, event-timed, L2 flushed before each), and the product
+    kernel's achieved FP64 rate over all its launches (library event timing),
+    per grid size.  The per-row latency of the product kernel is amortised
+    over more rows per warp as n grows."""
+    import ctypes
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+    from paper_2208_05683_gb300 import _abi
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    L = psf.lib()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for m in (128, 256, 384, 512, 768):
+        Z = psf.DeviceCSR.from_host(*syn.laplacian_2d(m), device=dev)
+        s = psf.Series(syn.coeffs("exp"), TOL)
+        for _ in range(2):
+            s.eval(Z)
+        lat = []
+        for it in range(5):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if it == 4:
+                _abi.check(L.psf_profile(1))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = s.eval_handle(Z, stream)
+            e1.record(stream)
+            e1.synchronize()
+            _abi.check(L.psf_result_destroy(h))
+            lat.append(e0.elapsed_time(e1))
+        nl, ms, fma = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _abi.check(L.psf_profile_read(ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(fma), 1))
+        _abi.check(L.psf_profile(0))
+        tf = 2.0 * fma.value / (ms.value / 1e3) / 1e12
+        rows.append({"grid": m, "n": m * m, "ms": statistics.median(lat), "evals_per_s": 1e3 / statistics.median(lat),
+                     "product_tflops": tf, "product_frac": tf / FP64_PEAK_TFLOPS, "product_ms": ms.value,
+                     "fma": fma.value})
+        print(f"{m}x{m}: {rows[-1]['ms']:.2f} ms, product kernel {tf:.3f} TFLOP/s "
+              f"({100 * tf / FP64_PEAK_TFLOPS:.1f} %)", file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "lap2d m x m, exp, tol 1e-12", "rows": rows}), flush=True)
+
+
 def measure_tol_sweep(args, dev):
     """The banded workload (n = 65536, half-bandwidth 5, ||Z||_1 = 2, exp)
     over tolerances 1e-8..1e-14: time, result density and products per
@@ -794,8 +841,12 @@ def main():
     ap.add_argument("--e2", action="store_true",
                     help="run the paper's banded N(0,1) experiment (n = 1000, w = 1..15) and exit")
     ap.add_argument("--e2-seeds", type=int, default=30, help="matrices per bandwidth in --e2")
+    ap.add_argument("--size-sweep", action="store_true",
+                    help="time the 2D Laplacian workload on grids 128..768 (product kernel rate per size) and exit")
     args = ap.parse_args()
-    if args.e2:
+    if args.size_sweep:
+        run_size_sweep(args)
+    elif args.e2:
         run_e2(args)
     elif args.case:
         run_case(args)

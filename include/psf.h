@@ -81,7 +81,10 @@ extern "C" {
 #define PSF_PARAM_ER 1            /* e_r of Algorithm 1 (default 0.1) */
 #define PSF_PARAM_ALG1_MAXIT 2    /* cap on Algorithm 1 passes (default 1000) */
 #define PSF_PARAM_POOL_ENTRIES 3  /* initial entry capacity of an evaluation's pool (0 = auto) */
-#define PSF_PARAM_KERNEL 4        /* product slot map: 0 auto, 1 column table, 2 bitmap */
+#define PSF_PARAM_KERNEL 4        /* product slot map: 0 auto, 1 column table, 2 bitmap,
+                                     3 bitmap with the wide column window for every product
+                                     (auto picks it for a step whose rows spanned more than
+                                     4608 columns in the series' previous evaluation) */
 #define PSF_PARAM_CHUNK_COLS 5    /* > 0: fewer columns per row chunk (tests of row chunking) */
 #define PSF_PARAM_CHUNK_SLOTS 6   /* > 0: fewer accumulator slots per row chunk (same) */
 

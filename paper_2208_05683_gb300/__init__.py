@@ -161,7 +161,8 @@ class Series:
     square   run the scheme on W = Z^2 for a series of only even or only odd
              powers (PSF_Z_SQUARE)
     s        override of the PS block size q (0 = Eq. 6)
-    kernel   slot map of the product kernel: "auto", "table" or "bitmap"
+    kernel   slot map of the product kernel: "auto", "table", "bitmap" or "window"
+             (the bitmap with its wide column window, for every product)
     chunk_cols, chunk_slots  > 0: smaller row chunks (to exercise row chunking)
     """
 
@@ -187,7 +188,7 @@ class Series:
             check(L.psf_series_set_param(h, PSF_PARAM_ALG1_MAXIT, float(maxit)))
         if pool_entries is not None:
             check(L.psf_series_set_param(h, PSF_PARAM_POOL_ENTRIES, float(pool_entries)))
-        kid = {"auto": 0, "table": 1, "bitmap": 2}[kernel]
+        kid = {"auto": 0, "table": 1, "bitmap": 2, "window": 3}[kernel]
         if kid:
             check(L.psf_series_set_param(h, PSF_PARAM_KERNEL, float(kid)))
         if chunk_cols:

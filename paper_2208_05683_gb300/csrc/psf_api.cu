@@ -131,13 +131,16 @@ unsigned long long arena_for(double row_len) {
 
 // Launch one product step into matrix slot `slot`, with Algorithm 1 when
 // threshold > 0.
+// wide_window: the previous evaluation's rows of this step spanned more
+// columns than one bitmap chunk (kBitmapColumns), so the bitmap map's wide
+// window is used.
 // reuse_k > 0: the step is baby step k and row slot `slot` still holds the
 // norm phase's Z^k; while no entry has been dropped (a device flag), the
 // product is skipped and k_reuse_pass1 does the step on those rows.
 int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
              double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
              NormSlot* absmax_slot = nullptr, double blen = 0.0, double alen = 0.0, int reuse_k = 0,
-             unsigned long long reuse_fma = 0, double out_len = 0.0) {
+             unsigned long long reuse_fma = 0, double out_len = 0.0, bool wide_window = false) {
     if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
@@ -186,7 +189,7 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     const double work = alen > 0.0 ? alen * blen : 0.0;
     const bool table = use_table(w.slot_map, work);
     if (reuse_k > 0) P.skip_unless = &w.C()->dropped;
-    CU(launch_product(P, table, w.st, out_len));
+    CU(launch_product(P, table, w.st, out_len, wide_window || w.slot_map == 3));
     if (reuse_k > 0) {
         ReuseArgs R{};
         R.n = w.n;
@@ -377,7 +380,8 @@ int psf_series_set_param(psf_series_t series, int32_t key, double value) {
             series->maxit = (int)value;
             return PSF_OK;
         case PSF_PARAM_KERNEL:
-            if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(PSF_EINVAL, "kernel must be 0, 1 or 2");
+            if (!(value == 0.0 || value == 1.0 || value == 2.0 || value == 3.0))
+                return fail(PSF_EINVAL, "kernel must be 0, 1, 2 or 3");
             series->kernel = (int)value;
             return PSF_OK;
         case PSF_PARAM_CHUNK_COLS:
@@ -677,8 +681,10 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                         RowView cur;
                         double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
                                                                               : zlen * (i - 1) * (i - 1);
+                        const bool wz = (size_t)(i - 2) < series->span_z.size() &&
+                                        series->span_z[(size_t)(i - 2)] > kBitmapColumns;
                         if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, i - 2, (size_t)(i - 2), &cur,
-                                           slots + i, blen, zlen)))
+                                           slots + i, blen, zlen, 0, 0ull, 0.0, wz)))
                             return rc;
                         if ((rc = mark_pool(w, i))) return rc;
                         if (i == 2) zsq = cur;
@@ -711,10 +717,12 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 if (cudaMemcpy(zs, w.stats.p, sizeof zs, cudaMemcpyDeviceToHost) != cudaSuccess)
                     return fail(PSF_ECUDA, "stats read-back");
                 series->len_z.assign(9, 0.0);
+                series->span_z.assign(9, 0u);
                 for (int i = 2; i <= 10; ++i) {
                     znnz[i] = (double)zs[i - 2].nnz_pre;
                     zfma[i] = zs[i - 2].fma;
                     series->len_z[(size_t)(i - 2)] = znnz[i - 1] / n;
+                    series->span_z[(size_t)(i - 2)] = zs[i - 2].span_max;
                 }
             }
             // ||Z||_1 always; Z^2..Z^10 when the chain ran (else estimated above)
@@ -811,8 +819,10 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                                                                          : pow_len(k);
                 // baby step k + 1 writes row slot k - 1, the slot of the norm phase's Z^(k+1)
                 const int rk = (reuse && !square && k + 1 <= 10 && slot == (size_t)(k - 1)) ? k + 1 : 0;
+                const bool wb = (size_t)(k - 1) < series->span_baby.size() &&
+                                series->span_baby[(size_t)(k - 1)] > kBitmapColumns;
                 if ((rc = run_step(w, &vm, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
-                                   &Zh[(size_t)k + 1], nullptr, blen, pow_len(1), rk, rk ? zfma[rk] : 0ull)))
+                                   &Zh[(size_t)k + 1], nullptr, blen, pow_len(1), rk, rk ? zfma[rk] : 0ull, 0.0, wb)))
                     return rc;
                 psf_step_info_t s{};
                 s.kind = 0;
@@ -883,8 +893,10 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     const double alen = pow_len(q);
                     const double olen =
                         (size_t)(i - 1) < series->out_giant.size() ? series->out_giant[(size_t)(i - 1)] : 0.0;
+                    const bool wg = (size_t)(i - 1) < series->span_giant.size() &&
+                                    series->span_giant[(size_t)(i - 1)] > kBitmapColumns;
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
-                                       &nxt, nullptr, blen, alen, 0, 0ull, olen)))
+                                       &nxt, nullptr, blen, alen, 0, 0ull, olen, wg)))
                         return rc;
                     s.kind = 1;
                     s.threshold = thr;
@@ -949,17 +961,21 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             series->len_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0.0);
             series->len_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             series->out_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
+            series->span_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0u);
+            series->span_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0u);
             {
                 double prev_len = pow_len(1);  // Z-hat_(1) = Z or W
                 size_t idx = 0;
                 for (int k = 1; k < q; ++k, ++idx) {
                     series->len_baby[(size_t)(k - 1)] = prev_len;
+                    series->span_baby[(size_t)(k - 1)] = ss[idx].span_max;
                     prev_len = (double)steps[idx].nnz_post / n;
                 }
                 double s_len = 0.0;
                 if (g == 0) s_len = (double)steps[idx++].nnz_post / n;  // S-hat_0
                 for (int i = 1; i < b; ++i, ++idx) {
                     series->len_giant[(size_t)(i - 1)] = s_len;
+                    series->span_giant[(size_t)(i - 1)] = ss[idx].span_max;
                     series->out_giant[(size_t)(i - 1)] = (double)steps[idx].nnz_pre / n;
                     s_len = (double)steps[idx].nnz_post / n;
                 }

@@ -57,7 +57,8 @@ struct StepStat {
     unsigned long long pool_end;    // 0: the step's entries end at the pool counter
     unsigned long long nnz_pre, nnz_post, ncand, fma;
     double eps_f, dropped;
-    int iters, pad;
+    int iters;
+    unsigned span_max;  // widest column window of the product's rows (hi - lo + 1)
 };
 
 // Per-matrix norm slot for the exact 1-norm kernel.

@@ -35,6 +35,9 @@ struct psf_series_s {
     // product kernel's accumulator variant for long rows)
     std::vector<double> out_giant;
     double len_odd = 0.0;  // row length of G-hat in F = Z G-hat (odd series, PSF_Z_SQUARE)
+    // widest column window of each step's rows (the bitmap map's wide window
+    // is used where it exceeded kBitmapColumns)
+    std::vector<unsigned> span_z, span_baby, span_giant;
     int kernel = 0;       // PSF_PARAM_KERNEL
     int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
     int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS

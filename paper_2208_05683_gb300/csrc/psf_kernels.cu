@@ -56,6 +56,12 @@ namespace psf {
 constexpr int kTabCap = 4160;  // columns of the table map
 constexpr int kBmWords = 144;  // bitmap words of the bitmap map (4608 columns)
 constexpr int kBmBits = kBmWords * 32;
+// The wide-window bitmap (16384 columns) for steps whose rows span more
+// columns than kBmBits (a grid of side M spreads a row over about 2rM
+// columns for a pattern of radius r): one column chunk instead of several,
+// at 5 blocks per SM instead of 7.
+constexpr int kBmWordsBig = 512;
+static_assert(kBmBits == kBitmapColumns, "the host's notion of the bitmap window");
 // Accumulator slots; with 7 bitmap blocks of 4 warps per SM shared memory is
 // full.  The bitmap map keeps a segment's a_rk in the last 32 slots, so a row
 // has kAccCap - 32 of them; its WIDE instantiation, for steps whose rows are
@@ -63,11 +69,11 @@ constexpr int kBmBits = kBmWords * 32;
 // up to kAccCap entries then takes one pass, not two column chunks).
 constexpr int kAccCap = 640;
 
-template <bool TAB>
+template <bool TAB, int W = kBmWords>
 struct ProdSmem;
 
 template <>
-struct ProdSmem<true> {
+struct ProdSmem<true, kBmWords> {
     static constexpr int kCols = kTabCap;
     static constexpr int kWarps = 2;
     static constexpr int kBlocksPerSm = 7;
@@ -79,21 +85,22 @@ struct ProdSmem<true> {
     unsigned short colbuf[kAccCap];
 };
 
-template <>
-struct ProdSmem<false> {
-    static constexpr int kCols = kBmBits;
+template <int W>
+struct ProdSmem<false, W> {
+    static constexpr int kCols = W * 32;
     static constexpr int kWarps = 4;
-    static constexpr int kBlocksPerSm = 7;  // 28 warps: registers (72) and shared memory
-    uint2 pm[kBmWords];  // .x = set bits before the word, .y = bitmap word
+    // 28 warps: registers (72) and shared memory; 20 with the wide window
+    static constexpr int kBlocksPerSm = W > kBmWords ? 5 : 7;
+    uint2 pm[W];  // .x = set bits before the word, .y = bitmap word
     double acc[kAccCap];  // the last 32 hold a_rk of the segment (not in WIDE)
     int kb[32];
     int kl[32];
     unsigned short colbuf[kAccCap];
 };
 
-template <bool TAB>
+template <bool TAB, int W = kBmWords>
 size_t prod_smem_bytes() {
-    return sizeof(ProdSmem<TAB>) * ProdSmem<TAB>::kWarps + sizeof(AddTerm) * kMaxAdd;
+    return sizeof(ProdSmem<TAB, W>) * ProdSmem<TAB, W>::kWarps + sizeof(AddTerm) * kMaxAdd;
 }
 
 // first position in [s, e) with col >= c (col ascending).  Pool positions
@@ -109,21 +116,23 @@ __device__ __forceinline__ int lower_bound_col(const int* col, int s, int e, int
 
 // slot of column offset o (o inside the current chunk's pattern)
 __device__ __forceinline__ int slot_lookup(const ProdSmem<true>& S, int o) { return S.tab[o]; }
-__device__ __forceinline__ int slot_lookup(const ProdSmem<false>& S, int o) {
+template <int W>
+__device__ __forceinline__ int slot_lookup(const ProdSmem<false, W>& S, int o) {
     const uint2 e = S.pm[o >> 5];
     return (int)e.x + __popc(e.y & ((1u << (o & 31)) - 1u));
 }
 
 // where a segment's a_rk are kept
 __device__ __forceinline__ double* ka_of(ProdSmem<true>& S) { return S.ka; }
-__device__ __forceinline__ double* ka_of(ProdSmem<false>& S) { return S.acc + (kAccCap - 32); }
+template <int W>
+__device__ __forceinline__ double* ka_of(ProdSmem<false, W>& S) { return S.acc + (kAccCap - 32); }
 
 // Load the segment [seg, seg + cnt) of A's row: a_rk (unless `store_a` is
 // false) and the range of B's row k restricted to columns [c0, c1) (the
 // whole row when `whole`).
-template <bool TAB>
+template <bool TAB, int W>
 __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1,
-                                             int lane, ProdSmem<TAB>& S, bool store_a) {
+                                             int lane, ProdSmem<TAB, W>& S, bool store_a) {
     if (lane < cnt) {
         int k = P.A.col[seg + lane];
         int b = P.B.rb[k], e = P.B.re[k];
@@ -166,9 +175,9 @@ __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<true>& S)
 // each column against [c0, cend); a B row needs no test, since
 // load_segment has already clipped it to that range (or, for a row that
 // takes one chunk, the range spans every B column of the row).
-template <bool CHK>
+template <bool CHK, int W>
 __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int e, int c0, int cend, int lane,
-                                         ProdSmem<false>& S) {
+                                         ProdSmem<false, W>& S) {
     const int m = (e - s + 31) >> 5;
     const int q0 = s + lane * m, q1 = min(e, q0 + m);
     unsigned curw = 0xffffffffu, mask = 0u;
@@ -194,8 +203,9 @@ __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int
 // Short B rows (at most 32 entries each): lane i marks the segment's B row i,
 // so the rows' column loads are in flight together instead of one row after
 // the other.  The rows are clipped to [c0, cend) (see mark_row).
+template <int W>
 __device__ __forceinline__ void mark_rows_short(const int* __restrict__ col, int cnt, int c0, int cend, int lane,
-                                                ProdSmem<false>& S) {
+                                                ProdSmem<false, W>& S) {
     if (lane >= cnt) return;
     const int s = S.kb[lane], e = s + S.kl[lane];
     unsigned curw = 0xffffffffu, mask = 0u;
@@ -219,16 +229,18 @@ __device__ __forceinline__ void mark_rows_short(const int* __restrict__ col, int
     }
     if (mask) atomicOr(&S.pm[curw].y, mask);
 }
-__device__ __forceinline__ void mark_one(int o, ProdSmem<false>& S) { atomicOr(&S.pm[o >> 5].y, 1u << (o & 31)); }
-__device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false>& S) {
+template <int W>
+__device__ __forceinline__ void mark_one(int o, ProdSmem<false, W>& S) { atomicOr(&S.pm[o >> 5].y, 1u << (o & 31)); }
+template <int W>
+__device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false, W>& S) {
     const int nw = (wlen + 31) >> 5;
     for (int w = lane; w < nw; w += 32) S.pm[w].y = 0u;
 }
 
 // Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
-template <bool TAB>
+template <bool TAB, int W>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
-                                          int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB>& S,
+                                          int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB, W>& S,
                                           bool store_a) {
     clear_map(cend - c0, lane, S);
     __syncwarp();
@@ -270,7 +282,8 @@ __device__ __forceinline__ int count_marks(int wlen, int lane, const ProdSmem<tr
     }
     return total;
 }
-__device__ __forceinline__ int count_marks(int wlen, int lane, const ProdSmem<false>& S) {
+template <int W>
+__device__ __forceinline__ int count_marks(int wlen, int lane, const ProdSmem<false, W>& S) {
     int s = 0;
     for (int w = lane; w < ((wlen + 31) >> 5); w += 32) s += __popc(S.pm[w].y);
     return warp_sum(s);
@@ -301,8 +314,9 @@ __device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSme
     *cut = cutoff;
     return min(run, cap);
 }
-__device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSmem<false>& S, int* cut) {
-    constexpr int per = (kBmWords + 31) / 32;  // words per lane (the last lanes' partly past nw)
+template <int W>
+__device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSmem<false, W>& S, int* cut) {
+    constexpr int per = (W + 31) / 32;  // words per lane (the last lanes' partly past nw)
     const int nw = (wlen + 31) >> 5;
     const int base = lane * per;
     int s = 0;
@@ -353,9 +367,9 @@ struct Chunk {
     double v[4];
 };
 
-template <bool TAB>
+template <bool TAB, int W>
 __device__ __forceinline__ void chunk_load(const int* __restrict__ bcol, const double* __restrict__ bval,
-                                           const ProdSmem<TAB>& S, int kk, int off, int lane, Chunk& ch) {
+                                           const ProdSmem<TAB, W>& S, int kk, int off, int lane, Chunk& ch) {
     const int len = S.kl[kk];
     const int* rc = bcol + S.kb[kk] + lane;
     const double* rv = bval + S.kb[kk] + lane;
@@ -370,8 +384,8 @@ __device__ __forceinline__ void chunk_load(const int* __restrict__ bcol, const d
     }
 }
 
-template <bool TAB>
-__device__ __forceinline__ void chunk_next(const ProdSmem<TAB>& S, int cnt, int& kk, int& off) {
+template <bool TAB, int W>
+__device__ __forceinline__ void chunk_next(const ProdSmem<TAB, W>& S, int cnt, int& kk, int& off) {
     off += 128;
     if (off >= S.kl[kk]) {
         off = 0;
@@ -385,8 +399,8 @@ __device__ __forceinline__ void chunk_next(const ProdSmem<TAB>& S, int cnt, int&
 // are independent and are interleaved.  `np` (the same in every lane) is the
 // number of pieces holding entries: a DFMA occupies the FP64 pipe for the
 // whole warp, so the empty pieces at a row's end are branched over.
-template <bool TAB>
-__device__ __forceinline__ void chunk_fold(ProdSmem<TAB>& S, const Chunk& ch, double a, int c0, int np = 4) {
+template <bool TAB, int W>
+__device__ __forceinline__ void chunk_fold(ProdSmem<TAB, W>& S, const Chunk& ch, double a, int c0, int np = 4) {
     int i[4];
     double x[4];
 #pragma unroll
@@ -444,8 +458,9 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int /*s
 }
 // One 32-lane piece of short B row kk (at most 32 entries): column -1 where
 // there is none.
+template <int W>
 __device__ __forceinline__ void short_load(const int* __restrict__ bcol, const double* __restrict__ bval,
-                                           const ProdSmem<false>& S, int cnt, int kk, int lane, int& c, double& v) {
+                                           const ProdSmem<false, W>& S, int cnt, int kk, int lane, int& c, double& v) {
     c = -1;
     v = 0.0;
     if (kk < cnt && lane < S.kl[kk]) {
@@ -454,16 +469,17 @@ __device__ __forceinline__ void short_load(const int* __restrict__ bcol, const d
         v = bval[q];
     }
 }
-__device__ __forceinline__ void short_fold(ProdSmem<false>& S, int c, double v, double a, int c0) {
+template <int W>
+__device__ __forceinline__ void short_fold(ProdSmem<false, W>& S, int c, double v, double a, int c0) {
     if (c >= 0) {
         const int i = slot_lookup(S, c - c0);
         S.acc[i] = __fma_rn(a, v, S.acc[i]);
     }
 }
 
-template <bool WIDE>
+template <bool WIDE, int W>
 __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int seg, int cnt, int c0, int lane,
-                                                   ProdSmem<false>& S) {
+                                                   ProdSmem<false, W>& S) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
     const double* ka = ka_of(S);
@@ -542,33 +558,38 @@ __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, 
     }
 }
 
-template <bool TAB, bool BATCH, bool WIDE>
-__global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBlocksPerSm) k_product(ProductArgs P) {
+template <bool TAB, bool BATCH, bool WIDE, int W = kBmWords>
+__global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W>::kBlocksPerSm)
+    k_product(ProductArgs P) {
     // a baby step whose product equals an already computed power (no entry
     // dropped so far) is done by k_reuse_pass1 instead (same value in all blocks)
     if (P.skip_unless && __ldcg(P.skip_unless) == 0) return;
-    constexpr int kWarps = ProdSmem<TAB>::kWarps;
+    using Smem = ProdSmem<TAB, W>;
+    constexpr int kWarps = Smem::kWarps;
     // columns and slots of one chunk (lowered only to exercise chunking)
-    const int kCols = P.chunk_cols > 0 && P.chunk_cols < ProdSmem<TAB>::kCols ? P.chunk_cols : ProdSmem<TAB>::kCols;
+    const int kCols = P.chunk_cols > 0 && P.chunk_cols < Smem::kCols ? P.chunk_cols : Smem::kCols;
     constexpr int kCapN = (TAB || WIDE) ? kAccCap : kAccCap - 32;  // a row's slots
     const int kSlots = P.chunk_slots > 0 && P.chunk_slots < kCapN ? P.chunk_slots : kCapN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
-    ProdSmem<TAB>* warps = reinterpret_cast<ProdSmem<TAB>*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
+    Smem* warps = reinterpret_cast<Smem*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nadd = P.nadd;
     for (int t = threadIdx.x; t < nadd; t += blockDim.x) add[t] = P.add[t];
     __shared__ unsigned long long blk_written, blk_cand, blk_absmax, blk_fma;
+    __shared__ int blk_span;
     if (threadIdx.x == 0) {
+        blk_span = 0;
         blk_fma = 0ull;
         blk_written = 0ull;
         blk_cand = 0ull;
         blk_absmax = 0ull;
     }
     __syncthreads();
-    ProdSmem<TAB>& S = warps[wib];
+    Smem& S = warps[wib];
     const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
     unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
+    int my_span = 0;  // widest column window of this warp's rows
     Arena arena;
     CandArena carena;
 
@@ -636,6 +657,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
                 if ((tmask >> t) & 1u) my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
         lo = warp_min(lo);
         hi = warp_max(hi);
+        my_span = max(my_span, hi - lo + 1);
         if (hi < lo) {
             if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
             if constexpr (BATCH) row_stats_batch(P, r_inst, my_fma - fma0, 0ull, 0, 0ull, lane);
@@ -776,11 +798,13 @@ __global__ void __launch_bounds__(ProdSmem<TAB>::kWarps * 32, ProdSmem<TAB>::kBl
         atomicAdd(&blk_written, my_written);
         atomicAdd(&blk_cand, my_cand);
         atomicMax(&blk_absmax, my_absmax);
+        atomicMax(&blk_span, my_span);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (blk_fma) atomicAdd(&P.ctl->fma_total, blk_fma);
         if (P.stat) {
+            if (blk_span > 0) atomicMax(&P.stat->span_max, (unsigned)blk_span);
             if (blk_fma) atomicAdd(&P.stat->fma, blk_fma);
             if (blk_written) atomicAdd(&P.stat->nnz_pre, blk_written);
             if (blk_cand) atomicAdd(&P.stat->ncand, blk_cand);
@@ -2096,12 +2120,14 @@ cudaError_t kernels_init() {
     int sms = 0;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    const void* prods[5] = {(const void*)k_product<true, false, false>, (const void*)k_product<false, false, false>,
+    const void* prods[6] = {(const void*)k_product<true, false, false>, (const void*)k_product<false, false, false>,
                             (const void*)k_product<true, true, false>, (const void*)k_product<false, true, false>,
-                            (const void*)k_product<false, false, true>};
-    const int psmem[5] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
-                          (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<false>()};
-    for (int i = 0; i < 5; ++i) {
+                            (const void*)k_product<false, false, true>,
+                            (const void*)k_product<false, false, true, kBmWordsBig>};
+    const int psmem[6] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
+                          (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<false>(),
+                          (int)prod_smem_bytes<false, kBmWordsBig>()};
+    for (int i = 0; i < 6; ++i) {
         err = cudaFuncSetAttribute(prods[i], cudaFuncAttributeMaxDynamicSharedMemorySize, psmem[i]);
         if (err != cudaSuccess) return err;
     }
@@ -2127,23 +2153,26 @@ cudaError_t kernels_init() {
 int num_sms() { return dcfg().sms; }
 static int sms_now() { return dcfg().sms; }
 
-template <bool TAB, bool BATCH, bool WIDE>
+template <bool TAB, bool BATCH, bool WIDE, int W = kBmWords>
 static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
-    constexpr int kWarps = ProdSmem<TAB>::kWarps;
+    constexpr int kWarps = ProdSmem<TAB, W>::kWarps;
     // one wave of resident blocks, rows strided over the warps (each warp
     // keeps one pool arena)
     long long blocks = ((long long)P.n + kWarps - 1) / kWarps;
-    const long long cap = (long long)sms_now() * ProdSmem<TAB>::kBlocksPerSm;
+    const long long cap = (long long)sms_now() * ProdSmem<TAB, W>::kBlocksPerSm;
     if (blocks > cap) blocks = cap;
-    k_product<TAB, BATCH, WIDE><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB>(), st>>>(P);
+    k_product<TAB, BATCH, WIDE, W><<<(unsigned)blocks, kWarps * 32, prod_smem_bytes<TAB, W>(), st>>>(P);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len) {
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len, bool wide_window) {
     if (P.n <= 0) return cudaSuccess;
     if (P.inst) return table ? prod_launch<true, true, false>(P, st) : prod_launch<false, true, false>(P, st);
     if (table) return prod_launch<true, false, false>(P, st);
+    // rows expected to span more columns than the bitmap covers: the wide
+    // window (with every accumulator slot, as WIDE)
+    if (wide_window) return prod_launch<false, false, true, kBmWordsBig>(P, st);
     // rows expected near or above the bitmap map's kAccCap - 32 slots: WIDE
     if (out_len > 0.9 * (kAccCap - 32)) return prod_launch<false, false, true>(P, st);
     return prod_launch<false, false, false>(P, st);

@@ -13,8 +13,13 @@ long long launch_count();
 void count_launches(int k);  // kernels launched by other translation units
 
 // out_len: the expected mean output row length (0: unknown), which picks the
-// bitmap map's wide-accumulator instantiation for long rows
-cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len = 0.0);
+// bitmap map's wide-accumulator instantiation for long rows; wide_window:
+// rows are expected to span more columns than the bitmap map covers, which
+// picks its wide-window instantiation (16384 columns)
+// columns one chunk of the bitmap map covers (the wide window: 16384)
+constexpr int kBitmapColumns = 4608;
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len = 0.0,
+                           bool wide_window = false);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
 cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
 cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st);

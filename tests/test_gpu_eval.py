@@ -46,11 +46,12 @@ def test_lap2d_32_bitwise(kind):
 
 @pytest.mark.parametrize("kernel,cols,slots", [("table", 0, 0), ("bitmap", 0, 0), ("table", 96, 0),
                                                ("bitmap", 64, 0), ("table", 0, 40), ("bitmap", 0, 33),
-                                               ("table", 40, 37)])
+                                               ("table", 40, 37), ("window", 0, 0), ("window", 64, 0),
+                                               ("window", 0, 33), ("window", 5000, 0)])
 def test_slot_maps_and_row_chunking_bitwise(kernel, cols, slots):
-    # both slot maps of the product kernel, and rows split into several column
-    # chunks (by width or by accumulator slots), give the oracle's result bit
-    # for bit
+    # both slot maps of the product kernel (the bitmap also with its wide
+    # column window), and rows split into several column chunks (by width or
+    # by accumulator slots), give the oracle's result bit for bit
     Z = ocsr(syn.laplacian_2d(24))
     for kind in ("exp", "cos"):
         got, ref = run_both(Z, syn.coeffs(kind), 1e-12, kernel=kernel, chunk_cols=cols, chunk_slots=slots)
@@ -506,7 +507,12 @@ def test_lap2d_768x768_rows_are_the_128x128_oracle_rows_shifted(kind):
     M, m = 768, 128
     a = syn.coeffs(kind)
     ref = psscf(ocsr(syn.laplacian_2d(m)), a, 1e-12)
-    got = psf.Series(a, 1e-12).eval(dev(syn.laplacian_2d(M)))
+    series = psf.Series(a, 1e-12)
+    Zd = dev(syn.laplacian_2d(M))
+    series.eval(Zd)
+    # the second evaluation runs the steps whose rows spanned more than 4608
+    # columns (about 2 x 25 grid rows of 768 here) with the wide column window
+    got = series.eval(Zd)
     p = ref.plan
     assert (got.info["N"], got.info["q"], got.info["b"], got.info["g"]) == (p.N, p.q, p.b, p.g)
     assert got.info["z"] == ref.norms[:11]
