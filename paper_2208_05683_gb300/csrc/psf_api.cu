@@ -613,6 +613,15 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     if ((rc = w.init(n, st, 16))) return rc;
     if ((rc = validate_inputs(w, {Z}))) return rc;
     w.slot_map = series->kernel;
+    // the column windows the series' previous evaluation measured (batches on
+    // other threads may update them)
+    std::vector<unsigned> span_z, span_baby, span_giant;
+    {
+        std::lock_guard<std::mutex> lock(series->span_mu);
+        span_z = series->span_z;
+        span_baby = series->span_baby;
+        span_giant = series->span_giant;
+    }
     w.chunk_cols = series->chunk_cols;
     w.chunk_slots = series->chunk_slots;
     const RowView vz = view_of(*Z);
@@ -681,8 +690,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                         RowView cur;
                         double blen = (size_t)(i - 2) < series->len_z.size() ? series->len_z[(size_t)(i - 2)]
                                                                               : zlen * (i - 1) * (i - 1);
-                        const bool wz = (size_t)(i - 2) < series->span_z.size() &&
-                                        series->span_z[(size_t)(i - 2)] > kBitmapColumns;
+                        const bool wz = (size_t)(i - 2) < span_z.size() && span_z[(size_t)(i - 2)] > kBitmapColumns;
                         if ((rc = run_step(w, &vz, &prev, {}, 0.0, 0.0, 1, i - 2, (size_t)(i - 2), &cur,
                                            slots + i, blen, zlen, 0, 0ull, 0.0, wz)))
                             return rc;
@@ -717,13 +725,15 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                 if (cudaMemcpy(zs, w.stats.p, sizeof zs, cudaMemcpyDeviceToHost) != cudaSuccess)
                     return fail(PSF_ECUDA, "stats read-back");
                 series->len_z.assign(9, 0.0);
-                series->span_z.assign(9, 0u);
+                std::vector<unsigned> sz(9, 0u);
                 for (int i = 2; i <= 10; ++i) {
                     znnz[i] = (double)zs[i - 2].nnz_pre;
                     zfma[i] = zs[i - 2].fma;
                     series->len_z[(size_t)(i - 2)] = znnz[i - 1] / n;
-                    series->span_z[(size_t)(i - 2)] = zs[i - 2].span_max;
+                    sz[(size_t)(i - 2)] = zs[i - 2].span_max;
                 }
+                std::lock_guard<std::mutex> lock(series->span_mu);
+                series->span_z = sz;
             }
             // ||Z||_1 always; Z^2..Z^10 when the chain ran (else estimated above)
             for (int i = 1; i <= (chain || submult ? 10 : 1); ++i) {
@@ -819,8 +829,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                                                                          : pow_len(k);
                 // baby step k + 1 writes row slot k - 1, the slot of the norm phase's Z^(k+1)
                 const int rk = (reuse && !square && k + 1 <= 10 && slot == (size_t)(k - 1)) ? k + 1 : 0;
-                const bool wb = (size_t)(k - 1) < series->span_baby.size() &&
-                                series->span_baby[(size_t)(k - 1)] > kBitmapColumns;
+                const bool wb = (size_t)(k - 1) < span_baby.size() && span_baby[(size_t)(k - 1)] > kBitmapColumns;
                 if ((rc = run_step(w, &vm, &Zh[(size_t)k], {}, thr, series->e_r, series->maxit, si, slot++,
                                    &Zh[(size_t)k + 1], nullptr, blen, pow_len(1), rk, rk ? zfma[rk] : 0ull, 0.0, wb)))
                     return rc;
@@ -893,8 +902,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     const double alen = pow_len(q);
                     const double olen =
                         (size_t)(i - 1) < series->out_giant.size() ? series->out_giant[(size_t)(i - 1)] : 0.0;
-                    const bool wg = (size_t)(i - 1) < series->span_giant.size() &&
-                                    series->span_giant[(size_t)(i - 1)] > kBitmapColumns;
+                    const bool wg = (size_t)(i - 1) < span_giant.size() && span_giant[(size_t)(i - 1)] > kBitmapColumns;
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
                                        &nxt, nullptr, blen, alen, 0, 0ull, olen, wg)))
                         return rc;
@@ -961,25 +969,29 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             series->len_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0.0);
             series->len_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             series->out_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
-            series->span_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0u);
-            series->span_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0u);
+            std::vector<unsigned> sb((size_t)(q > 1 ? q - 1 : 0), 0u), sg((size_t)(b > 1 ? b - 1 : 0), 0u);
             {
                 double prev_len = pow_len(1);  // Z-hat_(1) = Z or W
                 size_t idx = 0;
                 for (int k = 1; k < q; ++k, ++idx) {
                     series->len_baby[(size_t)(k - 1)] = prev_len;
-                    series->span_baby[(size_t)(k - 1)] = ss[idx].span_max;
+                    sb[(size_t)(k - 1)] = ss[idx].span_max;
                     prev_len = (double)steps[idx].nnz_post / n;
                 }
                 double s_len = 0.0;
                 if (g == 0) s_len = (double)steps[idx++].nnz_post / n;  // S-hat_0
                 for (int i = 1; i < b; ++i, ++idx) {
                     series->len_giant[(size_t)(i - 1)] = s_len;
-                    series->span_giant[(size_t)(i - 1)] = ss[idx].span_max;
+                    sg[(size_t)(i - 1)] = ss[idx].span_max;
                     series->out_giant[(size_t)(i - 1)] = (double)steps[idx].nnz_pre / n;
                     s_len = (double)steps[idx].nnz_post / n;
                 }
                 if (odd) series->len_odd = s_len;  // G-hat, the right factor of F = Z G-hat
+            }
+            {
+                std::lock_guard<std::mutex> lock(series->span_mu);
+                series->span_baby = sb;
+                series->span_giant = sg;
             }
             if ((rc = finish_result(w, F, r, c.nnz_total))) {
                 destroy_result(r);

@@ -90,6 +90,7 @@ struct StageTab {
     bool any_filter = false;
     bool any_product = false;
     bool any_reuse = false;  // some instance may take the norm phase's Z^k
+    bool wide = false;       // some instance's rows spanned more than one bitmap chunk last time
     int nadd = 0;
     double reuse_rows = 0.0, reuse_nnz = 0.0;  // size of those powers (arena estimate)
     double work_rows = 0.0, work_fma = 0.0;  // estimates for the slot map and arenas
@@ -201,6 +202,18 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         chain[(size_t)i] = !(series[i]->flags & PSF_Z_SUBMULT) && Zs[i].n > 0;
         any_chain = any_chain || chain[(size_t)i];
     }
+    // the column windows each series' previous evaluation measured, per step
+    // (read under the series' lock: batches on other threads may share it)
+    std::vector<std::vector<unsigned>> span_z((size_t)count), span_baby((size_t)count), span_giant((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        std::lock_guard<std::mutex> lock(series[i]->span_mu);
+        span_z[(size_t)i] = series[i]->span_z;
+        span_baby[(size_t)i] = series[i]->span_baby;
+        span_giant[(size_t)i] = series[i]->span_giant;
+    }
+    auto wide_of = [](const std::vector<unsigned>& v, int idx) {
+        return idx >= 0 && (size_t)idx < v.size() && v[(size_t)idx] > (unsigned)kBitmapColumns;
+    };
     std::vector<StepStat> zst;  // 9 * count
     unsigned long long z_fma_tot = 0;
     {
@@ -269,7 +282,9 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                     const double blen = zlen_all * (k - 1) * (k - 1);
                     P.arena = arena_for(zlen_all * blen);
                     const bool table = use_table(w.slot_map, zlen_all * blen);
-                    CU(launch_product(P, table, st));
+                    bool wz = false;
+                    for (int i = 0; i < count && !wz; ++i) wz = chain[(size_t)i] && wide_of(span_z[(size_t)i], k - 2);
+                    CU(launch_product(P, table, st, 0.0, wz));
                     if ((rc = mark_pool(w, k))) return rc;
                     prev = w.pooled(rb, re);
                 }
@@ -468,6 +483,9 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             }
             T.any_filter = T.any_filter || B.eps_g > 0.0;
             T.any_product = T.any_product || B.mode == kBatchProduct;
+            if (B.mode == kBatchProduct && !P.trivial)
+                T.wide = T.wide || (D.kind == 0 && wide_of(span_baby[(size_t)i], D.index - 2)) ||
+                         (D.kind == 1 && wide_of(span_giant[(size_t)i], D.index - 1));
         }
     }
     // device copies of the stage tables, one upload
@@ -628,7 +646,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 CU(cudaEventCreate(&e1));
                 CU(cudaEventRecord(e0, st));
             }
-            CU(launch_product(P, table, st));
+            CU(launch_product(P, table, st, 0.0, T.wide));
             if (g_prof.on) {
                 CU(cudaEventRecord(e1, st));
                 g_prof.ev.emplace_back(e0, e1);
@@ -783,6 +801,26 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 fma += ss.fma;
                 r->steps.push_back(s);
             }
+        }
+        // the column windows of this evaluation's steps, for the series' next one
+        {
+            std::vector<unsigned> sz, sb((size_t)(p.q > 1 ? p.q - 1 : 0), 0u),
+                sg((size_t)(p.b > 1 ? p.b - 1 : 0), 0u);
+            if (chain[(size_t)i]) {
+                sz.assign(9, 0u);
+                for (int k = 2; k <= 10; ++k) sz[(size_t)(k - 2)] = zst[(size_t)(k - 2) * count + (size_t)i].span_max;
+            }
+            for (size_t si = 0; si < nst && !P.trivial; ++si) {
+                const StageDesc& D = stages[si];
+                if (tabs[si].step[(size_t)i].mode != kBatchProduct) continue;
+                const unsigned sp = pst[si * (size_t)count + (size_t)i].span_max;
+                if (D.kind == 0 && D.index - 2 >= 0 && (size_t)(D.index - 2) < sb.size()) sb[(size_t)(D.index - 2)] = sp;
+                if (D.kind == 1 && D.index - 1 >= 0 && (size_t)(D.index - 1) < sg.size()) sg[(size_t)(D.index - 1)] = sp;
+            }
+            std::lock_guard<std::mutex> lock(series[i]->span_mu);
+            if (chain[(size_t)i]) series[i]->span_z = sz;
+            series[i]->span_baby = sb;
+            series[i]->span_giant = sg;
         }
         psf_info_t& inf = r->info;
         inf.N = p.N;

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -36,8 +37,10 @@ struct psf_series_s {
     std::vector<double> out_giant;
     double len_odd = 0.0;  // row length of G-hat in F = Z G-hat (odd series, PSF_Z_SQUARE)
     // widest column window of each step's rows (the bitmap map's wide window
-    // is used where it exceeded kBitmapColumns)
+    // is used where it exceeded kBitmapColumns); batches, which may run
+    // concurrently on one series, read and write them under span_mu
     std::vector<unsigned> span_z, span_baby, span_giant;
+    std::mutex span_mu;
     int kernel = 0;       // PSF_PARAM_KERNEL
     int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
     int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS

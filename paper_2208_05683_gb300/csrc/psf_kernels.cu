@@ -541,7 +541,7 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int seg
 // entries written and the largest |x| (per lane).
 __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, unsigned long long fma,
                                                 unsigned long long cand, int written, unsigned long long absmax,
-                                                int lane) {
+                                                int lane, int span = 0) {
     for (int o = 16; o; o >>= 1) {
         fma += __shfl_xor_sync(kFull, fma, o);
         cand += __shfl_xor_sync(kFull, cand, o);
@@ -553,6 +553,7 @@ __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, 
             if (fma) atomicAdd(&st->fma, fma);
             if (written) atomicAdd(&st->nnz_pre, (unsigned long long)written);
             if (cand) atomicAdd(&st->ncand, cand);
+            if (span > 0) atomicMax(&st->span_max, (unsigned)span);
         }
         if (P.absmax_slot && absmax) atomicMax(&(P.absmax_slot + (size_t)inst * P.absmax_stride)->absmax, absmax);
     }
@@ -778,7 +779,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
             P.out_re[r] = (int)(base + written);
         }
         if constexpr (BATCH) {
-            row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane);
+            row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane, hi - lo + 1);
             my_absmax = 0ull;
         } else if (lane == 0) {
             my_written += (unsigned long long)written;
@@ -2120,14 +2121,15 @@ cudaError_t kernels_init() {
     int sms = 0;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    const void* prods[6] = {(const void*)k_product<true, false, false>, (const void*)k_product<false, false, false>,
+    const void* prods[7] = {(const void*)k_product<true, false, false>, (const void*)k_product<false, false, false>,
                             (const void*)k_product<true, true, false>, (const void*)k_product<false, true, false>,
                             (const void*)k_product<false, false, true>,
-                            (const void*)k_product<false, false, true, kBmWordsBig>};
-    const int psmem[6] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
+                            (const void*)k_product<false, false, true, kBmWordsBig>,
+                            (const void*)k_product<false, true, false, kBmWordsBig>};
+    const int psmem[7] = {(int)prod_smem_bytes<true>(), (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<true>(),
                           (int)prod_smem_bytes<false>(), (int)prod_smem_bytes<false>(),
-                          (int)prod_smem_bytes<false, kBmWordsBig>()};
-    for (int i = 0; i < 6; ++i) {
+                          (int)prod_smem_bytes<false, kBmWordsBig>(), (int)prod_smem_bytes<false, kBmWordsBig>()};
+    for (int i = 0; i < 7; ++i) {
         err = cudaFuncSetAttribute(prods[i], cudaFuncAttributeMaxDynamicSharedMemorySize, psmem[i]);
         if (err != cudaSuccess) return err;
     }
@@ -2168,7 +2170,10 @@ static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
 
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len, bool wide_window) {
     if (P.n <= 0) return cudaSuccess;
-    if (P.inst) return table ? prod_launch<true, true, false>(P, st) : prod_launch<false, true, false>(P, st);
+    if (P.inst) {
+        if (table) return prod_launch<true, true, false>(P, st);
+        return wide_window ? prod_launch<false, true, false, kBmWordsBig>(P, st) : prod_launch<false, true, false>(P, st);
+    }
     if (table) return prod_launch<true, false, false>(P, st);
     // rows expected to span more columns than the bitmap covers: the wide
     // window (with every accumulator slot, as WIDE)

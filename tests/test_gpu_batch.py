@@ -254,3 +254,18 @@ def test_square_instances_in_a_mixed_batch(graph):
         assert alone.steps == g.steps, name
         for key in ("N", "q", "b", "g", "products", "z", "trunc", "budget", "nnz"):
             assert alone.info[key] == g.info[key], (name, key)
+
+
+def test_wide_column_window_in_a_repeated_batch():
+    # the 160 x 160 Laplacian's giant-step rows span about 6400 columns: the
+    # second batch of the same series runs those stages with the bitmap's
+    # wide column window; both batches give the oracle's results bit for bit
+    big = ocsr(syn.laplacian_2d(160))
+    small = ocsr(syn.banded_random(700, 6, 3, 2.0))
+    a = syn.coeffs("exp")
+    series = [psf.Series(a, 1e-12), psf.Series(a, 1e-12)]
+    refs = [psscf(big, a, 1e-12), psscf(small, a, 1e-12)]
+    for run in range(2):
+        got = psf.eval_batch(series, [dev(big), dev(small)])
+        for g, ref, name in zip(got, refs, ("lap2d 160", "banded")):
+            check_same(g, ref, f"{name} run {run}")
