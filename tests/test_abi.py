@@ -237,3 +237,22 @@ def test_torch_sparse_csr_round_trip_on_the_host():
         psf.DeviceCSR.from_torch(torch.zeros(3, 3))
     with pytest.raises(psf.PsfError):
         psf.DeviceCSR.from_torch(torch.zeros(3, 4).to_sparse_csr())
+
+
+def test_c_caller_compiles_links_and_plans(tmp_path):
+    # the header is plain C99 and the library serves a C caller (host-side
+    # entry points only: no GPU is touched)
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    lib = psf._build.build()
+    exe = str(tmp_path / "c_abi_check")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER),
+                    os.path.join(here, "c_abi_check.c"), lib, "-Wl,-rpath," + os.path.dirname(lib), "-o", exe],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.startswith("ok N=28 q=5 b=6 products=9"), out.stdout
