@@ -172,3 +172,25 @@ def test_s_override():
     assert (r.plan.q, r.plan.b) == (5, 4) and r.products == 7
     ref = fun_lap1d(256, -0.5, np.exp)
     assert norm1_dense(r.F.to_dense() - ref) <= 1e-12
+
+
+@pytest.mark.parametrize("w,kind", [(1, "exp"), (2, "exp"), (4, "exp"), (1, "cos"), (3, "cos")])
+def test_banded_normal_against_40_digit_reference(w, kind):
+    # the paper's second matrix family (banded, N(0, 1) entries), eps_tol =
+    # 1e-14, n = 40: within the tolerance (plus a few ulps of ||f(|Z|)||_1 for
+    # the rounding the first-order bound leaves out) of f(Z) computed in
+    # 40-digit arithmetic.  (At n = 60, w = 1 and 2, scipy's expm was off by
+    # 1e-12..1e-11 on these non-normal matrices, the filtered scheme by 3e-15
+    # and 2e-14: a library routine is not a tight enough pin here.)
+    mpmath = pytest.importorskip("mpmath")
+    n = 40
+    Z = csr(syn.banded_normal(n, w, 1000 * w + 3))
+    Zd = Z.to_dense()
+    r = psscf(Z, syn.coeffs(kind), 1e-14)
+    with mpmath.workdps(40):
+        M = mpmath.matrix(Zd.tolist())
+        E = mpmath.expm(M, method="taylor") if kind == "exp" else mpmath.cosm(M)
+        ref = np.array([[float(E[i, j]) for j in range(n)] for i in range(n)])
+    fa = scipy.linalg.expm(np.abs(Zd)) if kind == "exp" else scipy.linalg.coshm(np.abs(Zd))
+    margin = 8 * 2.0 ** -53 * norm1_dense(fa)
+    assert norm1_dense(r.F.to_dense() - ref) <= 1e-14 + margin, (w, kind)
