@@ -3,9 +3,9 @@
 Even series: f(Z) = g(Z^2) with c_k = a_{2k}; odd series: f(Z) = Z g(Z^2)
 with c_k = a_{2k+1}.  Algorithm 2 then runs on W = Z^2, with the norms of W
 bounded by z_{2i} of Z (Eq. 37 and Lemma 1 applied to Z).  Pinned by exact
-integer arithmetic, library routines (scipy's cosm, coshm, sinhm), the
-Kronecker closed form of the 2D Laplacian, and the relation between the
-truncation of the two plans.
+integer arithmetic, library routines (scipy's cosm, coshm, sinhm), f(Z) in
+40-digit arithmetic on non-normal matrices, the Kronecker closed form of the
+2D Laplacian, and the relation between the truncation of the two plans.
 """
 import math
 
@@ -153,3 +153,26 @@ def test_odd_single_term_is_a_scaled_copy_of_z():
     r = psscf(Z, syn.coeffs("sinh"), 10.0, square=True)
     assert r.plan.N == 1
     assert np.array_equal(r.F.to_dense(), Z.to_dense())
+
+
+@pytest.mark.parametrize("kind", ["cos", "cosh", "sinh"])
+def test_square_mode_on_banded_normal_against_40_digit_reference(kind):
+    # non-normal banded N(0, 1) matrices (the paper's second family), eps_tol =
+    # 1e-12: the substituted scheme is within the tolerance (plus a few ulps of
+    # ||f(|Z|)||_1 of rounding) of f(Z) in 40-digit arithmetic; sinh and cosh
+    # from (e^Z -/+ e^-Z) / 2
+    mpmath = pytest.importorskip("mpmath")
+    n = 30
+    Z = csr(syn.banded_normal(n, 2, 77))
+    Zd = Z.to_dense()
+    r = psscf(Z, syn.coeffs(kind), 1e-12, square=True)
+    with mpmath.workdps(40):
+        M = mpmath.matrix(Zd.tolist())
+        if kind == "cos":
+            E = mpmath.cosm(M)
+        else:
+            Ep, Em = mpmath.expm(M, method="taylor"), mpmath.expm(-M, method="taylor")
+            E = (Ep - Em) / 2 if kind == "sinh" else (Ep + Em) / 2
+        ref = np.array([[float(E[i, j]) for j in range(n)] for i in range(n)])
+    margin = 8 * 2.0 ** -53 * norm1_dense(scipy.linalg.coshm(np.abs(Zd)) + scipy.linalg.sinhm(np.abs(Zd)))
+    assert norm1_dense(r.F.to_dense() - ref) <= 1e-12 + margin, kind
