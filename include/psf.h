@@ -322,6 +322,10 @@ PSF_API int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out);
  * set to 0.  zeta/sigma may be NULL.  With PSF_Z_SQUARE the plan is that of
  * g in W = Z^2 (see the flag; tol / z_1 for an odd series, infinite when
  * z_1 = 0); info->z still lists the z_i of Z.
+ * Errors: PSF_EINVAL (null arguments, m < 1, tol, s, a non-finite
+ * coefficient, a norm that is negative or not finite, mixed parities with
+ * PSF_Z_SQUARE), PSF_ETOOBIG (m > 100000), PSF_ENOTCONV (Eq. 34 finds no
+ * truncation length within the m coefficients).
  */
 PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
              const double* norms, psf_info_t* info, double* zeta, double* sigma);

@@ -409,8 +409,13 @@ int psf_series_destroy(psf_series_t series) {
 int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags, const double* norms,
              psf_info_t* info, double* zeta, double* sigma) {
     if (!coeffs || m < 1 || !norms || !info) return fail(PSF_EINVAL, "null argument or m < 1");
+    if (m > 100000) return fail(PSF_ETOOBIG, "m = %lld coefficients (max 100000)", (long long)m);
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PSF_EINVAL, "tol must be finite and > 0");
     if (s < 0 || s > PSF_MAX_Q) return fail(PSF_EINVAL, "s out of range");
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(coeffs[i])) return fail(PSF_EINVAL, "coefficient %lld is not finite", (long long)i);
+    for (int i = 0; i <= ((flags & PSF_Z_SUBMULT) ? 1 : 10); ++i)
+        if (!(norms[i] >= 0.0) || !std::isfinite(norms[i])) return fail(PSF_EINVAL, "norm z_%d must be finite and >= 0", i);
     std::vector<double> a(coeffs, coeffs + m);
     const bool square = flags & PSF_Z_SQUARE;
     bool odd = false;

@@ -256,3 +256,17 @@ def test_c_caller_compiles_links_and_plans(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stdout + out.stderr
     assert out.stdout.startswith("ok N=28 q=5 b=6 products=9"), out.stdout
+
+
+def test_host_planner_rejects_bad_inputs():
+    norms = [1.0] + [2.0 ** i for i in range(1, 11)]
+    a = syn.coeffs("exp")
+    for bad_a, bad_n, code in ((a[:5] + [float("nan")] + a[6:], norms, _abi.PSF_EINVAL),
+                               (a, norms[:3] + [-1.0] + norms[4:], _abi.PSF_EINVAL),
+                               (a, norms[:2] + [float("inf")] + norms[3:], _abi.PSF_EINVAL),
+                               ([1e-30] * 100001, norms, _abi.PSF_ETOOBIG)):
+        with pytest.raises(psf.PsfError) as e:
+            psf.plan(bad_a, 1e-12, bad_n)
+        assert e.value.code == code
+    # SUBMULT reads only z_0 and z_1
+    psf.plan(a, 1e-12, [1.0, 2.0] + [float("nan")] * 9, submult=True)
