@@ -236,6 +236,9 @@ PSF_API int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, int3
  *   (destroy it with psf_result_destroy before psf_server_destroy).
  * psf_server_destroy: waits for the requests in flight and drops the
  *   completions not polled (their results are destroyed).
+ * Errors: PSF_EINVAL (null arguments, more than 64 workers, max_batch above
+ * 1024, a PSF_Z_ESTIMATE series or a malformed Z size on submit), PSF_ENOMEM,
+ * PSF_ECUDA.  A request's own failure is its completion's status.
  */
 typedef struct psf_server_s* psf_server_t;
 
@@ -279,6 +282,10 @@ PSF_API int psf_server_destroy(psf_server_t server);
  * with eps_g = threshold / (1 + e_r), so the dropped 1-norm is <= threshold;
  * threshold == 0 keeps every nonzero entry.  Synchronizes `stream` once.
  * Limits: nadd <= PSF_MAX_Q + 1.
+ * Errors: PSF_EINVAL (malformed or mismatched matrices, nadd out of range,
+ * a threshold that is negative or not finite),
+ * PSF_ENOTCONV (Algorithm 1 reached maxit passes), PSF_ETOOBIG (the product
+ * needs more than 2^31 - 2^20 pool entries), PSF_ENOMEM, PSF_ECUDA.
  */
 PSF_API int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, const double* alphas,
                        const psf_csr_t* const* addends, double threshold, double e_r,

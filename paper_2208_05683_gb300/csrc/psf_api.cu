@@ -491,7 +491,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     if ((A == nullptr) != (B == nullptr)) return fail(PSF_EINVAL, "A and B must both be given or both be null");
     if (nadd < 0 || nadd > kMaxAdd) return fail(PSF_EINVAL, "nadd = %d out of [0, %d]", nadd, kMaxAdd);
     if (nadd > 0 && (!alphas || !addends)) return fail(PSF_EINVAL, "null addend arrays");
-    if (!(threshold >= 0.0)) return fail(PSF_EINVAL, "threshold must be >= 0");
+    if (!(threshold >= 0.0) || !std::isfinite(threshold)) return fail(PSF_EINVAL, "threshold must be finite and >= 0");
     if (threshold > 0.0 && (!(e_r > 0.0) || !std::isfinite(e_r))) return fail(PSF_EINVAL, "e_r must be > 0");
     if (maxit < 1) return fail(PSF_EINVAL, "maxit must be >= 1");
     int n = -1;

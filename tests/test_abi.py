@@ -270,3 +270,15 @@ def test_host_planner_rejects_bad_inputs():
         assert e.value.code == code
     # SUBMULT reads only z_0 and z_1
     psf.plan(a, 1e-12, [1.0, 2.0] + [float("nan")] * 9, submult=True)
+
+
+def test_product_filter_host_checks():
+    # argument checks that precede any device work
+    import ctypes
+    L = psf.lib()
+    out = ctypes.c_void_p()
+    for thr, word in ((float("inf"), "threshold"), (float("nan"), "threshold"), (-1.0, "threshold")):
+        rc = L.psf_product_filter(None, None, 0, None, None, thr, 0.1, 10, None, ctypes.byref(out))
+        assert rc == _abi.PSF_EINVAL and word in L.psf_last_error().decode()
+    rc = L.psf_product_filter(None, None, _abi.PSF_MAX_Q + 2, None, None, 0.0, 0.1, 10, None, ctypes.byref(out))
+    assert rc == _abi.PSF_EINVAL and "nadd" in L.psf_last_error().decode()
