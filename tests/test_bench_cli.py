@@ -40,3 +40,21 @@ def test_reference_arm_other_ranks_exit_without_work():
                     {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}, timeout=120)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
+
+
+def test_clock_summary_keeps_the_timed_window():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    #        index, sm, max, power, active, hw_slow, hw_therm, sw_therm, sw_power_cap
+    idle = ["0", "1400", "2070", "300", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]
+    busy = ["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]
+    capped = ["0", "1900", "2070", "1400", "0x4", "Not Active", "Not Active", "Not Active", "Active"]
+    c.rows = [(0.0, idle), (1.0, busy), (1.05, capped), (1.1, busy), (5.0, idle)]
+    c.mark(0.9, 1.08)
+    s = c.summary()
+    # samples up to one period after the window's end belong to it
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    c.mark(2.0, 3.0)
+    assert c.summary()["reasons"] == ["unsampled"]
