@@ -282,3 +282,13 @@ def test_product_filter_host_checks():
         assert rc == _abi.PSF_EINVAL and word in L.psf_last_error().decode()
     rc = L.psf_product_filter(None, None, _abi.PSF_MAX_Q + 2, None, None, 0.0, 0.1, 10, None, ctypes.byref(out))
     assert rc == _abi.PSF_EINVAL and "nadd" in L.psf_last_error().decode()
+
+
+def test_binding_constants_match_the_header():
+    # every numeric #define of the header has the same value in the binding
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"^#define (PSF_[A-Z0-9_]+) (\d+)u?\b", text, flags=re.M))
+    assert len(defs) >= 25
+    for name, value in defs.items():
+        assert hasattr(_abi, name), name
+        assert getattr(_abi, name) == int(value), name
