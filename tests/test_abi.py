@@ -292,3 +292,32 @@ def test_binding_constants_match_the_header():
     for name, value in defs.items():
         assert hasattr(_abi, name), name
         assert getattr(_abi, name) == int(value), name
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    # the ctypes structures of the binding have the C structs' sizes and
+    # field offsets (as the C compiler lays them out from the header)
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = str(tmp_path / "c_abi_layout")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER),
+                    os.path.join(here, "c_abi_layout.c"), "-o", exe], check=True, capture_output=True, text=True)
+    lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {}
+    for line in filter(None, lines):
+        t, f, v = line.split()
+        c[(t, f)] = int(v)
+    pairs = {"psf_csr_t": _abi.CSRStruct, "psf_info_t": _abi.InfoStruct, "psf_step_info_t": _abi.StepStruct,
+             "psf_server_config_t": _abi.ServerConfig, "psf_completion_t": _abi.Completion,
+             "psf_server_stats_t": _abi.ServerStats}
+    for t, S in pairs.items():
+        assert ctypes.sizeof(S) == c[(t, "-")], t
+        fields = [f for f, _ in S._fields_]
+        assert {f for (tt, f) in c if tt == t and f != "-"} == set(fields), t
+        for f in fields:
+            assert getattr(S, f).offset == c[(t, f)], (t, f)
