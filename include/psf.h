@@ -121,7 +121,7 @@ typedef struct {
                            its step record still lists its product's count */
 } psf_info_t;
 
-/* Statistics of one filtered product (Alg. 2 l.5-6 or l.11-12). */
+/* Statistics of one filtered product of Algorithm 2 (a baby step, Eq. 11, or a giant step, Eq. 14). */
 typedef struct {
     int32_t kind;       /* 0 baby step (Eq. 11), 1 giant step (Eq. 14), 2 plain add,
                            3 the unfiltered F = Z G of an odd series (PSF_Z_SQUARE) */
@@ -304,18 +304,26 @@ PSF_API int psf_norm1(const psf_csr_t* M, void* stream, double* out);
  * that freeing device memory implies.
  *
  * Instead of a workspace per call, it uses one scratch region compiled into
- * the library (a static device array of about 4.3 MB: the fixed-point column
- * sums of PSF_NORM1_NOALLOC_MAX_N columns and a control block), and it reads
- * M's entries in place.
+ * the library: a static device array of 4,456,960 bytes (4.25 MiB) holding
+ * the fixed-point column sums of PSF_NORM1_NOALLOC_MAX_N columns and a
+ * control block, which every device that loads the library keeps until the
+ * process exits.  It reads M's entries in place.
  *  - M: device CSR, n <= PSF_NORM1_NOALLOC_MAX_N (else PSF_ETOOBIG, nothing
  *    is launched); malformed input gives PSF_EINVAL as for psf_norm1.
- *  - out: host pointer, receives the norm; the call synchronizes `stream`.
+ *  - out: host pointer, receives the norm.  Every call copies the result to
+ *    host memory and synchronizes `stream`, so it can never be called on a
+ *    stream that is being captured into a CUDA graph.
  *  - The first call on a device (with that device current) looks up the
- *    scratch region's address and configures the kernels; make it before any
- *    stream capture.  Later calls only launch kernels and copy 12 bytes back.
+ *    scratch region's address and configures the kernels, which may load the
+ *    library's device code; while another stream captures in global mode
+ *    that would invalidate the capture, so make the first call before any
+ *    capture starts.  The address is kept for the life of the process: do
+ *    not call it again after cudaDeviceReset() on that device.
  *  - The scratch region is shared: calls that overlap in time on one device
  *    (several threads, or several streams without ordering between them)
- *    race on it and give wrong results.  Serialize them.
+ *    race on it and give wrong results.  Serialize them.  Each call clears
+ *    the parts that must start at zero, so what a previous call left there
+ *    does not matter.
  */
 #define PSF_NORM1_NOALLOC_MAX_N 65536
 PSF_API int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out);

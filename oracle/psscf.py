@@ -16,7 +16,7 @@ from .sparse import CSR, alg1, axpy, matmul_add, norm1
 class StepStat:
     kind: str  # "baby" (Eq. 11), "giant" (Eq. 14) or "odd" (F = Z G-hat, square mode)
     index: int  # k of Z-hat_(k) or i of S-hat_i
-    threshold: float  # the bound passed to Alg. 2 l.6 / l.12 (0 = unfiltered)
+    threshold: float  # the bound the filter of this step must meet in Algorithm 2 (0 = unfiltered)
     nnz_pre: int
     nnz_post: int
     eps_f: float
@@ -45,7 +45,7 @@ def power_norms(Z: CSR):
 
 def block(a, N: int, q: int, i: int, Zh: dict, n: int) -> CSR:
     """B-hat_i = sum_{j=0}^{q-1} a_{iq+j} Z-hat_(j), Z-hat_(0) = I (Eq. 13,
-    Alg. 2 l.8/10), accumulated in ascending j; not filtered."""
+    Algorithm 2), accumulated in ascending j; not filtered."""
     X = None
     for j in range(q):
         idx = i * q + j

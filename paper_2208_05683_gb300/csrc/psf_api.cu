@@ -1242,10 +1242,14 @@ constexpr size_t kNaSticky = kNaSlot + round256(sizeof(NormSlot));
 constexpr size_t kNaWords = kNaSticky + round256(sizeof(unsigned) * kNaMaxN);
 constexpr size_t kNaBytes = kNaWords + sizeof(unsigned long long) * kChunks * kNaMaxN;
 
+// psf.h states this size; a change to the control block, kChunks or the
+// column limit must update it there too.
+static_assert(kNaBytes == 4456960, "the scratch size stated in psf.h");
 static __device__ __align__(256) unsigned char g_norm1_scratch[kNaBytes];
 
 // Device address of the scratch region, looked up once per device (with
-// that device current) and kept; the lookup is the call that may initialise
+// that device current) and kept for the life of the process (a
+// cudaDeviceReset would make it stale); the lookup is the call that may load
 // the module, which is why the first call belongs before any stream capture.
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mu;

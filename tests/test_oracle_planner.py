@@ -137,3 +137,27 @@ def test_plan_lap1d_values():
     exact = sum(Fraction(2) ** i / math.factorial(i) for i in range(20, 200))
     assert p.trunc == pytest.approx(float(exact), rel=1e-14)
     assert p.budget == 1e-12 - p.trunc
+
+
+def sig2(x):
+    return float(f"{x:.1e}")
+
+
+def test_plan_workload_thresholds_hand_derived():
+    # Thresholds of the two Laplacian workloads, derived by hand from
+    # Eqs. (24)-(26), (34) and (36) with the closed-form norms z_i = 2^i
+    # (1D, n = 256) and z_i = 4^i (2D, 128 x 128), eps_tol = 1e-12, in a
+    # calculation independent of this planner; kept to 2 significant digits.
+    Z1 = CSR(256, *syn.laplacian_1d(256))
+    p = planner.plan(syn.coeffs("exp"), 1e-12, power_norms(Z1))
+    assert (p.N, p.q, p.b, p.g) == (20, 4, 5, 0)
+    assert sig2(p.trunc) == 4.8e-13
+    assert {k: sig2(v) for k, v in p.zeta.items()} == {2: 6.6e-14, 3: 2.5e-13, 4: 1.1e-12}
+    assert {j: sig2(v) for j, v in p.sigma.items()} == {1: 1.8e-17, 2: 2.9e-16, 3: 4.7e-15, 4: 7.5e-14}
+    Z2 = CSR(128 * 128, *syn.laplacian_2d(128))
+    n2 = power_norms(Z2)
+    pe = planner.plan(syn.coeffs("exp"), 1e-12, n2)
+    assert (pe.N, pe.q, pe.b, pe.g) == (28, 5, 6, 0)
+    assert sig2(pe.sigma[1]) == 7.3e-26 and sig2(pe.sigma[5]) == 8.1e-14
+    pc = planner.plan(syn.coeffs("cos"), 1e-12, n2)
+    assert (pc.N, pc.q, pc.b, pc.g) == (27, 5, 6, 0)

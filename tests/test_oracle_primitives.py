@@ -143,9 +143,61 @@ def test_alg1_single_pass_and_degenerate_thresholds():
     # eps_g >= 1 still runs the first pass (reading: c_0 = +inf)
     rb = alg1(C, 100.0, 0.1)
     assert rb.iters == 1 and rb.kept.nnz == 0 and rb.c == math.fsum([0.01, 4.0])  # column 1
-    # ties at eps_f are dropped: keep means |x| > eps_f strictly
+    # ties at eps_f are dropped: keep means |x| > eps_f strictly, and the
+    # dropped tie counts in c (c is the norm of every entry not kept)
     rt = alg1(CSR.from_dense(np.array([[1.0, 0.0], [0.0, 0.5]])), 1.0, 10.0)
     assert rt.kept.nnz == 0
+    assert rt.iters == 1 and rt.c == 1.0
+
+
+# Hand traces with more passes.  Every value below is a multiple of 1/20 or a
+# power of two, so the column sums are exact and the trace can be done on
+# paper; several entries sit exactly on a later eps_f, so the ties decide the
+# column sums (and with them the whole trajectory) at every pass.
+#
+#   column 0: 1.0, 0.5, 0.5     column 2: 0.25, 0.25, 0.25
+#   column 1: 0.5, 0.5, 0.5     column 3: 0.3, 0.3, 0.3, 0.3 (4 x 4 case only)
+#
+# eps_g = 1, e_r = 0.1, loop while c > 1.1:
+#   pass 1: eps_f = 1        candidates: every entry (1.0 is a tie)
+#           sums 2.0, 1.5, 0.75 (, 1.2)  -> c_1 = 2.0, m_1 = 2
+#   pass 2: eps_f = 1/2      candidates: the 0.5 ties, 0.25, 0.3
+#           sums 1.0, 1.5, 0.75 (, 1.2)  -> c_2 = 1.5, m_2 = 3
+#   pass 3: eps_f = fl(1/3)  candidates: 0.25 (, 0.3)
+#           sums 0, 0, 0.75 (, 1.2)      -> 3 x 3: c_3 = 0.75, stop
+#                                           4 x 4: c_3 = 1.2, m_3 = 1.2 / fl(1/3)
+#   pass 4: eps_f = 1 / m_3  (0.2777...) candidates: 0.25 only
+#           sums 0, 0, 0.75, 0           -> c_4 = 0.75, stop
+# Keeping the ties in c_1 and c_2 matters: without the tie 1.0 in pass 1 the
+# trace would take c_1 = 1.5 and eps_f = 2/3 next.
+COLS3 = [[1.0, 0.5, 0.25], [0.5, 0.5, 0.25], [0.5, 0.5, 0.25]]
+
+
+def test_alg1_hand_worked_three_passes_with_ties():
+    r = alg1(CSR.from_dense(np.array(COLS3)), 1.0, 0.1)
+    assert r.iters == 3
+    assert r.eps_f == 1.0 / 3.0  # eps_g / m_2 with m_2 = c_2 / eps_f = 1.5 / 0.5 = 3
+    assert r.c == 0.75
+    np.testing.assert_array_equal(
+        r.kept.to_dense(), np.array([[1.0, 0.5, 0.0], [0.5, 0.5, 0.0], [0.5, 0.5, 0.0]]))
+
+
+def test_alg1_hand_worked_four_passes_with_ties():
+    D = np.zeros((5, 5))
+    D[:3, :3] = COLS3
+    D[:4, 3] = 0.3
+    D[0, 4], D[4, 4] = 4.0, 3.0  # never candidates
+    r = alg1(CSR.from_dense(D), 1.0, 0.1)
+    assert r.iters == 4
+    eps_f3 = 1.0 / 3.0
+    m_3 = 1.2 / eps_f3  # c_3 = 0.3 * 4 exactly rounded = fl(1.2); m_3 rounds to fl(3.6)
+    assert m_3 == 3.6
+    assert r.eps_f == 1.0 / 3.6
+    assert 0.25 < r.eps_f < 0.3
+    assert r.c == 0.75
+    K = D.copy()
+    K[:3, 2] = 0.0
+    np.testing.assert_array_equal(r.kept.to_dense(), K)
 
 
 @pytest.mark.parametrize("seed", range(8))

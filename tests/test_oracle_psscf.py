@@ -22,7 +22,7 @@ def test_exp_lap1d_n256_within_tol_of_dst_closed_form():
     ref = fun_lap1d(256, -0.5, np.exp)
     err = norm1_dense(r.F.to_dense() - ref)
     assert err <= 1e-12
-    # every filter respected its bound (Alg. 2 l.6 / l.12)
+    # every filter respected its bound (Algorithm 2, Eqs. 11 and 14)
     for s in r.steps:
         assert s.c <= s.threshold
         assert s.nnz_post <= s.nnz_pre

@@ -1,16 +1,19 @@
 """psf_norm1_noalloc: the exact 1-norm computed in the library's static
 scratch region, without allocating, called through the C ABI.
 
-It must give what psf_norm1 gives (the test tolerance is bitwise equality:
-both round the exact column sums correctly), on two calls in a row, whether
-this file runs alone in a fresh process or after every other test.  The
-file name sorts last so that the latter is the default order.
+It must give what psf_norm1 gives and what the CPU oracle's exact 1-norm
+gives (the test tolerance is bitwise equality: all three round the exact
+column sums correctly), on two calls in a row, whether this file runs alone
+in a fresh process or after every other test, and it must take no memory
+from the device's memory pool, from which the library's other entry points
+allocate.  The file name sorts last so that the latter is the default order.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synthetic as syn
 from gpu_helpers import dev
 
@@ -47,16 +50,70 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_noalloc_norm_equals_norm1_twice(case):
-    M = dev(CASES[case]())
+def test_noalloc_norm_equals_norm1_and_oracle_twice(case):
+    rp, col, val = CASES[case]()
+    expect = oracle.norm1(oracle.CSR(len(rp) - 1, rp, col, val))
+    M = dev((rp, col, val))
     L = psf.lib()
     rc, ref = c_norm1(L.psf_norm1, M)
     assert rc == _abi.PSF_OK
+    assert ref == expect
     for _ in range(2):
         rc, got = c_norm1(L.psf_norm1_noalloc, M)
         assert rc == _abi.PSF_OK, L.psf_last_error()
-        assert abs(got - ref) <= 1e-12 * abs(ref)
-        assert got == ref
+        assert abs(got - expect) <= 1e-12 * abs(expect)
+        assert got == expect
+
+
+# The library allocates its device memory with cudaMallocAsync from the
+# device's default memory pool.  The pool's in-use high-water mark, reset
+# before a call, shows whether the call took any memory from it, even memory
+# it gave back before returning.
+_USED_MEM_CURRENT, _USED_MEM_HIGH = 7, 8  # CUmemPool_attribute
+
+
+def _default_pool():
+    import torch
+    cu = ctypes.CDLL("libcuda.so.1")
+    d = ctypes.c_int()
+    assert cu.cuDeviceGet(ctypes.byref(d), torch.cuda.current_device()) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), d) == 0
+    return cu, pool
+
+
+def _pool_attr(cu, pool, attr):
+    v = ctypes.c_uint64()
+    assert cu.cuMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+    return v.value
+
+
+def _pool_high_after(cu, pool, call):
+    import torch
+    torch.cuda.synchronize()
+    cur = _pool_attr(cu, pool, _USED_MEM_CURRENT)
+    zero = ctypes.c_uint64(0)
+    assert cu.cuMemPoolSetAttribute(pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0
+    call()
+    torch.cuda.synchronize()
+    return cur, _pool_attr(cu, pool, _USED_MEM_HIGH), _pool_attr(cu, pool, _USED_MEM_CURRENT)
+
+
+def test_noalloc_takes_no_pool_memory():
+    M = dev(syn.laplacian_2d(96))
+    L = psf.lib()
+    cu, pool = _default_pool()
+    assert c_norm1(L.psf_norm1_noalloc, M)[0] == _abi.PSF_OK  # set-up done
+    # control: the allocating entry point raises the high-water mark
+    cur, high, after = _pool_high_after(cu, pool, lambda: c_norm1(L.psf_norm1, M))
+    assert high > cur
+    # two calls in a row take nothing
+    def twice():
+        for _ in range(2):
+            rc, got = c_norm1(L.psf_norm1_noalloc, M)
+            assert rc == _abi.PSF_OK and got == 4.0
+    cur, high, after = _pool_high_after(cu, pool, twice)
+    assert high <= cur and after == cur
 
 
 def test_noalloc_limits_and_bad_input():
