@@ -145,6 +145,57 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self_rows)}
 
 
+def config_dict(n: int, nnz: int, world: int) -> dict:
+    """The workload's config, the same in both arms."""
+    return {"workload": f"{WORKLOAD} exp+cos tol {TOL:g}", "n": n, "nnz": nnz, "evals_per_step": len(KINDS),
+            "l2": "flushed before each step (256 MB write)", "parallelism": f"replicas x{world}"}
+
+
+def fp64_peak_tflops(L, stream_ptr):
+    """This GPU's FP64 fma rate, measured by the library's probe kernel
+    (falls back to the nominal unit count x clock if the probe fails)."""
+    import ctypes
+    v = ctypes.c_double()
+    if L.psf_fp64_peak(stream_ptr, ctypes.byref(v)) == 0 and v.value > 0.0:
+        return v.value, "measured: psf_fp64_peak (8 independent fma chains per thread, 4 x 256 threads per SM)"
+    return FP64_PEAK_TFLOPS, "nominal: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
+
+
+def _oracle_eval_worker(task):
+    """One oracle evaluation in a worker process (the CPU baseline on all cores)."""
+    import oracle
+    import synthetic as syn
+    rp, col, val, kind = task
+    t0 = time.perf_counter()
+    oracle.psscf(oracle.CSR(len(rp) - 1, rp, col, val), syn.coeffs(kind), TOL)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(rp, col, val):
+    """The oracle as it stands on every host core: one evaluation per worker
+    process (exp and cos alternating), evaluations being independent; the
+    rate is evaluations over the wall time once the workers are up."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx) as ex:
+        list(ex.map(_noop, range(cores)))  # workers started and imports done
+        tasks = [(rp, col, val, KINDS[i % len(KINDS)]) for i in range(cores)]
+        t0 = time.perf_counter()
+        per = list(ex.map(_oracle_eval_worker, tasks))
+        dt = time.perf_counter() - t0
+    return {"value": cores / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} evaluations of the full {WORKLOAD} workload (exp and cos alternating), one per "
+                      f"worker process, {dt:.1f} s wall; single evaluation median {statistics.median(per):.2f} s"}
+
+
+def _noop(x):
+    import oracle  # noqa: F401
+    import synthetic  # noqa: F401
+    return x
+
+
 def make_inputs():
     import synthetic as syn
     rp, col, val = syn.workload(WORKLOAD)[0]
@@ -190,8 +241,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} exp+cos tol {TOL:g}", "n": Z.n, "nnz": Z.nnz,
-                   "evals_per_step": len(KINDS), "parallelism": "single host thread"},
+        "config": config_dict(Z.n, Z.nnz, world),
         "p50_ms": statistics.median(lat), "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} steps of exp+cos on the full workload"},
@@ -201,6 +251,7 @@ def run_reference(args):
 
 
 def run_psf(args):
+    import ctypes
     import numpy as np
     import torch
 
@@ -245,6 +296,8 @@ def run_psf(args):
                 lat.append(e0.elapsed_time(e1))
             _abi.check(L.psf_result_destroy(h))
 
+    fp64_peak, fp64_source = fp64_peak_tflops(L, ctypes.c_void_p(stream.cuda_stream))
+
     # the product kernel's slot-map crossover, timed on this workload (outside
     # the timed region; results do not depend on it)
     tuned = None
@@ -276,7 +329,6 @@ def run_psf(args):
     value, total_ms = job_rate(evals, sum(lat), world, dev)
 
     # ---- roofline of the product kernel (event-timed launches, separate pass)
-    import ctypes
     _abi.check(L.psf_profile(1))
     for _ in range(2):
         flush.zero_()
@@ -295,10 +347,10 @@ def run_psf(args):
         pass
     # DRAM rate of the product kernel: ncu bytes per launch x launches / event-timed duration
     dram_gbs = traffic * nl.value / (ms.value / 1e3) / 1e9 if traffic and ms.value > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_product",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": "k_product",
                 "dram_gbs": dram_gbs, "dram_frac_of_hbm": dram_gbs / hbm_peak_gbs() if dram_gbs else None,
-                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "peak_source": fp64_source, "peak_nominal": FP64_PEAK_TFLOPS,
                 "launches_timed": nl.value, "kernel_ms": ms.value, "algorithmic_fma": fma.value}
 
     # ---- end to end through the C ABI on host buffers: psf_eval_from_host
@@ -347,27 +399,11 @@ def run_psf(args):
             d2h = copied
     e2e_value, _ = job_rate(len(KINDS) * len(e2e_ms), sum(e2e_ms), world, dev)
 
-    # ---- dense FP64 PS on the same GPU: product count x measured DGEMM time
+    # ---- dense FP64 PS on the same GPU, run for real (same plan), with its
+    # accuracy against the closed form beside the sparse result's
     dense = None
     if not args.no_dense and rank == 0:
-        A = torch.randn(n, n, dtype=torch.float64, device=dev)
-        B = torch.randn(n, n, dtype=torch.float64, device=dev)
-        torch.matmul(A, B)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        C = torch.matmul(A, B)
-        e1.record()
-        e1.synchronize()
-        t_gemm = e0.elapsed_time(e1) / 1e3
-        del A, B, C
-        torch.cuda.empty_cache()
-        prods = {k: psf.plan(syn.coeffs(k), TOL, [4.0 ** i for i in range(11)])["products"] for k in KINDS}
-        t_eval = sum(prods.values()) * t_gemm / len(KINDS)
-        dense = {"evals_per_s": 1.0 / t_eval, "dgemm_s": t_gemm, "dgemm_tflops": 2.0 * n ** 3 / t_gemm / 1e12,
-                 "products_per_eval": prods,
-                 "how": "dense FP64 PS time = products x one measured torch.matmul float64 n x n"}
+        dense = measure_dense_ps(args, dev)
 
     # ---- the same workload with ||Z^2||..||Z^10|| estimated (PSF_Z_ESTIMATE)
     # instead of computed from the powers: an option's cost, not the headline
@@ -398,8 +434,9 @@ def run_psf(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(rp, col, val)
+        cpu["all_cores"] = cpu_baseline_all_cores(rp, col, val)
     batched = serving = sweep = None
-    if rank == 0 and world == 1 and args.sweep:
+    if rank == 0 and world == 1 and not args.no_sweep:
         sweep = measure_tol_sweep(args, dev)
     if rank == 0 and world == 1 and not args.no_batched:
         batched = measure_batched(args, dev, flush)
@@ -412,10 +449,8 @@ def run_psf(args):
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} exp+cos tol {TOL:g}", "n": n, "nnz": int(len(col)),
-                       "evals_per_step": len(KINDS), "l2": "flushed before each step (256 MB write)",
-                       "kernel": args.kernel, "autotune": tuned,
-                       "parallelism": f"replicas x{world}"},
+            "config": config_dict(n, int(len(col)), world),
+            "kernel": args.kernel, "autotune": tuned,
             "p50_ms": statistics.median(lat_sorted),
             "p99_ms": lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))],
             "roofline": roofline,
@@ -433,6 +468,123 @@ def run_psf(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def lap1d_closed_form(m: int, kind: str):
+    """f(A) for A = -0.5 tridiag(-1, 2, -1) (m x m) through its sine eigenbasis:
+    A = V diag(-(1 - cos(k pi / (m + 1)))) V with V the orthonormal DST-I
+    matrix; kind exp, cos or sin."""
+    import numpy as np
+    k = np.arange(1, m + 1)
+    V = np.sqrt(2.0 / (m + 1)) * np.sin(np.outer(k, k) * np.pi / (m + 1))
+    lam = -(1.0 - np.cos(k * np.pi / (m + 1)))
+    f = {"exp": np.exp, "cos": np.cos, "sin": np.sin}[kind](lam)
+    return (V * f) @ V
+
+
+def dense_ps(Zd, a, N: int, q: int, b: int):
+    """Unfiltered Paterson-Stockmeyer (Eqs. 2-4) on dense FP64 matrices with
+    torch.matmul: powers Z^2..Z^q, S_0 = B_{b-1}, S_i = B_{b-1-i} + Z^q S_{i-1},
+    B_i = sum_j a_{iq+j} Z^j (a_k = 0 for k >= N)."""
+    import torch
+    n = Zd.shape[0]
+    P = [torch.eye(n, dtype=torch.float64, device=Zd.device), Zd]
+    for _ in range(2, q + 1):
+        P.append(Zd @ P[-1])
+
+    def block(i):
+        B = torch.zeros_like(Zd)
+        for j in range(q):
+            if i * q + j < N and a[i * q + j] != 0.0:
+                B.add_(P[j], alpha=a[i * q + j])
+        return B
+
+    S = block(b - 1)
+    for i in range(1, b):
+        S = block(b - 1 - i) + P[q] @ S
+    return S
+
+
+def measure_dense_ps(args, dev):
+    """Dense FP64 PS (torch.matmul, cuBLAS) with the sparse scheme's own plan
+    (N, q, b) on the 2D Laplacian: event-timed at 64 x 64 (n = 4096, the same
+    plan as the 128 x 128 workload, ||Z||_1 = 4), with the 1-norm errors of the
+    dense and of the filtered sparse result against the closed form
+    exp/cos(A + B) of the Kronecker sum; the workload's n = 16384 projected by
+    n^3 (or run with --dense-full); and the 1D Laplacian n = 256 the same way."""
+    import numpy as np
+    import torch
+    import paper_2208_05683_gb300 as psf
+    import synthetic as syn
+
+    def dense_of(csr, n):
+        rp, col, val = (torch.as_tensor(np.asarray(x)).to(dev) for x in csr)
+        rows = torch.repeat_interleave(torch.arange(n, device=dev), (rp[1:] - rp[:-1]).long())
+        X = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        X[rows, col.long()] = val.double()
+        return X
+
+    def rel1(X, F):
+        return float(torch.linalg.matrix_norm(X - F, ord=1) / torch.linalg.matrix_norm(F, ord=1))
+
+    def timed_dense(Zd, a, p, reps=2):
+        dense_ps(Zd, a, p["N"], p["q"], p["b"])  # warm-up
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            D = dense_ps(Zd, a, p["N"], p["q"], p["b"])
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return D, min(ms)
+
+    def case(host, n, exact, kind):
+        a = syn.coeffs(kind)
+        Z = psf.DeviceCSR.from_host(*host, device=dev)
+        s = psf.Series(a, TOL)
+        s.eval(Z)
+        r = s.eval(Z)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            r = s.eval(Z)
+        torch.cuda.synchronize()
+        sparse_ms = (time.perf_counter() - t0) / 3 * 1e3
+        p = r.info
+        Zd = dense_of(host, n)
+        D, dense_ms = timed_dense(Zd, a, p)
+        F = exact.to(dev)
+        out = {"n": n, "kind": kind, "N": p["N"], "q": p["q"], "b": p["b"], "dense_ms": dense_ms,
+               "dense_evals_per_s": 1e3 / dense_ms, "sparse_ms": sparse_ms, "speedup_sparse": dense_ms / sparse_ms,
+               "dense_err_1": rel1(D, F), "sparse_err_1": rel1(dense_of(r.csr.to_host(), n), F),
+               "dense_density": float((D != 0).sum()) / n / n}
+        del D, Zd, F
+        torch.cuda.empty_cache()
+        return out
+
+    rows = []
+    m = 64
+    e1 = {k: torch.as_tensor(lap1d_closed_form(m, k)) for k in ("exp", "cos", "sin")}
+    exact2d = {"exp": torch.kron(e1["exp"], e1["exp"]),
+               "cos": torch.kron(e1["cos"], e1["cos"]) - torch.kron(e1["sin"], e1["sin"])}
+    for kind in KINDS:
+        rows.append(case(syn.laplacian_2d(m), m * m, exact2d[kind], kind))
+    rows.append(case(syn.laplacian_1d(256), 256, torch.as_tensor(lap1d_closed_form(256, "exp")), "exp"))
+    full = None
+    if args.dense_full:
+        M = 128
+        E = torch.as_tensor(lap1d_closed_form(M, "exp"))
+        full = case(syn.laplacian_2d(M), M * M, torch.kron(E, E), "exp")
+    per_kind = [r for r in rows if r["n"] == m * m]
+    proj_ms = sum(r["dense_ms"] for r in per_kind) / len(per_kind) * (128 * 128 / (m * m)) ** 3
+    return {"rows": rows, "full_size": full, "evals_per_s": 1e3 / proj_ms if full is None else 1e3 / full["dense_ms"],
+            "measured_at_full_size": full is not None,
+            "projected_n16384_ms": proj_ms,
+            "how": "dense PS run with torch.matmul float64 and the sparse plan's N, q, b; errors are relative "
+                   "1-norm errors against the closed form of the 2D/1D Laplacian; n = 16384 projected from "
+                   "n = 4096 by n^3 unless --dense-full"}
 
 
 def measure_batched(args, dev, flush):
@@ -835,9 +987,11 @@ def main():
     ap.add_argument("--no-estimate", action="store_true", help="skip the estimated-norms (PSF_Z_ESTIMATE) measurement")
     ap.add_argument("--no-square", action="store_true",
                     help="skip the cos/sinh measurement with the W = Z^2 substitution (PSF_Z_SQUARE)")
-    ap.add_argument("--serving-requests", type=int, default=300, help="requests of the serving measurement")
-    ap.add_argument("--sweep", action="store_true",
-                    help="add the tolerance sweep of the banded n = 65536 workload against dense PS")
+    ap.add_argument("--serving-requests", type=int, default=10000, help="requests of the serving measurement")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the tolerance sweep of the banded n = 65536 workload against dense PS")
+    ap.add_argument("--dense-full", action="store_true",
+                    help="also run dense FP64 PS at the workload's full size (n = 16384, about a minute)")
     ap.add_argument("--e2", action="store_true",
                     help="run the paper's banded N(0,1) experiment (n = 1000, w = 1..15) and exit")
     ap.add_argument("--e2-seeds", type=int, default=30, help="matrices per bandwidth in --e2")

@@ -48,6 +48,7 @@ extern "C" {
                            (Eq. 34), or Algorithm 1 reached its pass cap */
 #define PSF_ETIMEOUT 5  /* a bounded device-side wait expired */
 #define PSF_ETOOBIG 6   /* a size exceeds a documented limit (e.g. nnz >= 2^31) */
+#define PSF_ECANCELED 7 /* a server request was cancelled before it was admitted */
 
 /* ---- series flags (psf_series_create) ---- */
 #define PSF_SERIES 0u        /* power series: N from Eq. (34), thresholds Eq. (36) */
@@ -262,6 +263,7 @@ typedef struct {
     int32_t max_concurrent;  /* most batches in flight at once */
     int32_t pending;         /* waiting for admission */
     int64_t budget_peak;     /* most predicted bytes in flight at once */
+    int64_t cancelled;       /* withdrawn by psf_server_cancel (counted in completed) */
 } psf_server_stats_t;
 
 PSF_API int psf_server_create(const psf_server_config_t* config, psf_server_t* out);
@@ -269,6 +271,14 @@ PSF_API int psf_server_submit(psf_server_t server, psf_series_t series, const ps
 PSF_API int psf_server_poll(psf_server_t server, psf_completion_t* out, int32_t max, int32_t wait_ms,
                             int32_t* got);
 PSF_API int psf_server_stats(psf_server_t server, psf_server_stats_t* stats);
+/* psf_server_cancel: withdraw the oldest request with this tag that is still
+ * waiting for admission.  *cancelled receives 1 if one was withdrawn (it
+ * then completes at once with status PSF_ECANCELED and no result, so every
+ * submit still gives one completion, and its memory no longer counts
+ * against the budget) and 0 if no waiting request has the tag (unknown, or
+ * already admitted: an admitted request runs to completion).  Thread-safe.
+ * Errors: PSF_EINVAL (null arguments). */
+PSF_API int psf_server_cancel(psf_server_t server, uint64_t tag, int32_t* cancelled);
 PSF_API int psf_server_destroy(psf_server_t server);
 
 /*
@@ -374,20 +384,42 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
  * eps_f falls below that bound (default 6; 0 sets every candidate apart,
  * 2047 none).  An integer in [0, 2047]; results are the same for all. */
 #define PSF_TUNE_ALG1_FAR_SHIFT 4
+/* PSF_TUNE_BARRIER_BUDGET_NS: how long a block of a cooperative kernel
+ * (Algorithm 1's passes, the exact norms) waits at a grid-wide barrier
+ * before it gives up, in nanoseconds (default 2e9).  A wait that runs out
+ * records a device status and the call returns PSF_ETIMEOUT; the kernel's
+ * blocks all return (each wait is bounded), the GPU context stays usable and
+ * later calls are unaffected (every evaluation has its own control block).
+ * 0 gives up at once at any barrier not yet complete: a test of that path.
+ * An integer in [0, 6e10]. */
+#define PSF_TUNE_BARRIER_BUDGET_NS 5
+/* PSF_TUNE_FAIL_ADMISSION: fault injection for the serving loop.  k > 0
+ * makes the k-th request admitted from now on (by any worker of any server)
+ * fail as if its device memory could not be allocated: it completes with
+ * PSF_ENOMEM without running, and the other requests of its batch run as
+ * usual.  The count then returns to 0 (off).  An integer >= 0. */
+#define PSF_TUNE_FAIL_ADMISSION 6
 PSF_API int psf_tune_set(int32_t key, double value);
 PSF_API int psf_tune_get(int32_t key, double* value);
 PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,
                          double* saved_ms);
 
 /*
- * Instrumentation.  psf_launch_count: kernels this library has launched in
- * this process.  psf_profile(1) makes every later product-kernel launch
+ * Instrumentation (no counterpart in the paper).  psf_launch_count: kernels
+ * this library has launched in this process.  psf_profile(1) makes every later product-kernel launch
  * record a CUDA event pair on its stream; psf_profile_read waits for the
  * recorded events and returns the number of timed launches, their summed
  * duration in milliseconds and their algorithmic multiply-adds, then clears
  * the record if `reset`.  Not thread-safe with concurrent evaluations.
  */
 PSF_API int psf_launch_count(int64_t* count);
+/* psf_fp64_peak: this GPU's FP64 fused multiply-add rate, measured: every
+ * thread of 4 blocks x 256 threads per SM runs eight independent fma chains
+ * of 4096 steps; the best of three event-timed launches (after a warm-up) on
+ * `stream`, in TFLOP/s (2 flop per fma).  The denominator of the product
+ * kernel's roofline, whose work is FP64 multiply-adds.  Synchronizes
+ * `stream`.  Errors: PSF_EINVAL (null tflops), PSF_ECUDA. */
+PSF_API int psf_fp64_peak(void* stream, double* tflops);
 PSF_API int psf_profile(int32_t enable);
 PSF_API int psf_profile_read(int64_t* launches, double* ms, double* fma, int32_t reset);
 

@@ -311,6 +311,13 @@ class Server:
                         "queue_ms": c.queue_ms, "latency_ms": c.latency_ms, "result": res})
         return out
 
+    def cancel(self, tag: int) -> bool:
+        """Withdraw the oldest request with this tag still waiting for
+        admission; True if one was (it completes with PSF_ECANCELED)."""
+        got = ctypes.c_int32()
+        check(lib().psf_server_cancel(self._h, ctypes.c_uint64(int(tag)), ctypes.byref(got)))
+        return bool(got.value)
+
     def stats(self) -> dict:
         s = ServerStats()
         check(lib().psf_server_stats(self._h, ctypes.byref(s)))

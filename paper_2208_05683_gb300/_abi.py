@@ -7,7 +7,7 @@ import threading
 
 from . import _build
 
-PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_ENOTCONV, PSF_ETIMEOUT, PSF_ETOOBIG = range(7)
+PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_ENOTCONV, PSF_ETIMEOUT, PSF_ETOOBIG, PSF_ECANCELED = range(8)
 PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT, PSF_Z_ESTIMATE, PSF_Z_SQUARE = 0, 1, 2, 4, 8, 16
 PSF_PARAM_ER, PSF_PARAM_ALG1_MAXIT, PSF_PARAM_POOL_ENTRIES = 1, 2, 3
 PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
@@ -17,17 +17,19 @@ PSF_TUNE_TABLE_CROSSOVER = 1
 PSF_TUNE_BATCH_GRAPH = 2
 PSF_TUNE_BATCH_REUSE = 3
 PSF_TUNE_ALG1_FAR_SHIFT = 4
+PSF_TUNE_BARRIER_BUDGET_NS = 5
+PSF_TUNE_FAIL_ADMISSION = 6
 
-ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG"}
+ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG", 7: "ECANCELED"}
 
 # Every function the header declares (checked by the tests).
 EXPORTS = [
     "psf_version", "psf_last_error", "psf_series_create", "psf_series_set_param",
     "psf_series_destroy", "psf_eval", "psf_eval_from_host", "psf_eval_batch", "psf_product_filter", "psf_norm1",
     "psf_norm1_noalloc", "psf_server_create", "psf_server_submit", "psf_server_poll", "psf_server_stats",
-    "psf_server_destroy", "psf_tune_set", "psf_tune_get", "psf_autotune",
+    "psf_server_destroy", "psf_server_cancel", "psf_tune_set", "psf_tune_get", "psf_autotune",
     "psf_plan", "psf_result_csr", "psf_result_copy", "psf_result_info", "psf_result_step",
-    "psf_result_destroy", "psf_launch_count", "psf_profile", "psf_profile_read",
+    "psf_result_destroy", "psf_launch_count", "psf_profile", "psf_profile_read", "psf_fp64_peak",
 ]
 
 
@@ -54,7 +56,7 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("max_concurrent", ctypes.c_int32), ("pending", ctypes.c_int32),
-                ("budget_peak", ctypes.c_int64)]
+                ("budget_peak", ctypes.c_int64), ("cancelled", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -129,6 +131,7 @@ def _declare(h: ctypes.CDLL) -> None:
     h.psf_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32, i32, ctypes.POINTER(i32)]
     h.psf_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     h.psf_server_destroy.argtypes = [vp]
+    h.psf_server_cancel.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32)]
     h.psf_tune_set.argtypes = [i32, f64]
     h.psf_tune_get.argtypes = [i32, ctypes.POINTER(f64)]
     h.psf_autotune.argtypes = [vp, csrp, vp, ctypes.POINTER(f64), ctypes.POINTER(f64)]
@@ -142,6 +145,7 @@ def _declare(h: ctypes.CDLL) -> None:
     h.psf_launch_count.argtypes = [ctypes.POINTER(i64)]
     h.psf_profile.argtypes = [i32]
     h.psf_profile_read.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(f64), ctypes.POINTER(f64), i32]
+    h.psf_fp64_peak.argtypes = [vp, ctypes.POINTER(f64)]
     for name in EXPORTS:
         if name not in ("psf_last_error",):
             getattr(h, name).restype = ctypes.c_int

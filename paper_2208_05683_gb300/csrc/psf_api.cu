@@ -8,6 +8,7 @@
 // norms ||Z^i||_1 (the plan needs them) and at the end (to size the result).
 // A pool that turns out too small is detected on the device; the phase is
 // then repeated with the capacity the device asked for.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -52,6 +53,7 @@ std::atomic<double> g_table_crossover{1e300};
 std::atomic<bool> g_batch_graph{true};
 std::atomic<bool> g_batch_reuse{true};
 std::atomic<int> g_far_shift{6};
+std::atomic<long long> g_fail_admission{0};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
@@ -1045,6 +1047,16 @@ int psf_tune_set(int32_t key, double value) {
                 return fail(PSF_EINVAL, "far shift must be an integer in [0, 2047]");
             g_far_shift.store((int)value);
             return PSF_OK;
+        case PSF_TUNE_BARRIER_BUDGET_NS:
+            if (!(value >= 0.0 && value <= 6e10 && value == std::floor(value)))
+                return fail(PSF_EINVAL, "barrier budget must be an integer number of ns in [0, 6e10]");
+            set_barrier_budget_ns((unsigned long long)value);
+            return PSF_OK;
+        case PSF_TUNE_FAIL_ADMISSION:
+            if (!(value >= 0.0 && value <= 1e15 && value == std::floor(value)))
+                return fail(PSF_EINVAL, "admission count must be a non-negative integer");
+            g_fail_admission.store((long long)value);
+            return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
     }
@@ -1064,6 +1076,12 @@ int psf_tune_get(int32_t key, double* value) {
             return PSF_OK;
         case PSF_TUNE_ALG1_FAR_SHIFT:
             *value = (double)g_far_shift.load();
+            return PSF_OK;
+        case PSF_TUNE_BARRIER_BUDGET_NS:
+            *value = (double)barrier_budget_ns();
+            return PSF_OK;
+        case PSF_TUNE_FAIL_ADMISSION:
+            *value = (double)g_fail_admission.load();
             return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
@@ -1125,6 +1143,35 @@ int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* 
     g_table_crossover.store(best_c);
     *crossover = best_c;
     if (saved_ms) *saved_ms = cur_t - best_t;
+    return PSF_OK;
+}
+
+int psf_fp64_peak(void* stream, double* tflops) {
+    if (!tflops) return fail(PSF_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(kernels_init());
+    const int blocks = fp64_probe_blocks(), iters = 4096;
+    DevBuf out;
+    CU(out.alloc(sizeof(double) * (size_t)blocks * 256, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {  // the first is a warm-up
+        err = cudaEventRecord(e0, st);
+        if (err == cudaSuccess) err = launch_fp64_probe(iters, out.as<double>(), st);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        const double flop = 2.0 * 8.0 * iters * 256.0 * blocks;
+        if (err == cudaSuccess && rep > 0 && ms > 0.0f) best = std::max(best, flop / (ms * 1e-3) / 1e12);
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    out.release();
+    if (err != cudaSuccess) return fail(PSF_ECUDA, "fp64 probe: %s", cudaGetErrorString(err));
+    *tflops = best;
     return PSF_OK;
 }
 

@@ -167,6 +167,7 @@ struct Alg1BatchArgs {
     unsigned long long* cand_x;
     int* inst_dropped;   // optional: set to 1 for the instances that dropped entries
     int far_shift;       // as in Alg1Args
+    unsigned long long budget_ns;  // grid-barrier wait limit (set by the launcher)
 };
 
 // One input matrix of a batch (device CSR, 0-based local columns).
@@ -193,6 +194,7 @@ struct Alg1Args {
     int* cand_col;               // two candidate lists of ctl->cand_cap entries each
     unsigned long long* cand_x;
     int far_shift;               // candidates at or below eps_g / 2^far_shift are set apart
+    unsigned long long budget_ns;  // grid-barrier wait limit (set by the launcher)
 };
 
 // Arguments of k_reuse_pass1 (a baby step that equals a power of the norm
@@ -248,6 +250,7 @@ struct NormArgs {
     Ctl* ctl;
     const int* inst;            // batch: instance of each column (nullptr: one instance)
     int slot_stride;
+    unsigned long long budget_ns;  // grid-barrier wait limit (set by the launcher)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -633,7 +636,8 @@ __device__ __forceinline__ unsigned long long far_split(double eps_g, int shift)
 }
 
 // Grid-wide barrier for cooperative launches, with a bounded wait: after
-// `budget_ns` it records kDevTimeout and returns false.
+// `budget_ns` it records kDevTimeout and returns false (a budget of 0 gives
+// up at once unless the barrier is already complete: a test of that path).
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned long long budget_ns) {
     __syncthreads();
     __shared__ int ok;
@@ -650,7 +654,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned long long budget
         } else {
             unsigned long long t0 = global_ns();
             while (*gen == g) {
-                if (global_ns() - t0 > budget_ns) {
+                if (budget_ns == 0ull || global_ns() - t0 > budget_ns) {
                     atomicOr(&ctl->status, kDevTimeout);
                     ok = 0;
                     break;

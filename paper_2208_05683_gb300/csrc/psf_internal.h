@@ -199,6 +199,8 @@ extern std::atomic<bool> g_batch_graph;
 extern std::atomic<bool> g_batch_reuse;
 // Algorithm 1 sets candidates at or below eps_g / 2^g_far_shift apart (PSF_TUNE_ALG1_FAR_SHIFT)
 extern std::atomic<int> g_far_shift;
+// fault injection: the k-th server admission from now fails (PSF_TUNE_FAIL_ADMISSION)
+extern std::atomic<long long> g_fail_admission;
 // slot_map 1: table, 2: bitmap, 0: by the work per row and the crossover
 inline bool use_table(int slot_map, double work_per_row) {
     return slot_map == 1 || (slot_map == 0 && work_per_row >= g_table_crossover.load(std::memory_order_relaxed));

@@ -993,7 +993,6 @@ __global__ void __launch_bounds__(256) k_reuse_copy_batch(ProductArgs P) {
 // decisions without further communication.
 constexpr int kAlg1Threads = 1024;  // one block per SM: few grid-barrier arrivals
 constexpr int kAlg1BlocksPerSm = 1;
-constexpr unsigned long long kBarrierBudgetNs = 2000000000ull;  // 2 s
 
 __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Args A) {
     const int lane = threadIdx.x & 31;
@@ -1055,7 +1054,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
                 }
             }
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+        if (!grid_barrier(A.ctl, A.budget_ns)) {
             alive = false;
             break;
         }
@@ -1125,7 +1124,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
                     }
                 }
             }
-            if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+            if (!grid_barrier(A.ctl, A.budget_ns)) {
                 alive = false;
                 break;
             }
@@ -1151,7 +1150,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
                 }
             }
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+        if (!grid_barrier(A.ctl, A.budget_ns)) {
             alive = false;
             break;
         }
@@ -1170,7 +1169,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
         // once all blocks reach the first barrier.
         const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
         const int sx = it & 1, sc = (it - 1) & 1;
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         if (gt == 0) A.ctl->cslot[sc] = 0ull;
         unsigned long long mx = 0ull;
         for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
@@ -1179,13 +1178,13 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
         }
         mx = warp_max_u64(mx);
         if (lane == 0 && mx) atomicMax(&A.ctl->cslot[sx], mx);
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         const int lsb = lsb_for_bound(__ldcg(&A.ctl->cslot[sx]));
         for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
             const unsigned long long xb = mag_bits(__ldcg(A.val + q));
             if (xb != 0ull && xb <= fb) exact_add_checked(A.words, A.sticky, A.col[q], A.n, xb, lsb, A.ctl);
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         unsigned long long local = 0ull;
         for (int j = gt; j < A.n; j += nthreads) {
             const double s = chunk_round(A.words + j, n, A.sticky + j, lsb, true);
@@ -1194,7 +1193,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
         }
         local = warp_max_u64(local);
         if (lane == 0 && local) atomicMax(&A.ctl->cslot[sc], local);
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         c = __longlong_as_double((long long)__ldcg(&A.ctl->cslot[sc]));
     }
     if (!(c > 0.0)) {
@@ -1294,7 +1293,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
             for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) A.cslot[2 * i + ((pass + 1) & 1)] = 0ull;
             if (threadIdx.x == 0) A.ctl->cand_cnt[(pass + 1) & 1] = 0ull;  // the next rescan's output list
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+        if (!grid_barrier(A.ctl, A.budget_ns)) {
             alive = false;
             break;
         }
@@ -1395,7 +1394,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
                     }
                 }
             }
-            if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+            if (!grid_barrier(A.ctl, A.budget_ns)) {
                 alive = false;
                 break;
             }
@@ -1425,7 +1424,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
                     exact_add(A.words + col, n, A.sticky + col, xb[u], A.bstep[i].e_lsb);
             }
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) {
+        if (!grid_barrier(A.ctl, A.budget_ns)) {
             alive = false;
             break;
         }
@@ -1450,11 +1449,11 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
         __shared__ int s_lsb[kMaxBatch];
         // every block has read the maxima: slot 2i takes the largest
         // candidate, slot 2i + 1 the new c
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         if (blockIdx.x == 0)
             for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
                 if (s_state[i] == 4) A.cslot[2 * i] = A.cslot[2 * i + 1] = 0ull;
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         for (unsigned long long q = p0 + (unsigned long long)gt; q < p1; q += (unsigned long long)nthreads) {
             const unsigned long long xb = mag_bits(__ldcg(A.val + q));
             if (xb == 0ull) continue;
@@ -1464,7 +1463,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
             if (s_state[i] == 4 && xb <= (unsigned long long)__double_as_longlong(s_eps[i]))
                 atomicMax(&A.cslot[2 * i], xb);
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
             if (s_state[i] == 4) s_lsb[i] = lsb_for_bound(__ldcg(&A.cslot[2 * i]));
         __syncthreads();
@@ -1477,7 +1476,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
             if (s_state[i] == 4 && xb <= (unsigned long long)__double_as_longlong(s_eps[i]))
                 exact_add(A.words + col, n, A.sticky + col, xb, s_lsb[i]);
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         for (int j = gt; j < A.n; j += nthreads) {
             const int i = A.inst[j];
             if (s_state[i] != 4) continue;
@@ -1485,7 +1484,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
             const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
             if (vb) atomicMax(&A.cslot[2 * i + 1], vb);
         }
-        if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+        if (!grid_barrier(A.ctl, A.budget_ns)) return;
         for (int i = threadIdx.x; i < A.ninst; i += blockDim.x)
             if (s_state[i] == 4) {
                 s_c[i] = __longlong_as_double((long long)__ldcg(&A.cslot[2 * i + 1]));
@@ -1588,7 +1587,7 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(NormArgs A) {
             }
         }
     }
-    if (!grid_barrier(A.ctl, kBarrierBudgetNs)) return;
+    if (!grid_barrier(A.ctl, A.budget_ns)) return;
     const int lane = threadIdx.x & 31;
     for (int mi = 0; mi < A.count; ++mi) {
         unsigned long long* words = A.words + (size_t)mi * kChunks * n;
@@ -2095,6 +2094,10 @@ struct DevCfg {
 };
 constexpr int kMaxDevices = 64;
 static DevCfg g_dev[kMaxDevices];
+// wait limit of every grid barrier (PSF_TUNE_BARRIER_BUDGET_NS)
+static std::atomic<unsigned long long> g_barrier_budget_ns{kBarrierBudgetDefaultNs};
+void set_barrier_budget_ns(unsigned long long ns) { g_barrier_budget_ns.store(ns); }
+unsigned long long barrier_budget_ns() { return g_barrier_budget_ns.load(); }
 static std::mutex g_init_mu;
 static std::atomic<long long> g_launches{0};
 
@@ -2187,6 +2190,7 @@ cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {
     cudaError_t err = cudaMemsetAsync(&A.ctl->cslot[0], 0, sizeof(A.ctl->cslot), st);
     if (err != cudaSuccess) return err;
     Alg1Args a = A;
+    a.budget_ns = barrier_budget_ns();
     void* args[] = {&a};
     ++g_launches;
     return cudaLaunchCooperativeKernel((const void*)k_alg1, dim3(dcfg().alg1_blocks), dim3(kAlg1Threads), args,
@@ -2195,6 +2199,7 @@ cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {
 
 cudaError_t launch_norms(const NormArgs& A, cudaStream_t st) {
     NormArgs a = A;
+    a.budget_ns = barrier_budget_ns();
     void* args[] = {&a};
     ++g_launches;
     return cudaLaunchCooperativeKernel((const void*)k_norms, dim3(dcfg().norm_blocks), dim3(kNormThreads), args,
@@ -2244,6 +2249,33 @@ cudaError_t launch_gather(int n, const RowView& src, const int* rowptr, int* col
     return cudaGetLastError();
 }
 
+// FP64 rate probe: every thread runs eight independent chains of fused
+// multiply-adds (enough in flight to fill the pipe); the result is stored so
+// that none of the work can be dropped.
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double a, double b, double* out) {
+    double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+    double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+    for (int i = 0; i < iters; ++i) {
+        x0 = __fma_rn(x0, a, b);
+        x1 = __fma_rn(x1, a, b);
+        x2 = __fma_rn(x2, a, b);
+        x3 = __fma_rn(x3, a, b);
+        x4 = __fma_rn(x4, a, b);
+        x5 = __fma_rn(x5, a, b);
+        x6 = __fma_rn(x6, a, b);
+        x7 = __fma_rn(x7, a, b);
+    }
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+int fp64_probe_blocks() { return sms_now() * 4; }
+
+cudaError_t launch_fp64_probe(int iters, double* out, cudaStream_t st) {
+    k_fp64_probe<<<fp64_probe_blocks(), 256, 0, st>>>(iters, 0.999999, 1e-7, out);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_identity(int n, double alpha, int* rowptr, int* col, double* val, cudaStream_t st) {
     k_identity<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, alpha, rowptr, col, val);
     ++g_launches;
@@ -2278,6 +2310,7 @@ cudaError_t launch_alg1_batch(const Alg1BatchArgs& A, cudaStream_t st) {
     cudaError_t err = cudaMemsetAsync(A.cslot, 0, sizeof(unsigned long long) * 2 * (size_t)A.ninst, st);
     if (err != cudaSuccess) return err;
     Alg1BatchArgs a = A;
+    a.budget_ns = barrier_budget_ns();
     void* args[] = {&a};
     ++g_launches;
     return cudaLaunchCooperativeKernel((const void*)k_alg1_batch, dim3(dcfg().alg1b_blocks), dim3(kAlg1Threads), args,

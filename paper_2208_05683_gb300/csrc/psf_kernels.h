@@ -8,6 +8,11 @@
 namespace psf {
 
 cudaError_t kernels_init();
+// wait limit of the cooperative kernels' grid barriers (default 2 s); a wait
+// that runs out records kDevTimeout, and the call reports PSF_ETIMEOUT
+constexpr unsigned long long kBarrierBudgetDefaultNs = 2000000000ull;
+void set_barrier_budget_ns(unsigned long long ns);
+unsigned long long barrier_budget_ns();
 int num_sms();
 long long launch_count();
 void count_launches(int k);  // kernels launched by other translation units
@@ -53,5 +58,9 @@ cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bou
 cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st);
 cudaError_t launch_reuse_copy_batch(const ProductArgs& P, cudaStream_t st);
 cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st);  // then rounds (k_norms_finish)
+// FP64 rate probe: fp64_probe_blocks() blocks of 256 threads, 8 x iters
+// fused multiply-adds per thread, one double per thread written to out
+int fp64_probe_blocks();
+cudaError_t launch_fp64_probe(int iters, double* out, cudaStream_t st);
 
 }  // namespace psf

@@ -96,6 +96,47 @@ void psf_server_s::worker(cudaStream_t stream) {
             st.budget_peak = std::max(st.budget_peak, (int64_t)inflight_bytes);
         }
         const Clock::time_point t_admit = Clock::now();
+        // fault injection (PSF_TUNE_FAIL_ADMISSION): the request whose
+        // admission brings the count down to zero fails as if its device
+        // memory could not be allocated; the rest of the batch runs
+        std::vector<psf_completion_t> failed_adm;
+        for (size_t i = 0; i < batch.size();) {
+            long long k = g_fail_admission.load();
+            bool inject = false;
+            while (k > 0 && !g_fail_admission.compare_exchange_weak(k, k - 1)) {
+            }
+            inject = k == 1;
+            if (!inject) {
+                ++i;
+                continue;
+            }
+            psf_completion_t c{};
+            c.tag = batch[i].tag;
+            c.status = PSF_ENOMEM;
+            c.batch_size = (int)batch.size();
+            c.queue_ms = ms_between(batch[i].t_submit, t_admit);
+            c.latency_ms = ms_between(batch[i].t_submit, Clock::now());
+            failed_adm.push_back(c);
+            batch.erase(batch.begin() + (long)i);
+        }
+        if (!failed_adm.empty()) {
+            std::lock_guard<std::mutex> lk(mu);
+            for (const psf_completion_t& c : failed_adm) {
+                done.push_back(c);
+                ++st.completed;
+                ++st.failed;
+            }
+        }
+        if (batch.empty()) {
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                inflight_bytes -= bytes;
+                --busy;
+            }
+            cv_done.notify_all();
+            cv_work.notify_all();
+            continue;
+        }
         const int count = (int)batch.size();
         std::vector<psf_series_t> ser((size_t)count);
         std::vector<psf_csr_t> zs((size_t)count);
@@ -204,6 +245,32 @@ int psf_server_submit(psf_server_t s, psf_series_t series, const psf_csr_t* Z, u
         ++s->st.submitted;
     }
     s->cv_work.notify_one();
+    return PSF_OK;
+}
+
+int psf_server_cancel(psf_server_t s, uint64_t tag, int32_t* cancelled) {
+    if (!s || !cancelled) return fail(PSF_EINVAL, "null argument");
+    *cancelled = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+            if (it->tag != tag) continue;
+            psf_completion_t c{};
+            c.tag = tag;
+            c.status = PSF_ECANCELED;
+            c.queue_ms = c.latency_ms = ms_between(it->t_submit, Clock::now());
+            s->pending.erase(it);
+            s->done.push_back(c);
+            ++s->st.completed;
+            ++s->st.cancelled;
+            *cancelled = 1;
+            break;
+        }
+    }
+    if (*cancelled) {
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
     return PSF_OK;
 }
 

@@ -24,5 +24,6 @@ int main(void) {
     S(psf_server_stats_t); F(psf_server_stats_t, submitted); F(psf_server_stats_t, completed);
     F(psf_server_stats_t, failed); F(psf_server_stats_t, batches); F(psf_server_stats_t, max_concurrent);
     F(psf_server_stats_t, pending); F(psf_server_stats_t, budget_peak);
+    F(psf_server_stats_t, cancelled);
     return 0;
 }

@@ -58,3 +58,45 @@ def test_clock_summary_keeps_the_timed_window():
     assert s["reasons"] == ["sw_power_cap"]
     c.mark(2.0, 3.0)
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_reference_and_repo_arms_share_the_config():
+    sys.path.insert(0, ROOT)
+    import bench
+    cfg = bench.config_dict(128 * 128, 81408, 1)
+    assert cfg["workload"] == "lap2d_128x128 exp+cos tol 1e-12" and cfg["parallelism"] == "replicas x1"
+    # both arms build their config with this one function
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert src.count("config_dict(") == 3  # the definition and the two arms
+
+
+def test_dense_ps_baseline_matches_closed_form_and_oracle():
+    # the dense baseline on the CPU (torch float64): same plan as the sparse
+    # scheme, unfiltered, against the 1D Laplacian's closed form and the
+    # oracle's unfiltered PS
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synthetic as syn
+    m = 40
+    rp, col, val = syn.laplacian_1d(m)
+    Z = oracle.CSR(m, rp, col, val)
+    a = syn.coeffs("exp")
+    ref = oracle.psscf(Z, a, 1e-12, filtered=False)
+    p = ref.plan
+    D = bench.dense_ps(torch.as_tensor(Z.to_dense()), a, p.N, p.q, p.b).numpy()
+    F = bench.lap1d_closed_form(m, "exp")
+    err = np.abs(D - F).sum(axis=0).max() / np.abs(F).sum(axis=0).max()
+    assert err <= 1e-12
+    U = ref.F.to_dense()
+    assert np.abs(D - U).max() <= 1e-14 * np.abs(U).max()
+    # cos through the Kronecker closed form of a small 2D Laplacian
+    c, s = bench.lap1d_closed_form(6, "cos"), bench.lap1d_closed_form(6, "sin")
+    Z2 = oracle.CSR(36, *syn.laplacian_2d(6))
+    a = syn.coeffs("cos")
+    p = oracle.psscf(Z2, a, 1e-12).plan
+    D2 = bench.dense_ps(torch.as_tensor(Z2.to_dense()), a, p.N, p.q, p.b).numpy()
+    F2 = np.kron(c, c) - np.kron(s, s)
+    assert np.abs(D2 - F2).sum(axis=0).max() <= 1e-12 * np.abs(F2).sum(axis=0).max()
