@@ -296,8 +296,6 @@ def run_psf(args):
                 lat.append(e0.elapsed_time(e1))
             _abi.check(L.psf_result_destroy(h))
 
-    fp64_peak, fp64_source = fp64_peak_tflops(L, ctypes.c_void_p(stream.cuda_stream))
-
     # the product kernel's slot-map crossover, timed on this workload (outside
     # the timed region; results do not depend on it)
     tuned = None
@@ -338,6 +336,8 @@ def run_psf(args):
     _abi.check(L.psf_profile_read(ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(fma), 1))
     _abi.check(L.psf_profile(0))
     achieved = 2.0 * fma.value / (ms.value / 1e3) / 1e12
+    # the FP64 pipe's rate, measured now that the GPU is warm
+    fp64_peak, fp64_source = fp64_peak_tflops(L, ctypes.c_void_p(stream.cuda_stream))
     traffic = None
     try:
         prof = json.load(open(PROFILE_JSON))
@@ -894,11 +894,14 @@ def run_e2(args):
     rows = []
     for kind in ("exp", "cos"):
         a = syn.coeffs(kind)
-        filt, unf = psf.Series(a, tol), psf.Series(a, tol, filtered=False)
+        filt, unf = psf.Series(a, tol, dense_xover=1e300), psf.Series(a, tol, filtered=False, dense_xover=1e300)
+        # every product step as dense tiles, and the automatic choice
+        dns, auto = psf.Series(a, tol, dense_xover=0.0), psf.Series(a, tol)
         # cos also with the W = Z^2 substitution (PSF_Z_SQUARE)
         sq = psf.Series(a, tol, square=True) if kind == "cos" else None
         for w in range(1, 16):
-            acc = {k: [] for k in ("psscf_ms", "ps_ms", "ref_ms", "psscf_density", "ps_density", "ref_density",
+            acc = {k: [] for k in ("psscf_ms", "ps_ms", "ref_ms", "dense_tiles_ms", "auto_ms",
+                                   "psscf_density", "ps_density", "ref_density",
                                    "psscf_err_fro", "ps_err_fro", "psscf_err_1", "ps_err_1", "N",
                                    "square_ms", "square_err_fro", "square_density")}
             for seed in range(seeds):
@@ -906,10 +909,12 @@ def run_e2(args):
                 Z = psf.DeviceCSR.from_host(*host, device=dev)
                 Zd = dense_of(host)
                 if seed == 0:  # untimed first evaluation at this bandwidth
-                    filt.eval(Z), unf.eval(Z), reference(kind, Zd)
+                    filt.eval(Z), unf.eval(Z), reference(kind, Zd), dns.eval(Z), auto.eval(Z)
                     if sq is not None:
                         sq.eval(Z)
                 rf, tf = timed(lambda: filt.eval(Z))
+                acc["dense_tiles_ms"].append(timed(lambda: dns.eval(Z))[1])
+                acc["auto_ms"].append(timed(lambda: auto.eval(Z))[1])
                 ru, tu = timed(lambda: unf.eval(Z))
                 ref, tr = timed(lambda: reference(kind, Zd))
                 ef, eu = errors(rf, ref), errors(ru, ref)
@@ -933,13 +938,74 @@ def run_e2(args):
             row.update({k: float(np.mean(v)) for k, v in acc.items() if v})
             row["psscf_err_fro_max"] = float(np.max(acc["psscf_err_fro"]))
             rows.append(row)
-            print(f"{kind} w={w:2d}: psscf {row['psscf_ms']:7.2f} ms  ps {row['ps_ms']:7.2f} ms  "
+            print(f"{kind} w={w:2d}: psscf {row['psscf_ms']:7.2f} ms  dense tiles {row['dense_tiles_ms']:7.2f} ms  "
+                  f"auto {row['auto_ms']:7.2f} ms  ps {row['ps_ms']:7.2f} ms  "
                   f"dense {row['ref_ms']:7.2f} ms  density {row['psscf_density']:.3f} / {row['ps_density']:.3f}  "
                   f"err {row['psscf_err_fro']:.2e} / {row['ps_err_fro']:.2e}  "
                   f"square {row.get('square_ms', float('nan')):7.2f} ms", file=sys.stderr, flush=True)
     print(json.dumps({"experiment": "banded_normal n=1000, w=1..15, N(0,1), exp and cos, eps_tol=1e-14",
                       "seeds_per_w": seeds, "reference": "torch.linalg.matrix_exp float64 / complex128 on the GPU",
                       "timing": "wall clock per evaluation through the Python API, synchronized", "rows": rows}))
+
+
+def run_dense_xover(args):
+    """Where dense tiles beat the sparse kernel: one product step C = A B of
+    random matrices (n = 1000, 2000, 4000; densities spread so that the
+    algorithmic multiply-adds per n^3 run from about 1e-4 to 1), timed
+    through psf_product_filter as the sparse kernel and as dense tiles (the
+    library's event timing of the product launches, median of 3), and the
+    multiply-adds per n^3 from which dense tiles are faster."""
+    import ctypes
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+    import paper_2208_05683_gb300 as psf
+    from paper_2208_05683_gb300 import _abi
+    torch.cuda.set_device(0)
+    L = psf.lib()
+    old = psf.tune_get(_abi.PSF_TUNE_DENSE_XOVER)
+    rows = []
+    try:
+        for n in (1000, 2000, 4000):
+            for d in (0.003, 0.01, 0.03, 0.06, 0.1, 0.2, 0.35, 0.6, 1.0):
+                rng = np.random.default_rng(int(1000 * d) + n)
+                mats = []
+                for _ in range(2):
+                    m = sp.random(n, n, density=d, random_state=rng, format="csr",
+                                  data_rvs=lambda k: rng.uniform(-1, 1, k))
+                    m.sort_indices()
+                    mats.append(psf.DeviceCSR.from_host(m.indptr.astype(np.int32), m.indices.astype(np.int32),
+                                                         m.data.astype(np.float64), device="cuda:0"))
+                t = {}
+                for name, v in (("sparse", 1e300), ("dense", 0.0)):
+                    psf.tune_set(_abi.PSF_TUNE_DENSE_XOVER, v)
+                    psf.product_filter(mats[0], mats[1], [], 0.0)
+                    ms = []
+                    for _ in range(3):
+                        _abi.check(L.psf_profile(1))
+                        r = psf.product_filter(mats[0], mats[1], [], 0.0)
+                        nl, pms, fma = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+                        _abi.check(L.psf_profile_read(ctypes.byref(nl), ctypes.byref(pms), ctypes.byref(fma), 1))
+                        _abi.check(L.psf_profile(0))
+                        ms.append(pms.value)
+                    t[name] = statistics.median(ms)
+                    fma_n = r.steps[0]["fma"]
+                rho = fma_n / float(n) ** 3
+                rows.append({"n": n, "density": d, "fma_per_n3": rho, "sparse_ms": t["sparse"], "dense_ms": t["dense"],
+                             "sparse_tflops": 2 * fma_n / t["sparse"] / 1e9,
+                             "dense_tflops_on_n3": 2 * float(n) ** 3 / t["dense"] / 1e9})
+                print(f"n={n} d={d}: fma/n^3 {rho:.2e}  sparse {t['sparse']:.3f} ms  dense {t['dense']:.3f} ms",
+                      file=sys.stderr, flush=True)
+                del mats
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_DENSE_XOVER, old)
+    cross = {}
+    for n in sorted({r["n"] for r in rows}):
+        rs = sorted((r for r in rows if r["n"] == n), key=lambda r: r["fma_per_n3"])
+        win = [r["fma_per_n3"] for r in rs if r["dense_ms"] <= r["sparse_ms"]]
+        cross[n] = min(win) if win else None
+    print(json.dumps({"experiment": "one product step, random A B, sparse kernel vs dense tiles",
+                      "crossover_fma_per_n3": cross, "rows": rows}))
 
 
 def ctypes_i64(fn) -> int:
@@ -995,10 +1061,14 @@ def main():
     ap.add_argument("--e2", action="store_true",
                     help="run the paper's banded N(0,1) experiment (n = 1000, w = 1..15) and exit")
     ap.add_argument("--e2-seeds", type=int, default=30, help="matrices per bandwidth in --e2")
+    ap.add_argument("--dense-xover", action="store_true",
+                    help="time one product step as the sparse kernel and as dense tiles over densities and exit")
     ap.add_argument("--size-sweep", action="store_true",
                     help="time the 2D Laplacian workload on grids 128..768 (product kernel rate per size) and exit")
     args = ap.parse_args()
-    if args.size_sweep:
+    if args.dense_xover:
+        run_dense_xover(args)
+    elif args.size_sweep:
         run_size_sweep(args)
     elif args.e2:
         run_e2(args)

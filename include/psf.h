@@ -88,6 +88,11 @@ extern "C" {
                                      4608 columns in the series' previous evaluation) */
 #define PSF_PARAM_CHUNK_COLS 5    /* > 0: fewer columns per row chunk (tests of row chunking) */
 #define PSF_PARAM_CHUNK_SLOTS 6   /* > 0: fewer accumulator slots per row chunk (same) */
+#define PSF_PARAM_DENSE_XOVER 7   /* dense-tile crossover of this series (see PSF_TUNE_DENSE_XOVER):
+                                     a product step with at least this many algorithmic
+                                     multiply-adds per n^3 runs as FP64 dense tiles
+                                     (0: every product step, 1e300: none; -1, the default:
+                                     the process-wide value) */
 
 #define PSF_MAX_Q 23 /* largest supported PS block size q */
 
@@ -399,6 +404,22 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
  * PSF_ENOMEM without running, and the other requests of its batch run as
  * usual.  The count then returns to 0 (off).  An integer >= 0. */
 #define PSF_TUNE_FAIL_ADMISSION 6
+/* PSF_TUNE_DENSE_XOVER: process-wide dense-tile crossover.  A product step of
+ * psf_eval (unless the series sets PSF_PARAM_DENSE_XOVER) or
+ * psf_product_filter whose algorithmic multiply-adds (sum over output rows of
+ * sum_{k in A_r} nnz(B_k); for psf_eval the count of the same step in the
+ * series' previous evaluation, else n times the product of the operands'
+ * mean row lengths) reach this value times n^3 runs as an FP64 dense tile
+ * product: both operands expanded to dense n x n arrays, every output entry
+ * folded over k = 0..n-1 in order (the sparse order with zero terms, which
+ * leave it unchanged), then the nonzero entries written back with
+ * Algorithm 1's first pass.  Results are bitwise those of the sparse kernel.
+ * Needs 3 n^2 doubles of device memory; steps with n > 16384 always run
+ * sparse, and psf_eval_batch always runs sparse.  Default 0.15: one product
+ * of random matrices (n = 1000..4000, GB300) ran faster as dense tiles from
+ * 0.14-0.19 multiply-adds per n^3 on (the tiles run at 0.97-1.19 TFLOP/s,
+ * the sparse kernel at 0.1-0.5); a value >= 0. */
+#define PSF_TUNE_DENSE_XOVER 7
 PSF_API int psf_tune_set(int32_t key, double value);
 PSF_API int psf_tune_get(int32_t key, double* value);
 PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,
@@ -415,8 +436,9 @@ PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, 
 PSF_API int psf_launch_count(int64_t* count);
 /* psf_fp64_peak: this GPU's FP64 fused multiply-add rate, measured: every
  * thread of 4 blocks x 256 threads per SM runs eight independent fma chains
- * of 4096 steps; the best of three event-timed launches (after a warm-up) on
- * `stream`, in TFLOP/s (2 flop per fma).  The denominator of the product
+ * of 8192 steps; the best of five event-timed launches (after three warm-up
+ * launches, about 50 ms, while the clocks rise) on `stream`, in TFLOP/s
+ * (2 flop per fma).  The denominator of the product
  * kernel's roofline, whose work is FP64 multiply-adds.  Synchronizes
  * `stream`.  Errors: PSF_EINVAL (null tflops), PSF_ECUDA. */
 PSF_API int psf_fp64_peak(void* stream, double* tflops);

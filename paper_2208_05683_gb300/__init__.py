@@ -27,7 +27,7 @@ from . import _build
 from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_ESTIMATE, PSF_Z_SQUARE, PSF_Z_SUBMULT,
                    PSF_PARAM_ALG1_MAXIT,
                    PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS,
-                   PSF_PARAM_CHUNK_SLOTS, PSF_MAX_Q, PSF_NORM1_NOALLOC_MAX_N,
+                   PSF_PARAM_CHUNK_SLOTS, PSF_PARAM_DENSE_XOVER, PSF_MAX_Q, PSF_NORM1_NOALLOC_MAX_N,
                    PsfError, CSRStruct, InfoStruct, StepStruct, ServerConfig, Completion, ServerStats, lib, check)
 
 __all__ = [
@@ -164,13 +164,16 @@ class Series:
     kernel   slot map of the product kernel: "auto", "table", "bitmap" or "window"
              (the bitmap with its wide column window, for every product)
     chunk_cols, chunk_slots  > 0: smaller row chunks (to exercise row chunking)
+    dense_xover  dense-tile crossover in multiply-adds per n^3 (0: every product
+             step as dense tiles, 1e300: none, None: the process-wide value)
     """
 
     def __init__(self, coeffs, tol: float, *, poly: bool = False, filtered: bool = True,
                  submult: bool = False, estimate: bool = False, square: bool = False, s: int = 0,
                  e_r: float | None = None,
                  maxit: int | None = None, pool_entries: int | None = None,
-                 kernel: str = "auto", chunk_cols: int = 0, chunk_slots: int = 0):
+                 kernel: str = "auto", chunk_cols: int = 0, chunk_slots: int = 0,
+                 dense_xover: float | None = None):
         L = lib()
         a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
         flags = (PSF_POLY if poly else PSF_SERIES) | (0 if filtered else PSF_NOFILTER) | \
@@ -195,6 +198,8 @@ class Series:
             check(L.psf_series_set_param(h, PSF_PARAM_CHUNK_COLS, float(chunk_cols)))
         if chunk_slots:
             check(L.psf_series_set_param(h, PSF_PARAM_CHUNK_SLOTS, float(chunk_slots)))
+        if dense_xover is not None:
+            check(L.psf_series_set_param(h, PSF_PARAM_DENSE_XOVER, float(dense_xover)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -11,6 +11,7 @@ PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_ENOTCONV, PSF_ETIMEOUT, PSF_ETOOB
 PSF_SERIES, PSF_POLY, PSF_NOFILTER, PSF_Z_SUBMULT, PSF_Z_ESTIMATE, PSF_Z_SQUARE = 0, 1, 2, 4, 8, 16
 PSF_PARAM_ER, PSF_PARAM_ALG1_MAXIT, PSF_PARAM_POOL_ENTRIES = 1, 2, 3
 PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS, PSF_PARAM_CHUNK_SLOTS = 4, 5, 6
+PSF_PARAM_DENSE_XOVER = 7
 PSF_MAX_Q = 23
 PSF_NORM1_NOALLOC_MAX_N = 65536
 PSF_TUNE_TABLE_CROSSOVER = 1
@@ -19,6 +20,7 @@ PSF_TUNE_BATCH_REUSE = 3
 PSF_TUNE_ALG1_FAR_SHIFT = 4
 PSF_TUNE_BARRIER_BUDGET_NS = 5
 PSF_TUNE_FAIL_ADMISSION = 6
+PSF_TUNE_DENSE_XOVER = 7
 
 ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG", 7: "ECANCELED"}
 

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpsf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["psf_kernels.cu", "psf_api.cu", "psf_batch.cu", "psf_normest.cu", "psf_server.cpp", "psf_plan.cpp"]
+SOURCES = ["psf_kernels.cu", "psf_api.cu", "psf_batch.cu", "psf_normest.cu", "psf_dense.cu", "psf_server.cpp",
+           "psf_plan.cpp"]
 _lock = threading.Lock()
 
 

@@ -54,6 +54,7 @@ std::atomic<bool> g_batch_graph{true};
 std::atomic<bool> g_batch_reuse{true};
 std::atomic<int> g_far_shift{6};
 std::atomic<long long> g_fail_admission{0};
+std::atomic<double> g_dense_xover{kDenseXoverDefault};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
@@ -142,7 +143,8 @@ unsigned long long arena_for(double row_len) {
 int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddTerm>& add,
              double threshold, double e_r, int maxit, int stat_index, size_t slot, RowView* out,
              NormSlot* absmax_slot = nullptr, double blen = 0.0, double alen = 0.0, int reuse_k = 0,
-             unsigned long long reuse_fma = 0, double out_len = 0.0, bool wide_window = false) {
+             unsigned long long reuse_fma = 0, double out_len = 0.0, bool wide_window = false,
+             double fma_hint = 0.0) {
     if (add.size() > (size_t)kMaxAdd) return fail(PSF_ETOOBIG, "%zu addend terms (max %d)", add.size(), kMaxAdd);
     int *rb, *re;
     int rc = w.rows_for(slot, &rb, &re);
@@ -191,7 +193,20 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     const double work = alen > 0.0 ? alen * blen : 0.0;
     const bool table = use_table(w.slot_map, work);
     if (reuse_k > 0) P.skip_unless = &w.C()->dropped;
-    CU(launch_product(P, table, w.st, out_len, wide_window || w.slot_map == 3));
+    // dense tiles for a product with at least dense_xover n^3 multiply-adds
+    // (the previous evaluation's count of this step, else the estimate from
+    // the operands' mean row lengths)
+    const double nd = (double)w.n;
+    const double fma_est = fma_hint > 0.0 ? fma_hint : work * nd;
+    const bool dense = A && reuse_k == 0 && w.n > 0 && w.n <= kDenseMaxN && fma_est >= w.dense_xover * nd * nd * nd;
+    if (dense) {
+        const size_t bytes = sizeof(double) * (size_t)w.n * (size_t)w.n;
+        for (DevBuf& d : w.dense)
+            if (!d.p) CU(d.alloc(bytes, w.st));
+        CU(launch_dense_product(P, w.dense[0].as<double>(), w.dense[1].as<double>(), w.dense[2].as<double>(), w.st));
+    } else {
+        CU(launch_product(P, table, w.st, out_len, wide_window || w.slot_map == 3));
+    }
     if (reuse_k > 0) {
         ReuseArgs R{};
         R.n = w.n;
@@ -394,6 +409,10 @@ int psf_series_set_param(psf_series_t series, int32_t key, double value) {
             if (!(value >= 0.0) || value > 1e9) return fail(PSF_EINVAL, "chunk slots out of range");
             series->chunk_slots = (int)value;
             return PSF_OK;
+        case PSF_PARAM_DENSE_XOVER:
+            if (!(value == -1.0 || value >= 0.0)) return fail(PSF_EINVAL, "dense crossover must be -1 or >= 0");
+            series->dense_xover = value;
+            return PSF_OK;
         case PSF_PARAM_POOL_ENTRIES:
             if (!(value >= 0.0) || value > (double)INT32_MAX) return fail(PSF_EINVAL, "pool entries out of range");
             series->pool_hint = (unsigned long long)value;
@@ -511,6 +530,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     if ((rc = prepare(st))) return rc;
     Work w;
     if ((rc = w.init(n, st, 1))) return rc;
+    w.dense_xover = g_dense_xover.load();
     CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
     if ((rc = validate_inputs(w, {A, B}))) return rc;
     for (int t = 0; t < nadd; ++t)
@@ -620,6 +640,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
     if ((rc = w.init(n, st, 16))) return rc;
     if ((rc = validate_inputs(w, {Z}))) return rc;
     w.slot_map = series->kernel;
+    w.dense_xover = series->dense_xover >= 0.0 ? series->dense_xover : g_dense_xover.load();
     // the column windows the series' previous evaluation measured (batches on
     // other threads may update them)
     std::vector<unsigned> span_z, span_baby, span_giant;
@@ -910,8 +931,10 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     const double olen =
                         (size_t)(i - 1) < series->out_giant.size() ? series->out_giant[(size_t)(i - 1)] : 0.0;
                     const bool wg = (size_t)(i - 1) < span_giant.size() && span_giant[(size_t)(i - 1)] > kBitmapColumns;
+                    const double fh =
+                        (size_t)(i - 1) < series->fma_giant.size() ? series->fma_giant[(size_t)(i - 1)] : 0.0;
                     if ((rc = run_step(w, &Zh[(size_t)q], &S, add, thr, series->e_r, series->maxit, si, sslot[nslot],
-                                       &nxt, nullptr, blen, alen, 0, 0ull, olen, wg)))
+                                       &nxt, nullptr, blen, alen, 0, 0ull, olen, wg, fh)))
                         return rc;
                     s.kind = 1;
                     s.threshold = thr;
@@ -975,6 +998,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             // B-operand row lengths of this evaluation, for the next one
             series->len_baby.assign((size_t)(q > 1 ? q - 1 : 0), 0.0);
             series->len_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
+            series->fma_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             series->out_giant.assign((size_t)(b > 1 ? b - 1 : 0), 0.0);
             std::vector<unsigned> sb((size_t)(q > 1 ? q - 1 : 0), 0u), sg((size_t)(b > 1 ? b - 1 : 0), 0u);
             {
@@ -991,6 +1015,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
                     series->len_giant[(size_t)(i - 1)] = s_len;
                     sg[(size_t)(i - 1)] = ss[idx].span_max;
                     series->out_giant[(size_t)(i - 1)] = (double)steps[idx].nnz_pre / n;
+                    series->fma_giant[(size_t)(i - 1)] = (double)steps[idx].fma;
                     s_len = (double)steps[idx].nnz_post / n;
                 }
                 if (odd) series->len_odd = s_len;  // G-hat, the right factor of F = Z G-hat
@@ -1057,6 +1082,10 @@ int psf_tune_set(int32_t key, double value) {
                 return fail(PSF_EINVAL, "admission count must be a non-negative integer");
             g_fail_admission.store((long long)value);
             return PSF_OK;
+        case PSF_TUNE_DENSE_XOVER:
+            if (!(value >= 0.0)) return fail(PSF_EINVAL, "dense crossover must be >= 0");
+            g_dense_xover.store(value);
+            return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
     }
@@ -1082,6 +1111,9 @@ int psf_tune_get(int32_t key, double* value) {
             return PSF_OK;
         case PSF_TUNE_FAIL_ADMISSION:
             *value = (double)g_fail_admission.load();
+            return PSF_OK;
+        case PSF_TUNE_DENSE_XOVER:
+            *value = g_dense_xover.load();
             return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
@@ -1150,14 +1182,16 @@ int psf_fp64_peak(void* stream, double* tflops) {
     if (!tflops) return fail(PSF_EINVAL, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
     CU(kernels_init());
-    const int blocks = fp64_probe_blocks(), iters = 4096;
+    const int blocks = fp64_probe_blocks(), iters = 8192;
     DevBuf out;
     CU(out.alloc(sizeof(double) * (size_t)blocks * 256, st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU(cudaEventCreate(&e0));
     cudaError_t err = cudaEventCreate(&e1);
     double best = 0.0;
-    for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {  // the first is a warm-up
+    // three warm-up launches (about 50 ms: the clocks rise from idle), then
+    // the best of five
+    for (int rep = 0; rep < 8 && err == cudaSuccess; ++rep) {
         err = cudaEventRecord(e0, st);
         if (err == cudaSuccess) err = launch_fp64_probe(iters, out.as<double>(), st);
         if (err == cudaSuccess) err = cudaEventRecord(e1, st);
@@ -1165,7 +1199,7 @@ int psf_fp64_peak(void* stream, double* tflops) {
         float ms = 0.0f;
         if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
         const double flop = 2.0 * 8.0 * iters * 256.0 * blocks;
-        if (err == cudaSuccess && rep > 0 && ms > 0.0f) best = std::max(best, flop / (ms * 1e-3) / 1e12);
+        if (err == cudaSuccess && rep >= 3 && ms > 0.0f) best = std::max(best, flop / (ms * 1e-3) / 1e12);
     }
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -44,6 +44,10 @@ struct psf_series_s {
     int kernel = 0;       // PSF_PARAM_KERNEL
     int chunk_cols = 0;   // PSF_PARAM_CHUNK_COLS
     int chunk_slots = 0;  // PSF_PARAM_CHUNK_SLOTS
+    double dense_xover = -1.0;  // PSF_PARAM_DENSE_XOVER (-1: the process-wide PSF_TUNE_DENSE_XOVER)
+    // multiply-adds of each giant step in the previous evaluation (the
+    // dense-tile choice of the next one)
+    std::vector<double> fma_giant;
 };
 
 struct psf_result_s {
@@ -117,6 +121,8 @@ struct Work {
     cudaStream_t st = nullptr;
     DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val, cand_col, cand_x, scan;
     DevBuf nwords;  // 24-bit-piece column sums of the norm phase (zero between uses)
+    DevBuf dense[3];  // the dense-tile path's A, B and C (n^2 doubles each), allocated on first use
+    double dense_xover = 1e300;  // dense tiles for a step with at least this many multiply-adds per n^3
     unsigned long long cap = 0, ccap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
@@ -201,6 +207,9 @@ extern std::atomic<bool> g_batch_reuse;
 extern std::atomic<int> g_far_shift;
 // fault injection: the k-th server admission from now fails (PSF_TUNE_FAIL_ADMISSION)
 extern std::atomic<long long> g_fail_admission;
+// the dense-tile crossover in multiply-adds per n^3 (PSF_TUNE_DENSE_XOVER)
+constexpr double kDenseXoverDefault = 0.15;
+extern std::atomic<double> g_dense_xover;
 // slot_map 1: table, 2: bitmap, 0: by the work per row and the crossover
 inline bool use_table(int slot_map, double work_per_row) {
     return slot_map == 1 || (slot_map == 0 && work_per_row >= g_table_crossover.load(std::memory_order_relaxed));

@@ -58,6 +58,11 @@ cudaError_t launch_bounds(int ninst, const int* off, const int* rowptr, int* bou
 cudaError_t launch_reuse_pass1(const ReuseArgs& R, cudaStream_t st);
 cudaError_t launch_reuse_copy_batch(const ProductArgs& P, cudaStream_t st);
 cudaError_t launch_norms_rows(const NormRowsArgs& A, cudaStream_t st);  // then rounds (k_norms_finish)
+// Dense-tile form of a product step (psf_dense.cu): the same output rows,
+// statistics and Algorithm 1 first pass as launch_product, through dense
+// n x n buffers Ad, Bd, Cd (each n^2 doubles, device).
+constexpr int kDenseMaxN = 16384;
+cudaError_t launch_dense_product(const ProductArgs& P, double* Ad, double* Bd, double* Cd, cudaStream_t st);
 // FP64 rate probe: fp64_probe_blocks() blocks of 256 threads, 8 x iters
 // fused multiply-adds per thread, one double per thread written to out
 int fp64_probe_blocks();
