@@ -116,10 +116,12 @@ __device__ __forceinline__ int lower_bound_col(const int* col, int s, int e, int
 
 // slot of column offset o (o inside the current chunk's pattern)
 __device__ __forceinline__ int slot_lookup(const ProdSmem<true>& S, int o) { return S.tab[o]; }
+// (o's own bit is set: the set bits at or below it, shifted to the top,
+// count one more than the bits below it)
 template <int W>
 __device__ __forceinline__ int slot_lookup(const ProdSmem<false, W>& S, int o) {
     const uint2 e = S.pm[o >> 5];
-    return (int)e.x + __popc(e.y & ((1u << (o & 31)) - 1u));
+    return (int)e.x + __popc(e.y << (~o & 31)) - 1;
 }
 
 // where a segment's a_rk are kept
@@ -526,10 +528,33 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int seg
                 S.acc[i] = __fma_rn(a, bval[q], S.acc[i]);
             }
         } else {
-            for (int off = 0; off < len; off += 128) {
-                Chunk ch;
-                chunk_load<false>(bcol, bval, S, kk, off, lane, ch);
-                chunk_fold<false>(S, ch, a, c0, min(4, (len - off + 31) >> 5));
+            // whole 128-entry chunks: four full pieces, no per-lane tests
+            const int* __restrict__ rc = bcol + S.kb[kk] + lane;
+            const double* __restrict__ rv = bval + S.kb[kk] + lane;
+            int off = 0;
+            for (; off + 128 <= len; off += 128) {
+                int j[4];
+                double v[4], x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    j[u] = rc[off + 32 * u];
+                    v[u] = rv[off + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) j[u] = slot_lookup(S, j[u] - c0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = S.acc[j[u]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) S.acc[j[u]] = __fma_rn(a, v[u], x[u]);
+            }
+            // whole 32-entry pieces left, then the last partial piece
+            for (; off + 32 <= len; off += 32) {
+                const int j = slot_lookup(S, rc[off] - c0);
+                S.acc[j] = __fma_rn(a, rv[off], S.acc[j]);
+            }
+            if (off + lane < len) {
+                const int j = slot_lookup(S, rc[off] - c0);
+                S.acc[j] = __fma_rn(a, rv[off], S.acc[j]);
             }
         }
         __syncwarp();
