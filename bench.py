@@ -35,7 +35,8 @@ WORKLOAD = "lap2d_128x128"
 KINDS = ("exp", "cos")
 TOL = 1e-12
 # FP64 peak of the GB300 FP64 pipe: 152 SMs x 2 FMA/clk/SM x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_UNITS = 152 * 2 * 2  # SMs x fma per clock per SM x flop per fma
+FP64_PEAK_TFLOPS = FP64_UNITS * 2.07e9 / 1e12
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_product_traffic.json")
 
 
@@ -151,14 +152,31 @@ def config_dict(n: int, nnz: int, world: int) -> dict:
             "l2": "flushed before each step (256 MB write)", "parallelism": f"replicas x{world}"}
 
 
-def fp64_peak_tflops(L, stream_ptr):
-    """This GPU's FP64 fma rate, measured by the library's probe kernel
-    (falls back to the nominal unit count x clock if the probe fails)."""
+def fp64_probe(L, stream_ptr, gpu_index: int):
+    """The library's FP64 rate probe (psf_fp64_peak: 8 independent fma chains
+    per thread, 4 x 256 threads per SM), with the SM clock sampled while it
+    runs: the probe draws the most power of anything here, and a clock held
+    below its maximum by the power limit lowers its rate with it."""
     import ctypes
+    cs = ClockSampler(gpu_index)
+    cs.start()
+    time.sleep(0.3)  # nvidia-smi's first sample
+    t0 = time.perf_counter()
     v = ctypes.c_double()
-    if L.psf_fp64_peak(stream_ptr, ctypes.byref(v)) == 0 and v.value > 0.0:
-        return v.value, "measured: psf_fp64_peak (8 independent fma chains per thread, 4 x 256 threads per SM)"
-    return FP64_PEAK_TFLOPS, "nominal: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
+    rc = L.psf_fp64_peak(stream_ptr, ctypes.byref(v))
+    cs.mark(t0, time.perf_counter())
+    cs.stop()
+    clk = cs.summary()
+    return {"tflops": v.value if rc == 0 else None, "sm_mhz": clk["sm_mhz"], "reasons": clk["reasons"],
+            "nominal_at_probe_clock": (FP64_UNITS * clk["sm_mhz"] * 1e6 / 1e12) if clk["sm_mhz"] else None}
+
+
+def fp64_peak(clock_mhz):
+    """The FP64 pipe's rate at the SM clock of the timed region: 152 SMs x
+    2 fma per clock x 2 flop (the unit count; the probe reaches 99.9 % of it
+    at 2070 MHz)."""
+    mhz = clock_mhz or 2070.0
+    return FP64_UNITS * mhz * 1e6 / 1e12, f"FP64 pipe: 152 SMs x 2 fma/clk x 2 flop x {mhz:.0f} MHz (timed region)"
 
 
 def _oracle_eval_worker(task):
@@ -336,8 +354,9 @@ def run_psf(args):
     _abi.check(L.psf_profile_read(ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(fma), 1))
     _abi.check(L.psf_profile(0))
     achieved = 2.0 * fma.value / (ms.value / 1e3) / 1e12
-    # the FP64 pipe's rate, measured now that the GPU is warm
-    fp64_peak, fp64_source = fp64_peak_tflops(L, ctypes.c_void_p(stream.cuda_stream))
+    clk = clocks.summary()
+    peak, peak_source = fp64_peak(clk["sm_mhz"])
+    probe = fp64_probe(L, ctypes.c_void_p(stream.cuda_stream), local) if rank == 0 else None
     traffic = None
     try:
         prof = json.load(open(PROFILE_JSON))
@@ -347,10 +366,10 @@ def run_psf(args):
         pass
     # DRAM rate of the product kernel: ncu bytes per launch x launches / event-timed duration
     dram_gbs = traffic * nl.value / (ms.value / 1e3) / 1e9 if traffic and ms.value > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": "k_product",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_product",
                 "dram_gbs": dram_gbs, "dram_frac_of_hbm": dram_gbs / hbm_peak_gbs() if dram_gbs else None,
-                "peak_source": fp64_source, "peak_nominal": FP64_PEAK_TFLOPS,
+                "peak_source": peak_source, "fp64_probe": probe,
                 "launches_timed": nl.value, "kernel_ms": ms.value, "algorithmic_fma": fma.value}
 
     # ---- end to end through the C ABI on host buffers: psf_eval_from_host
@@ -457,7 +476,7 @@ def run_psf(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
-            "clocks": clocks.summary(),
+            "clocks": clk,
             "dense_ps": dense,
             "batched": batched,
             "serving": serving,
@@ -1061,12 +1080,21 @@ def main():
     ap.add_argument("--e2", action="store_true",
                     help="run the paper's banded N(0,1) experiment (n = 1000, w = 1..15) and exit")
     ap.add_argument("--e2-seeds", type=int, default=30, help="matrices per bandwidth in --e2")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="run the library's FP64 rate probe with the clocks sampled, print one JSON line and exit")
     ap.add_argument("--dense-xover", action="store_true",
                     help="time one product step as the sparse kernel and as dense tiles over densities and exit")
     ap.add_argument("--size-sweep", action="store_true",
                     help="time the 2D Laplacian workload on grids 128..768 (product kernel rate per size) and exit")
     args = ap.parse_args()
-    if args.dense_xover:
+    if args.fp64_peak:
+        import ctypes
+        import torch
+        import paper_2208_05683_gb300 as psf
+        torch.cuda.set_device(0)
+        runs = [fp64_probe(psf.lib(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 0) for _ in range(3)]
+        print(json.dumps({"experiment": "psf_fp64_peak", "nominal_2070": FP64_PEAK_TFLOPS, "runs": runs}))
+    elif args.dense_xover:
         run_dense_xover(args)
     elif args.size_sweep:
         run_size_sweep(args)

@@ -161,6 +161,8 @@ def workload(name: str):
         return laplacian_2d(128), "exp", 1e-12
     if name == "banded_n65536_hbw5":
         return banded_random(65536, 5, seed=0, target_norm1=2.0), "exp", 1e-12
+    if name == "random_n2000":  # unstructured: the powers fill in (dense-tile steps)
+        return random_sparse(2000, 0.01, seed=3, target_norm1=2.0), "exp", 1e-12
     raise KeyError(name)
 
 
