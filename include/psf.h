@@ -89,10 +89,10 @@ extern "C" {
 #define PSF_PARAM_CHUNK_COLS 5    /* > 0: fewer columns per row chunk (tests of row chunking) */
 #define PSF_PARAM_CHUNK_SLOTS 6   /* > 0: fewer accumulator slots per row chunk (same) */
 #define PSF_PARAM_DENSE_XOVER 7   /* dense-tile crossover of this series (see PSF_TUNE_DENSE_XOVER):
-                                     a product step with at least this many algorithmic
-                                     multiply-adds per n^3 runs as FP64 dense tiles
-                                     (0: every product step, 1e300: none; -1, the default:
-                                     the process-wide value) */
+                                     a giant step with at least this many algorithmic
+                                     multiply-adds per n^3 in the previous evaluation, n >= 512,
+                                     runs as FP64 dense tiles (0: every product step, any n;
+                                     1e300: none; -1, the default: the process-wide value) */
 
 #define PSF_MAX_Q 23 /* largest supported PS block size q */
 
@@ -406,13 +406,15 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
 #define PSF_TUNE_FAIL_ADMISSION 6
 /* PSF_TUNE_DENSE_XOVER: process-wide dense-tile crossover.  A product step of
  * psf_eval (unless the series sets PSF_PARAM_DENSE_XOVER) or
- * psf_product_filter whose algorithmic multiply-adds (sum over output rows of
- * sum_{k in A_r} nnz(B_k); for psf_eval the count of the same step in the
- * series' previous evaluation, else n times the product of the operands'
- * mean row lengths) reach this value times n^3 runs as an FP64 dense tile
- * product: both operands expanded to dense n x n arrays, every output entry
- * folded over k = 0..n-1 in order (the sparse order with zero terms, which
- * leave it unchanged), then the nonzero entries written back with
+ * psf_product_filter runs as an FP64 dense tile product when its algorithmic
+ * multiply-adds (sum over output rows of sum_{k in A_r} nnz(B_k)) reach this
+ * value times n^3 and n >= 512.  The count is, for psf_eval, that of the same
+ * giant step in the series' previous evaluation (a first evaluation runs
+ * sparse), and for psf_product_filter n times the product of the operands'
+ * mean row lengths.  A crossover of 0 makes every product step dense, at any
+ * n.  Dense tiles: both operands expanded to dense n x n arrays, every output
+ * entry folded over k = 0..n-1 in order (the sparse order with zero terms,
+ * which leave it unchanged), then the nonzero entries written back with
  * Algorithm 1's first pass.  Results are bitwise those of the sparse kernel.
  * Needs 3 n^2 doubles of device memory; steps with n > 16384 always run
  * sparse, and psf_eval_batch always runs sparse.  Default 0.15: one product

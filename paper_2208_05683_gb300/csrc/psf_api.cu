@@ -193,12 +193,17 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
     const double work = alen > 0.0 ? alen * blen : 0.0;
     const bool table = use_table(w.slot_map, work);
     if (reuse_k > 0) P.skip_unless = &w.C()->dropped;
-    // dense tiles for a product with at least dense_xover n^3 multiply-adds
-    // (the previous evaluation's count of this step, else the estimate from
-    // the operands' mean row lengths)
+    // dense tiles for a product with at least dense_xover n^3 multiply-adds:
+    // every product step when the crossover is 0; otherwise a step whose count
+    // is known (the same step of the previous evaluation, or a single product
+    // whose operands' mean row lengths give its expected count) and n >= 512
+    // (below that either form takes a few tens of microseconds, and the dense
+    // form's extra launches dominate)
     const double nd = (double)w.n;
-    const double fma_est = fma_hint > 0.0 ? fma_hint : work * nd;
-    const bool dense = A && reuse_k == 0 && w.n > 0 && w.n <= kDenseMaxN && fma_est >= w.dense_xover * nd * nd * nd;
+    const double fma_est = fma_hint > 0.0 ? fma_hint : (w.dense_estimate ? work * nd : 0.0);
+    const bool dense = A && reuse_k == 0 && w.n > 0 && w.n <= kDenseMaxN &&
+                       (w.dense_xover == 0.0 ||
+                        (w.n >= kDenseMinN && fma_est > 0.0 && fma_est >= w.dense_xover * nd * nd * nd));
     if (dense) {
         const size_t bytes = sizeof(double) * (size_t)w.n * (size_t)w.n;
         for (DevBuf& d : w.dense)
@@ -531,6 +536,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
     Work w;
     if ((rc = w.init(n, st, 1))) return rc;
     w.dense_xover = g_dense_xover.load();
+    w.dense_estimate = true;  // one product: the operands' mean row lengths give its expected count
     CU(cudaMemsetAsync(w.stats.p, 0, sizeof(StepStat), st));
     if ((rc = validate_inputs(w, {A, B}))) return rc;
     for (int t = 0; t < nadd; ++t)

@@ -272,6 +272,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                     P.words = w.words.as<unsigned long long>();
                     P.sticky = w.sticky.as<unsigned>();
                     P.inst = inst;
+                    P.inst_off = d_off.as<int>();
                     P.bstep = d_zstep.as<BatchStep>();
                     P.ninst = count;
                     P.absmax_slot = slots + k;
@@ -622,6 +623,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
             P.words = w.words.as<unsigned long long>();
             P.sticky = w.sticky.as<unsigned>();
             P.inst = inst;
+            P.inst_off = d_off.as<int>();
             P.bstep = reinterpret_cast<const BatchStep*>(d_tab.as<unsigned char>() + step_off[si]);
             P.alpha_tab = reinterpret_cast<const double*>(d_tab.as<unsigned char>() + alpha_off[si]);
             P.ninst = count;

@@ -134,6 +134,7 @@ struct ProductArgs {
     const int* skip_unless;     // non-null: the launch does nothing while *skip_unless == 0
     // batch (inst == nullptr: one instance, the fields above apply to all rows)
     const int* inst;            // instance of each row, n entries
+    const int* inst_off;        // first row (= column) of each instance, ninst + 1 entries (optional)
     const BatchStep* bstep;     // per instance
     const double* alpha_tab;    // [t * ninst + i]: coefficient of term t for instance i (+0: absent)
     int ninst;

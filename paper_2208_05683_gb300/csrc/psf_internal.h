@@ -123,6 +123,7 @@ struct Work {
     DevBuf nwords;  // 24-bit-piece column sums of the norm phase (zero between uses)
     DevBuf dense[3];  // the dense-tile path's A, B and C (n^2 doubles each), allocated on first use
     double dense_xover = 1e300;  // dense tiles for a step with at least this many multiply-adds per n^3
+    bool dense_estimate = false;  // a step without a recorded count may use the row-length estimate
     unsigned long long cap = 0, ccap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
@@ -209,6 +210,7 @@ extern std::atomic<int> g_far_shift;
 extern std::atomic<long long> g_fail_admission;
 // the dense-tile crossover in multiply-adds per n^3 (PSF_TUNE_DENSE_XOVER)
 constexpr double kDenseXoverDefault = 0.15;
+constexpr int kDenseMinN = 512;  // the automatic choice leaves smaller products sparse
 extern std::atomic<double> g_dense_xover;
 // slot_map 1: table, 2: bitmap, 0: by the work per row and the crossover
 inline bool use_table(int slot_map, double work_per_row) {

@@ -134,10 +134,12 @@ __device__ __forceinline__ double* ka_of(ProdSmem<false, W>& S) { return S.acc +
 // whole row when `whole`).
 template <bool TAB, int W>
 __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1,
-                                             int lane, ProdSmem<TAB, W>& S, bool store_a) {
+                                             int lane, ProdSmem<TAB, W>& S, bool store_a,
+                                             unsigned long long* fma = nullptr) {
     if (lane < cnt) {
         int k = P.A.col[seg + lane];
         int b = P.B.rb[k], e = P.B.re[k];
+        if (fma) *fma += (unsigned long long)(e - b);
         if (!whole) {
             int b2 = lower_bound_col(P.B.col, b, e, c0);
             e = lower_bound_col(P.B.col, b2, e, c1);
@@ -243,7 +245,7 @@ __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false, W>
 template <bool TAB, int W>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
                                           int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB, W>& S,
-                                          bool store_a) {
+                                          bool store_a, unsigned long long* fma = nullptr) {
     clear_map(cend - c0, lane, S);
     __syncwarp();
     for (int t = 0; t < nadd; ++t) {
@@ -258,7 +260,7 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
     }
     for (int seg = pa0; seg < pa1; seg += 32) {
         const int cnt = min(32, pa1 - seg);
-        load_segment<TAB>(P, seg, cnt, whole, c0, cend, lane, S, store_a);
+        load_segment<TAB>(P, seg, cnt, whole, c0, cend, lane, S, store_a, fma);
         if constexpr (!TAB) {
             if (warp_max(lane < cnt ? S.kl[lane] : 0) <= 32) {
                 mark_rows_short(P.B.col, cnt, c0, cend, lane, S);
@@ -648,9 +650,28 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
             my_cand = 0ull;
         }
         const unsigned long long fma0 = BATCH ? 0ull : my_fma, cand0 = BATCH ? 0ull : my_cand;
-        // ---- column window of row r and the row's multiply-add count
+        // ---- column window of row r and the row's multiply-add count.  A
+        // matrix (or a batch instance) of at most one map's columns is its own
+        // window: no loads to find the row's, and the B row lengths are counted
+        // while the map is built
         int lo = INT_MAX, hi = -1;
-        for (int t = 0; t < nadd; ++t) {
+        bool fixed = false;
+        if constexpr (!TAB) {
+            int w0 = 0, w1 = P.n;
+            if constexpr (BATCH) {
+                w1 = -1;
+                if (P.inst_off) {
+                    w0 = P.inst_off[r_inst];
+                    w1 = P.inst_off[r_inst + 1];
+                }
+            }
+            if (w1 > w0 && w1 - w0 <= kCols) {
+                lo = w0;
+                hi = w1 - 1;
+                fixed = true;
+            }
+        }
+        for (int t = 0; t < nadd && !fixed; ++t) {
             if (!((tmask >> t) & 1u)) continue;
             const AddTerm& T = add[t];
             if (!T.rb) {
@@ -669,7 +690,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
             pa0 = P.A.rb[r];
             pa1 = P.A.re[r];
         }
-        for (int p = pa0 + lane; p < pa1; p += 32) {
+        for (int p = pa0 + lane; p < pa1 && !fixed; p += 32) {
             int k = P.A.col[p];
             int s = P.B.rb[k], e = P.B.re[k];
             my_fma += (unsigned long long)(e - s);
@@ -694,7 +715,8 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
         long long total = 0;
         bool reuse = false;
         if (hi - lo + 1 <= kCols) {
-            build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE);
+            build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE,
+                           fixed ? &my_fma : nullptr);
             total = count_marks(hi - lo + 1, lane, S);
             reuse = true;
         } else {
