@@ -586,6 +586,246 @@ __device__ __forceinline__ void row_stats_batch(const ProductArgs& P, int inst, 
     }
 }
 
+// Per-warp state of the product kernel across the rows a warp processes.
+struct RowState {
+    unsigned long long written = 0ull, cand = 0ull, absmax = 0ull, fma = 0ull;
+    int span = 0;  // widest column window of this warp's rows
+    Arena arena;
+    CandArena carena;
+};
+
+// One output row r of C = sum_t alpha_t M_t + A B (see k_product), processed
+// by one warp with the slot map S.
+template <bool TAB, bool BATCH, bool WIDE, int W>
+__device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm* add, ProdSmem<TAB, W>& S,
+                                            RowState& st, int r, int lane) {
+    using Smem = ProdSmem<TAB, W>;
+    // columns and slots of one chunk (lowered only to exercise chunking)
+    const int kCols = P.chunk_cols > 0 && P.chunk_cols < Smem::kCols ? P.chunk_cols : Smem::kCols;
+    constexpr int kCapN = (TAB || WIDE) ? kAccCap : kAccCap - 32;  // a row's slots
+    const int kSlots = P.chunk_slots > 0 && P.chunk_slots < kCapN ? P.chunk_slots : kCapN;
+    const int nadd = P.nadd;
+    const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
+    unsigned long long& my_written = st.written;
+    unsigned long long& my_cand = st.cand;
+    unsigned long long& my_absmax = st.absmax;
+    unsigned long long& my_fma = st.fma;
+    int& my_span = st.span;
+    Arena& arena = st.arena;
+    CandArena& carena = st.carena;
+
+
+    // ---- the row's terms: single instance, every term and the product;
+    // batch, what the row's instance does in this step
+    bool prod = P.A.rb != nullptr;
+    unsigned tmask = kFull;  // terms present in this row (batch: coefficient != 0)
+    int r_inst = 0;
+    if constexpr (BATCH) {
+        r_inst = P.inst[r];
+        const BatchStep bs = P.bstep[r_inst];
+        // the row equals the norm phase's power: k_reuse_copy_batch writes it
+        if (bs.reuse && __ldcg(P.inst_dropped + r_inst) == 0) return;
+        if (bs.mode == kBatchSkip || bs.mode == kBatchPass) {
+            if (lane == 0) {
+                P.out_rb[r] = bs.mode == kBatchPass ? P.B.rb[r] : 0;
+                P.out_re[r] = bs.mode == kBatchPass ? P.B.re[r] : 0;
+            }
+            return;
+        }
+        prod = bs.mode == kBatchProduct;
+        const double a_lane = lane < nadd ? P.alpha_tab[(size_t)lane * P.ninst + r_inst] : 0.0;
+        tmask = __ballot_sync(kFull, __double_as_longlong(a_lane) != 0ll);
+    }
+    // batch: the counters are per row (reported per instance after each
+    // row); single: running totals, reported per block at the end
+    if constexpr (BATCH) {
+        my_fma = 0ull;
+        my_cand = 0ull;
+    }
+    const unsigned long long fma0 = BATCH ? 0ull : my_fma, cand0 = BATCH ? 0ull : my_cand;
+    // ---- column window of row r and the row's multiply-add count.  A
+    // matrix (or a batch instance) of at most one map's columns is its own
+    // window: no loads to find the row's, and the B row lengths are counted
+    // while the map is built
+    int lo = INT_MAX, hi = -1;
+    bool fixed = false;
+    if constexpr (!TAB) {
+        int w0 = 0, w1 = P.n;
+        if constexpr (BATCH) {
+            w1 = -1;
+            if (P.inst_off) {
+                w0 = P.inst_off[r_inst];
+                w1 = P.inst_off[r_inst + 1];
+            }
+        }
+        if (w1 > w0 && w1 - w0 <= kCols) {
+            lo = w0;
+            hi = w1 - 1;
+            fixed = true;
+        }
+    }
+    for (int t = 0; t < nadd && !fixed; ++t) {
+        if (!((tmask >> t) & 1u)) continue;
+        const AddTerm& T = add[t];
+        if (!T.rb) {
+            lo = min(lo, r);
+            hi = max(hi, r);
+        } else {
+            int s = T.rb[r], e = T.re[r];
+            if (s < e) {
+                lo = min(lo, T.col[s]);
+                hi = max(hi, T.col[e - 1]);
+            }
+        }
+    }
+    int pa0 = 0, pa1 = 0;
+    if (prod) {
+        pa0 = P.A.rb[r];
+        pa1 = P.A.re[r];
+    }
+    for (int p = pa0 + lane; p < pa1 && !fixed; p += 32) {
+        int k = P.A.col[p];
+        int s = P.B.rb[k], e = P.B.re[k];
+        my_fma += (unsigned long long)(e - s);
+        if (s < e) {
+            lo = min(lo, P.B.col[s]);
+            hi = max(hi, P.B.col[e - 1]);
+        }
+    }
+    if (lane == 0)
+        for (int t = 0; t < nadd; ++t)
+            if ((tmask >> t) & 1u) my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    my_span = max(my_span, hi - lo + 1);
+    if (hi < lo) {
+        if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
+        if constexpr (BATCH) row_stats_batch(P, r_inst, my_fma - fma0, 0ull, 0, 0ull, lane);
+        return;
+    }
+
+    // ---- exact entry count of the row, reserve it in the pool
+    long long total = 0;
+    bool reuse = false;
+    if (hi - lo + 1 <= kCols) {
+        build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE,
+                       fixed ? &my_fma : nullptr);
+        total = count_marks(hi - lo + 1, lane, S);
+        reuse = true;
+    } else {
+        for (long long c0 = lo; c0 <= hi; c0 += kCols) {
+            int cend = (int)min((long long)hi + 1, c0 + kCols);
+            build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE);
+            total += count_marks(cend - (int)c0, lane, S);
+        }
+    }
+    const long long base = arena_take(arena, (unsigned long long)((total + 3) & ~3LL), P.arena, P.ctl, P.pool_val, lane);
+    if (base < 0) {
+        if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
+        return;
+    }
+    const bool single = reuse && total <= kSlots;
+    int written = 0;
+    int c0 = lo;
+    while (c0 <= hi) {
+        int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
+        if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE);
+        reuse = false;
+        int cut;
+        const int cnt = assign_slots(cend - c0, kSlots, lane, S, &cut);
+        const int c1 = c0 + cut;
+        for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
+        __syncwarp();
+
+        // ---- weighted sum of the addends, t ascending
+        for (int t = 0; t < nadd; ++t) {
+            if (!((tmask >> t) & 1u)) continue;
+            const AddTerm& T = add[t];
+            // batch: the row's instance's coefficient (a small, cached table)
+            const double alpha = BATCH ? P.alpha_tab[(size_t)t * P.ninst + r_inst] : T.alpha;
+            if (!T.rb) {
+                if (lane == 0 && r >= c0 && r < c1) {
+                    int i = slot_lookup(S, r - c0);
+                    S.acc[i] = __fma_rn(alpha, 1.0, S.acc[i]);
+                }
+            } else {
+                int s = T.rb[r], e = T.re[r];
+                for (int q = s + lane; q < e; q += 32) {
+                    int c = T.col[q];
+                    if (c >= c0 && c < c1) {
+                        int i = slot_lookup(S, c - c0);
+                        S.acc[i] = __fma_rn(alpha, T.val[q], S.acc[i]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---- product A B: k of row r ascending
+        for (int seg = pa0; seg < pa1; seg += 32) {
+            const int cnt_seg = min(32, pa1 - seg);
+            load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S, !WIDE);
+            accumulate_segment<WIDE>(P, seg, cnt_seg, c0, lane, S);
+        }
+
+        // ---- write back the nonzero entries in column order; the entries
+        // with |x| <= eps_g enter the column sums of Algorithm 1's first pass
+        // (batch: the filter of the row's instance, read here rather than
+        // held in registers through the row)
+        unsigned long long r_eps = eps_bits;
+        int r_lsb = P.e_lsb;
+        bool r_filt = P.filtering != 0;
+        if constexpr (BATCH) {
+            const BatchStep& bs = P.bstep[r_inst];
+            r_filt = bs.eps_g > 0.0;
+            r_eps = (unsigned long long)__double_as_longlong(bs.eps_g);
+            r_lsb = bs.e_lsb;
+        }
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            int i = i0 + lane;
+            double x = 0.0;
+            int c = 0;
+            if (i < cnt) {
+                x = S.acc[i];
+                c = c0 + (int)S.colbuf[i];
+            }
+            unsigned long long xb = mag_bits(x);
+            bool nz = i < cnt && xb != 0ull;
+            unsigned m = __ballot_sync(kFull, nz);
+            const bool cand = nz && r_filt && xb <= r_eps;
+            if (nz) {
+                long long pos = (long long)base + written + __popc(m & lanemask_lt());
+                P.pool_col[pos] = c;
+                P.pool_val[pos] = x;
+                my_absmax = xb > my_absmax ? xb : my_absmax;
+                if (cand) {
+                    exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, r_lsb);
+                    ++my_cand;
+                }
+            }
+            if (P.cand_col)
+                cand_push(carena, cand, c, xb, P.cand_col, P.cand_x, &P.ctl->cand_cnt[0], P.cand_cap,
+                          P.cand_chunk, &P.ctl->cand_over, lane);
+            written += __popc(m);
+        }
+        __syncwarp();
+        c0 = c1;
+    }
+    // the row's unused reserved slots read as exact zeros (never candidates)
+    const long long rend = base + ((total + 3) & ~3LL);
+    for (long long q = base + written + lane; q < rend; q += 32) P.pool_val[q] = 0.0;
+    if (lane == 0) {
+        P.out_rb[r] = (int)base;
+        P.out_re[r] = (int)(base + written);
+    }
+    if constexpr (BATCH) {
+        row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane, hi - lo + 1);
+        my_absmax = 0ull;
+    } else if (lane == 0) {
+        my_written += (unsigned long long)written;
+    }
+}
+
 template <bool TAB, bool BATCH, bool WIDE, int W = kBmWords>
 __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W>::kBlocksPerSm)
     k_product(ProductArgs P) {
@@ -594,10 +834,6 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
     if (P.skip_unless && __ldcg(P.skip_unless) == 0) return;
     using Smem = ProdSmem<TAB, W>;
     constexpr int kWarps = Smem::kWarps;
-    // columns and slots of one chunk (lowered only to exercise chunking)
-    const int kCols = P.chunk_cols > 0 && P.chunk_cols < Smem::kCols ? P.chunk_cols : Smem::kCols;
-    constexpr int kCapN = (TAB || WIDE) ? kAccCap : kAccCap - 32;  // a row's slots
-    const int kSlots = P.chunk_slots > 0 && P.chunk_slots < kCapN ? P.chunk_slots : kCapN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
     Smem* warps = reinterpret_cast<Smem*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
@@ -615,238 +851,24 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
     }
     __syncthreads();
     Smem& S = warps[wib];
-    const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(P.eps_g);
-    unsigned long long my_written = 0ull, my_cand = 0ull, my_absmax = 0ull, my_fma = 0ull;
-    int my_span = 0;  // widest column window of this warp's rows
-    Arena arena;
-    CandArena carena;
-
-    for (int r = blockIdx.x * kWarps + wib; r < P.n; r += gridDim.x * kWarps) {
-        // ---- the row's terms: single instance, every term and the product;
-        // batch, what the row's instance does in this step
-        bool prod = P.A.rb != nullptr;
-        unsigned tmask = kFull;  // terms present in this row (batch: coefficient != 0)
-        int r_inst = 0;
-        if constexpr (BATCH) {
-            r_inst = P.inst[r];
-            const BatchStep bs = P.bstep[r_inst];
-            // the row equals the norm phase's power: k_reuse_copy_batch writes it
-            if (bs.reuse && __ldcg(P.inst_dropped + r_inst) == 0) continue;
-            if (bs.mode == kBatchSkip || bs.mode == kBatchPass) {
-                if (lane == 0) {
-                    P.out_rb[r] = bs.mode == kBatchPass ? P.B.rb[r] : 0;
-                    P.out_re[r] = bs.mode == kBatchPass ? P.B.re[r] : 0;
-                }
-                continue;
-            }
-            prod = bs.mode == kBatchProduct;
-            const double a_lane = lane < nadd ? P.alpha_tab[(size_t)lane * P.ninst + r_inst] : 0.0;
-            tmask = __ballot_sync(kFull, __double_as_longlong(a_lane) != 0ll);
-        }
-        // batch: the counters are per row (reported per instance after each
-        // row); single: running totals, reported per block at the end
-        if constexpr (BATCH) {
-            my_fma = 0ull;
-            my_cand = 0ull;
-        }
-        const unsigned long long fma0 = BATCH ? 0ull : my_fma, cand0 = BATCH ? 0ull : my_cand;
-        // ---- column window of row r and the row's multiply-add count.  A
-        // matrix (or a batch instance) of at most one map's columns is its own
-        // window: no loads to find the row's, and the B row lengths are counted
-        // while the map is built
-        int lo = INT_MAX, hi = -1;
-        bool fixed = false;
-        if constexpr (!TAB) {
-            int w0 = 0, w1 = P.n;
-            if constexpr (BATCH) {
-                w1 = -1;
-                if (P.inst_off) {
-                    w0 = P.inst_off[r_inst];
-                    w1 = P.inst_off[r_inst + 1];
-                }
-            }
-            if (w1 > w0 && w1 - w0 <= kCols) {
-                lo = w0;
-                hi = w1 - 1;
-                fixed = true;
-            }
-        }
-        for (int t = 0; t < nadd && !fixed; ++t) {
-            if (!((tmask >> t) & 1u)) continue;
-            const AddTerm& T = add[t];
-            if (!T.rb) {
-                lo = min(lo, r);
-                hi = max(hi, r);
-            } else {
-                int s = T.rb[r], e = T.re[r];
-                if (s < e) {
-                    lo = min(lo, T.col[s]);
-                    hi = max(hi, T.col[e - 1]);
-                }
-            }
-        }
-        int pa0 = 0, pa1 = 0;
-        if (prod) {
-            pa0 = P.A.rb[r];
-            pa1 = P.A.re[r];
-        }
-        for (int p = pa0 + lane; p < pa1 && !fixed; p += 32) {
-            int k = P.A.col[p];
-            int s = P.B.rb[k], e = P.B.re[k];
-            my_fma += (unsigned long long)(e - s);
-            if (s < e) {
-                lo = min(lo, P.B.col[s]);
-                hi = max(hi, P.B.col[e - 1]);
-            }
-        }
-        if (lane == 0)
-            for (int t = 0; t < nadd; ++t)
-                if ((tmask >> t) & 1u) my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
-        lo = warp_min(lo);
-        hi = warp_max(hi);
-        my_span = max(my_span, hi - lo + 1);
-        if (hi < lo) {
-            if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
-            if constexpr (BATCH) row_stats_batch(P, r_inst, my_fma - fma0, 0ull, 0, 0ull, lane);
-            continue;
-        }
-
-        // ---- exact entry count of the row, reserve it in the pool
-        long long total = 0;
-        bool reuse = false;
-        if (hi - lo + 1 <= kCols) {
-            build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE,
-                           fixed ? &my_fma : nullptr);
-            total = count_marks(hi - lo + 1, lane, S);
-            reuse = true;
-        } else {
-            for (long long c0 = lo; c0 <= hi; c0 += kCols) {
-                int cend = (int)min((long long)hi + 1, c0 + kCols);
-                build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE);
-                total += count_marks(cend - (int)c0, lane, S);
-            }
-        }
-        const long long base = arena_take(arena, (unsigned long long)((total + 3) & ~3LL), P.arena, P.ctl, P.pool_val, lane);
-        if (base < 0) {
-            if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
-            continue;
-        }
-        const bool single = reuse && total <= kSlots;
-        int written = 0;
-        int c0 = lo;
-        while (c0 <= hi) {
-            int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
-            if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE);
-            reuse = false;
-            int cut;
-            const int cnt = assign_slots(cend - c0, kSlots, lane, S, &cut);
-            const int c1 = c0 + cut;
-            for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
-            __syncwarp();
-
-            // ---- weighted sum of the addends, t ascending
-            for (int t = 0; t < nadd; ++t) {
-                if (!((tmask >> t) & 1u)) continue;
-                const AddTerm& T = add[t];
-                // batch: the row's instance's coefficient (a small, cached table)
-                const double alpha = BATCH ? P.alpha_tab[(size_t)t * P.ninst + r_inst] : T.alpha;
-                if (!T.rb) {
-                    if (lane == 0 && r >= c0 && r < c1) {
-                        int i = slot_lookup(S, r - c0);
-                        S.acc[i] = __fma_rn(alpha, 1.0, S.acc[i]);
-                    }
-                } else {
-                    int s = T.rb[r], e = T.re[r];
-                    for (int q = s + lane; q < e; q += 32) {
-                        int c = T.col[q];
-                        if (c >= c0 && c < c1) {
-                            int i = slot_lookup(S, c - c0);
-                            S.acc[i] = __fma_rn(alpha, T.val[q], S.acc[i]);
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-
-            // ---- product A B: k of row r ascending
-            for (int seg = pa0; seg < pa1; seg += 32) {
-                const int cnt_seg = min(32, pa1 - seg);
-                load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S, !WIDE);
-                accumulate_segment<WIDE>(P, seg, cnt_seg, c0, lane, S);
-            }
-
-            // ---- write back the nonzero entries in column order; the entries
-            // with |x| <= eps_g enter the column sums of Algorithm 1's first pass
-            // (batch: the filter of the row's instance, read here rather than
-            // held in registers through the row)
-            unsigned long long r_eps = eps_bits;
-            int r_lsb = P.e_lsb;
-            bool r_filt = P.filtering != 0;
-            if constexpr (BATCH) {
-                const BatchStep& bs = P.bstep[r_inst];
-                r_filt = bs.eps_g > 0.0;
-                r_eps = (unsigned long long)__double_as_longlong(bs.eps_g);
-                r_lsb = bs.e_lsb;
-            }
-            for (int i0 = 0; i0 < cnt; i0 += 32) {
-                int i = i0 + lane;
-                double x = 0.0;
-                int c = 0;
-                if (i < cnt) {
-                    x = S.acc[i];
-                    c = c0 + (int)S.colbuf[i];
-                }
-                unsigned long long xb = mag_bits(x);
-                bool nz = i < cnt && xb != 0ull;
-                unsigned m = __ballot_sync(kFull, nz);
-                const bool cand = nz && r_filt && xb <= r_eps;
-                if (nz) {
-                    long long pos = (long long)base + written + __popc(m & lanemask_lt());
-                    P.pool_col[pos] = c;
-                    P.pool_val[pos] = x;
-                    my_absmax = xb > my_absmax ? xb : my_absmax;
-                    if (cand) {
-                        exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, r_lsb);
-                        ++my_cand;
-                    }
-                }
-                if (P.cand_col)
-                    cand_push(carena, cand, c, xb, P.cand_col, P.cand_x, &P.ctl->cand_cnt[0], P.cand_cap,
-                              P.cand_chunk, &P.ctl->cand_over, lane);
-                written += __popc(m);
-            }
-            __syncwarp();
-            c0 = c1;
-        }
-        // the row's unused reserved slots read as exact zeros (never candidates)
-        const long long rend = base + ((total + 3) & ~3LL);
-        for (long long q = base + written + lane; q < rend; q += 32) P.pool_val[q] = 0.0;
-        if (lane == 0) {
-            P.out_rb[r] = (int)base;
-            P.out_re[r] = (int)(base + written);
-        }
-        if constexpr (BATCH) {
-            row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane, hi - lo + 1);
-            my_absmax = 0ull;
-        } else if (lane == 0) {
-            my_written += (unsigned long long)written;
-        }
-    }
+    RowState st;
+    for (int r = blockIdx.x * kWarps + wib; r < P.n; r += gridDim.x * kWarps)
+        product_row<TAB, BATCH, WIDE, W>(P, add, S, st, r, lane);
     // the unused end of this warp's arena reads as exact zeros too, and the
     // unused end of its candidate chunk as holes
-    arena_close(arena, P.pool_val, lane);
-    if (P.cand_col) cand_close(carena, P.cand_x, lane);
+    arena_close(st.arena, P.pool_val, lane);
+    if (P.cand_col) cand_close(st.carena, P.cand_x, lane);
     if constexpr (BATCH) return;
     // ---- block totals for the step statistics
-    my_cand = (unsigned long long)warp_sum((int)my_cand);
-    my_absmax = warp_max_u64(my_absmax);
-    for (int o = 16; o; o >>= 1) my_fma += __shfl_xor_sync(kFull, my_fma, o);
+    st.cand = (unsigned long long)warp_sum((int)st.cand);
+    st.absmax = warp_max_u64(st.absmax);
+    for (int o = 16; o; o >>= 1) st.fma += __shfl_xor_sync(kFull, st.fma, o);
     if (lane == 0) {
-        atomicAdd(&blk_fma, my_fma);
-        atomicAdd(&blk_written, my_written);
-        atomicAdd(&blk_cand, my_cand);
-        atomicMax(&blk_absmax, my_absmax);
-        atomicMax(&blk_span, my_span);
+        atomicAdd(&blk_fma, st.fma);
+        atomicAdd(&blk_written, st.written);
+        atomicAdd(&blk_cand, st.cand);
+        atomicMax(&blk_absmax, st.absmax);
+        atomicMax(&blk_span, st.span);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -860,6 +882,7 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
         if (P.absmax_slot && blk_absmax) atomicMax(&P.absmax_slot->absmax, blk_absmax);
     }
 }
+
 
 // Keep the entries of row [s, e) with |x| > fb (bits), in place and in
 // column order; the dropped tail is cleared to exact zeros.  Returns the new
