@@ -422,6 +422,17 @@ PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uin
  * 0.14-0.19 multiply-adds per n^3 on (the tiles run at 0.97-1.19 TFLOP/s,
  * the sparse kernel at 0.1-0.5); a value >= 0. */
 #define PSF_TUNE_DENSE_XOVER 7
+/* PSF_TUNE_ROW_BITMAPS: the sparse product kernel of psf_eval and
+ * psf_product_filter can mark a row's output pattern from column bitmaps of
+ * B's rows (built by one launch before the product, a 32-bit word per entry
+ * of the entry pool) a word at a time instead of a column at a time; B rows
+ * with more bitmap words than entries are marked by column.  0: never.
+ * 1 (default): for products whose A rows average at least 12 entries and
+ * whose B rows average at least 32 (each B row is marked many times and has
+ * words to share; the giant steps of near-sparse series).  2: for every
+ * product.  Results are the same either way; with 0 a call allocates no
+ * bitmap words. */
+#define PSF_TUNE_ROW_BITMAPS 8
 PSF_API int psf_tune_set(int32_t key, double value);
 PSF_API int psf_tune_get(int32_t key, double* value);
 PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, double* crossover,

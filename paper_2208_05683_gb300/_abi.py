@@ -21,6 +21,7 @@ PSF_TUNE_ALG1_FAR_SHIFT = 4
 PSF_TUNE_BARRIER_BUDGET_NS = 5
 PSF_TUNE_FAIL_ADMISSION = 6
 PSF_TUNE_DENSE_XOVER = 7
+PSF_TUNE_ROW_BITMAPS = 8
 
 ERROR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "ETOOBIG", 7: "ECANCELED"}
 

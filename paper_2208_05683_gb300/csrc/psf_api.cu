@@ -55,6 +55,7 @@ std::atomic<bool> g_batch_reuse{true};
 std::atomic<int> g_far_shift{6};
 std::atomic<long long> g_fail_admission{0};
 std::atomic<double> g_dense_xover{kDenseXoverDefault};
+std::atomic<int> g_row_bitmaps{1};
 thread_local TuneRecorder* g_tune_rec = nullptr;
 
 cudaError_t configure_mempool() {
@@ -210,6 +211,15 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
             if (!d.p) CU(d.alloc(bytes, w.st));
         CU(launch_dense_product(P, w.dense[0].as<double>(), w.dense[1].as<double>(), w.dense[2].as<double>(), w.st));
     } else {
+        // the bitmap map marks B rows from their column bitmaps (built here,
+        // one launch over B); the chunked test settings keep the column marks
+        const int bm = g_row_bitmaps.load();
+        if (A && !table && bm > 0 && w.bits_cap >= w.cap && w.chunk_cols <= 0 && w.chunk_slots <= 0 &&
+            (bm == 2 || (alen >= kBitmapMinA && blen >= kBitmapMinB))) {
+            CU(launch_row_bitmaps(w.n, *B, w.bhdr.as<int2>(), w.pool_bits.as<unsigned>(), w.st));
+            P.bhdr = w.bhdr.as<int2>();
+            P.bbits = w.pool_bits.as<unsigned>();
+        }
         CU(launch_product(P, table, w.st, out_len, wide_window || w.slot_map == 3));
     }
     if (reuse_k > 0) {
@@ -1092,6 +1102,10 @@ int psf_tune_set(int32_t key, double value) {
             if (!(value >= 0.0)) return fail(PSF_EINVAL, "dense crossover must be >= 0");
             g_dense_xover.store(value);
             return PSF_OK;
+        case PSF_TUNE_ROW_BITMAPS:
+            if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(PSF_EINVAL, "row bitmaps must be 0, 1 or 2");
+            g_row_bitmaps.store((int)value);
+            return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);
     }
@@ -1120,6 +1134,9 @@ int psf_tune_get(int32_t key, double* value) {
             return PSF_OK;
         case PSF_TUNE_DENSE_XOVER:
             *value = g_dense_xover.load();
+            return PSF_OK;
+        case PSF_TUNE_ROW_BITMAPS:
+            *value = (double)g_row_bitmaps.load();
             return PSF_OK;
         default:
             return fail(PSF_EINVAL, "unknown tuning key %d", key);

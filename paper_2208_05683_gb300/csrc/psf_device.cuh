@@ -145,6 +145,11 @@ struct ProductArgs {
     // phase's Z^k) instead of the product
     const int* inst_dropped;
     RowView power;
+    // column bitmaps of B's rows (nullptr: none): bhdr[k] = {first column of
+    // row k / 32, words}, the words at bbits[B.rb[k]] on (0 words: row k has
+    // no bitmap)
+    const int2* bhdr;
+    const unsigned* bbits;
 };
 
 // Algorithm 1 passes 2, 3, ... and compaction for every filtered instance of

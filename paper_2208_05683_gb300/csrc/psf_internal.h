@@ -116,15 +116,23 @@ extern Profile g_prof;
 constexpr unsigned long long kMaxPool = (1ull << 31) - (1ull << 20);
 
 // Device workspace shared by the phases of one evaluation.
+// products mark their output pattern from column bitmaps of B's rows
+// (PSF_TUNE_ROW_BITMAPS: 0 never, 1 when A's rows average at least
+// kBitmapMinA entries and B's kBitmapMinB, 2 always)
+extern std::atomic<int> g_row_bitmaps;
+constexpr double kBitmapMinA = 12.0;
+constexpr double kBitmapMinB = 32.0;
+
 struct Work {
     int n = 0;
     cudaStream_t st = nullptr;
     DevBuf ctl, stats, slots, words, sticky, pool_col, pool_val, cand_col, cand_x, scan;
     DevBuf nwords;  // 24-bit-piece column sums of the norm phase (zero between uses)
     DevBuf dense[3];  // the dense-tile path's A, B and C (n^2 doubles each), allocated on first use
+    DevBuf bhdr, pool_bits;  // column bitmaps of a product's B rows: n headers, a word per pool entry
     double dense_xover = 1e300;  // dense tiles for a step with at least this many multiply-adds per n^3
     bool dense_estimate = false;  // a step without a recorded count may use the row-length estimate
-    unsigned long long cap = 0, ccap = 0;
+    unsigned long long cap = 0, ccap = 0, bits_cap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
     int chunk_cols = 0, chunk_slots = 0;
@@ -147,6 +155,7 @@ struct Work {
         CU(sticky.alloc(sizeof(unsigned) * nn * kMaxNorms, st));
         CU(cudaMemsetAsync(sticky.p, 0, sizeof(unsigned) * nn * kMaxNorms, st));
         CU(scan.alloc(sizeof(long long) * scan_scratch_len(n_), st));
+        CU(bhdr.alloc(sizeof(int2) * nn, st));
         return PSF_OK;
     }
     // (re)allocate the entry pool and reset the device control block
@@ -161,6 +170,10 @@ struct Work {
             ccap = cap / 2 > 1024 ? cap / 2 : 1024;
             CU(cand_col.alloc(sizeof(int) * 2 * ccap, st));
             CU(cand_x.alloc(sizeof(unsigned long long) * 2 * ccap, st));
+        }
+        if (g_row_bitmaps.load() > 0 && bits_cap < cap) {
+            CU(pool_bits.alloc(sizeof(unsigned) * cap, st));
+            bits_cap = cap;
         }
         Ctl h{};
         h.pool_cap = cap;

@@ -135,11 +135,17 @@ __device__ __forceinline__ double* ka_of(ProdSmem<false, W>& S) { return S.acc +
 template <bool TAB, int W>
 __device__ __forceinline__ void load_segment(const ProductArgs& P, int seg, int cnt, bool whole, int c0, int c1,
                                              int lane, ProdSmem<TAB, W>& S, bool store_a,
-                                             unsigned long long* fma = nullptr) {
+                                             unsigned long long* fma = nullptr, int* kwn = nullptr) {
     if (lane < cnt) {
         int k = P.A.col[seg + lane];
         int b = P.B.rb[k], e = P.B.re[k];
         if (fma) *fma += (unsigned long long)(e - b);
+        if (kwn) {
+            // B row k's bitmap: its first word's offset in the window (c0 is a
+            // multiple of 32 and the window holds the whole row) and its words
+            const int2 h = P.bhdr[k];
+            kwn[lane] = h.y > 0 ? ((h.x - (c0 >> 5)) << 16) | h.y : 0;
+        }
         if (!whole) {
             int b2 = lower_bound_col(P.B.col, b, e, c0);
             e = lower_bound_col(P.B.col, b2, e, c1);
@@ -209,8 +215,8 @@ __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int
 // the other.  The rows are clipped to [c0, cend) (see mark_row).
 template <int W>
 __device__ __forceinline__ void mark_rows_short(const int* __restrict__ col, int cnt, int c0, int cend, int lane,
-                                                ProdSmem<false, W>& S) {
-    if (lane >= cnt) return;
+                                                ProdSmem<false, W>& S, bool active = true) {
+    if (lane >= cnt || !active) return;
     const int s = S.kb[lane], e = s + S.kl[lane];
     unsigned curw = 0xffffffffu, mask = 0u;
 #pragma unroll 2
@@ -241,8 +247,56 @@ __device__ __forceinline__ void clear_map(int wlen, int lane, ProdSmem<false, W>
     for (int w = lane; w < nw; w += 32) S.pm[w].y = 0u;
 }
 
+// The B rows of A's row [pa0, pa1) into the bitmap, for a row that takes one
+// chunk whose first column c0 is a multiple of 32: a B row with a bitmap
+// (bhdr) is ORed in a word at a time, lane l collecting the window words
+// l, l + 32, ... in registers (coalesced loads, no shared-memory traffic
+// until the end); the others are marked column by column as in build_map.
+template <int W>
+__device__ __forceinline__ void mark_from_bitmaps(const ProductArgs& P, int pa0, int pa1, int c0, int cend, int lane,
+                                                  ProdSmem<false, W>& S, bool store_a, unsigned long long* fma) {
+    constexpr int R = (W + 31) / 32;
+    unsigned reg[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) reg[u] = 0u;
+    int* kwn = reinterpret_cast<int*>(S.colbuf);  // free until the slots are assigned
+    const unsigned* __restrict__ bits = P.bbits;
+    for (int seg = pa0; seg < pa1; seg += 32) {
+        const int cnt = min(32, pa1 - seg);
+        load_segment<false>(P, seg, cnt, true, c0, cend, lane, S, store_a, fma, kwn);
+        // rows without a bitmap: short ones one per lane, long ones by the warp
+        const int my = lane < cnt && kwn[lane] == 0 ? S.kl[lane] : 0;
+        mark_rows_short(P.B.col, cnt, c0, cend, lane, S, my > 0 && my <= 32);
+        unsigned longm = __ballot_sync(kFull, my > 32);
+        while (longm) {
+            const int i = __ffs(longm) - 1;
+            longm &= longm - 1u;
+            mark_row<false>(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+        }
+        for (int i = 0; i < cnt; ++i) {
+            const int h = kwn[i];
+            if (h == 0) continue;
+            const int kw = h >> 16, kn = h & 0xffff;
+            const int base = S.kb[i] - kw;  // bits[base + w]: window word w
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int w = lane + 32 * u;
+                if (w >= kw && w < kw + kn) reg[u] |= bits[base + w];
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int w = lane + 32 * u;
+        if (w < W && reg[u]) S.pm[w].y |= reg[u];
+    }
+    __syncwarp();
+}
+
 // Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
-template <bool TAB, int W>
+// BMP: B row bitmaps may be used (the single-matrix kernels).
+template <bool TAB, bool BMP = false, int W>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
                                           int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB, W>& S,
                                           bool store_a, unsigned long long* fma = nullptr) {
@@ -256,6 +310,12 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
         } else {
             if constexpr (TAB) mark_row(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
             else mark_row<true>(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
+        }
+    }
+    if constexpr (!TAB && BMP) {
+        if (whole && P.bhdr) {
+            mark_from_bitmaps(P, pa0, pa1, c0, cend, lane, S, store_a, fma);
+            return;
         }
     }
     for (int seg = pa0; seg < pa1; seg += 32) {
@@ -649,6 +709,7 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
     // while the map is built
     int lo = INT_MAX, hi = -1;
     bool fixed = false;
+    int fixed_span = 0;
     if constexpr (!TAB) {
         int w0 = 0, w1 = P.n;
         if constexpr (BATCH) {
@@ -658,10 +719,13 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
                 w1 = P.inst_off[r_inst + 1];
             }
         }
-        if (w1 > w0 && w1 - w0 <= kCols) {
-            lo = w0;
+        // with B row bitmaps the window starts at a multiple of 32 columns
+        const int a0 = P.bhdr ? (w0 & ~31) : w0;
+        if (w1 > w0 && w1 - a0 <= kCols) {
+            lo = a0;
             hi = w1 - 1;
             fixed = true;
+            fixed_span = w1 - w0;
         }
     }
     for (int t = 0; t < nadd && !fixed; ++t) {
@@ -697,19 +761,23 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
             if ((tmask >> t) & 1u) my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
     lo = warp_min(lo);
     hi = warp_max(hi);
-    my_span = max(my_span, hi - lo + 1);
+    const int row_span = fixed ? fixed_span : hi - lo + 1;  // the statistic: before any alignment
+    my_span = max(my_span, row_span);
     if (hi < lo) {
         if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
         if constexpr (BATCH) row_stats_batch(P, r_inst, my_fma - fma0, 0ull, 0, 0ull, lane);
         return;
+    }
+    if constexpr (!TAB) {
+        if (P.bhdr) lo &= ~31;
     }
 
     // ---- exact entry count of the row, reserve it in the pool
     long long total = 0;
     bool reuse = false;
     if (hi - lo + 1 <= kCols) {
-        build_map<TAB>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE,
-                       fixed ? &my_fma : nullptr);
+        build_map<TAB, !BATCH>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE,
+                               fixed ? &my_fma : nullptr);
         total = count_marks(hi - lo + 1, lane, S);
         reuse = true;
     } else {
@@ -819,7 +887,7 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
         P.out_re[r] = (int)(base + written);
     }
     if constexpr (BATCH) {
-        row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane, hi - lo + 1);
+        row_stats_batch(P, r_inst, my_fma - fma0, my_cand - cand0, written, my_absmax, lane, row_span);
         my_absmax = 0ull;
     } else if (lane == 0) {
         my_written += (unsigned long long)written;
@@ -1839,6 +1907,48 @@ __global__ void k_norms_finish(int n, int count, NormSlot* slots, unsigned long 
     }
 }
 
+// ---------------------------------------------------------------- k_row_bitmaps
+// Column bitmap of every row of B for the product's symbolic pass: hdr[r] =
+// {first column / 32, words}, the words at bits[rb[r]] on.  A row gets one
+// only if it needs no more words than it has entries (so they fit its own
+// pool range) and no more than one window's; otherwise words = 0.  One warp
+// per row: each 32-entry piece ORs runs of lanes with the same word (the
+// columns ascend) and the first lane of a run adds it to the word.
+__global__ void k_row_bitmaps(int n, RowView B, int2* hdr, unsigned* bits) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
+        const int s = B.rb[r], e = B.re[r];
+        int2 h = make_int2(0, 0);
+        if (e > s) {
+            const int w0 = B.col[s] >> 5;
+            const int nw = (B.col[e - 1] >> 5) - w0 + 1;
+            h.x = w0;
+            if (nw <= e - s && nw <= kBmWordsBig) {
+                h.y = nw;
+                for (int j = lane; j < nw; j += 32) bits[s + j] = 0u;
+                __syncwarp();
+                for (int q0 = s; q0 < e; q0 += 32) {
+                    const int q = q0 + lane;
+                    const bool in = q < e;
+                    const int c = in ? B.col[q] : 0;
+                    const int wi = in ? (c >> 5) - w0 : -1 - lane;
+                    unsigned v = in ? 1u << (c & 31) : 0u;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const unsigned v2 = __shfl_down_sync(kFull, v, d);
+                        const int w2 = __shfl_down_sync(kFull, wi, d);
+                        if (lane + d < 32 && w2 == wi) v |= v2;
+                    }
+                    const int wp = __shfl_up_sync(kFull, wi, 1);
+                    if (in && (lane == 0 || wp != wi)) atomicOr(bits + s + wi, v);
+                }
+            }
+        }
+        if (lane == 0) hdr[r] = h;
+    }
+}
+
 // ---------------------------------------------------------------- plumbing
 // max |x| over the pool entries [mark[i], mark[i+1])
 __global__ void k_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot) {
@@ -2254,6 +2364,16 @@ cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, do
     // rows expected near or above the bitmap map's kAccCap - 32 slots: WIDE
     if (out_len > 0.9 * (kAccCap - 32)) return prod_launch<false, false, true>(P, st);
     return prod_launch<false, false, false>(P, st);
+}
+
+cudaError_t launch_row_bitmaps(int n, const RowView& B, int2* hdr, unsigned* bits, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = ((long long)n + 7) / 8;
+    const long long cap = (long long)sms_now() * 8;
+    if (blocks > cap) blocks = cap;
+    k_row_bitmaps<<<(unsigned)blocks, 256, 0, st>>>(n, B, hdr, bits);
+    ++g_launches;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st) {

@@ -25,6 +25,9 @@ void count_launches(int k);  // kernels launched by other translation units
 constexpr int kBitmapColumns = 4608;
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len = 0.0,
                            bool wide_window = false);
+// column bitmaps of B's rows for the product's symbolic pass
+// (ProductArgs::bhdr, bbits); bits has one word per entry of B's index space
+cudaError_t launch_row_bitmaps(int n, const RowView& B, int2* hdr, unsigned* bits, cudaStream_t st);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
 cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
 cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st);
