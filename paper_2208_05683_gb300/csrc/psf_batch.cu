@@ -648,6 +648,15 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 CU(cudaEventCreate(&e1));
                 CU(cudaEventRecord(e0, st));
             }
+            // giant stages mark their rows from column bitmaps of S's rows
+            // (each S row is read by every row of Z-hat_(q) that needs it)
+            const int bm = g_row_bitmaps.load();
+            if (D.kind == 1 && !table && !T.wide && bm > 0 && w.bits_cap >= w.cap && w.chunk_cols <= 0 &&
+                w.chunk_slots <= 0 && (bm == 2 || fma_row >= kBitmapMinA * kBitmapMinB)) {
+                CU(launch_row_bitmaps(n, P.B, w.bhdr.as<int2>(), w.pool_bits.as<unsigned>(), st));
+                P.bhdr = w.bhdr.as<int2>();
+                P.bbits = w.pool_bits.as<unsigned>();
+            }
             CU(launch_product(P, table, st, 0.0, T.wide));
             if (g_prof.on) {
                 CU(cudaEventRecord(e1, st));

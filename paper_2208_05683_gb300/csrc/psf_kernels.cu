@@ -295,7 +295,7 @@ __device__ __forceinline__ void mark_from_bitmaps(const ProductArgs& P, int pa0,
 }
 
 // Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
-// BMP: B row bitmaps may be used (the single-matrix kernels).
+// BMP: B row bitmaps may be used (not in the batch kernel's wide window).
 template <bool TAB, bool BMP = false, int W>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
                                           int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB, W>& S,
@@ -776,8 +776,8 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
     long long total = 0;
     bool reuse = false;
     if (hi - lo + 1 <= kCols) {
-        build_map<TAB, !BATCH>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S, !WIDE,
-                               fixed ? &my_fma : nullptr);
+        build_map<TAB, (!BATCH || W == kBmWords)>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S,
+                                                   !WIDE, fixed ? &my_fma : nullptr);
         total = count_marks(hi - lo + 1, lane, S);
         reuse = true;
     } else {

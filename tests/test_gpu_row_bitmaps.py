@@ -164,3 +164,22 @@ def test_row_bitmaps_key_checks():
     for bad in (-1, 0.5, 3):
         with pytest.raises(psf.PsfError):
             psf.tune_set(_abi.PSF_TUNE_ROW_BITMAPS, bad)
+
+
+def test_batch_with_and_without_bitmaps_bitwise(row_bitmaps):
+    # the giant stages of a block-diagonal batch: instance windows start
+    # anywhere, aligned down to 32 columns for the bitmaps
+    cases = [(ocsr(syn.laplacian_2d(17 + 5 * (i % 4))), ("exp", "cos", "sinh")[i % 3]) for i in range(9)]
+    cases.append((ocsr(syn.banded_random(700, 6, 3, 2.0)), "exp"))
+    cases.append((ocsr(syn.banded_normal(300, 11, 5)), "cosh"))
+    refs = [psscf(Z, syn.coeffs(k), 1e-12) for Z, k in cases]
+    series = [psf.Series(syn.coeffs(k), 1e-12) for _, k in cases]
+    runs = []
+    for v in (2.0, 0.0):
+        row_bitmaps(v)
+        for rep in range(2):  # the second batch knows every stage's sizes
+            got = psf.eval_batch(series, [dev(Z) for Z, _ in cases])
+            for i, (g, ref) in enumerate(zip(got, refs)):
+                check_same(g, ref, f"instance {i}, bitmaps {v}, batch {rep}")
+        runs.append([g.steps for g in got])
+    assert runs[0] == runs[1]
