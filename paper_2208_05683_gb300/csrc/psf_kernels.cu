@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
                 if (v) atomicMax(&A.ctl->cslot[it & 1], v);
                 if (blockIdx.x == 0) {
                     A.ctl->cslot[(it + 1) & 1] = 0ull;
-                    A.ctl->cand_cnt[(it + 1) & 1] = 0ull;  // the next rescan's output list
+                    if (it == 0) A.ctl->cand_cnt[1] = 0ull;  // the first rescan's output list
                 }
             }
         }
@@ -1207,24 +1207,46 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1(Alg1Arg
         eps_f = A.eps_g / m;
         const unsigned long long fb = (unsigned long long)__double_as_longlong(eps_f);
         if (!over) {
-            // rescan the candidates of the previous pass (list (it-1)&1) into
-            // list it&1.  The first rescan sets the candidates at or below
-            // eps_g / 2^far_shift (default 2^6) apart, in the back half of
-            // list 1: they cannot leave while eps_f stays above that, so
-            // later rescans read only the front halves (the near candidates)
-            // and the far half is read again (in place) only once eps_f falls
-            // below it.
-            const int bi = (it - 1) & 1, bo = it & 1;
+            // The first rescan reads the product's candidates (list 0) and
+            // writes those still at or below eps_f to list 1: the near ones
+            // (above eps_g / 2^far_shift, default 2^6) to its front half, the
+            // far ones to its back half.  The far ones cannot leave while
+            // eps_f stays above that bound; later rescans read the near
+            // ones in place, subtracting and clearing (|x| = 0: a hole) those
+            // that leave, and read the far half (in place) only once eps_f
+            // falls below the bound.
             const bool first = it == 1;
             const unsigned long long half = ccap / 2;
-            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), first ? ccap : half);
-            const int* ic = A.cand_col + (size_t)bi * ccap;
-            const unsigned long long* ix = A.cand_x + (size_t)bi * ccap;
             int* fcol = A.cand_col + ccap + half;
             unsigned long long* fx = A.cand_x + ccap + half;
+            const unsigned long long nt = (unsigned long long)nthreads;
+            if (!first) {
+                const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[1]), half);
+                const int* ic = A.cand_col + ccap;
+                unsigned long long* ix = A.cand_x + ccap;
+                for (unsigned long long q0 = (unsigned long long)gt; q0 < cnt; q0 += 4ull * nt) {
+                    unsigned long long xb[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned long long q = q0 + (unsigned long long)u * nt;
+                        xb[u] = q < cnt ? __ldcg(ix + q) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (xb[u] > fb) {  // 0 (a hole) never
+                            const unsigned long long q = q0 + (unsigned long long)u * nt;
+                            exact_sub_checked(A.words, A.sticky, __ldcg(ic + q), A.n, xb[u], A.e_lsb, A.ctl);
+                            ix[q] = 0ull;
+                        }
+                    }
+                }
+            }
+            const unsigned long long cnt = first ? min(__ldcg(&A.ctl->cand_cnt[0]), ccap) : 0ull;
+            const int* ic = A.cand_col;
+            const unsigned long long* ix = A.cand_x;
+            const int bo = 1;
             CandArena ca, cf;
             // four candidates per thread at a time, all loads issued first
-            const unsigned long long nt = (unsigned long long)nthreads;
             for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += 4ull * nt) {
                 unsigned long long xb[4];
                 int col[4];
@@ -1429,7 +1451,7 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
         }
         if (blockIdx.x == 0) {
             for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) A.cslot[2 * i + ((pass + 1) & 1)] = 0ull;
-            if (threadIdx.x == 0) A.ctl->cand_cnt[(pass + 1) & 1] = 0ull;  // the next rescan's output list
+            if (threadIdx.x == 0 && pass == 0) A.ctl->cand_cnt[1] = 0ull;  // the first rescan's output list
         }
         if (!grid_barrier(A.ctl, A.budget_ns)) {
             alive = false;
@@ -1461,20 +1483,53 @@ __global__ void __launch_bounds__(kAlg1Threads, kAlg1BlocksPerSm) k_alg1_batch(A
         __syncthreads();
         if (s_left == 0) break;
         if (!over) {
-            // rescan the candidates of the previous pass into the other list;
-            // the first rescan sets each instance's candidates at or below its
-            // eps_g / 2^far_shift apart in the back half of list 1 (as in k_alg1)
-            const int bi = pass & 1, bo = (pass + 1) & 1;
+            // the first rescan reads the product's candidates (list 0) into
+            // list 1, each instance's candidates at or below its eps_g /
+            // 2^far_shift in its back half; later rescans read the front half
+            // in place (as in k_alg1), clearing the entries that leave and
+            // those of instances that have finished
             const bool first = pass == 0;
             const unsigned long long half = ccap / 2;
-            const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[bi]), first ? ccap : half);
-            const int* ic = A.cand_col + (size_t)bi * ccap;
-            const unsigned long long* ix = A.cand_x + (size_t)bi * ccap;
             int* fcol = A.cand_col + ccap + half;
             unsigned long long* fx = A.cand_x + ccap + half;
+            const unsigned long long nt = (unsigned long long)nthreads;
+            if (!first) {
+                const unsigned long long cnt = min(__ldcg(&A.ctl->cand_cnt[1]), half);
+                const int* ic = A.cand_col + ccap;
+                unsigned long long* ix = A.cand_x + ccap;
+                for (unsigned long long q0 = (unsigned long long)gt; q0 < cnt; q0 += 4ull * nt) {
+                    unsigned long long xb[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned long long q = q0 + (unsigned long long)u * nt;
+                        xb[u] = q < cnt ? __ldcg(ix + q) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (!xb[u]) continue;
+                        const unsigned long long q = q0 + (unsigned long long)u * nt;
+                        const int cq = __ldcg(ic + q);
+                        if ((unsigned)cq >= (unsigned)A.n) {
+                            atomicOr(&A.ctl->status, kDevInternal);
+                            continue;
+                        }
+                        const int i = A.inst[cq];
+                        if (s_state[i] != 0) {
+                            ix[q] = 0ull;
+                        } else if (xb[u] > (unsigned long long)__double_as_longlong(s_eps[i])) {
+                            // an entry that leaves the list leaves the column sums
+                            exact_sub(A.words + cq, n, A.sticky + cq, xb[u], A.bstep[i].e_lsb);
+                            ix[q] = 0ull;
+                        }
+                    }
+                }
+            }
+            const unsigned long long cnt = first ? min(__ldcg(&A.ctl->cand_cnt[0]), ccap) : 0ull;
+            const int* ic = A.cand_col;
+            const unsigned long long* ix = A.cand_x;
+            const int bo = 1;
             CandArena ca, cf;
             // four candidates per thread at a time, all loads issued first
-            const unsigned long long nt = (unsigned long long)nthreads;
             for (unsigned long long q0 = (unsigned long long)(gt & ~31); q0 < cnt; q0 += 4ull * nt) {
                 unsigned long long xb[4];
                 int col[4];
