@@ -633,6 +633,15 @@ def measure_batched(args, dev, flush):
 
     for _ in range(3):
         once()
+    # the library's batch autotuner on these instances: slot-map crossover
+    # per size class of work per row, row bitmaps, baby-step reuse
+    tune = None
+    if not args.no_autotune:
+        bt = _abi.BatchTune()
+        _abi.check(L.psf_autotune_batch(sh, zs, count, sp, ctypes.byref(bt)))
+        tune = bt.as_dict()
+        if tune["table_crossover"] >= 1e300:
+            tune["table_crossover"] = "never"
     reps, ms = 5, []
     c0 = ctypes_i64(L.psf_launch_count)
     for _ in range(reps):
@@ -663,7 +672,7 @@ def measure_batched(args, dev, flush):
     return {"instances": count, "rows": int(sum(z.n for z in Zs)), "nnz": int(sum(z.nnz for z in Zs)),
             "inst_per_s": count / (med / 1e3), "ms_per_batch": med, "launches_per_batch": launches,
             "product_tflops": 2.0 * fma.value / (pms.value / 1e3) / 1e12 if pms.value > 0 else None,
-            "algorithmic_fma": fma.value,
+            "algorithmic_fma": fma.value, "autotune": tune,
             "sequential_inst_per_s": count / t_seq, "speedup_vs_sequential": (count / (med / 1e3)) / (count / t_seq),
             "how": "median of 5 event-timed psf_eval_batch calls (L2 flushed before each), inputs resident"}
 

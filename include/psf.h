@@ -439,6 +439,36 @@ PSF_API int psf_autotune(psf_series_t series, const psf_csr_t* Z, void* stream, 
                          double* saved_ms);
 
 /*
+ * psf_autotune_batch: tune the process-wide settings for one batch of
+ * instances (series[i], Z[i]), i < count, on that batch itself:
+ *  1. one warm-up psf_eval_batch (sizes are learnt), then the batch's time
+ *     with the settings on entry (median of 3 event-timed calls);
+ *  2. the slot map per stage: the batch evaluated once with the column-table
+ *     map and once with the bitmap map (graph capture off for these two),
+ *     every product launch event-timed with its work per row, and the
+ *     PSF_TUNE_TABLE_CROSSOVER that minimises the summed product time (as
+ *     psf_autotune, over the batch's size classes of work per row);
+ *  3. with that crossover, PSF_TUNE_ROW_BITMAPS in {0, 1} and
+ *     PSF_TUNE_BATCH_REUSE in {0, 1}, each timed as whole batches (median
+ *     of 3); the fastest is kept.
+ * The chosen settings are set process-wide and returned in *out with the
+ * batch's time before and after.  Every setting gives bitwise the same
+ * results; only speed changes.  Synchronizes `stream`; not thread-safe with
+ * evaluations running concurrently on other threads.
+ */
+typedef struct {
+    double table_crossover;   /* chosen PSF_TUNE_TABLE_CROSSOVER (1e300: never) */
+    int32_t row_bitmaps;      /* chosen PSF_TUNE_ROW_BITMAPS */
+    int32_t batch_reuse;      /* chosen PSF_TUNE_BATCH_REUSE */
+    int32_t configs;          /* whole-batch configurations timed */
+    int32_t launches;         /* product launches timed per slot map */
+    double ms_before;         /* median ms of one psf_eval_batch with the settings on entry */
+    double ms_after;          /* the same with the chosen settings */
+} psf_batch_tune_t;
+PSF_API int psf_autotune_batch(const psf_series_t* series, const psf_csr_t* Z, int32_t count, void* stream,
+                               psf_batch_tune_t* out);
+
+/*
  * Instrumentation (no counterpart in the paper).  psf_launch_count: kernels
  * this library has launched in this process.  psf_profile(1) makes every later product-kernel launch
  * record a CUDA event pair on its stream; psf_profile_read waits for the

@@ -28,11 +28,12 @@ from ._abi import (PSF_NOFILTER, PSF_OK, PSF_POLY, PSF_SERIES, PSF_Z_ESTIMATE, P
                    PSF_PARAM_ALG1_MAXIT,
                    PSF_PARAM_ER, PSF_PARAM_POOL_ENTRIES, PSF_PARAM_KERNEL, PSF_PARAM_CHUNK_COLS,
                    PSF_PARAM_CHUNK_SLOTS, PSF_PARAM_DENSE_XOVER, PSF_MAX_Q, PSF_NORM1_NOALLOC_MAX_N,
-                   PsfError, CSRStruct, InfoStruct, StepStruct, ServerConfig, Completion, ServerStats, lib, check)
+                   PsfError, CSRStruct, InfoStruct, StepStruct, ServerConfig, Completion, ServerStats, BatchTune,
+                   lib, check)
 
 __all__ = [
     "DeviceCSR", "Series", "Result", "eval_batch", "product_filter", "norm1", "norm1_noalloc", "plan",
-    "Server", "autotune", "tune_get", "tune_set", "PsfError",
+    "Server", "autotune", "autotune_batch", "tune_get", "tune_set", "PsfError",
     "PSF_SERIES", "PSF_POLY", "PSF_NOFILTER", "PSF_Z_SUBMULT", "PSF_Z_ESTIMATE", "PSF_Z_SQUARE", "PSF_MAX_Q",
     "build", "lib",
 ]
@@ -389,6 +390,20 @@ def autotune(series: "Series", Z: DeviceCSR, stream=None):
     zs = Z._struct()
     check(lib().psf_autotune(series._h, ctypes.byref(zs), _stream_ptr(stream), ctypes.byref(c), ctypes.byref(saved)))
     return c.value, saved.value
+
+
+def autotune_batch(series, Zs, stream=None) -> dict:
+    """psf_autotune_batch: tune the slot-map crossover, row bitmaps and
+    baby-step reuse on this batch of instances (series[i], Zs[i]) and keep
+    the fastest; returns the chosen settings and the batch's time before
+    and after (ms)."""
+    count = len(Zs)
+    sh = (ctypes.c_void_p * count)(*[s._h.value for s in series])
+    Zs = [_as_device_csr(z) for z in Zs]
+    zs = (CSRStruct * count)(*[z._struct() for z in Zs])
+    out = BatchTune()
+    check(lib().psf_autotune_batch(sh, zs, count, _stream_ptr(stream), ctypes.byref(out)))
+    return out.as_dict()
 
 
 def tune_get(key: int = 1) -> float:

@@ -33,6 +33,7 @@ EXPORTS = [
     "psf_server_destroy", "psf_server_cancel", "psf_tune_set", "psf_tune_get", "psf_autotune",
     "psf_plan", "psf_result_csr", "psf_result_copy", "psf_result_info", "psf_result_step",
     "psf_result_destroy", "psf_launch_count", "psf_profile", "psf_profile_read", "psf_fp64_peak",
+    "psf_autotune_batch",
 ]
 
 
@@ -60,6 +61,15 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("max_concurrent", ctypes.c_int32), ("pending", ctypes.c_int32),
                 ("budget_peak", ctypes.c_int64), ("cancelled", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchTune(ctypes.Structure):
+    _fields_ = [("table_crossover", ctypes.c_double), ("row_bitmaps", ctypes.c_int32),
+                ("batch_reuse", ctypes.c_int32), ("configs", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("ms_before", ctypes.c_double), ("ms_after", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -149,6 +159,7 @@ def _declare(h: ctypes.CDLL) -> None:
     h.psf_profile.argtypes = [i32]
     h.psf_profile_read.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(f64), ctypes.POINTER(f64), i32]
     h.psf_fp64_peak.argtypes = [vp, ctypes.POINTER(f64)]
+    h.psf_autotune_batch.argtypes = [ctypes.POINTER(vp), csrp, i32, vp, ctypes.POINTER(BatchTune)]
     for name in EXPORTS:
         if name not in ("psf_last_error",):
             getattr(h, name).restype = ctypes.c_int

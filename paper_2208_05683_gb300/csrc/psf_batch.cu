@@ -24,6 +24,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <new>
 #include <vector>
@@ -285,7 +286,18 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                     const bool table = use_table(w.slot_map, zlen_all * blen);
                     bool wz = false;
                     for (int i = 0; i < count && !wz; ++i) wz = chain[(size_t)i] && wide_of(span_z[(size_t)i], k - 2);
+                    cudaEvent_t t0 = nullptr, t1 = nullptr;
+                    if (g_tune_rec) {
+                        CU(cudaEventCreate(&t0));
+                        CU(cudaEventCreate(&t1));
+                        CU(cudaEventRecord(t0, st));
+                    }
                     CU(launch_product(P, table, st, 0.0, wz));
+                    if (g_tune_rec) {
+                        CU(cudaEventRecord(t1, st));
+                        g_tune_rec->work.push_back(zlen_all * blen);
+                        g_tune_rec->ev.emplace_back(t0, t1);
+                    }
                     if ((rc = mark_pool(w, k))) return rc;
                     prev = w.pooled(rb, re);
                 }
@@ -643,7 +655,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                                cudaMemcpyDeviceToDevice, st));
             const bool table = use_table(w.slot_map, fma_row);
             cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (g_prof.on) {
+            if (g_prof.on || g_tune_rec) {
                 CU(cudaEventCreate(&e0));
                 CU(cudaEventCreate(&e1));
                 CU(cudaEventRecord(e0, st));
@@ -658,7 +670,11 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
                 P.bbits = w.pool_bits.as<unsigned>();
             }
             CU(launch_product(P, table, st, 0.0, T.wide));
-            if (g_prof.on) {
+            if (g_tune_rec) {
+                CU(cudaEventRecord(e1, st));
+                g_tune_rec->work.push_back(fma_row);
+                g_tune_rec->ev.emplace_back(e0, e1);
+            } else if (g_prof.on) {
                 CU(cudaEventRecord(e1, st));
                 g_prof.ev.emplace_back(e0, e1);
             }
@@ -712,7 +728,7 @@ int eval_group(const psf_series_t* series, const psf_csr_t* Zs, int count, cudaS
         // captured into a CUDA graph and launched as one unit (no host work
         // between its ~2 launches per stage); direct launches while the
         // product kernel is being profiled, or when graphs are switched off
-        const bool use_graph = !g_prof.on && g_batch_graph.load();
+        const bool use_graph = !g_prof.on && !g_tune_rec && g_batch_graph.load();
         cudaGraphExec_t exec = nullptr;
         if (use_graph) {
             // recorded on a stream of the library (capture is not allowed on
@@ -894,5 +910,132 @@ extern "C" int psf_eval_batch(const psf_series_t* series, const psf_csr_t* Zs, i
         }
         start = end;
     }
+    return PSF_OK;
+}
+
+// ---- psf_autotune_batch
+
+namespace {
+
+// One psf_eval_batch, its results released.
+int run_batch_once(const psf_series_t* series, const psf_csr_t* Z, int32_t count, void* stream) {
+    std::vector<psf_result_t> outs((size_t)count, nullptr);
+    const int rc = psf_eval_batch(series, Z, count, stream, outs.data());
+    for (psf_result_t r : outs)
+        if (r) psf_result_destroy(r);
+    return rc;
+}
+
+// Median event-timed milliseconds of `reps` psf_eval_batch calls.
+int time_batch(const psf_series_t* series, const psf_csr_t* Z, int32_t count, void* stream, int reps, double* ms) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    std::vector<double> t;
+    int rc = err == cudaSuccess ? PSF_OK : fail(PSF_ECUDA, "autotune events: %s", cudaGetErrorString(err));
+    for (int i = 0; i < reps && rc == PSF_OK; ++i) {
+        float v = 0.0f;
+        if ((err = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        if ((rc = run_batch_once(series, Z, count, stream))) break;
+        if ((err = cudaEventRecord(e1, st)) != cudaSuccess || (err = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (err = cudaEventElapsedTime(&v, e0, e1)) != cudaSuccess)
+            break;
+        t.push_back(v);
+    }
+    if (rc == PSF_OK && err != cudaSuccess) rc = fail(PSF_ECUDA, "autotune timing: %s", cudaGetErrorString(err));
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return PSF_OK;
+}
+
+// The batch once with the slot-map crossover `c`, every product launch timed.
+int time_launches(const psf_series_t* series, const psf_csr_t* Z, int32_t count, void* stream, double c,
+                  std::vector<double>& work, std::vector<double>& ms) {
+    TuneRecorder rec;
+    const double saved = g_table_crossover.load();
+    g_table_crossover.store(c);
+    g_tune_rec = &rec;
+    int rc = run_batch_once(series, Z, count, stream);
+    g_tune_rec = nullptr;
+    g_table_crossover.store(saved);
+    if (rc == PSF_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        rc = fail(PSF_ECUDA, "autotune sync");
+    for (auto& pr : rec.ev) {
+        float t = 0.0f;
+        if (rc == PSF_OK && cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess)
+            rc = fail(PSF_ECUDA, "autotune timing");
+        ms.push_back(t);
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    work = rec.work;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int psf_autotune_batch(const psf_series_t* series, const psf_csr_t* Z, int32_t count, void* stream,
+                                  psf_batch_tune_t* out) {
+    if (!series || !Z || !out || count <= 0) return fail(PSF_EINVAL, "null argument or empty batch");
+    *out = psf_batch_tune_t{};
+    const double c0 = g_table_crossover.load();
+    const int bm0 = g_row_bitmaps.load();
+    const bool reuse0 = g_batch_reuse.load();
+    int rc = run_batch_once(series, Z, count, stream);  // warm-up: sizes are learnt
+    if (rc == PSF_OK) rc = time_batch(series, Z, count, stream, 3, &out->ms_before);
+    if (rc) return rc;
+    // the slot map per launch: the table everywhere, then the bitmap everywhere
+    std::vector<double> work[2], ms[2];
+    rc = time_launches(series, Z, count, stream, 0.0, work[0], ms[0]);
+    if (rc == PSF_OK) rc = time_launches(series, Z, count, stream, 1e300, work[1], ms[1]);
+    if (rc) return rc;
+    if (work[0] != work[1]) return fail(PSF_ECUDA, "autotune: the two runs launched different products");
+    double best_c = 1e300, best_t = 0.0;
+    for (double v : ms[1]) best_t += v;  // never the table
+    for (double c : work[0]) {
+        double t = 0.0;
+        for (size_t i = 0; i < work[0].size(); ++i) t += work[0][i] >= c ? ms[0][i] : ms[1][i];
+        if (t < best_t || (t == best_t && c > best_c)) {
+            best_t = t;
+            best_c = c;
+        }
+    }
+    out->launches = (int32_t)work[0].size();
+    // row bitmaps and baby-step reuse, as whole batches with that crossover
+    double best_ms = std::numeric_limits<double>::infinity();
+    int best_bm = bm0;
+    bool best_reuse = reuse0;
+    g_table_crossover.store(best_c);
+    for (int bm = 0; bm <= 1 && rc == PSF_OK; ++bm) {
+        for (int ru = 0; ru <= 1 && rc == PSF_OK; ++ru) {
+            g_row_bitmaps.store(bm);
+            g_batch_reuse.store(ru != 0);
+            double t = 0.0;
+            rc = run_batch_once(series, Z, count, stream);  // the pool for this setting
+            if (rc == PSF_OK) rc = time_batch(series, Z, count, stream, 3, &t);
+            ++out->configs;
+            if (rc == PSF_OK && t < best_ms) {
+                best_ms = t;
+                best_bm = bm;
+                best_reuse = ru != 0;
+            }
+        }
+    }
+    if (rc) {
+        g_table_crossover.store(c0);
+        g_row_bitmaps.store(bm0);
+        g_batch_reuse.store(reuse0);
+        return rc;
+    }
+    g_row_bitmaps.store(best_bm);
+    g_batch_reuse.store(best_reuse);
+    out->table_crossover = best_c;
+    out->row_bitmaps = best_bm;
+    out->batch_reuse = best_reuse ? 1 : 0;
+    out->ms_after = best_ms;
     return PSF_OK;
 }

@@ -25,5 +25,8 @@ int main(void) {
     F(psf_server_stats_t, failed); F(psf_server_stats_t, batches); F(psf_server_stats_t, max_concurrent);
     F(psf_server_stats_t, pending); F(psf_server_stats_t, budget_peak);
     F(psf_server_stats_t, cancelled);
+    S(psf_batch_tune_t); F(psf_batch_tune_t, table_crossover); F(psf_batch_tune_t, row_bitmaps);
+    F(psf_batch_tune_t, batch_reuse); F(psf_batch_tune_t, configs); F(psf_batch_tune_t, launches);
+    F(psf_batch_tune_t, ms_before); F(psf_batch_tune_t, ms_after);
     return 0;
 }

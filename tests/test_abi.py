@@ -314,7 +314,7 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
         c[(t, f)] = int(v)
     pairs = {"psf_csr_t": _abi.CSRStruct, "psf_info_t": _abi.InfoStruct, "psf_step_info_t": _abi.StepStruct,
              "psf_server_config_t": _abi.ServerConfig, "psf_completion_t": _abi.Completion,
-             "psf_server_stats_t": _abi.ServerStats}
+             "psf_server_stats_t": _abi.ServerStats, "psf_batch_tune_t": _abi.BatchTune}
     for t, S in pairs.items():
         assert ctypes.sizeof(S) == c[(t, "-")], t
         fields = [f for f, _ in S._fields_]
