@@ -908,9 +908,12 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nadd = P.nadd;
     for (int t = threadIdx.x; t < nadd; t += blockDim.x) add[t] = P.add[t];
-    __shared__ unsigned long long blk_written, blk_cand, blk_absmax, blk_fma;
+    __shared__ unsigned long long blk_written, blk_cand, blk_absmax, blk_fma, blk_arena;
     __shared__ int blk_span;
     if (threadIdx.x == 0) {
+        // the block's warps take their first pool arenas with one atomic: at
+        // the launch every warp wants one at once, on the same counter
+        blk_arena = atomicAdd(&P.ctl->pool_used, (unsigned long long)kWarps * P.arena);
         blk_span = 0;
         blk_fma = 0ull;
         blk_written = 0ull;
@@ -920,6 +923,11 @@ __global__ void __launch_bounds__(ProdSmem<TAB, W>::kWarps * 32, ProdSmem<TAB, W
     __syncthreads();
     Smem& S = warps[wib];
     RowState st;
+    // (past the pool's capacity the first row's arena_take reports the overflow)
+    if (blk_arena + (unsigned long long)kWarps * P.arena <= P.ctl->pool_cap) {
+        st.arena.next = blk_arena + (unsigned long long)wib * P.arena;
+        st.arena.end = st.arena.next + P.arena;
+    }
     for (int r = blockIdx.x * kWarps + wib; r < P.n; r += gridDim.x * kWarps)
         product_row<TAB, BATCH, WIDE, W>(P, add, S, st, r, lane);
     // the unused end of this warp's arena reads as exact zeros too, and the
