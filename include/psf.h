@@ -85,7 +85,9 @@ extern "C" {
 #define PSF_PARAM_KERNEL 4        /* product slot map: 0 auto, 1 column table, 2 bitmap,
                                      3 bitmap with the wide column window for every product
                                      (auto picks it for a step whose rows spanned more than
-                                     4608 columns in the series' previous evaluation) */
+                                     4608 columns in the series' previous evaluation),
+                                     4 one row per block of four warps (shared bitmap map,
+                                     2560 accumulator slots) for every product */
 #define PSF_PARAM_CHUNK_COLS 5    /* > 0: fewer columns per row chunk (tests of row chunking) */
 #define PSF_PARAM_CHUNK_SLOTS 6   /* > 0: fewer accumulator slots per row chunk (same) */
 #define PSF_PARAM_DENSE_XOVER 7   /* dense-tile crossover of this series (see PSF_TUNE_DENSE_XOVER):

@@ -162,7 +162,8 @@ class Series:
     square   run the scheme on W = Z^2 for a series of only even or only odd
              powers (PSF_Z_SQUARE)
     s        override of the PS block size q (0 = Eq. 6)
-    kernel   slot map of the product kernel: "auto", "table", "bitmap" or "window"
+    kernel   slot map of the product kernel: "auto", "table", "bitmap", "window" or
+             "cta" (one output row per block of four warps)
              (the bitmap with its wide column window, for every product)
     chunk_cols, chunk_slots  > 0: smaller row chunks (to exercise row chunking)
     dense_xover  dense-tile crossover in multiply-adds per n^3 (0: every product
@@ -192,7 +193,7 @@ class Series:
             check(L.psf_series_set_param(h, PSF_PARAM_ALG1_MAXIT, float(maxit)))
         if pool_entries is not None:
             check(L.psf_series_set_param(h, PSF_PARAM_POOL_ENTRIES, float(pool_entries)))
-        kid = {"auto": 0, "table": 1, "bitmap": 2, "window": 3}[kernel]
+        kid = {"auto": 0, "table": 1, "bitmap": 2, "window": 3, "cta": 4}[kernel]
         if kid:
             check(L.psf_series_set_param(h, PSF_PARAM_KERNEL, float(kid)))
         if chunk_cols:

@@ -220,7 +220,8 @@ int run_step(Work& w, const RowView* A, const RowView* B, const std::vector<AddT
             P.bhdr = w.bhdr.as<int2>();
             P.bbits = w.pool_bits.as<unsigned>();
         }
-        CU(launch_product(P, table, w.st, out_len, wide_window || w.slot_map == 3));
+        const bool cta = A && !table && (w.slot_map == 4 || (w.slot_map == 0 && use_cta(w.n, alen, blen)));
+        CU(launch_product(P, table, w.st, out_len, wide_window || w.slot_map == 3, cta));
     }
     if (reuse_k > 0) {
         ReuseArgs R{};
@@ -412,8 +413,8 @@ int psf_series_set_param(psf_series_t series, int32_t key, double value) {
             series->maxit = (int)value;
             return PSF_OK;
         case PSF_PARAM_KERNEL:
-            if (!(value == 0.0 || value == 1.0 || value == 2.0 || value == 3.0))
-                return fail(PSF_EINVAL, "kernel must be 0, 1, 2 or 3");
+            if (!(value == 0.0 || value == 1.0 || value == 2.0 || value == 3.0 || value == 4.0))
+                return fail(PSF_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
             series->kernel = (int)value;
             return PSF_OK;
         case PSF_PARAM_CHUNK_COLS:

@@ -134,7 +134,7 @@ struct Work {
     bool dense_estimate = false;  // a step without a recorded count may use the row-length estimate
     unsigned long long cap = 0, ccap = 0, bits_cap = 0;
     std::vector<DevBuf*> rows;  // 2n ints each: rb then re
-    int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap
+    int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap, 3 wide window, 4 CTA per row
     int chunk_cols = 0, chunk_slots = 0;
 
     ~Work() {
@@ -228,6 +228,18 @@ extern std::atomic<double> g_dense_xover;
 // slot_map 1: table, 2: bitmap, 0: by the work per row and the crossover
 inline bool use_table(int slot_map, double work_per_row) {
     return slot_map == 1 || (slot_map == 0 && work_per_row >= g_table_crossover.load(std::memory_order_relaxed));
+}
+
+// One output row per block of four warps (k_product_cta) for a product of
+// the single-matrix path when its rows fit one wave of blocks (7 per SM), so
+// that warps would otherwise sit idle, and its B rows average at least 16
+// entries (they are shared by the block's 128 threads); PSF_PARAM_KERNEL 4
+// forces it.  Measured on GB300: the banded N(0, 1) family at n = 1000 runs
+// 1.3-1.6x faster from bandwidth 8 on; at n = 4096 and above the warp per row
+// is faster (1.4-2.7x).
+inline bool use_cta(int n, double alen, double blen) {
+    (void)alen;
+    return n > 0 && n <= 7 * num_sms() && blen >= 16.0;
 }
 
 // Recorder of product launches for psf_autotune (set on the calling thread

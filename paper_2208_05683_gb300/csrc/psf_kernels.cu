@@ -1012,6 +1012,390 @@ __device__ __forceinline__ int compact_row(int* col, double* val, int s, int e, 
     return w;
 }
 
+// ---------------------------------------------------------------- k_product_cta
+// One output row per block of four warps: for matrices with fewer rows than
+// the warp-per-row kernel has resident warps, whose B rows are long.  The
+// block's warps share one bitmap slot map over the row's window (up to 4608
+// columns) and kCtaCap accumulator slots:
+//  - symbolic pass: each warp marks the B rows of every fourth 32-entry
+//    segment of A's row (from their bitmaps when the step has them), ORing
+//    into the shared map; a block-wide scan numbers the columns;
+//  - numeric pass: the addends in order, then the B rows in k order, each B
+//    row's entries spread over the block's 128 threads (four independent
+//    read-modify-writes per thread: a B row's entries have distinct
+//    columns), with a block barrier after each B row, so that every slot is
+//    folded in the order of k_product (addends t ascending, then k
+//    ascending) and the results are bitwise the same;
+//  - write-back: each warp takes a quarter of the slots in column order,
+//    positions from a block-wide count, Algorithm 1's first pass as in
+//    k_product.
+// A row whose window or pattern does not fit is computed by the block's
+// first warp with the warp-per-row code (bitmap map, every accumulator
+// slot) in the same shared memory, the other warps waiting.
+constexpr int kCtaWarps = 4;
+constexpr int kCtaCap = 2560;
+
+struct CtaSmem {
+    uint2 pm[kBmWords];  // the first member, as in ProdSmem<false, kBmWords> (mark_row uses only pm)
+    double acc[kCtaCap];
+    unsigned short colbuf[kCtaCap];
+    int kb[kCtaWarps][32];
+    int kl[kCtaWarps][32];
+    int kwn[kCtaWarps][32];
+    double ka[32];
+    int wcnt[kCtaWarps];
+    int lo, hi, total, fits;
+    long long base;
+};
+static_assert(sizeof(ProdSmem<false, kBmWords>) <= sizeof(CtaSmem), "the warp-per-row fallback fits");
+
+size_t cta_smem_bytes() { return sizeof(CtaSmem) + sizeof(AddTerm) * kMaxAdd; }
+
+// block-wide exclusive scan of one int per thread; *total gets the sum
+__device__ __forceinline__ int cta_excl_scan(int v, int tid, int* wsum, int* total) {
+    const int lane = tid & 31, wib = tid >> 5;
+    const int x = warp_excl_scan(v, lane);
+    if (lane == 31) wsum[wib] = x + v;
+    __syncthreads();
+    int before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kCtaWarps; ++w) {
+        before += w < wib ? wsum[w] : 0;
+        all += wsum[w];
+    }
+    *total = all;
+    __syncthreads();
+    return before + x;
+}
+
+__device__ __forceinline__ void cta_row(const ProductArgs& P, const AddTerm* add, CtaSmem& S, RowState& st, int r,
+                                        int tid) {
+    const int lane = tid & 31, wib = tid >> 5;
+    constexpr int kT = kCtaWarps * 32;
+    const int nadd = P.nadd;
+    const bool prod = P.A.rb != nullptr;
+    int pa0 = 0, pa1 = 0;
+    if (prod) {
+        pa0 = P.A.rb[r];
+        pa1 = P.A.re[r];
+    }
+    // ---- column window: the matrix itself when it is at most one map wide
+    int lo = INT_MAX, hi = -1;
+    int row_span = 0;
+    if (P.n <= kBmBits) {
+        lo = 0;
+        hi = P.n - 1;
+        row_span = P.n;
+    } else {
+        if (tid == 0)
+            for (int t = 0; t < nadd; ++t) {
+                const AddTerm& T = add[t];
+                if (!T.rb) {
+                    lo = min(lo, r);
+                    hi = max(hi, r);
+                } else if (T.rb[r] < T.re[r]) {
+                    lo = min(lo, T.col[T.rb[r]]);
+                    hi = max(hi, T.col[T.re[r] - 1]);
+                }
+            }
+        for (int p = pa0 + tid; p < pa1; p += kT) {
+            const int k = P.A.col[p];
+            const int s = P.B.rb[k], e = P.B.re[k];
+            if (s < e) {
+                lo = min(lo, P.B.col[s]);
+                hi = max(hi, P.B.col[e - 1]);
+            }
+        }
+        lo = warp_min(lo);
+        hi = warp_max(hi);
+        if (lane == 0) {
+            S.kb[wib][0] = lo;
+            S.kl[wib][0] = hi;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kCtaWarps; ++w) {
+            lo = min(lo, S.kb[w][0]);
+            hi = max(hi, S.kl[w][0]);
+        }
+        __syncthreads();
+        row_span = hi - lo + 1;
+    }
+    if (hi < lo) {  // no entry at all
+        if (tid == 0) P.out_rb[r] = P.out_re[r] = 0;
+        return;
+    }
+    st.span = max(st.span, row_span);
+    if (P.bhdr) lo &= ~31;
+    const int wlen = hi - lo + 1;
+    const int nw = (wlen + 31) >> 5;
+    if (wlen > kBmBits) {
+        // wider than the map: the first warp computes the row alone
+        if (wib == 0)
+            product_row<false, false, true, kBmWords>(P, add, *reinterpret_cast<ProdSmem<false, kBmWords>*>(&S), st,
+                                                      r, lane);
+        __syncthreads();
+        return;
+    }
+    // ---- symbolic pass
+    for (int w = tid; w < nw; w += kT) S.pm[w].y = 0u;
+    __syncthreads();
+    ProdSmem<false, kBmWords>& M = *reinterpret_cast<ProdSmem<false, kBmWords>*>(&S);  // its pm is S.pm
+    if (wib == 0) {
+        for (int t = 0; t < nadd; ++t) {
+            const AddTerm& T = add[t];
+            if (!T.rb) {
+                if (lane == 0 && r >= lo && r <= hi) mark_one(r - lo, M);
+            } else {
+                mark_row<true>(T.col, T.rb[r], T.re[r], lo, hi + 1, lane, M);
+            }
+        }
+    }
+    unsigned long long rf = 0ull;  // this thread's share of the row's multiply-adds
+    constexpr int R = (kBmWords + 31) / 32;
+    unsigned reg[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) reg[u] = 0u;
+    for (int seg = pa0 + 32 * wib; seg < pa1; seg += 32 * kCtaWarps) {
+        const int cnt = min(32, pa1 - seg);
+        if (lane < cnt) {
+            const int k = P.A.col[seg + lane];
+            const int b = P.B.rb[k], e = P.B.re[k];
+            rf += (unsigned long long)(e - b);
+            S.kb[wib][lane] = b;
+            S.kl[wib][lane] = e - b;
+            int h = 0;
+            if (P.bhdr) {
+                const int2 bh = P.bhdr[k];
+                h = bh.y > 0 ? ((bh.x - (lo >> 5)) << 16) | bh.y : 0;
+            }
+            S.kwn[wib][lane] = h;
+        }
+        __syncwarp();
+        // rows without a bitmap: short ones one per lane, long ones by the warp
+        const int my = lane < cnt && S.kwn[wib][lane] == 0 ? S.kl[wib][lane] : 0;
+        if (my > 0 && my <= 32) {
+            const int s0 = S.kb[wib][lane];
+            unsigned curw = 0xffffffffu, mask = 0u;
+            for (int q = s0; q < s0 + my; ++q) {
+                const unsigned off = (unsigned)(P.B.col[q] - lo), w = off >> 5;
+                if (w != curw) {
+                    if (mask) atomicOr(&S.pm[curw].y, mask);
+                    curw = w;
+                    mask = 0u;
+                }
+                mask |= 1u << (off & 31);
+            }
+            if (mask) atomicOr(&S.pm[curw].y, mask);
+        }
+        unsigned longm = __ballot_sync(kFull, my > 32);
+        while (longm) {
+            const int i = __ffs(longm) - 1;
+            longm &= longm - 1u;
+            mark_row<false>(P.B.col, S.kb[wib][i], S.kb[wib][i] + S.kl[wib][i], lo, hi + 1, lane, M);
+        }
+        for (int i = 0; i < cnt; ++i) {
+            const int h = S.kwn[wib][i];
+            if (h == 0) continue;
+            const int kw = h >> 16, kn = h & 0xffff;
+            const int base = S.kb[wib][i] - kw;  // bits[base + w]: window word w
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int w = lane + 32 * u;
+                if (w >= kw && w < kw + kn) reg[u] |= P.bbits[base + w];
+            }
+        }
+        __syncwarp();
+    }
+    if (wib == 0 && lane == 0)
+        for (int t = 0; t < nadd; ++t) rf += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int w = lane + 32 * u;
+        if (w < kBmWords && reg[u]) atomicOr(&S.pm[w].y, reg[u]);
+    }
+    __syncthreads();
+    // ---- number the columns: thread t takes words 2t and 2t + 1 (in order)
+    static_assert(2 * kCtaWarps * 32 >= kBmWords, "two words per thread cover the map");
+    int total = 0;
+    {
+        const int w0 = 2 * tid, w1 = 2 * tid + 1;
+        const int c0 = w0 < nw ? __popc(S.pm[w0].y) : 0;
+        const int c1 = w1 < nw ? __popc(S.pm[w1].y) : 0;
+        const int ex = cta_excl_scan(c0 + c1, tid, S.wcnt, &total);
+        if (w0 < nw) S.pm[w0].x = (unsigned)ex;
+        if (w1 < nw) S.pm[w1].x = (unsigned)(ex + c0);
+    }
+    if (total > kCtaCap) {
+        // more entries than slots: the first warp computes the row alone
+        // (with its own counts; this pass's are dropped)
+        if (wib == 0)
+            product_row<false, false, true, kBmWords>(P, add, *reinterpret_cast<ProdSmem<false, kBmWords>*>(&S), st,
+                                                      r, lane);
+        __syncthreads();
+        return;
+    }
+    st.fma += rf;
+    if (wib == 0) {
+        const long long b = arena_take(st.arena, (unsigned long long)((total + 3) & ~3), P.arena, P.ctl, P.pool_val,
+                                       lane);
+        if (lane == 0) S.base = b;
+    }
+    for (int w = tid; w < nw; w += kT) {
+        unsigned bits = S.pm[w].y;
+        int idx = (int)S.pm[w].x;
+        while (bits) {
+            S.colbuf[idx++] = (unsigned short)(w * 32 + __ffs(bits) - 1);
+            bits &= bits - 1u;
+        }
+    }
+    for (int i = tid; i < total; i += kT) S.acc[i] = 0.0;
+    __syncthreads();
+    const long long base = S.base;
+    if (base < 0) {
+        if (tid == 0) P.out_rb[r] = P.out_re[r] = 0;
+        return;
+    }
+    // ---- numeric pass: the addends, t ascending
+    for (int t = 0; t < nadd; ++t) {
+        const AddTerm& T = add[t];
+        if (!T.rb) {
+            if (tid == 0) {
+                const int i = slot_lookup(M, r - lo);
+                S.acc[i] = __fma_rn(T.alpha, 1.0, S.acc[i]);
+            }
+        } else {
+            for (int q = T.rb[r] + tid; q < T.re[r]; q += kT) {
+                const int i = slot_lookup(M, T.col[q] - lo);
+                S.acc[i] = __fma_rn(T.alpha, T.val[q], S.acc[i]);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- the B rows, k ascending, a block barrier after each
+    const int* __restrict__ bcol = P.B.col;
+    const double* __restrict__ bval = P.B.val;
+    for (int seg = pa0; seg < pa1; seg += 32) {
+        const int cnt = min(32, pa1 - seg);
+        __syncthreads();  // every thread is done with the last segment (its last rows may be empty)
+        if (wib == 0 && lane < cnt) {
+            const int k = P.A.col[seg + lane];
+            const int b = P.B.rb[k];
+            S.kb[0][lane] = b;
+            S.kl[0][lane] = P.B.re[k] - b;
+            S.ka[lane] = P.A.val[seg + lane];
+        }
+        __syncthreads();
+        for (int kk = 0; kk < cnt; ++kk) {
+            const int len = S.kl[0][kk];
+            if (len == 0) continue;
+            const double a = S.ka[kk];
+            const int* __restrict__ rc = bcol + S.kb[0][kk];
+            const double* __restrict__ rv = bval + S.kb[0][kk];
+            int off = tid;
+            for (; off + 3 * kT < len; off += 4 * kT) {
+                int j[4];
+                double v[4], x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    j[u] = rc[off + u * kT];
+                    v[u] = rv[off + u * kT];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) j[u] = slot_lookup(M, j[u] - lo);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = S.acc[j[u]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) S.acc[j[u]] = __fma_rn(a, v[u], x[u]);
+            }
+            for (; off < len; off += kT) {
+                const int j = slot_lookup(M, rc[off] - lo);
+                S.acc[j] = __fma_rn(a, rv[off], S.acc[j]);
+            }
+            __syncthreads();
+        }
+    }
+    // ---- write-back: warp w takes slots [w Q, (w + 1) Q) in column order
+    const int Q = ((total + kCtaWarps - 1) / kCtaWarps + 31) & ~31;
+    const int s0 = min(total, wib * Q), s1 = min(total, s0 + Q);
+    int mine = 0;
+    for (int i0 = s0; i0 < s1; i0 += 32) {
+        const int i = i0 + lane;
+        mine += __popc(__ballot_sync(kFull, i < s1 && mag_bits(S.acc[i]) != 0ull));
+    }
+    int written = 0;
+    const int before = cta_excl_scan(lane == 0 ? mine : 0, tid, S.wcnt, &written);
+    const long long wbase = base + __shfl_sync(kFull, before, 0);
+    const bool filt = P.filtering != 0;
+    const unsigned long long r_eps = (unsigned long long)__double_as_longlong(P.eps_g);
+    int w_off = 0;
+    for (int i0 = s0; i0 < s1; i0 += 32) {
+        const int i = i0 + lane;
+        double x = 0.0;
+        int c = 0;
+        if (i < s1) {
+            x = S.acc[i];
+            c = lo + (int)S.colbuf[i];
+        }
+        const unsigned long long xb = mag_bits(x);
+        const bool nz = i < s1 && xb != 0ull;
+        const unsigned m = __ballot_sync(kFull, nz);
+        const bool cand = nz && filt && xb <= r_eps;
+        if (nz) {
+            const long long pos = wbase + w_off + __popc(m & lanemask_lt());
+            P.pool_col[pos] = c;
+            P.pool_val[pos] = x;
+            st.absmax = xb > st.absmax ? xb : st.absmax;
+            if (cand) {
+                exact_add(P.words + c, (size_t)P.n, P.sticky + c, xb, P.e_lsb);
+                ++st.cand;
+            }
+        }
+        if (P.cand_col)
+            cand_push(st.carena, cand, c, xb, P.cand_col, P.cand_x, &P.ctl->cand_cnt[0], P.cand_cap, P.cand_chunk,
+                      &P.ctl->cand_over, lane);
+        w_off += __popc(m);
+    }
+    // the row's unused reserved slots read as exact zeros (never candidates)
+    const long long rend = base + ((total + 3) & ~3);
+    for (long long q = base + written + tid; q < rend; q += kT) P.pool_val[q] = 0.0;
+    if (tid == 0) {
+        P.out_rb[r] = (int)base;
+        P.out_re[r] = (int)(base + written);
+        st.written += (unsigned long long)written;
+    }
+    __syncthreads();  // the map and the accumulator are free for the next row
+}
+
+__global__ void __launch_bounds__(kCtaWarps * 32, 7) k_product_cta(ProductArgs P) {
+    if (P.skip_unless && __ldcg(P.skip_unless) == 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AddTerm* add = reinterpret_cast<AddTerm*>(smem_raw);
+    CtaSmem& S = *reinterpret_cast<CtaSmem*>(smem_raw + sizeof(AddTerm) * kMaxAdd);
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    for (int t = tid; t < P.nadd; t += blockDim.x) add[t] = P.add[t];
+    __syncthreads();
+    RowState st;
+    for (int r = blockIdx.x; r < P.n; r += gridDim.x) cta_row(P, add, S, st, r, tid);
+    if (wib == 0) arena_close(st.arena, P.pool_val, lane);
+    if (P.cand_col) cand_close(st.carena, P.cand_x, lane);
+    st.cand = (unsigned long long)warp_sum((int)st.cand);
+    st.absmax = warp_max_u64(st.absmax);
+    for (int o = 16; o; o >>= 1) st.fma += __shfl_xor_sync(kFull, st.fma, o);
+    st.written = __shfl_sync(kFull, st.written, 0);
+    st.span = warp_max(st.span);
+    if (lane == 0) {
+        if (st.fma) atomicAdd(&P.ctl->fma_total, st.fma);
+        if (P.stat) {
+            if (st.span > 0) atomicMax(&P.stat->span_max, (unsigned)st.span);
+            if (st.fma) atomicAdd(&P.stat->fma, st.fma);
+            if (st.written) atomicAdd(&P.stat->nnz_pre, st.written);
+            if (st.cand) atomicAdd(&P.stat->ncand, st.cand);
+        }
+        if (P.absmax_slot && st.absmax) atomicMax(&P.absmax_slot->absmax, st.absmax);
+    }
+}
+
 // ---------------------------------------------------------------- k_reuse_pass1
 // A baby step Z-hat_(k) = filter(Z Z-hat_(k-1)) while no earlier step has
 // dropped an entry: Z-hat_(k-1) is then the power Z^(k-1) of the norm phase,
@@ -2379,6 +2763,9 @@ cudaError_t kernels_init() {
         err = cudaFuncSetAttribute(prods[i], cudaFuncAttributeMaxDynamicSharedMemorySize, psmem[i]);
         if (err != cudaSuccess) return err;
     }
+    err = cudaFuncSetAttribute((const void*)k_product_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)cta_smem_bytes());
+    if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute((const void*)k_norms_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)norms_rows_smem_bytes());
     if (err != cudaSuccess) return err;
@@ -2414,8 +2801,19 @@ static cudaError_t prod_launch(const ProductArgs& P, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len, bool wide_window) {
+static cudaError_t cta_launch(const ProductArgs& P, cudaStream_t st) {
+    long long blocks = P.n;
+    const long long cap = (long long)sms_now() * 7;
+    if (blocks > cap) blocks = cap;
+    k_product_cta<<<(unsigned)blocks, kCtaWarps * 32, cta_smem_bytes(), st>>>(P);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len, bool wide_window,
+                           bool cta) {
     if (P.n <= 0) return cudaSuccess;
+    if (cta && !table && !P.inst && P.chunk_cols <= 0 && P.chunk_slots <= 0) return cta_launch(P, st);
     if (P.inst) {
         if (table) return prod_launch<true, true, false>(P, st);
         return wide_window ? prod_launch<false, true, false, kBmWordsBig>(P, st) : prod_launch<false, true, false>(P, st);

@@ -23,8 +23,10 @@ void count_launches(int k);  // kernels launched by other translation units
 // picks its wide-window instantiation (16384 columns)
 // columns one chunk of the bitmap map covers (the wide window: 16384)
 constexpr int kBitmapColumns = 4608;
+// cta: one row per block of four warps (k_product_cta), for single-matrix
+// steps with long B rows and fewer rows than resident warps
 cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, double out_len = 0.0,
-                           bool wide_window = false);
+                           bool wide_window = false, bool cta = false);
 // column bitmaps of B's rows for the product's symbolic pass
 // (ProductArgs::bhdr, bbits); bits has one word per entry of B's index space
 cudaError_t launch_row_bitmaps(int n, const RowView& B, int2* hdr, unsigned* bits, cudaStream_t st);
