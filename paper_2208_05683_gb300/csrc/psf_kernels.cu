@@ -409,14 +409,26 @@ __device__ __forceinline__ int assign_slots(int wlen, int cap, int lane, ProdSme
         }
         cutoff = warp_min(found);
     }
-    for (int w = lane; w < nw; w += 32) {
-        unsigned bits = S.pm[w].y;
-        int idx = (int)S.pm[w].x;
-        while (bits) {
-            const int o = w * 32 + __ffs(bits) - 1;
-            if (o < cutoff) S.colbuf[idx] = (unsigned short)o;
-            ++idx;
-            bits &= bits - 1u;
+    if (nw <= 8) {
+        // a few words: lane l takes bit l of one word at a time (no lane
+        // walks a word's set bits alone)
+        for (int w = 0; w < nw; ++w) {
+            const unsigned bits = S.pm[w].y;
+            if ((bits >> lane) & 1u) {
+                const int o = w * 32 + lane;
+                if (o < cutoff) S.colbuf[(int)S.pm[w].x + __popc(bits & lanemask_lt())] = (unsigned short)o;
+            }
+        }
+    } else {
+        for (int w = lane; w < nw; w += 32) {
+            unsigned bits = S.pm[w].y;
+            int idx = (int)S.pm[w].x;
+            while (bits) {
+                const int o = w * 32 + __ffs(bits) - 1;
+                if (o < cutoff) S.colbuf[idx] = (unsigned short)o;
+                ++idx;
+                bits &= bits - 1u;
+            }
         }
     }
     __syncwarp();
