@@ -56,6 +56,13 @@ def test_series_create_rejects_bad_arguments():
         _abi.check(psf.lib().psf_series_set_param(s._h, 99, 1.0))
     with pytest.raises(psf.PsfError):
         _abi.check(psf.lib().psf_series_set_param(s._h, _abi.PSF_PARAM_ER, -1.0))
+    # product kernel: 0 auto .. 4 one row per block of four warps
+    for k in (0.0, 1.0, 2.0, 3.0, 4.0):
+        _abi.check(psf.lib().psf_series_set_param(s._h, _abi.PSF_PARAM_KERNEL, k))
+    for bad in (-1.0, 2.5, 5.0):
+        with pytest.raises(psf.PsfError):
+            _abi.check(psf.lib().psf_series_set_param(s._h, _abi.PSF_PARAM_KERNEL, bad))
+    psf.Series(syn.coeffs("exp"), 1e-12, kernel="cta")
 
 
 def _same(a, b):
@@ -134,6 +141,17 @@ def test_tuning_keys_are_checked_on_the_host():
                 psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, bad)
     finally:
         psf.tune_set(_abi.PSF_TUNE_ALG1_FAR_SHIFT, old)
+    old = psf.tune_get(_abi.PSF_TUNE_ROW_BITMAPS)
+    assert old == 1.0
+    try:
+        for v in (0.0, 2.0, 1.0):
+            psf.tune_set(_abi.PSF_TUNE_ROW_BITMAPS, v)
+            assert psf.tune_get(_abi.PSF_TUNE_ROW_BITMAPS) == v
+        for bad in (-1.0, 0.5, 3.0):
+            with pytest.raises(psf.PsfError):
+                psf.tune_set(_abi.PSF_TUNE_ROW_BITMAPS, bad)
+    finally:
+        psf.tune_set(_abi.PSF_TUNE_ROW_BITMAPS, old)
     for key in (_abi.PSF_TUNE_BATCH_GRAPH, _abi.PSF_TUNE_BATCH_REUSE):
         old = psf.tune_get(key)
         assert old == 1.0
