@@ -113,7 +113,7 @@ int status_to_code(int st) {
     return PSF_OK;
 }
 
-// Validate input matrices on the device and wait for the verdict: nothing
+// Validate input matrices on the device and wait for the outcome: nothing
 // indexes with an input's columns before this returns PSF_OK.
 int validate_inputs(Work& w, std::initializer_list<const psf_csr_t*> ms) {
     for (const psf_csr_t* m : ms)
@@ -1396,7 +1396,7 @@ extern "C" int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out) 
     NormSlot* slot = reinterpret_cast<NormSlot*>(base + kNaSlot);
     unsigned* sticky = reinterpret_cast<unsigned*>(base + kNaSticky);
     unsigned long long* words = reinterpret_cast<unsigned long long*>(base + kNaWords);
-    // clear what must start at zero, check the input (its verdict is read
+    // clear what must start at zero, check the input (its outcome is read
     // with the result; the norm kernels never index with a column outside
     // [0, n)), then max |x| and the exact column sums over M's entries
     CU(launch_norm_scratch_init(ctl, slot, words, sticky, M->n, M->nnz, st));
