@@ -498,7 +498,7 @@ __device__ __forceinline__ void chunk_fold(ProdSmem<TAB, W>& S, const Chunk& ch,
 // consecutive B rows (the order of the fma chain).
 template <bool WIDE>
 __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int /*seg*/, int cnt, int c0, int lane,
-                                                   ProdSmem<true>& S) {
+                                                   ProdSmem<true>& S, bool /*wide_row*/) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
     int k0 = 0, o0 = 0;
@@ -555,13 +555,15 @@ __device__ __forceinline__ void short_fold(ProdSmem<false, W>& S, int c, double 
 
 template <bool WIDE, int W>
 __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int seg, int cnt, int c0, int lane,
-                                                   ProdSmem<false, W>& S) {
+                                                   ProdSmem<false, W>& S, bool wide_row) {
     const int* __restrict__ bcol = P.B.col;
     const double* __restrict__ bval = P.B.val;
     const double* ka = ka_of(S);
-    // a_rk of row kk: kept in the accumulator's last slots, or (WIDE) read
-    // from A's row (the same address in every lane)
-    auto a_of = [&](int kk) { return WIDE ? P.A.val[seg + kk] : ka[kk]; };
+    // a_rk of row kk: kept in the accumulator's last slots, or (WIDE, or a
+    // row that takes every slot) read from A's row (the same address in
+    // every lane)
+    const bool a_global = WIDE || wide_row;
+    auto a_of = [&](int kk) { return a_global ? P.A.val[seg + kk] : ka[kk]; };
     if (warp_max(lane < cnt ? S.kl[lane] : 0) <= 32) {
         // every B row is one piece: the pieces of the next three rows are
         // loaded while one is folded (rows in k order, a warp barrier between)
@@ -804,7 +806,19 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
         if (lane == 0) P.out_rb[r] = P.out_re[r] = 0;
         return;
     }
-    const bool single = reuse && total <= kSlots;
+    // a row of the narrow accumulator that fits every slot (kAccCap) in one
+    // chunk takes them all and reads a_rk from A's row, as WIDE does,
+    // instead of two column chunks (single-matrix kernels: the batch kernel
+    // runs at its register limit)
+    bool wide_row = WIDE;
+    int slots = kSlots;
+    if constexpr (!TAB && !WIDE && !BATCH) {
+        if (reuse && total > kSlots && total <= kAccCap && P.chunk_slots <= 0) {
+            wide_row = true;
+            slots = kAccCap;
+        }
+    }
+    const bool single = reuse && total <= slots;
     int written = 0;
     int c0 = lo;
     while (c0 <= hi) {
@@ -812,7 +826,7 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
         if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE);
         reuse = false;
         int cut;
-        const int cnt = assign_slots(cend - c0, kSlots, lane, S, &cut);
+        const int cnt = assign_slots(cend - c0, slots, lane, S, &cut);
         const int c1 = c0 + cut;
         for (int i = lane; i < cnt; i += 32) S.acc[i] = 0.0;
         __syncwarp();
@@ -844,8 +858,8 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
         // ---- product A B: k of row r ascending
         for (int seg = pa0; seg < pa1; seg += 32) {
             const int cnt_seg = min(32, pa1 - seg);
-            load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S, !WIDE);
-            accumulate_segment<WIDE>(P, seg, cnt_seg, c0, lane, S);
+            load_segment<TAB>(P, seg, cnt_seg, single, c0, c1, lane, S, !wide_row);
+            accumulate_segment<WIDE>(P, seg, cnt_seg, c0, lane, S, wide_row);
         }
 
         // ---- write back the nonzero entries in column order; the entries

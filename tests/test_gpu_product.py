@@ -147,3 +147,33 @@ def test_malformed_input_is_rejected():
         with pytest.raises(psf.PsfError) as e:
             psf.Series(syn.coeffs("exp"), 1e-12).eval_host(*bad)
         assert e.value.code == 1, i
+
+
+def test_rows_of_609_to_640_entries_take_every_slot():
+    # banded factors whose product rows have 600..640 entries: the narrow
+    # accumulator keeps a_rk in its last 32 slots (608 left), so such a row
+    # takes all 640 slots with a_rk read from A's row instead of two column
+    # chunks; with and without the filter, against the oracle bit for bit
+    rng = np.random.default_rng(21)
+    n = 2000
+
+    def band(h):
+        rows, cols = [], []
+        for d in range(-h, h + 1):
+            r = np.arange(max(0, -d), min(n, n - d))
+            rows.append(r)
+            cols.append(r + d)
+        rows, cols = np.concatenate(rows), np.concatenate(cols)
+        vals = rng.uniform(-1, 1, len(rows)) * 10.0 ** (-12 * rng.uniform(0, 1, len(rows)))
+        return CSR.from_scipy(sp.csr_matrix((vals, (rows, cols)), shape=(n, n)))
+
+    A, B = band(150), band(160)
+    C = matmul_add(A, B, axpy(0.5, None, None, n))
+    lens = np.diff(C.rowptr)
+    assert ((lens > 608) & (lens <= 640)).sum() > n // 2
+    got = psf.product_filter(dev(A), dev(B), [(0.5, None)], 0.0)
+    assert_csr_bitwise(got.csr, C, "unfiltered")
+    ref = alg1(C, 1e-14 / 1.1, 0.1)
+    got = psf.product_filter(dev(A), dev(B), [(0.5, None)], 1e-14, 0.1)
+    assert_csr_bitwise(got.csr, ref.kept, "filtered")
+    assert got.steps[0]["iters"] == ref.iters and got.steps[0]["eps_f"] == ref.eps_f
