@@ -273,16 +273,25 @@ __device__ __forceinline__ void mark_from_bitmaps(const ProductArgs& P, int pa0,
             longm &= longm - 1u;
             mark_row<false>(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
         }
-        for (int i = 0; i < cnt; ++i) {
-            const int h = kwn[i];
-            if (h == 0) continue;
-            const int kw = h >> 16, kn = h & 0xffff;
-            const int base = S.kb[i] - kw;  // bits[base + w]: window word w
+        // two B rows at a time: both rows' words are loaded before either is
+        // ORed in, so the loads of consecutive rows are in flight together
+        for (int i = 0; i < cnt; i += 2) {
+            unsigned t0[R], t1[R];
 #pragma unroll
-            for (int u = 0; u < R; ++u) {
-                const int w = lane + 32 * u;
-                if (w >= kw && w < kw + kn) reg[u] |= bits[base + w];
+            for (int j = 0; j < 2; ++j) {
+                const int h = i + j < cnt ? kwn[i + j] : 0;
+                const int kw = h >> 16, kn = h & 0xffff;
+                const int base = S.kb[i + j < cnt ? i + j : i] - kw;  // bits[base + w]: window word w
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    const int w = lane + 32 * u;
+                    const unsigned x = h != 0 && w >= kw && w < kw + kn ? bits[base + w] : 0u;
+                    if (j == 0) t0[u] = x;
+                    else t1[u] = x;
+                }
             }
+#pragma unroll
+            for (int u = 0; u < R; ++u) reg[u] |= t0[u] | t1[u];
         }
         __syncwarp();
     }
