@@ -273,25 +273,27 @@ __device__ __forceinline__ void mark_from_bitmaps(const ProductArgs& P, int pa0,
             longm &= longm - 1u;
             mark_row<false>(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
         }
-        // two B rows at a time: both rows' words are loaded before either is
-        // ORed in, so the loads of consecutive rows are in flight together
-        for (int i = 0; i < cnt; i += 2) {
-            unsigned t0[R], t1[R];
+        // U B rows at a time (4; 2 for the wide window's 16 words per lane):
+        // their words are loaded before any is ORed in, so the loads of
+        // consecutive rows are in flight together
+        constexpr int U = R <= 5 ? 4 : 2;
+        for (int i = 0; i < cnt; i += U) {
+            unsigned t[U][R];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < U; ++j) {
                 const int h = i + j < cnt ? kwn[i + j] : 0;
                 const int kw = h >> 16, kn = h & 0xffff;
                 const int base = S.kb[i + j < cnt ? i + j : i] - kw;  // bits[base + w]: window word w
 #pragma unroll
                 for (int u = 0; u < R; ++u) {
                     const int w = lane + 32 * u;
-                    const unsigned x = h != 0 && w >= kw && w < kw + kn ? bits[base + w] : 0u;
-                    if (j == 0) t0[u] = x;
-                    else t1[u] = x;
+                    t[j][u] = h != 0 && w >= kw && w < kw + kn ? bits[base + w] : 0u;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < R; ++u) reg[u] |= t0[u] | t1[u];
+            for (int j = 0; j < U; ++j)
+#pragma unroll
+                for (int u = 0; u < R; ++u) reg[u] |= t[j][u];
         }
         __syncwarp();
     }
