@@ -310,7 +310,7 @@ __device__ __forceinline__ void mark_from_bitmaps(const ProductArgs& P, int pa0,
 template <bool TAB, bool BMP = false, int W>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
                                           int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB, W>& S,
-                                          bool store_a, unsigned long long* fma = nullptr) {
+                                          bool store_a, int ab, int ae, unsigned long long* fma = nullptr) {
     clear_map(cend - c0, lane, S);
     __syncwarp();
     for (int t = 0; t < nadd; ++t) {
@@ -319,8 +319,10 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
         if (!T.rb) {
             if (lane == 0 && r >= c0 && r < cend) mark_one(r - c0, S);
         } else {
-            if constexpr (TAB) mark_row(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
-            else mark_row<true>(T.col, T.rb[r], T.re[r], c0, cend, lane, S);
+            // (term t's row range is in lane t)
+            const int s = __shfl_sync(kFull, ab, t), e = __shfl_sync(kFull, ae, t);
+            if constexpr (TAB) mark_row(T.col, s, e, c0, cend, lane, S);
+            else mark_row<true>(T.col, s, e, c0, cend, lane, S);
         }
     }
     if constexpr (!TAB && BMP) {
@@ -753,18 +755,22 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
             fixed_span = w1 - w0;
         }
     }
-    for (int t = 0; t < nadd && !fixed; ++t) {
-        if (!((tmask >> t) & 1u)) continue;
-        const AddTerm& T = add[t];
+    // addend term t's row range, in lane t (the terms' loads in parallel;
+    // the loops over the terms below take it with a shuffle)
+    int ab = 0, ae = 0;
+    const bool my_term = lane < nadd && ((tmask >> lane) & 1u);
+    if (my_term && add[lane].rb) {
+        ab = add[lane].rb[r];
+        ae = add[lane].re[r];
+    }
+    if (!fixed && my_term) {
+        const AddTerm& T = add[lane];
         if (!T.rb) {
             lo = min(lo, r);
             hi = max(hi, r);
-        } else {
-            int s = T.rb[r], e = T.re[r];
-            if (s < e) {
-                lo = min(lo, T.col[s]);
-                hi = max(hi, T.col[e - 1]);
-            }
+        } else if (ab < ae) {
+            lo = min(lo, T.col[ab]);
+            hi = max(hi, T.col[ae - 1]);
         }
     }
     int pa0 = 0, pa1 = 0;
@@ -781,9 +787,7 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
             hi = max(hi, P.B.col[e - 1]);
         }
     }
-    if (lane == 0)
-        for (int t = 0; t < nadd; ++t)
-            if ((tmask >> t) & 1u) my_fma += add[t].rb ? (unsigned long long)(add[t].re[r] - add[t].rb[r]) : 1ull;
+    if (my_term) my_fma += add[lane].rb ? (unsigned long long)(ae - ab) : 1ull;
     lo = warp_min(lo);
     hi = warp_max(hi);
     const int row_span = fixed ? fixed_span : hi - lo + 1;  // the statistic: before any alignment
@@ -802,13 +806,13 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
     bool reuse = false;
     if (hi - lo + 1 <= kCols) {
         build_map<TAB, (!BATCH || W == kBmWords)>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S,
-                                                   !WIDE, fixed ? &my_fma : nullptr);
+                                                   !WIDE, ab, ae, fixed ? &my_fma : nullptr);
         total = count_marks(hi - lo + 1, lane, S);
         reuse = true;
     } else {
         for (long long c0 = lo; c0 <= hi; c0 += kCols) {
             int cend = (int)min((long long)hi + 1, c0 + kCols);
-            build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE);
+            build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE, ab, ae);
             total += count_marks(cend - (int)c0, lane, S);
         }
     }
@@ -834,7 +838,7 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
     int c0 = lo;
     while (c0 <= hi) {
         int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
-        if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE);
+        if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE, ab, ae);
         reuse = false;
         int cut;
         const int cnt = assign_slots(cend - c0, slots, lane, S, &cut);
@@ -854,7 +858,7 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
                     S.acc[i] = __fma_rn(alpha, 1.0, S.acc[i]);
                 }
             } else {
-                int s = T.rb[r], e = T.re[r];
+                const int s = __shfl_sync(kFull, ab, t), e = __shfl_sync(kFull, ae, t);
                 for (int q = s + lane; q < e; q += 32) {
                     int c = T.col[q];
                     if (c >= c0 && c < c1) {
