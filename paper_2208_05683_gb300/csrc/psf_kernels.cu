@@ -1269,7 +1269,9 @@ __device__ __forceinline__ void cta_row(const ProductArgs& P, const AddTerm* add
     }
     if (total > kCtaCap) {
         // more entries than slots: the first warp computes the row alone
-        // (with its own counts; this pass's are dropped)
+        // (with its own counts; this pass's are dropped), once every thread
+        // is done with the map
+        __syncthreads();
         if (wib == 0)
             product_row<false, false, true, kBmWords>(P, add, *reinterpret_cast<ProdSmem<false, kBmWords>*>(&S), st,
                                                       r, lane);
@@ -1282,12 +1284,17 @@ __device__ __forceinline__ void cta_row(const ProductArgs& P, const AddTerm* add
                                        lane);
         if (lane == 0) S.base = b;
     }
-    for (int w = tid; w < nw; w += kT) {
-        unsigned bits = S.pm[w].y;
-        int idx = (int)S.pm[w].x;
-        while (bits) {
-            S.colbuf[idx++] = (unsigned short)(w * 32 + __ffs(bits) - 1);
-            bits &= bits - 1u;
+    // the column list: each thread fills the two words whose prefixes it wrote
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int w = 2 * tid + k;
+        if (w < nw) {
+            unsigned bits = S.pm[w].y;
+            int idx = (int)S.pm[w].x;
+            while (bits) {
+                S.colbuf[idx++] = (unsigned short)(w * 32 + __ffs(bits) - 1);
+                bits &= bits - 1u;
+            }
         }
     }
     for (int i = tid; i < total; i += kT) S.acc[i] = 0.0;

@@ -61,3 +61,19 @@ def test_cta_twice_and_square_mode_bitwise():
     ref = psscf(Z, syn.coeffs("cosh"), 1e-12, square=True)
     for rep in range(2):
         check_same(s.eval(dev(Z)), ref, f"evaluation {rep}")
+
+
+def test_cta_repeated_runs_are_identical():
+    # the block's warps share the row's map and accumulator: repeated runs
+    # (different warp timings) give the same bits, equal to the warp-per-row
+    # kernel's and the oracle's
+    Z = ocsr(syn.laplacian_2d(70))
+    a = syn.coeffs("exp")
+    ref = psscf(Z, a, 1e-12)
+    base = psf.Series(a, 1e-12, kernel="bitmap").eval(dev(Z))
+    check_same(base, ref, "warp per row")
+    s = psf.Series(a, 1e-12, kernel="cta")
+    for rep in range(6):
+        got = s.eval(dev(Z))
+        check_same(got, ref, f"run {rep}")
+        assert got.steps == base.steps, f"run {rep}"
