@@ -636,14 +636,28 @@ __device__ __forceinline__ void accumulate_segment(const ProductArgs& P, int seg
 #pragma unroll
                 for (int u = 0; u < 4; ++u) S.acc[j[u]] = __fma_rn(a, v[u], x[u]);
             }
-            // whole 32-entry pieces left, then the last partial piece
-            for (; off + 32 <= len; off += 32) {
-                const int j = slot_lookup(S, rc[off] - c0);
-                S.acc[j] = __fma_rn(a, rv[off], S.acc[j]);
-            }
-            if (off + lane < len) {
-                const int j = slot_lookup(S, rc[off] - c0);
-                S.acc[j] = __fma_rn(a, rv[off], S.acc[j]);
+            // the rest (up to four pieces, the last one partial), two pieces
+            // at a time with their read-modify-writes interleaved
+            for (; off < len; off += 64) {
+                const bool in0 = off + lane < len;
+                const bool two = off + 32 < len;  // (the same in every lane)
+                const bool in1 = two && off + 32 + lane < len;
+                int j0 = 0, j1 = 0;
+                double v0 = 0.0, v1 = 0.0, x0 = 0.0, x1 = 0.0;
+                if (in0) {
+                    j0 = rc[off];
+                    v0 = rv[off];
+                }
+                if (in1) {
+                    j1 = rc[off + 32];
+                    v1 = rv[off + 32];
+                }
+                if (in0) j0 = slot_lookup(S, j0 - c0);
+                if (in1) j1 = slot_lookup(S, j1 - c0);
+                if (in0) x0 = S.acc[j0];
+                if (in1) x1 = S.acc[j1];
+                if (in0) S.acc[j0] = __fma_rn(a, v0, x0);
+                if (two && in1) S.acc[j1] = __fma_rn(a, v1, x1);
             }
         }
         __syncwarp();
