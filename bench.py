@@ -374,7 +374,10 @@ def run_psf(args):
 
     # ---- end to end through the C ABI on host buffers: psf_eval_from_host
     # (pinned host Z copied in by the library) and psf_result_copy into
-    # pinned host arrays, both evaluations, copies inside the timed region
+    # pinned host arrays, both evaluations, copies inside the timed region.
+    # Each result is copied out on a second stream once its evaluation is
+    # done, so the first result's copy runs while the second evaluation
+    # computes; the step ends when both copies have landed.
     pin = [torch.as_tensor(x).pin_memory() for x in (np.asarray(rp, np.int32), np.asarray(col, np.int32),
                                                       np.asarray(val, np.float64))]
     zs_host = _abi.CSRStruct(n, int(len(col)), pin[0].data_ptr(), pin[1].data_ptr(), pin[2].data_ptr())
@@ -392,12 +395,15 @@ def run_psf(args):
         return [host_buf[(k, name)] for name in ("rowptr", "col", "val")]
 
     st_ptr = ctypes.c_void_p(stream.cuda_stream)
+    copy_stream = torch.cuda.Stream(device=dev)
+    cp_ptr = ctypes.c_void_p(copy_stream.cuda_stream)
     for it in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        copy_stream.wait_event(e0)
         handles, copied = [], 0
         for k in KINDS:
             h = ctypes.c_void_p()
@@ -405,10 +411,16 @@ def run_psf(args):
             info = _abi.InfoStruct()
             _abi.check(L.psf_result_info(h, ctypes.byref(info)))
             hr, hc, hv = host_arrays(k, int(info.nnz))
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy_stream.wait_event(done)
             _abi.check(L.psf_result_copy(h, ctypes.c_void_p(hr.data_ptr()), ctypes.c_void_p(hc.data_ptr()),
-                                         ctypes.c_void_p(hv.data_ptr()), st_ptr))
+                                         ctypes.c_void_p(hv.data_ptr()), cp_ptr))
             copied += (n + 1) * 4 + int(info.nnz) * 12
             handles.append(h)
+        landed = torch.cuda.Event()
+        landed.record(copy_stream)
+        stream.wait_event(landed)
         e1.record(stream)
         e1.synchronize()
         for h in handles:

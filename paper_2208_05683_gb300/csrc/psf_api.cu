@@ -95,7 +95,60 @@ int check_csr(const psf_csr_t* m, int n, const char* what) {
 }
 
 
+// ---- mailboxes of the read-backs (see psf_internal.h)
+static std::mutex g_mbox_mu;
+static std::vector<std::pair<void*, void*>> g_mbox_free;
+std::pair<void*, void*> mailbox_take() {
+    {
+        std::lock_guard<std::mutex> g(g_mbox_mu);
+        if (!g_mbox_free.empty()) {
+            auto m = g_mbox_free.back();
+            g_mbox_free.pop_back();
+            return m;
+        }
+    }
+    void* h = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc(&h, kMboxBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return {nullptr, nullptr};
+    }
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        return {nullptr, nullptr};
+    }
+    return {h, d};
+}
+void mailbox_give(std::pair<void*, void*> m) {
+    std::lock_guard<std::mutex> g(g_mbox_mu);
+    g_mbox_free.push_back(m);
+}
+// Step records (bytes of device memory at src) to dst on the host, after
+// the stream's work: through the mailbox when they fit, else a copy.
+int read_stats(Work& w, void* dst, const void* src, size_t bytes) {
+    if (w.mbox.first && bytes % 4 == 0 && bytes <= kMboxBytes - kMboxStats) {
+        CU(launch_export(src, static_cast<char*>(w.mbox.second) + kMboxStats, bytes, w.st));
+        CU(cudaStreamSynchronize(w.st));
+        memcpy(dst, static_cast<char*>(w.mbox.first) + kMboxStats, bytes);
+        return PSF_OK;
+    }
+    CU(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return PSF_OK;
+}
+
+// The control block (and the norm slots) to the host, after the stream's work.
 int read_back(Work& w, Ctl& c, NormSlot* slots) {
+    if (w.mbox.first) {
+        char* hd = static_cast<char*>(w.mbox.second);
+        CU(launch_export(w.ctl.p, hd, sizeof(Ctl), w.st));
+        if (slots) CU(launch_export(w.slots.p, hd + kMboxSlots, sizeof(NormSlot) * kMaxNorms, w.st));
+        CU(cudaStreamSynchronize(w.st));
+        const char* hh = static_cast<const char*>(w.mbox.first);
+        memcpy(&c, hh, sizeof(Ctl));
+        if (slots) memcpy(slots, hh + kMboxSlots, sizeof(NormSlot) * kMaxNorms);
+        return PSF_OK;
+    }
     CU(cudaMemcpyAsync(&c, w.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, w.st));
     if (slots) CU(cudaMemcpyAsync(slots, w.slots.p, sizeof(NormSlot) * kMaxNorms, cudaMemcpyDeviceToHost, w.st));
     CU(cudaStreamSynchronize(w.st));
@@ -608,7 +661,7 @@ int psf_product_filter(const psf_csr_t* A, const psf_csr_t* B, int32_t nadd, con
         destroy_result(r);
         return rc;
     }
-    if (cudaMemcpy(&ss, w.stats.p, sizeof ss, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (read_stats(w, &ss, w.stats.p, sizeof ss) != PSF_OK) {
         destroy_result(r);
         return fail(PSF_ECUDA, "stats read-back");
     }
@@ -767,7 +820,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             if (z_used > series->z_need) series->z_need = z_used;
             if (chain) {
                 StepStat zs[9];
-                if (cudaMemcpy(zs, w.stats.p, sizeof zs, cudaMemcpyDeviceToHost) != cudaSuccess)
+                if (read_stats(w, zs, w.stats.p, sizeof zs) != PSF_OK)
                     return fail(PSF_ECUDA, "stats read-back");
                 series->len_z.assign(9, 0.0);
                 std::vector<unsigned> sz(9, 0u);
@@ -997,8 +1050,7 @@ int psf_eval(psf_series_t series, const psf_csr_t* Z, void* stream, psf_result_t
             }
             std::vector<StepStat> ss(steps.size());
             if (!ss.empty()) {
-                if (cudaMemcpy(ss.data(), w.stats.p, sizeof(StepStat) * ss.size(), cudaMemcpyDeviceToHost) !=
-                    cudaSuccess) {
+                if (read_stats(w, ss.data(), w.stats.p, sizeof(StepStat) * ss.size()) != PSF_OK) {
                     destroy_result(r);
                     return fail(PSF_ECUDA, "stats read-back");
                 }

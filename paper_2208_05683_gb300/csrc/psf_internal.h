@@ -115,6 +115,23 @@ extern Profile g_prof;
 // capacity stays 2^20 below 2^31 and no position plus offset overflows.
 constexpr unsigned long long kMaxPool = (1ull << 31) - (1ull << 20);
 
+// Mailboxes: pinned host buffers mapped into the device's address space,
+// {host, device} pointers, into which k_export writes the control block
+// (offset 0), the norm slots (kMboxSlots) and the step records (kMboxStats)
+// that the host reads back.  A kernel's stores take no copy engine, so these
+// reads do not wait behind a large device-to-host copy in flight on another
+// stream (a user copying one result out while the next evaluation runs).
+// Each evaluation's workspace takes one from a process-wide free list and
+// gives it back; they are kept for the life of the process (which must not
+// outlive a cudaDeviceReset).  {nullptr, nullptr} if none could be made: the
+// read-backs then use copies.
+constexpr size_t kMboxBytes = 64 * 1024, kMboxSlots = 4096, kMboxStats = 8192;
+static_assert(sizeof(Ctl) % 4 == 0 && sizeof(Ctl) <= kMboxSlots, "control block in its mailbox part");
+static_assert(sizeof(NormSlot) * kMaxNorms % 4 == 0 && kMboxSlots + sizeof(NormSlot) * kMaxNorms <= kMboxStats,
+              "norm slots in their mailbox part");
+std::pair<void*, void*> mailbox_take();
+void mailbox_give(std::pair<void*, void*> m);
+
 // Device workspace shared by the phases of one evaluation.
 // products mark their output pattern from column bitmaps of B's rows
 // (PSF_TUNE_ROW_BITMAPS: 0 never, 1 when A's rows average at least
@@ -137,13 +154,16 @@ struct Work {
     int slot_map = 0;            // 0 auto (by products per row), 1 table, 2 bitmap, 3 wide window, 4 CTA per row
     int chunk_cols = 0, chunk_slots = 0;
 
+    std::pair<void*, void*> mbox{nullptr, nullptr};
     ~Work() {
         for (DevBuf* b : rows) delete b;
+        if (mbox.first) mailbox_give(mbox);
     }
     Ctl* C() const { return ctl.as<Ctl>(); }
     int init(int n_, cudaStream_t s, int nstats) {
         n = n_;
         st = s;
+        if (!mbox.first) mbox = mailbox_take();
         CU(ctl.alloc(sizeof(Ctl), st));
         CU(cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st));
         CU(stats.alloc(sizeof(StepStat) * (size_t)(nstats > 0 ? nstats : 1), st));

@@ -8,6 +8,9 @@
 //                 column sums and the candidate list of the entries
 //                 |x| <= eps_g); a batch instantiation reads per-row
 //                 instance parameters.
+//  k_product_cta  the same step with one output row per block of four warps
+//                 (matrices of at most one wave of rows with long B rows).
+//  k_row_bitmaps  column bitmaps of B's rows for the symbolic pass.
 //  k_reuse_pass1  a baby step equal to a power of the norm phase: the first
 //                 pass of Algorithm 1 on that power's rows.
 //  k_reuse_copy_batch  the same for the instances of a batch: those rows
@@ -19,6 +22,8 @@
 //  k_norms_finish column sums in shared memory; rounding and maxima.
 //  k_norms        exact 1-norms from flat pool ranges (psf_norm1 and its
 //                 allocation-free variant).
+//  k_export       small device records written into pinned, device-mapped
+//                 host memory (the host's read-backs take no copy engine).
 //  k_absmax, k_validate*, k_copy_rows*, k_scan_*, k_gather*, k_identity,
 //  k_inst_table, k_compose_rows, k_bounds: plumbing.
 #include <atomic>
@@ -210,6 +215,52 @@ __device__ __forceinline__ void mark_row(const int* __restrict__ col, int s, int
     }
     if (mask) atomicOr(&S.pm[curw].y, mask);
 }
+// Two B rows at once, each as mark_row<false> marks it (lane l walks its
+// contiguous slice of each row): the column loads of both rows are issued
+// before either row's columns are ORed in, so the second row's loads do not
+// wait for the first row's marking.  The rows are clipped to the window.
+template <int W>
+__device__ __forceinline__ void mark_row_pair(const int* __restrict__ col, int sa, int ea, int sb, int eb, int c0,
+                                              int lane, ProdSmem<false, W>& S) {
+    const int ma = (ea - sa + 31) >> 5, mb = (eb - sb + 31) >> 5;
+    int qa = sa + lane * ma, qb = sb + lane * mb;
+    const int qa1 = min(ea, qa + ma), qb1 = min(eb, qb + mb);
+    unsigned wa = 0xffffffffu, ka = 0u, wb = 0xffffffffu, kb = 0u;
+    while (qa < qa1 || qb < qb1) {
+        int cs[2][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            cs[0][u] = qa + u < qa1 ? col[qa + u] : 0;
+            cs[1][u] = qb + u < qb1 ? col[qb + u] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (qa + u >= qa1) continue;
+            const unsigned off = (unsigned)(cs[0][u] - c0), w = off >> 5;
+            if (w != wa) {
+                if (ka) atomicOr(&S.pm[wa].y, ka);
+                wa = w;
+                ka = 0u;
+            }
+            ka |= 1u << (off & 31);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (qb + u >= qb1) continue;
+            const unsigned off = (unsigned)(cs[1][u] - c0), w = off >> 5;
+            if (w != wb) {
+                if (kb) atomicOr(&S.pm[wb].y, kb);
+                wb = w;
+                kb = 0u;
+            }
+            kb |= 1u << (off & 31);
+        }
+        qa += 4;
+        qb += 4;
+    }
+    if (ka) atomicOr(&S.pm[wa].y, ka);
+    if (kb) atomicOr(&S.pm[wb].y, kb);
+}
 // Short B rows (at most 32 entries each): lane i marks the segment's B row i,
 // so the rows' column loads are in flight together instead of one row after
 // the other.  The rows are clipped to [c0, cend) (see mark_row).
@@ -307,7 +358,9 @@ __device__ __forceinline__ void mark_from_bitmaps(const ProductArgs& P, int pa0,
 
 // Mark every output column of row r in [c0, cend) (cend - c0 <= kCols).
 // BMP: B row bitmaps may be used (not in the batch kernel's wide window).
-template <bool TAB, bool BMP = false, int W>
+// PAIR: long B rows are marked two at a time (not in the batch kernel, which
+// runs at its register limit).
+template <bool TAB, bool BMP = false, bool PAIR = false, int W>
 __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* add, int nadd, unsigned tmask, int r,
                                           int c0, int cend, int pa0, int pa1, bool whole, int lane, ProdSmem<TAB, W>& S,
                                           bool store_a, int ab, int ae, unsigned long long* fma = nullptr) {
@@ -341,9 +394,15 @@ __device__ __forceinline__ void build_map(const ProductArgs& P, const AddTerm* a
                 continue;
             }
         }
-        for (int i = 0; i < cnt; ++i) {
-            if constexpr (TAB) mark_row(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
-            else mark_row<false>(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+        if constexpr (TAB) {
+            for (int i = 0; i < cnt; ++i) mark_row(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
+        } else {
+            int i = 0;
+            if constexpr (PAIR)
+                for (; i + 1 < cnt; i += 2)
+                    mark_row_pair(P.B.col, S.kb[i], S.kb[i] + S.kl[i], S.kb[i + 1], S.kb[i + 1] + S.kl[i + 1], c0,
+                                  lane, S);
+            for (; i < cnt; ++i) mark_row<false>(P.B.col, S.kb[i], S.kb[i] + S.kl[i], c0, cend, lane, S);
         }
         __syncwarp();
     }
@@ -819,14 +878,15 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
     long long total = 0;
     bool reuse = false;
     if (hi - lo + 1 <= kCols) {
-        build_map<TAB, (!BATCH || W == kBmWords)>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S,
+        build_map<TAB, (!BATCH || W == kBmWords), !BATCH>(P, add, nadd, tmask, r, lo, hi + 1, pa0, pa1, true, lane, S,
                                                    !WIDE, ab, ae, fixed ? &my_fma : nullptr);
         total = count_marks(hi - lo + 1, lane, S);
         reuse = true;
     } else {
         for (long long c0 = lo; c0 <= hi; c0 += kCols) {
             int cend = (int)min((long long)hi + 1, c0 + kCols);
-            build_map<TAB>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE, ab, ae);
+            build_map<TAB, false, !BATCH>(P, add, nadd, tmask, r, (int)c0, cend, pa0, pa1, false, lane, S, !WIDE, ab,
+                                          ae);
             total += count_marks(cend - (int)c0, lane, S);
         }
     }
@@ -852,7 +912,8 @@ __device__ __forceinline__ void product_row(const ProductArgs& P, const AddTerm*
     int c0 = lo;
     while (c0 <= hi) {
         int cend = (int)min((long long)hi + 1, (long long)c0 + kCols);
-        if (!reuse) build_map<TAB>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE, ab, ae);
+        if (!reuse)
+            build_map<TAB, false, !BATCH>(P, add, nadd, tmask, r, c0, cend, pa0, pa1, false, lane, S, !WIDE, ab, ae);
         reuse = false;
         int cut;
         const int cnt = assign_slots(cend - c0, slots, lane, S, &cut);
@@ -1494,11 +1555,24 @@ __global__ void __launch_bounds__(256) k_reuse_pass1(ReuseArgs R) {
         }
     }
     cand_close(ca, R.cand_x, lane);
+    // the counts go to the step's record once per block: one atomic per warp
+    // on the same two words queued behind one another at the launch's end
+    __shared__ unsigned long long blk_nnz, blk_cand;
+    if (threadIdx.x == 0) {
+        blk_nnz = 0ull;
+        blk_cand = 0ull;
+    }
+    __syncthreads();
     nnz = (unsigned long long)warp_sum((int)nnz);
     cand = (unsigned long long)warp_sum((int)cand);
     if (lane == 0) {
-        if (nnz) atomicAdd(&R.stat->nnz_pre, nnz);
-        if (cand) atomicAdd(&R.stat->ncand, cand);
+        if (nnz) atomicAdd(&blk_nnz, nnz);
+        if (cand) atomicAdd(&blk_cand, cand);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blk_nnz) atomicAdd(&R.stat->nnz_pre, blk_nnz);
+        if (blk_cand) atomicAdd(&R.stat->ncand, blk_cand);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         R.stat->fma = R.fma;
@@ -2416,6 +2490,17 @@ __global__ void k_norms_finish(int n, int count, NormSlot* slots, unsigned long 
     }
 }
 
+// ---------------------------------------------------------------- k_export
+// Copy nwords 32-bit words of a device record (the control block, norm slots,
+// step records) into pinned host memory mapped into the device's address
+// space.  The host reads the words after synchronising with the stream.  A
+// kernel's stores take no copy engine, so these small read-backs do not
+// queue behind a large device-to-host copy that another stream has in
+// flight (a result being copied out while the next evaluation runs).
+__global__ void k_export(const unsigned* src, unsigned* dst, int nwords) {
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = __ldcg(src + i);
+}
+
 // ---------------------------------------------------------------- k_row_bitmaps
 // Column bitmap of every row of B for the product's symbolic pass: hdr[r] =
 // {first column / 32, words}, the words at bits[rb[r]] on.  A row gets one
@@ -3096,6 +3181,12 @@ cudaError_t launch_reuse_copy_batch(const ProductArgs& P, cudaStream_t st) {
     const long long cap = (long long)num_sms() * 8;
     if (blocks > cap) blocks = cap;
     k_reuse_copy_batch<<<(unsigned)blocks, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const void* src, void* dst, size_t bytes, cudaStream_t st) {
+    k_export<<<1, 256, 0, st>>>(static_cast<const unsigned*>(src), static_cast<unsigned*>(dst), (int)(bytes / 4));
+    ++g_launches;
     return cudaGetLastError();
 }
 

@@ -30,6 +30,9 @@ cudaError_t launch_product(const ProductArgs& P, bool table, cudaStream_t st, do
 // column bitmaps of B's rows for the product's symbolic pass
 // (ProductArgs::bhdr, bbits); bits has one word per entry of B's index space
 cudaError_t launch_row_bitmaps(int n, const RowView& B, int2* hdr, unsigned* bits, cudaStream_t st);
+// bytes (a multiple of 4) of device memory at src to dst, the device address
+// of pinned, mapped host memory, by a kernel on st (k_export)
+cudaError_t launch_export(const void* src, void* dst, size_t bytes, cudaStream_t st);
 cudaError_t launch_alg1(const Alg1Args& A, cudaStream_t st);
 cudaError_t launch_norms(const NormArgs& A, cudaStream_t st);
 cudaError_t launch_absmax(const double* pool_val, const Ctl* ctl, int i, NormSlot* slot, cudaStream_t st);

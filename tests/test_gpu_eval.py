@@ -336,6 +336,40 @@ def test_host_to_host_path_bitwise():
     assert info0["nnz"] == 5
 
 
+def test_result_copied_out_while_the_next_evaluation_runs_bitwise():
+    # psf_result_copy of one result into pinned host arrays on a second
+    # stream, in flight while the next psf_eval runs on the first (its
+    # read-backs go through the mapped mailbox, not behind that copy): both
+    # results are the oracle's bit for bit, three times over
+    import ctypes
+    import torch
+    from paper_2208_05683_gb300 import _abi
+    L = _abi.lib()
+    Z = ocsr(syn.laplacian_2d(64))
+    refs = {k: psscf(Z, syn.coeffs(k), 1e-12) for k in ("exp", "cos")}
+    series = {k: psf.Series(syn.coeffs(k), 1e-12) for k in refs}
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    nnz = refs["exp"].F.nnz
+    hr = torch.empty(Z.n + 1, dtype=torch.int32, pin_memory=True)
+    hc = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
+    hv = torch.empty(nnz, dtype=torch.float64, pin_memory=True)
+    for rep in range(3):
+        h = series["exp"].eval_handle(dev(Z), main)
+        done = torch.cuda.Event()
+        done.record(main)
+        side.wait_event(done)
+        _abi.check(L.psf_result_copy(h, ctypes.c_void_p(hr.data_ptr()), ctypes.c_void_p(hc.data_ptr()),
+                                     ctypes.c_void_p(hv.data_ptr()), ctypes.c_void_p(side.cuda_stream)))
+        got_cos = series["cos"].eval(dev(Z), main)
+        side.synchronize()
+        _abi.check(L.psf_result_destroy(h))
+        F = refs["exp"].F
+        assert np.array_equal(hr.numpy(), F.rowptr) and np.array_equal(hc.numpy(), F.col), rep
+        assert np.array_equal(hv.numpy().view(np.uint64), np.asarray(F.val).view(np.uint64)), rep
+        check_same(got_cos, refs["cos"], f"cos, copy in flight, run {rep}")
+
+
 def square_cases():
     return {
         "lap2d": (ocsr(syn.laplacian_2d(40)), 1e-12),
