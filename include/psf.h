@@ -178,6 +178,11 @@ PSF_API int psf_series_destroy(psf_series_t series);
  * and giant steps S-hat_i = filter(B-hat_{b-1-i} + Z-hat_(q) S-hat_{i-1}) with
  * Algorithm 1 after every product.  Synchronizes `stream` three times (input
  * validation; after the norms, to plan; at the end, to size the result).
+ * What the host reads at those points is written by a kernel into pinned,
+ * device-mapped host memory (kept by the library, a few 64 KB buffers for
+ * the life of the process), not copied by a copy engine: a large
+ * device-to-host copy on another stream, such as the previous result's
+ * psf_result_copy, does not delay the evaluation.
  * The result CSR is canonical (sorted columns, no stored zeros).
  * The series records sizes seen by the evaluation (pool entries, row
  * lengths) and sizes the next evaluation's workspace from them; from its
@@ -492,8 +497,12 @@ PSF_API int psf_profile_read(int64_t* launches, double* ms, double* fma, int32_t
 
 /* Read access to a result. */
 PSF_API int psf_result_csr(psf_result_t r, psf_csr_t* view);          /* library-owned device arrays */
+/* psf_result_copy: into caller arrays, device or host (pinned: asynchronous
+ * on `stream`; a null array is skipped).  On a stream other than the next
+ * evaluation's (ordered after this result's evaluation by an event), the
+ * copy of one result runs while the next evaluation computes. */
 PSF_API int psf_result_copy(psf_result_t r, int32_t* rowptr, int32_t* col, double* val,
-                    void* stream);  /* into caller arrays, device or host (pinned: asynchronous) */
+                    void* stream);
 PSF_API int psf_result_info(psf_result_t r, psf_info_t* info);
 PSF_API int psf_result_step(psf_result_t r, int32_t i, psf_step_info_t* step);
 PSF_API int psf_result_destroy(psf_result_t r);
