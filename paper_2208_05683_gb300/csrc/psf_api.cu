@@ -128,8 +128,10 @@ void mailbox_give(std::pair<void*, void*> m) {
 // the stream's work: through the mailbox when they fit, else a copy.
 int read_stats(Work& w, void* dst, const void* src, size_t bytes) {
     if (w.mbox.first && bytes % 4 == 0 && bytes <= kMboxBytes - kMboxStats) {
+        w.mbox_pending = true;
         CU(launch_export(src, static_cast<char*>(w.mbox.second) + kMboxStats, bytes, w.st));
         CU(cudaStreamSynchronize(w.st));
+        w.mbox_pending = false;
         memcpy(dst, static_cast<char*>(w.mbox.first) + kMboxStats, bytes);
         return PSF_OK;
     }
@@ -141,9 +143,11 @@ int read_stats(Work& w, void* dst, const void* src, size_t bytes) {
 int read_back(Work& w, Ctl& c, NormSlot* slots) {
     if (w.mbox.first) {
         char* hd = static_cast<char*>(w.mbox.second);
+        w.mbox_pending = true;
         CU(launch_export(w.ctl.p, hd, sizeof(Ctl), w.st));
         if (slots) CU(launch_export(w.slots.p, hd + kMboxSlots, sizeof(NormSlot) * kMaxNorms, w.st));
         CU(cudaStreamSynchronize(w.st));
+        w.mbox_pending = false;
         const char* hh = static_cast<const char*>(w.mbox.first);
         memcpy(&c, hh, sizeof(Ctl));
         if (slots) memcpy(slots, hh + kMboxSlots, sizeof(NormSlot) * kMaxNorms);

@@ -155,9 +155,15 @@ struct Work {
     int chunk_cols = 0, chunk_slots = 0;
 
     std::pair<void*, void*> mbox{nullptr, nullptr};
+    bool mbox_pending = false;  // an export into the mailbox may still be in flight
     ~Work() {
         for (DevBuf* b : rows) delete b;
-        if (mbox.first) mailbox_give(mbox);
+        if (mbox.first) {
+            // (an error path can leave an export unsynchronised: let it land
+            // before another evaluation takes the mailbox)
+            if (mbox_pending) cudaStreamSynchronize(st);
+            mailbox_give(mbox);
+        }
     }
     Ctl* C() const { return ctl.as<Ctl>(); }
     int init(int n_, cudaStream_t s, int nstats) {
