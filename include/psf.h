@@ -356,13 +356,17 @@ PSF_API int psf_norm1_noalloc(const psf_csr_t* M, void* stream, double* out);
  * PSF_Z_SUBMULT), fill N, q, b, g, products, z, alpha10, trunc, budget, and
  * the thresholds zeta[k] (k = 2..q, index k) and sigma[j] (j = 1+g..b-1,
  * index j), each array of length PSF_MAX_Q + 2 (host), entries not defined
- * set to 0.  zeta/sigma may be NULL.  With PSF_Z_SQUARE the plan is that of
+ * set to 0.  zeta/sigma may be NULL (a plan with q > PSF_MAX_Q + 1 or
+ * b > PSF_MAX_Q + 2, possible with a small s or a very long series, has
+ * thresholds past those arrays: PSF_ETOOBIG unless they are NULL).  With
+ * PSF_Z_SQUARE the plan is that of
  * g in W = Z^2 (see the flag; tol / z_1 for an odd series, infinite when
  * z_1 = 0); info->z still lists the z_i of Z.
  * Errors: PSF_EINVAL (null arguments, m < 1, tol, s, a non-finite
  * coefficient, a norm that is negative or not finite, mixed parities with
- * PSF_Z_SQUARE), PSF_ETOOBIG (m > 100000), PSF_ENOTCONV (Eq. 34 finds no
- * truncation length within the m coefficients).
+ * PSF_Z_SQUARE), PSF_ETOOBIG (m > 100000; thresholds past the arrays, see
+ * above), PSF_ENOTCONV (Eq. 34 finds no truncation length within the m
+ * coefficients).
  */
 PSF_API int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t flags,
              const double* norms, psf_info_t* info, double* zeta, double* sigma);

@@ -418,18 +418,21 @@ def tune_set(key: int, value: float) -> None:
 
 
 def plan(coeffs, tol: float, norms, *, poly: bool = False, submult: bool = False, s: int = 0,
-         square: bool = False):
-    """The host planner: N, q, b, g, z, truncation bound, budget, zeta, sigma."""
+         square: bool = False, thresholds: bool = True):
+    """The host planner: N, q, b, g, z, truncation bound, budget, and with
+    ``thresholds`` zeta and sigma (PsfError PSF_ETOOBIG when q or b is past
+    their PSF_MAX_Q + 2 entries; thresholds=False plans without them)."""
     L = lib()
     a = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
     nz = list(norms) + [0.0] * (11 - len(norms))
     nrm = (ctypes.c_double * 11)(*[float(x) for x in nz[:11]])
     info = InfoStruct()
-    zeta = (ctypes.c_double * (PSF_MAX_Q + 2))()
-    sigma = (ctypes.c_double * (PSF_MAX_Q + 2))()
+    zeta = (ctypes.c_double * (PSF_MAX_Q + 2))() if thresholds else None
+    sigma = (ctypes.c_double * (PSF_MAX_Q + 2))() if thresholds else None
     flags = (PSF_POLY if poly else 0) | (PSF_Z_SUBMULT if submult else 0) | (PSF_Z_SQUARE if square else 0)
     check(L.psf_plan(a, len(coeffs), int(s), float(tol), flags, nrm, ctypes.byref(info), zeta, sigma))
     d = info.as_dict()
-    d["zeta"] = {k: zeta[k] for k in range(2, d["q"] + 1)}
-    d["sigma"] = {j: sigma[j] for j in range(1 + d["g"], d["b"])}
+    if thresholds:
+        d["zeta"] = {k: zeta[k] for k in range(2, d["q"] + 1)}
+        d["sigma"] = {j: sigma[j] for j in range(1 + d["g"], d["b"])}
     return d

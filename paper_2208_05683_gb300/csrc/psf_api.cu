@@ -523,6 +523,11 @@ int psf_plan(const double* coeffs, int64_t m, int32_t s, double tol, uint32_t fl
     Plan p;
     if (make_plan(a, tol, flags & PSF_POLY, flags & PSF_Z_SUBMULT, s, norms, p, square ? 2 : 1))
         return fail(PSF_ENOTCONV, "no truncation length within %zu coefficients (Eq. 34)", a.size());
+    // the thresholds go to indices 2..q and 1+g..b-1 of arrays of
+    // PSF_MAX_Q + 2 entries
+    if ((zeta && p.q > PSF_MAX_Q + 1) || (sigma && p.b > PSF_MAX_Q + 2))
+        return fail(PSF_ETOOBIG, "q = %d, b = %d: the thresholds do not fit arrays of PSF_MAX_Q + 2 entries "
+                    "(pass NULL zeta and sigma for the rest of the plan)", p.q, p.b);
     std::memset(info, 0, sizeof *info);
     info->N = p.N;
     info->q = p.q;

@@ -111,6 +111,61 @@ def test_host_planner_poly_and_override(N):
     assert got["z"] == ref.z[:11]
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_host_planner_random_sweep_bitwise(seed):
+    # seeded random coefficient sets (decaying, flat, with zeros and sign
+    # changes), power-norm sequences that are not submultiplicative in
+    # general, tolerances 1e-15..1e-5, series and polynomial mode, SUBMULT
+    # and the s override: the C++ planner gives the oracle's plan bit for
+    # bit, and both report "not converged" for the same inputs
+    rng = np.random.default_rng(1000 + seed)
+    for case in range(40):
+        m = int(rng.integers(2, 130))
+        if rng.uniform() < 0.5:
+            r = rng.uniform(0.2, 6.0)
+            a = [r ** i / math.factorial(i) for i in range(m)]
+        else:
+            a = list(rng.standard_normal(m) * 10.0 ** rng.uniform(-12, 0, m))
+        for i in range(m):
+            if rng.uniform() < 0.15:
+                a[i] = 0.0
+            elif rng.uniform() < 0.3:
+                a[i] = -a[i]
+        z1 = rng.uniform(0.05, 6.0)
+        norms = [1.0, z1]
+        for i in range(2, 11):
+            norms.append(norms[-1] * z1 * rng.uniform(0.2, 1.0))
+        tol = 10.0 ** rng.uniform(-15, -5)
+        poly = rng.uniform() < 0.25
+        submult = rng.uniform() < 0.25
+        s = int(rng.integers(1, 12)) if rng.uniform() < 0.2 else 0
+        what = f"seed {seed} case {case}: m={m} tol={tol:.3e} poly={poly} submult={submult} s={s}"
+        try:
+            ref = planner.plan(a, tol, norms, poly=poly, s=s, submult=submult)
+        except ValueError:
+            with pytest.raises(psf.PsfError) as e:
+                psf.plan(a, tol, norms, poly=poly, submult=submult, s=s)
+            assert e.value.code == _abi.PSF_ENOTCONV, what
+            continue
+        bare = psf.plan(a, tol, norms, poly=poly, submult=submult, s=s, thresholds=False)
+        assert (bare["N"], bare["q"], bare["b"], bare["g"]) == (ref.N, ref.q, ref.b, ref.g), what
+        assert bare["trunc"] == ref.trunc and _same(bare["budget"], ref.budget), what
+        assert bare["z"] == ref.z[:11], what
+        if ref.q > _abi.PSF_MAX_Q + 1 or ref.b > _abi.PSF_MAX_Q + 2:
+            # thresholds past the header's arrays of PSF_MAX_Q + 2 entries
+            with pytest.raises(psf.PsfError) as e:
+                psf.plan(a, tol, norms, poly=poly, submult=submult, s=s)
+            assert e.value.code == _abi.PSF_ETOOBIG, what
+            continue
+        got = psf.plan(a, tol, norms, poly=poly, submult=submult, s=s)
+        assert (got["N"], got["q"], got["b"], got["g"]) == (ref.N, ref.q, ref.b, ref.g), what
+        assert set(got["zeta"]) == set(ref.zeta) and set(got["sigma"]) == set(ref.sigma), what
+        for k in ref.zeta:
+            assert _same(got["zeta"][k], ref.zeta[k]), (what, k)
+        for j in ref.sigma:
+            assert _same(got["sigma"][j], ref.sigma[j]), (what, j)
+
+
 def test_host_planner_not_converged():
     with pytest.raises(psf.PsfError) as e:
         psf.plan(syn.coeffs("exp", 6), 1e-12, [1.0] + [10.0 ** i for i in range(1, 11)])
