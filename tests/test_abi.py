@@ -166,6 +166,51 @@ def test_host_planner_random_sweep_bitwise(seed):
             assert _same(got["sigma"][j], ref.sigma[j]), (what, j)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_host_planner_square_random_sweep_bitwise(seed):
+    # PSF_Z_SQUARE on seeded random series of one parity: the plan of g in
+    # W = Z^2 (z of W = z_{2i} of Z, tol / z_1 for an odd series) is the
+    # oracle's bit for bit, with the same "not converged" cases
+    rng = np.random.default_rng(2000 + seed)
+    for case in range(40):
+        m = int(rng.integers(2, 130))
+        odd = bool(rng.uniform() < 0.5)
+        r = rng.uniform(0.2, 5.0)
+        a = [0.0] * m
+        for i in range(int(odd), m, 2):
+            a[i] = (-1.0) ** (i // 2) * r ** i / math.factorial(i) if rng.uniform() < 0.9 else 0.0
+        if not any(a):
+            continue
+        z1 = rng.uniform(0.05, 6.0)
+        norms = [1.0, z1]
+        for i in range(2, 11):
+            norms.append(norms[-1] * z1 * rng.uniform(0.2, 1.0))
+        tol = 10.0 ** rng.uniform(-15, -5)
+        poly = rng.uniform() < 0.25
+        submult = rng.uniform() < 0.25
+        what = f"seed {seed} case {case}: m={m} odd={odd} tol={tol:.3e} poly={poly} submult={submult}"
+        c, o = planner.split_even_odd(a)
+        assert o == odd, what
+        tol_g = tol / norms[1] if odd else tol
+        try:
+            ref = planner.plan(c, tol_g, norms, poly=poly, submult=submult, stride=2)
+        except ValueError:
+            with pytest.raises(psf.PsfError) as e:
+                psf.plan(a, tol, norms, poly=poly, submult=submult, square=True)
+            assert e.value.code == _abi.PSF_ENOTCONV, what
+            continue
+        got = psf.plan(a, tol, norms, poly=poly, submult=submult, square=True, thresholds=False)
+        assert (got["N"], got["q"], got["b"], got["g"]) == (ref.N, ref.q, ref.b, ref.g), what
+        assert got["products"] == planner.mult_count(ref.N) + 1 + int(odd), what
+        assert got["trunc"] == ref.trunc and _same(got["budget"], ref.budget), what
+        if ref.q <= _abi.PSF_MAX_Q + 1 and ref.b <= _abi.PSF_MAX_Q + 2:
+            got = psf.plan(a, tol, norms, poly=poly, submult=submult, square=True)
+            for k in ref.zeta:
+                assert _same(got["zeta"][k], ref.zeta[k]), (what, k)
+            for j in ref.sigma:
+                assert _same(got["sigma"][j], ref.sigma[j]), (what, j)
+
+
 def test_host_planner_not_converged():
     with pytest.raises(psf.PsfError) as e:
         psf.plan(syn.coeffs("exp", 6), 1e-12, [1.0] + [10.0 ** i for i in range(1, 11)])
