@@ -115,12 +115,13 @@ def test_host_planner_poly_and_override(N):
 def test_host_planner_random_sweep_bitwise(seed):
     # seeded random coefficient sets (decaying, flat, with zeros and sign
     # changes), power-norm sequences that are not submultiplicative in
-    # general, tolerances 1e-15..1e-5, series and polynomial mode, SUBMULT
-    # and the s override: the C++ planner gives the oracle's plan bit for
-    # bit, and both report "not converged" for the same inputs
+    # general (and those of zero and nilpotent matrices), tolerances
+    # 1e-15..1e-5, series and polynomial mode, SUBMULT and the s override:
+    # the C++ planner gives the oracle's plan bit for bit, and both report
+    # "not converged" for the same inputs
     rng = np.random.default_rng(1000 + seed)
     for case in range(40):
-        m = int(rng.integers(2, 130))
+        m = int(rng.integers(1, 130))
         if rng.uniform() < 0.5:
             r = rng.uniform(0.2, 6.0)
             a = [r ** i / math.factorial(i) for i in range(m)]
@@ -131,14 +132,16 @@ def test_host_planner_random_sweep_bitwise(seed):
                 a[i] = 0.0
             elif rng.uniform() < 0.3:
                 a[i] = -a[i]
-        z1 = rng.uniform(0.05, 6.0)
+        # the zero matrix, or a nilpotent one (powers vanish from some i on)
+        z1 = 0.0 if rng.uniform() < 0.05 else rng.uniform(0.05, 6.0)
+        cut = int(rng.integers(2, 11)) if rng.uniform() < 0.15 else 11
         norms = [1.0, z1]
         for i in range(2, 11):
-            norms.append(norms[-1] * z1 * rng.uniform(0.2, 1.0))
+            norms.append(0.0 if i >= cut else norms[-1] * z1 * rng.uniform(0.2, 1.0))
         tol = 10.0 ** rng.uniform(-15, -5)
         poly = rng.uniform() < 0.25
         submult = rng.uniform() < 0.25
-        s = int(rng.integers(1, 12)) if rng.uniform() < 0.2 else 0
+        s = int(rng.integers(1, _abi.PSF_MAX_Q + 1)) if rng.uniform() < 0.2 else 0
         what = f"seed {seed} case {case}: m={m} tol={tol:.3e} poly={poly} submult={submult} s={s}"
         try:
             ref = planner.plan(a, tol, norms, poly=poly, s=s, submult=submult)
